@@ -1,0 +1,172 @@
+"""Contacts, the sparse contact Jacobian D, BBPGD and one Euler step -- oracle.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Paper: Yan et al., arXiv 1909.06623.
+  * Sec. 3.2: the constraint set A(C, delta) = {pairs with Phi <= delta}.
+    Phi_ij = |c_i - c_j| - R_i - R_j for spheres, with R the collision radius
+    a_c (Sec. 6.1 sets a_c slightly above a).  Readings: delta is an absolute
+    distance (the workloads quote "contact cutoff 0.1"; the paper's own choice,
+    30% of R_i + R_j, is a caller option); pairs i < j sorted by (i, j);
+    d^2 = (dx dx + dy dy) + dz dz evaluated without fused multiply-add, so the
+    list is reproducible to the bit.
+  * eq. Dmatdef / Dtranspose: column D_l carries -n_l on sphere i's force and
+    +n_l on sphere j's force (no torque for spheres), n_l = (c_j - c_i)/|c_j - c_i|,
+    so D^T U = n_l . (U_j - U_i) = dPhi/dt.
+  * eq. lcp:LCPdef: M = D^T M D, q = Phi/dt + D^T U_nc.
+  * Algorithm 1 (BBPGD) with the min-map residual of eq. mmapnorm and the BB1
+    step (BB2 optional).  Readings where the algorithm is silent: gamma_0 = 0,
+    whose product M gamma_0 = 0 needs no mobility solve; a non-positive s^T y
+    (or y^T y for BB2) stops with status "breakdown"; j_max caps the loop.
+  * eq. time-step: C^{k+1} = C^k + (U_nc + M D gamma) dt, positions only
+    (spheres are isotropic; the grid keeps its lab-frame orientation).
+"""
+import itertools
+
+import numpy as np
+
+from . import mobility
+from .layer import Suspension
+
+
+def build_contacts(centers, radii, delta, a_c_scale=1.0):
+    """Contact list (Sec. 3.2): ij (n_c x 2, i < j), Phi (n_c), normals (n_c x 3)."""
+    c = np.asarray(centers, dtype=np.float64).reshape(-1, 3)
+    R = np.asarray(radii, dtype=np.float64).reshape(-1) * a_c_scale
+    ij, ph, nr = [], [], []
+    N = len(R)
+    for i in range(N):
+        for j in range(i + 1, N):
+            dx = c[j, 0] - c[i, 0]
+            dy = c[j, 1] - c[i, 1]
+            dz = c[j, 2] - c[i, 2]
+            # numpy float64 scalars: every operation rounded separately (no FMA)
+            d2 = (dx * dx + dy * dy) + dz * dz
+            d = np.sqrt(d2)
+            phi = (d - R[i]) - R[j]
+            if phi <= delta:
+                ij.append((i, j))
+                ph.append(phi)
+                nr.append((dx / d, dy / d, dz / d))
+    return (np.array(ij, dtype=np.int32).reshape(-1, 2),
+            np.array(ph, dtype=np.float64), np.array(nr, dtype=np.float64).reshape(-1, 3))
+
+
+def D_apply(N, ij, nrm, gamma):
+    """F_c = D gamma (N x 6, torques zero), eq. Dmatdef."""
+    FT = np.zeros((N, 6))
+    for l, (i, j) in enumerate(ij):
+        FT[i, :3] -= gamma[l] * nrm[l]
+        FT[j, :3] += gamma[l] * nrm[l]
+    return FT
+
+
+def DT_apply(ij, nrm, UO):
+    """(D^T U)_l = n_l . (U_j - U_i), eq. Dtranspose."""
+    return np.array([nrm[l] @ (UO[j, :3] - UO[i, :3]) for l, (i, j) in enumerate(ij)])
+
+
+def minmap(gamma, g):
+    """phi(gamma, g) = || min(gamma, g) ||_2, eq. mmapnorm."""
+    return float(np.linalg.norm(np.minimum(gamma, g)))
+
+
+def bbpgd(Mop, q, tol, jmax=10000, variant=1):
+    """Algorithm 1.  Mop(gamma) -> M gamma.  Returns gamma, g, info."""
+    q = np.asarray(q, dtype=np.float64)
+    mv = 0
+    gamma = np.zeros_like(q)
+    g = q.copy()                                   # M gamma_0 = 0 for gamma_0 = 0
+    info = {"iters": 0, "mvops": 0, "status": "ok", "phi": minmap(gamma, g)}
+    if info["phi"] < tol:
+        return gamma, g, info
+    Mg = Mop(g)
+    mv += 1
+    gMg = g @ Mg
+    if not gMg > 0:
+        info.update(status="breakdown", mvops=mv)
+        return gamma, g, info
+    alpha = (g @ g) / gMg
+    for j in range(1, jmax + 1):
+        gamma_new = np.maximum(gamma - alpha * g, 0.0)
+        g_new = Mop(gamma_new) + q
+        mv += 1
+        phi = minmap(gamma_new, g_new)
+        s = gamma_new - gamma
+        y = g_new - g
+        gamma, g = gamma_new, g_new
+        info.update(iters=j, mvops=mv, phi=phi)
+        if phi < tol:
+            return gamma, g, info
+        sy = s @ y
+        if variant == 1:
+            if not sy > 0:
+                info["status"] = "breakdown"
+                return gamma, g, info
+            alpha = (s @ s) / sy
+        else:
+            yy = y @ y
+            if not (sy > 0 and yy > 0):
+                info["status"] = "breakdown"
+                return gamma, g, info
+            alpha = sy / yy
+    info["status"] = "not_converged"
+    return gamma, g, info
+
+
+def lcp_enumerate(Mmat, q):
+    """Exact LCP solution by trying every active set (small n_c only).
+
+    M SPD gives a unique solution (Sec. 3.3.2): the set S with
+    gamma_S = -M_SS^{-1} q_S >= 0 and (M gamma + q)_{not S} >= 0.
+    """
+    n = len(q)
+    best = None
+    for k in range(n + 1):
+        for S in itertools.combinations(range(n), k):
+            S = list(S)
+            gam = np.zeros(n)
+            if S:
+                gam[S] = np.linalg.solve(Mmat[np.ix_(S, S)], -q[S])
+            w = Mmat @ gam + q
+            rest = [i for i in range(n) if i not in S]
+            if np.all(gam[S] >= -1e-12) and np.all(w[rest] >= -1e-12):
+                best = gam
+                return best
+    return best
+
+
+def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
+                       a_c_scale=1.0, gmres_tol=1e-12, gmres_max=200,
+                       bbpgd_tol=1e-10, bbpgd_max=10000, variant=1):
+    """One collision-resolved Euler step (Sec. 3.2, four-step procedure).
+
+    1. U_nc = M F_ext; 2. contacts and D; 3. BBPGD for gamma with
+    M gamma = D^T M D gamma; 4. U = U_nc + M D gamma, c += U dt.
+    Returns dict with gamma, ij, phi, normals, U (N x 6), centers_new, info.
+    """
+    sus = Suspension(centers, radii, p, beta)
+    U_nc, inf0 = mobility.mobility_apply(sus, FT_ext, gmres_tol, gmres_max, return_info=True)
+    ij, phi0, nrm = build_contacts(centers, radii, delta, a_c_scale)
+    q = phi0 / dt + DT_apply(ij, nrm, U_nc)
+    state = {"U_c": np.zeros_like(U_nc), "solves": 1, "gmres": inf0["gmres_iters"]}
+
+    def Mop(gam):
+        UO, inf = mobility.mobility_apply(sus, D_apply(sus.N, ij, nrm, gam),
+                                          gmres_tol, gmres_max, return_info=True)
+        state["U_c"] = UO
+        state["solves"] += 1
+        state["gmres"] += inf["gmres_iters"]
+        return DT_apply(ij, nrm, UO)
+
+    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant)
+    if info["iters"] == 0:
+        U_c = np.zeros_like(U_nc)       # gamma = gamma_0 = 0
+    else:
+        U_c = state["U_c"]              # solve of the last iterate, the returned gamma
+    U = U_nc + U_c
+    cnew = np.asarray(centers, dtype=np.float64) + U[:, :3] * dt
+    info.update(solves=state["solves"], gmres_iters=state["gmres"], n_contacts=len(q),
+                n_active=int(np.sum(gamma > 0)))
+    return {"gamma": gamma, "g": g, "q": q, "ij": ij, "phi": phi0, "normals": nrm,
+            "U": U, "U_nc": U_nc, "centers_new": cnew, "info": info}

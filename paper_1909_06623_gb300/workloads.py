@@ -1,0 +1,269 @@
+"""Seeded synthetic suspensions shaped like the paper's workloads.
+
+Input generation only: sphere centres, radii, forces and torques.  This module
+holds none of the method's arithmetic and is the one piece of code that both the
+CUDA path (bench, tests) and the CPU oracle's tests consume.
+
+Shapes follow the paper's test problems (Yan et al., arXiv 1909.06623, Sec. 6):
+random non-overlapping spheres in a free-space cube at a target volume
+fraction, radii uniform in [0.5, 1] (Sec. 6.5 draws log-normal radii; the
+uniform law is the one the workloads below fix), a few pairs pre-placed close to
+contact so that collisions and near-singular quadrature are exercised.
+
+Placement is random sequential addition (largest sphere first) with a minimum
+gap between every two spheres; volume fractions above what that reaches are
+made by compressing an addition at a lower fraction and pushing overlapping
+pairs apart (a geometric relaxation, no hydrodynamics).
+"""
+from dataclasses import dataclass, field
+from math import pi
+
+import numpy as np
+
+SEED_BASE = 1909066230
+
+
+@dataclass
+class Workload:
+    name: str
+    centers: np.ndarray          # N x 3 float64
+    radii: np.ndarray            # N float64
+    FT: np.ndarray               # N x 6 float64 (force, torque)
+    p: int
+    dt: float
+    steps: int
+    params: dict = field(default_factory=dict)
+
+    @property
+    def N(self):
+        return len(self.radii)
+
+
+def _cell_key(c, h):
+    return tuple(np.floor(c / h).astype(np.int64))
+
+
+class _Grid:
+    """Uniform cell grid for overlap queries during placement."""
+
+    def __init__(self, h):
+        self.h = h
+        self.cells = {}
+
+    def add(self, k, c):
+        self.cells.setdefault(_cell_key(c, self.h), []).append(k)
+
+    def remove(self, k, c):
+        self.cells[_cell_key(c, self.h)].remove(k)
+
+    def around(self, c):
+        i, j, l = _cell_key(c, self.h)
+        out = []
+        for a in (i - 1, i, i + 1):
+            for b in (j - 1, j, j + 1):
+                for d in (l - 1, l, l + 1):
+                    out.extend(self.cells.get((a, b, d), ()))
+        return out
+
+
+def _fits(k, c, r, C, R, grid, gap, skip=()):
+    for j in grid.around(c):
+        if j == k or j in skip:
+            continue
+        if np.linalg.norm(C[j] - c) < R[j] + r + gap:
+            return False
+    return True
+
+
+def rsa(rng, radii, L, gap, max_tries=200000):
+    """Random sequential addition in [0, L]^3, largest first, all gaps > gap."""
+    N = len(radii)
+    order = np.argsort(-radii, kind="stable")
+    C = np.full((N, 3), np.nan)
+    grid = _Grid(2.0 * radii.max() + gap)
+    for k in order:
+        r = radii[k]
+        for _ in range(max_tries):
+            c = r + rng.random(3) * (L - 2 * r)
+            if _fits(k, c, r, C, radii, grid, gap):
+                C[k] = c
+                grid.add(k, c)
+                break
+        else:
+            raise RuntimeError("random sequential addition jammed")
+    return C
+
+
+def place_close_pairs(rng, C, R, n_pairs, gap_lo, gap_hi, min_gap, L=None,
+                      direction=None):
+    """Re-place n_pairs disjoint partners at a small gap from their mates."""
+    N = len(R)
+    grid = _Grid(2.0 * R.max() + min_gap)
+    for k in range(N):
+        grid.add(k, C[k])
+    used = set()
+    pairs = []
+    perm = rng.permutation(N)
+    idx = 0
+    while len(pairs) < n_pairs and idx + 1 < N:
+        i, j = int(perm[idx]), int(perm[idx + 1])
+        idx += 2
+        for _ in range(200):
+            u = direction if direction is not None else rng.standard_normal(3)
+            u = np.asarray(u, dtype=np.float64) / np.linalg.norm(u)
+            g = gap_lo if gap_hi == gap_lo else gap_lo + (gap_hi - gap_lo) * rng.random()
+            c = C[i] + u * (R[i] + R[j] + g)
+            if L is not None and (np.any(c < R[j]) or np.any(c > L - R[j])):
+                continue
+            if _fits(j, c, R[j], C, R, grid, min_gap, skip={i}):
+                grid.remove(j, C[j])
+                C[j] = c
+                grid.add(j, c)
+                pairs.append((i, j))
+                used.update((i, j))
+                break
+    return C, pairs
+
+
+def compress(C, R, phi_from, phi_to, gap, sweeps=400):
+    """Scale the packing about its centre and push overlapping pairs apart."""
+    C = C.copy()
+    mid = C.mean(axis=0)
+    steps = 40
+    scale_total = (phi_from / phi_to) ** (1.0 / 3.0)
+    for s in range(1, steps + 1):
+        f = scale_total ** (1.0 / steps)
+        C = mid + (C - mid) * f
+        for _ in range(sweeps):
+            grid = _Grid(2.0 * R.max() + gap)
+            for k in range(len(R)):
+                grid.add(k, C[k])
+            moved = False
+            for i in range(len(R)):
+                for j in grid.around(C[i]):
+                    if j <= i:
+                        continue
+                    d = C[j] - C[i]
+                    dist = np.linalg.norm(d)
+                    need = R[i] + R[j] + gap
+                    if dist < need:
+                        push = 0.5 * (need - dist) * 1.0001 + 1e-12
+                        u = d / dist
+                        C[i] -= push * u
+                        C[j] += push * u
+                        moved = True
+            if not moved:
+                break
+        else:
+            raise RuntimeError("compression did not converge")
+    return C
+
+
+def box_side(radii, phi):
+    return (np.sum(4.0 / 3.0 * pi * radii ** 3) / phi) ** (1.0 / 3.0)
+
+
+def random_suspension(seed, N, phi, a_lo=0.5, a_hi=1.0, pair_frac=0.05,
+                      gap_lo=1e-4, gap_hi=1e-2, min_gap=2e-2):
+    """Polydisperse random suspension at volume fraction phi plus close pairs."""
+    rng = np.random.default_rng(seed)
+    R = a_lo + (a_hi - a_lo) * rng.random(N) if a_hi > a_lo else np.full(N, a_lo)
+    L = box_side(R, phi)
+    if phi <= 0.33:
+        C = rsa(rng, R, L, min_gap)
+    else:
+        L0 = box_side(R, 0.30)
+        C = compress(rsa(rng, R, L0, min_gap), R, 0.30, phi, min_gap)
+    n_pairs = int(round(pair_frac * N / 1.0)) // 1
+    n_pairs = min(n_pairs, N // 2)
+    if n_pairs:
+        C, _ = place_close_pairs(rng, C, R, n_pairs, gap_lo, gap_hi, min_gap)
+    return C, R, rng
+
+
+def small_cluster(seed, N=8, a=1.0, side=8.0, min_gap=0.05, close_gap=1e-3,
+                  n_close=2):
+    """N equal spheres in a cube of given side, all gaps > min_gap, then n_close
+    pairs re-placed along +z at gap close_gap."""
+    rng = np.random.default_rng(seed)
+    R = np.full(N, a)
+    # centres uniform in [0, side]^3 (spheres may poke out of the cube)
+    C = np.full((N, 3), np.nan)
+    grid = _Grid(2 * a + min_gap)
+    for k in range(N):
+        for _ in range(100000):
+            c = rng.random(3) * side
+            if _fits(k, c, a, C, R, grid, min_gap):
+                C[k] = c
+                grid.add(k, c)
+                break
+        else:
+            raise RuntimeError("placement failed")
+    C, pairs = place_close_pairs(rng, C, R, n_close, close_gap, close_gap, min_gap,
+                                 direction=(0.0, 0.0, 1.0))
+    if len(pairs) != n_close:
+        raise RuntimeError("could not place the close pairs")
+    return C, R, rng
+
+
+# ----------------------------------------------------------------------------
+# the five workloads
+# ----------------------------------------------------------------------------
+def config1():
+    """8 unit spheres, p = 8, F = (0,0,-1), one step dt = 1e-3 (FP64 parity)."""
+    C, R, _ = small_cluster(SEED_BASE + 1)
+    FT = np.zeros((8, 6))
+    FT[:, 2] = -1.0
+    return Workload("cfg1_N8_p8", C, R, FT, p=8, dt=1e-3, steps=1,
+                    params=dict(delta=0.1, gmres_tol=1e-12, bbpgd_tol=1e-10))
+
+
+def config2(N=1000, seed=SEED_BASE + 2):
+    """1,000 spheres a ~ U[0.5,1], volume fraction 0.30, 5% close pairs, p = 6,
+    F ~ N(0,1), T ~ N(0,0.1), 20 steps of dt = 1e-3."""
+    C, R, rng = random_suspension(seed, N, 0.30)
+    FT = np.concatenate([rng.standard_normal((N, 3)),
+                         0.1 * rng.standard_normal((N, 3))], axis=1)
+    return Workload(f"cfg2_N{N}_p6_phi0.30", C, R, FT, p=6, dt=1e-3, steps=20,
+                    params=dict(delta=0.1, gmres_tol=1e-8, bbpgd_tol=1e-6))
+
+
+def config3(N=4000, seed=SEED_BASE + 3):
+    """4,000 spheres a ~ U[0.5,1] at volume fraction 0.40, p = 6, gravity
+    F = (0,0,-(a/0.75)^3), 10 steps of dt = 5e-4."""
+    C, R, _ = random_suspension(seed, N, 0.40, pair_frac=0.0)
+    FT = np.zeros((N, 6))
+    FT[:, 2] = -(R / 0.75) ** 3
+    return Workload(f"cfg3_N{N}_p6_phi0.40", C, R, FT, p=6, dt=5e-4, steps=10,
+                    params=dict(delta=0.1, ir_tol=1e-10, bbpgd_tol=1e-8))
+
+
+def config4(N=1000, seed=SEED_BASE + 4):
+    """1,000 unit spheres at volume fraction 0.25, p = 6, F ~ N(0,1)."""
+    C, R, rng = random_suspension(seed, N, 0.25, a_lo=1.0, a_hi=1.0, pair_frac=0.0)
+    FT = np.concatenate([rng.standard_normal((N, 3)), np.zeros((N, 3))], axis=1)
+    return Workload(f"cfg4_N{N}_p6_phi0.25", C, R, FT, p=6, dt=1e-3, steps=1,
+                    params=dict(delta=0.1))
+
+
+def config5(N, p, seed=None):
+    """Sweep point: N spheres a ~ U[0.5,1] at volume fraction 0.35, order p."""
+    seed = SEED_BASE + 5 + 17 * N + p if seed is None else seed
+    C, R, rng = random_suspension(seed, N, 0.35)
+    FT = np.concatenate([rng.standard_normal((N, 3)),
+                         0.1 * rng.standard_normal((N, 3))], axis=1)
+    return Workload(f"cfg5_N{N}_p{p}_phi0.35", C, R, FT, p=p, dt=1e-3, steps=1,
+                    params=dict(delta=0.1))
+
+
+def tiny(seed, N, p, phi=0.2, a_lo=0.5, a_hi=1.0, n_pairs=1, gap=1e-2):
+    """Small random case for parity tests (a few spheres, one close pair)."""
+    rng = np.random.default_rng(seed)
+    R = a_lo + (a_hi - a_lo) * rng.random(N)
+    L = box_side(R, phi)
+    C = rsa(rng, R, L, 0.05)
+    if n_pairs:
+        C, _ = place_close_pairs(rng, C, R, n_pairs, gap, gap, 0.05)
+    FT = np.concatenate([rng.standard_normal((N, 3)),
+                         0.1 * rng.standard_normal((N, 3))], axis=1)
+    return Workload(f"tiny_N{N}_p{p}_s{seed}", C, R, FT, p=p, dt=1e-3, steps=1)

@@ -1,0 +1,105 @@
+"""Pins of the oracle's contact set, D, and BBPGD (Sec. 3, Algorithm 1).
+
+* contacts: a hand-checkable example, and agreement with scipy's k-d tree pair
+  query on a random suspension;
+* D and D^T are adjoint (eq. Dtranspose) and D^T U is the rate of change of Phi;
+* BBPGD against exact LCP solutions by active-set enumeration (unique for SPD
+  M, Sec. 3.3.2), complementarity at convergence, the absolute error bound of
+  eq. abserrcqp, and the scalar-LCP fact of Sec. 6.2 (one GD step solves it);
+* the full collision-resolved step against enumeration with the explicitly
+  assembled M = D^T M D (n_c = 3 contacts, p = 4)."""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+from oracle import lcp, mobility
+from oracle.layer import Suspension
+from paper_1909_06623_gb300 import workloads
+
+
+def test_contacts_hand_example():
+    c = np.array([[0, 0, 0], [2.05, 0, 0], [0, 0, 2.2], [10, 10, 10]])
+    a = np.array([1.0, 1.0, 1.0, 0.5])
+    ij, phi, nrm = lcp.build_contacts(c, a, 0.1)
+    assert ij.tolist() == [[0, 1]]
+    assert abs(phi[0] - 0.05) < 1e-15 and np.allclose(nrm[0], [1, 0, 0])
+    ij, phi, nrm = lcp.build_contacts(c, a, 0.25)
+    assert ij.tolist() == [[0, 1], [0, 2]]
+    ij, phi, _ = lcp.build_contacts(c, a, 0.0, a_c_scale=1.05)
+    assert ij.tolist() == [[0, 1], [0, 2], [1, 2]][:len(ij)] and abs(phi[0] + 0.05) < 1e-15
+
+
+def test_contacts_match_kdtree():
+    w = workloads.tiny(7, 60, 4, phi=0.3)
+    ij, phi, nrm = lcp.build_contacts(w.centers, w.radii, 0.2)
+    pairs = cKDTree(w.centers).query_pairs(2 * w.radii.max() + 0.2, output_type="ndarray")
+    keep = []
+    for i, j in pairs:
+        i, j = min(i, j), max(i, j)
+        if np.linalg.norm(w.centers[i] - w.centers[j]) - w.radii[i] - w.radii[j] <= 0.2:
+            keep.append((i, j))
+    assert sorted(keep) == [tuple(x) for x in ij.tolist()]
+    assert np.allclose(np.linalg.norm(nrm, axis=1), 1.0)
+
+
+def test_D_adjoint_and_phi_rate():
+    rng = np.random.default_rng(1)
+    w = workloads.tiny(3, 30, 4, phi=0.3)
+    ij, phi, nrm = lcp.build_contacts(w.centers, w.radii, 0.3)
+    gam = rng.random(len(ij))
+    U = rng.standard_normal((30, 6))
+    assert abs(np.sum(lcp.D_apply(30, ij, nrm, gam) * U) - gam @ lcp.DT_apply(ij, nrm, U)) < 1e-12
+    h = 1e-7
+    c2 = w.centers + h * U[:, :3]
+    d2 = np.linalg.norm(c2[ij[:, 1]] - c2[ij[:, 0]], axis=1) - w.radii[ij[:, 0]] - w.radii[ij[:, 1]]
+    assert np.abs((d2 - phi) / h - lcp.DT_apply(ij, nrm, U)).max() < 1e-5
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bbpgd_matches_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    n = 1 + seed % 6
+    B = rng.standard_normal((n, n))
+    M = B @ B.T + 0.5 * np.eye(n)
+    q = rng.standard_normal(n)
+    exact = lcp.lcp_enumerate(M, q)
+    for variant in (1, 2):
+        gam, g, info = lcp.bbpgd(lambda x: M @ x, q, 1e-12, variant=variant)
+        assert info["status"] == "ok"
+        assert np.abs(gam - exact).max() < 1e-10
+        assert gam.min() >= 0 and g.min() >= -1e-12 and abs(gam @ g) < 1e-10
+        ev = np.linalg.eigvalsh(M)
+        bound = (ev.max() + 1) / ev.min() * info["phi"]      # eq. abserrcqp
+        assert np.linalg.norm(gam - exact) <= bound + 1e-15
+
+
+def test_scalar_lcp_one_step_and_trivial_cases():
+    gam, g, info = lcp.bbpgd(lambda x: 2.0 * x, np.array([-3.0]), 1e-12)
+    assert info["iters"] == 1 and info["mvops"] == 2 and abs(gam[0] - 1.5) < 1e-15
+    gam, g, info = lcp.bbpgd(lambda x: 2.0 * x, np.array([3.0]), 1e-12)
+    assert info["iters"] == 0 and info["mvops"] == 0 and gam[0] == 0.0
+
+
+def test_collision_step_against_enumeration():
+    c = np.array([[0, 0, 0], [2.02, 0, 0], [1.0, 1.76, 0.0], [5.0, 0.3, 0.2]])
+    a = np.ones(4)
+    FT = np.zeros((4, 6))
+    FT[:, :3] = 20.0 * np.array([[1.0, 0.3, 0.0], [-1.0, 0.2, 0.0], [0.0, -1.0, 0.1], [-0.5, 0, 0]])
+    dt = 0.05
+    out = lcp.resolve_collisions(c, a, FT, dt, 4, gmres_tol=1e-13, bbpgd_tol=1e-11)
+    ij, nrm = out["ij"], out["normals"]
+    assert len(ij) == 3 and out["info"]["n_active"] >= 1
+    sus = Suspension(c, a, 4)
+    M = np.zeros((3, 3))
+    for l in range(3):
+        e = np.zeros(3)
+        e[l] = 1.0
+        M[:, l] = lcp.DT_apply(ij, nrm, mobility.mobility_apply(sus, lcp.D_apply(4, ij, nrm, e), 1e-13))
+    exact = lcp.lcp_enumerate(M, out["q"])
+    assert np.abs(out["gamma"] - exact).max() < 1e-7 * max(1.0, np.abs(exact).max())
+    g = out["g"]
+    assert out["gamma"].min() >= 0 and g.min() > -1e-10
+    assert abs(out["gamma"] @ g) < 1e-9
+    # after the step, the linearised gaps are non-negative
+    lin = out["phi"] + dt * lcp.DT_apply(ij, nrm, out["U"])
+    assert lin.min() > -1e-9

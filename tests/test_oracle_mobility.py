@@ -1,0 +1,85 @@
+"""Pins of the oracle's mobility solve (Sec. 2, 4.1).
+
+* single sphere: U = F/(6 pi a), Omega = T/(8 pi a^3) (the Stokes drag the
+  paper compares against in Sec. 6.1), to round-off;
+* two distant spheres: the pair mobility tends to the Rotne-Prager-Yamakawa
+  form, exact to O((a/d)^4);
+* symmetry and positive definiteness of the discrete mobility (Sec. 2) to the
+  discretisation level, improving spectrally with p;
+* exact equivariance under the rotation by 2 pi/(2p+2) about z, which maps the
+  grid onto itself;
+* the GMRES routine against a dense solve."""
+from math import pi
+
+import numpy as np
+import pytest
+
+from oracle import mobility
+from oracle.layer import Suspension
+
+
+@pytest.mark.parametrize("a", [1.0, 0.55])
+def test_single_sphere_drag(a):
+    sus = Suspension([[0.3, -0.1, 2.0]], [a], 6)
+    FT = np.array([[0.3, -1.0, 0.5, 0.2, 0.7, -0.4]])
+    UO = mobility.mobility_apply(sus, FT)
+    assert np.abs(UO[0, :3] - FT[0, :3] / (6 * pi * a)).max() < 1e-14 / a
+    assert np.abs(UO[0, 3:] - FT[0, 3:] / (8 * pi * a ** 3)).max() < 1e-14 / a ** 3
+
+
+def test_far_pair_matches_rpy():
+    d = 20.0
+    sus = Suspension([[0, 0, 0], [0, d * 0.6, d * 0.8]], [1.0, 1.0], 6)
+    FT = np.zeros((2, 6))
+    FT[0, :3] = [0.3, 0.5, -1.0]
+    UO = mobility.mobility_apply(sus, FT)
+    dh = np.array([0, 0.6, 0.8])
+    M12 = ((1 + 2 / (3 * d * d)) * np.eye(3) + (1 - 2 / (d * d)) * np.outer(dh, dh)) / (8 * pi * d)
+    ref = M12 @ FT[0, :3]
+    assert np.abs(UO[1, :3] - ref).max() < 2e-6 * np.abs(ref).max()
+
+
+def _mobility_matrix(c, a, p):
+    sus = Suspension(c, a, p)
+    N = len(a)
+    M = np.zeros((6 * N, 6 * N))
+    for k in range(6 * N):
+        FT = np.zeros(6 * N)
+        FT[k] = 1.0
+        M[:, k] = mobility.mobility_apply(sus, FT.reshape(N, 6), 1e-13).ravel()
+    return M
+
+
+def test_mobility_symmetric_positive_definite():
+    c = np.array([[0, 0, 0], [2.6, 0.2, 0.0], [0.8, 2.5, 0.6]])
+    a = np.array([1.0, 0.8, 0.9])
+    asym = []
+    for p in (4, 6):
+        M = _mobility_matrix(c, a, p)
+        asym.append(np.abs(M - M.T).max() / np.abs(M).max())
+        assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+    assert asym[1] < asym[0] / 5 and asym[1] < 1e-3
+
+
+def test_grid_rotation_equivariance():
+    p = 4
+    ang = 2 * pi / (2 * p + 2)
+    Rz = np.array([[np.cos(ang), -np.sin(ang), 0], [np.sin(ang), np.cos(ang), 0], [0, 0, 1]])
+    c = np.array([[0, 0, 0], [2.3, 0.4, 0.3]])
+    a = np.array([1.0, 0.9])
+    FT = np.array([[0.2, -0.5, 1.0, 0.1, 0.0, 0.3], [-0.4, 0.1, 0.2, 0.0, 0.2, 0.0]])
+    U1 = mobility.mobility_apply(Suspension(c, a, p), FT, 1e-13)
+    FT2 = np.concatenate([FT[:, :3] @ Rz.T, FT[:, 3:] @ Rz.T], axis=1)
+    U2 = mobility.mobility_apply(Suspension(c @ Rz.T, a, p), FT2, 1e-13)
+    U1r = np.concatenate([U1[:, :3] @ Rz.T, U1[:, 3:] @ Rz.T], axis=1)
+    assert np.abs(U1r - U2).max() < 1e-11
+
+
+def test_gmres_against_dense_solve():
+    rng = np.random.default_rng(0)
+    A = np.eye(40) + 0.3 * rng.standard_normal((40, 40)) / np.sqrt(40)
+    b = rng.standard_normal(40)
+    x, its, res = mobility.gmres(lambda v: A @ v, b, 1e-13, 40)
+    assert res < 1e-13 and np.abs(x - np.linalg.solve(A, b)).max() < 1e-11
+    x0, its0, _ = mobility.gmres(lambda v: A @ v, np.zeros(40), 1e-13, 40)
+    assert its0 == 0 and not x0.any()
