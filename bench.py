@@ -1,0 +1,371 @@
+"""Benchmark: collision-resolved time steps of a 1,000-sphere suspension.
+
+Workload (default): 1,000 spheres, radii uniform in [0.5, 1], volume fraction
+0.30, 5% of pairs pre-placed at gaps U(1e-4, 1e-2), order p = 6 (98 nodes per
+sphere, 98,000 nodes), F ~ N(0,1), T ~ N(0,0.1), dt = 1e-3, mixed precision
+(FP32 far field with compensated sums, FP64 Krylov / BBPGD / near and self
+quadrature).  One "step" = one call of sps_resolve_collisions: the U_nc
+mobility solve, the contact set, BBPGD (each iteration a mobility solve) and the
+Euler update; positions advance step after step.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("collision-resolved steps/s and layer-potential interactions/s vs FP64 GPU, "
+          "% roofline")
+FLOPS_PER_PAIR = {"K": 30, "S": 29}   # algorithmic FP32 operations per pair term
+SMS, LANES = 152, 128
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        d = {}
+    mhz = float(d.get("sm_max_mhz", 2070.0))
+    return {"fp32_tflops": SMS * LANES * 2 * mhz * 1e6 / 1e12, "sm_max_mhz": mhz,
+            "hbm_gbs": d.get("hbm_gbs", 6800.0), "source": "measured" if d else "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def workload(name):
+    from paper_1909_06623_gb300 import workloads
+    if name == "cfg2":
+        return workloads.config2()
+    if name.startswith("cfg5"):
+        _, N, p = name.split("_")
+        return workloads.config5(int(N), int(p))
+    raise ValueError(name)
+
+
+def ctx_params(precision):
+    return dict(p=6, delta=0.1, beta=1.75, gmres_tol=1e-6 if precision == "mixed" else 1e-8,
+                gmres_max=100, bbpgd_tol=1e-5, bbpgd_max=200,
+                precision=1 if precision == "mixed" else 0)
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) leg: a bounded sample of one layer-operator application
+# ---------------------------------------------------------------------------
+def oracle_sample(w, n_targets=3, seed=0):
+    """Times the FP64 oracle's traction operator K on n_targets target spheres
+    (self + near + all-pairs far field for those spheres) and scales it to one
+    full application (x N / n_targets)."""
+    from oracle.layer import Suspension
+    sus = Suspension(w.centers, w.radii, w.p)
+    rng = np.random.default_rng(seed)
+    sig = rng.standard_normal((sus.N * sus.P, 3))
+    tg = list(rng.choice(sus.N, n_targets, replace=False))
+    t0 = time.perf_counter()
+    sus.apply("K", sig, targets=tg)
+    dt = time.perf_counter() - t0
+    return dt * sus.N / n_targets, dt
+
+
+def matvecs_per_step_estimate(stats_list):
+    """Layer-operator applications per step from the GPU run's counters:
+    every GMRES iteration applies I/2+K+L once; every solve adds the K of its
+    right-hand side and the S of its velocity."""
+    if not stats_list:
+        return 60.0
+    tot = [s["gmres_iters"] + 2 * s["mobility_solves"] for s in stats_list]
+    return float(np.mean(tot))
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, w):
+    steps, warm = args.steps, args.warmup
+    times = []
+    for k in range(warm + steps):
+        full, sample = oracle_sample(w, seed=k)
+        if k >= warm:
+            times.append(full)
+    mv = args.ref_matvecs_per_step
+    step_s = float(np.mean(times)) * mv
+    val = 1.0 / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "N": w.N, "p": w.p,
+                                            "l2": "cpu"},
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": (f"FP64 numpy oracle: traction operator K on 3 of {w.N} "
+                                        f"target spheres per step (all-pairs far field + VSH "
+                                        f"near/self), scaled x{w.N}/3 to one application and "
+                                        f"x{mv:.0f} applications per step")},
+            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+    import paper_1909_06623_gb300 as sps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = sps.Context(stream=stream, **ctx_params(args.precision))
+    pos = dev(w.centers)
+    rad = dev(w.radii)
+    FT = dev(w.FT)
+    gam = torch.empty(16 * w.N, dtype=torch.float64, device="cuda")
+    UO = torch.empty(w.N, 6, dtype=torch.float64, device="cuda")
+    pos_out = torch.empty_like(pos)
+    allow = (4, 5)        # NOT_CONVERGED / BREAKDOWN are reported, not fatal
+
+    def step(p_in):
+        ctx.resolve_collisions(p_in, rad, FT, w.dt, gamma=gam, UO=UO, pos_out=pos_out,
+                               gamma_cap=gam.numel(), allow=allow)
+        return ctx.last_stats
+
+    for _ in range(args.warmup):
+        step(pos)
+        pos.copy_(pos_out)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    sps._lib.load().sps_profile(ctx.h, 1)
+    for k in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        stats.append(dict(step(pos)))
+        ev[k][1].record(stream)
+        pos.copy_(pos_out)
+    torch.cuda.synchronize()
+    ph_ms = (ctypes.c_double * 10)()
+    ph_n = (ctypes.c_longlong * 10)()
+    sps._lib.load().sps_profile_read(ctx.h, ph_ms, ph_n)
+    sps._lib.load().sps_profile(ctx.h, 0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # dominant kernel: far-field traction N-body (phase 0)
+    N, P = w.N, (w.p + 1) * (2 * w.p + 2)
+    NP = N * P
+    n_near = stats[-1]["n_near_pairs"]
+    pairs = NP * NP - P * P * (N + n_near)
+    farK_ms, farK_n = ph_ms[0], ph_n[0]
+    farS_ms, farS_n = ph_ms[1], ph_n[1]
+    avgK = farK_ms / max(farK_n, 1)
+    pk = peaks()
+    achieved = FLOPS_PER_PAIR["K"] * pairs / (avgK * 1e-3) / 1e12
+    interactions = pairs * (farK_n + farS_n) / total_s
+    phases = ["far_K", "far_S", "far_aux", "near_K", "near_S", "self_vsh", "krylov", "contact",
+              "bbpgd", "geometry"]
+    phase_report = {nm: {"ms": round(ph_ms[i], 3), "launches": int(ph_n[i])}
+                    for i, nm in enumerate(phases)}
+    launches = int(sum(s["kernel_launches"] for s in stats))
+
+    # e2e: same step through the host-buffer entry point (copies inside)
+    e2e = None
+    if args.e2e_steps > 0:
+        hpos = torch.as_tensor(w.centers, dtype=torch.float64).pin_memory()
+        hrad = torch.as_tensor(w.radii, dtype=torch.float64).pin_memory()
+        hFT = torch.as_tensor(w.FT, dtype=torch.float64).pin_memory()
+        hg = torch.empty(16 * N, dtype=torch.float64).pin_memory()
+        hU = torch.empty(N, 6, dtype=torch.float64).pin_memory()
+        hp = torch.empty(N, 3, dtype=torch.float64).pin_memory()
+        hpos.copy_(pos.cpu())
+        ctx.resolve_collisions_host(hpos, hrad, hFT, w.dt, hg, hU, hp, allow=allow)
+        hpos.copy_(hp)
+        # re-run timing cleanly (per-call wall time, flush outside)
+        e2e_times = []
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            nc = ctx.resolve_collisions_host(hpos, hrad, hFT, w.dt, hg, hU, hp, allow=allow)
+            e2e_times.append(time.perf_counter() - t1)
+            hpos.copy_(hp)
+        e2e_total = sum(e2e_times)
+        e2e = {"value": args.e2e_steps / e2e_total, "unit": "steps/s",
+               "h2d_bytes_per_step": int(8 * (3 * N + N + 6 * N)),
+               "d2h_bytes_per_step": int(8 * (6 * N + 3 * N + nc)),
+               "steps": args.e2e_steps}
+
+    # FP64 vs mixed: one traction-operator application each, same geometry
+    mv = {}
+    for prec in ("fp64", "mixed"):
+        c2 = sps.Context(stream=stream, **ctx_params(prec))
+        c2.set_geometry(pos, rad)
+        sig = torch.randn(3, NP, dtype=torch.float64, device="cuda")
+        out = torch.empty_like(sig)
+        c2.layer_apply(sps.SPS_OP_K, sig, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 1 if prec == "fp64" else 5
+        e0.record(stream)
+        for _ in range(reps):
+            c2.layer_apply(sps.SPS_OP_K, sig, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mv[prec] = e0.elapsed_time(e1) / reps
+        c2.close()
+    mvps = matvecs_per_step_estimate(stats)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        full, sample = oracle_sample(w)
+        cpu_step = full * mvps
+        cpu = {"value": 1.0 / cpu_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": (f"FP64 numpy oracle: traction operator K on 3 of {N} target spheres "
+                          f"({sample:.1f} s), scaled x{N}/3 to one application and "
+                          f"x{mvps:.0f} applications per step (this run's GMRES counts)")}
+
+    if rank == 0:
+        last = stats[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "N": N, "p": w.p, "nodes": NP, "precision": args.precision,
+                       "gmres_tol": ctx.prm.gmres_tol, "bbpgd_tol": ctx.prm.bbpgd_tol,
+                       "dt": w.dt, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "interactions_per_s": interactions,
+            "roofline": {"bound": "alu", "kernel": "k_far32<K> (far-field traction N-body)",
+                         "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / pk["fp32_tflops"], "traffic": None,
+                         "flops_per_pair": FLOPS_PER_PAIR["K"], "pairs_per_launch": pairs,
+                         "avg_launch_ms": avgK,
+                         "peak_note": (f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz "
+                                       f"(sm_max_mhz {pk['source']})")},
+            "fp64_gpu": {"traction_matvec_ms": mv["fp64"], "mixed_traction_matvec_ms": mv["mixed"],
+                         "mixed_speedup": mv["fp64"] / mv["mixed"],
+                         "fp64_steps_per_s_est": 1.0 / (mvps * mv["fp64"] / 1e3),
+                         "matvecs_per_step": mvps},
+            "solver": {"gmres_iters_per_step": float(np.mean([s["gmres_iters"] for s in stats])),
+                       "mobility_solves_per_step": float(np.mean([s["mobility_solves"] for s in stats])),
+                       "bbpgd_iters": [s["bbpgd_iters"] for s in stats],
+                       "n_contacts": last["n_contacts"], "n_active": last["n_active"],
+                       "n_near_pairs": n_near, "status": [s["status"] for s in stats],
+                       "final_phi": last["final_phi"], "gmres_res_max": last["gmres_res_max"]},
+            "phases_ms": phase_report,
+            "step_ms": step_ms,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-matvecs-per-step", type=float, default=60.0)
+    args = ap.parse_args()
+    w = workload(args.workload)
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, w)
+        return
+    run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * sps.h -- C ABI of the GB300 library for collision-resolving suspensions of
+ * rigid spheres in Stokes flow (Yan, Corona, Malhotra, Veerapaneni, Shelley,
+ * "A scalable computational platform for particulate Stokes suspensions",
+ * arXiv 1909.06623).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Viscosity is 1 (Sec. 4.1).  Lengths, forces and times are in the caller's
+ *    units.
+ *  - Unless a name ends in _host, every array argument is a DEVICE pointer
+ *    owned by the caller (for instance a torch CUDA tensor), must stay valid
+ *    until the call returns, and is accessed in stream order on the stream
+ *    given to sps_create.  Calls return after their work is complete (they read
+ *    back convergence scalars), so outputs may be used right away.
+ *  - Per-sphere arrays are row-major: pos[i*3 + d], FT[i*6 + k] (force then
+ *    torque), UO[i*6 + k] (velocity then angular velocity).
+ *  - Surface fields (densities, velocities, tractions) are stored as three
+ *    component planes of length NP = N * P, P = (p+1)(2p+2) nodes per sphere:
+ *    f[c*NP + i*P + k], node k = ring * (2p+2) + azimuth, rings in ascending
+ *    cos(theta) (Gauss-Legendre nodes), azimuth phi_l = 2 pi l / (2p+2).
+ *  - Every call returns an sps_status.  On an error nothing is guaranteed
+ *    about the outputs except where stated; sps_last_error() describes it.
+ *  - The context owns its scratch memory (device buffers sized by the last
+ *    geometry) and the contact list.  A context is not thread safe.
+ */
+#ifndef SPS_H
+#define SPS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPS_OK = 0,
+  SPS_ERR_INVALID_ARG = 1,   /* bad size, null pointer, p out of range ...   */
+  SPS_ERR_CUDA = 2,          /* a CUDA call failed (message has the reason)  */
+  SPS_ERR_OOM = 3,           /* device allocation failed                     */
+  SPS_ERR_NOT_CONVERGED = 4, /* an iteration hit its cap; outputs hold the
+                                last iterate                                  */
+  SPS_ERR_BREAKDOWN = 5,     /* BBPGD step length undefined (s^T y <= 0)     */
+  SPS_ERR_CAPACITY = 6,      /* output buffer too small (gamma_cap)          */
+  SPS_ERR_NO_GEOMETRY = 7,   /* call needs sps_set_geometry first            */
+  SPS_ERR_NONFINITE = 8      /* NaN or Inf met in an input or a residual     */
+} sps_status;
+
+typedef enum { SPS_FP64 = 0, SPS_MIXED = 1 } sps_precision;
+
+/* Layer operators of Sec. 4.1 evaluated on all surface nodes. */
+typedef enum {
+  SPS_OP_S = 0, /* single layer S[sigma](x) = int G(x-y) sigma(y) dS_y         */
+  SPS_OP_K = 1, /* traction operator K[sigma](x) = int T(x-y) n(x) sigma(y) dS_y */
+  SPS_OP_A = 2  /* (I/2 + K + L)[sigma], the operator of eq. rigidbodyrho      */
+} sps_op;
+
+typedef struct sps_params {
+  int p;              /* spherical-harmonic order, 1 <= p <= 16 (Sec. 4.2)   */
+  double beta;        /* near pair when |c_i-c_j| < beta (a_i+a_j) (Sec. 4.2)*/
+  double delta;       /* contact set: Phi <= delta, absolute (Sec. 3.2)       */
+  double a_c_scale;   /* collision radius a_c = a_c_scale * a (Sec. 6.1)      */
+  double gmres_tol;   /* relative residual of the mobility solve (Sec. 4.1)   */
+  int gmres_max;      /* GMRES iteration cap (Krylov basis size)              */
+  double bbpgd_tol;   /* min-map residual tolerance eps_tol (eq. mmapnorm)    */
+  int bbpgd_max;      /* j_max of Algorithm 1                                 */
+  int precision;      /* sps_precision                                        */
+  int bb_variant;     /* 1: alpha^BB1, 2: alpha^BB2 (Algorithm 1)            */
+  double ir_tol;      /* SPS_MIXED: refine against an FP64 residual until
+                         ||r||/||b|| < ir_tol; 0 disables refinement          */
+  int ir_max;         /* refinement sweep cap                                 */
+} sps_params;
+
+typedef struct sps_stats {
+  int status;           /* sps_status of the call                            */
+  int mobility_solves;  /* mobility problems solved (MVOPs + the U_nc solve) */
+  int gmres_iters;      /* GMRES iterations summed over solves               */
+  int gmres_iters_max;  /* largest per solve                                 */
+  int bbpgd_iters;      /* gradient steps of Algorithm 1                     */
+  int mvops;            /* evaluations of M gamma (Sec. 6.2)                 */
+  int n_contacts;       /* size of the contact set A                         */
+  int n_active;         /* contacts with gamma > 0 (the active set A_c)      */
+  int n_near_pairs;     /* directed near pairs (i, j), i != j                */
+  int ir_sweeps;        /* refinement sweeps (SPS_MIXED with ir_tol > 0)     */
+  long long kernel_launches; /* kernels launched by this call                */
+  double final_phi;     /* min-map residual at exit                          */
+  double gmres_res_max; /* largest final relative residual over the solves   */
+} sps_stats;
+
+typedef struct sps_ctx sps_ctx;
+
+/* Fills *out with the defaults: p 6, beta 1.75, delta 0.1, a_c_scale 1,
+ * gmres 1e-10 / 200, bbpgd 1e-8 / 10000, FP64, BB1, no refinement. */
+int sps_default_params(sps_params* out);
+
+/* Creates a context.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: INVALID_ARG (p out of range, non-positive tolerances), CUDA, OOM. */
+int sps_create(const sps_params* prm, void* stream, sps_ctx** out);
+int sps_destroy(sps_ctx* ctx);
+
+/* Human-readable description of the last error on ctx (never NULL). */
+const char* sps_last_error(const sps_ctx* ctx);
+
+/* Surface nodes for a geometry: the grid of Sec. 5.4 scaled and centred on
+ * each sphere, and the near-pair lists of Sec. 4.2.  n >= 1; pos n x 3, radii n
+ * (device).  Radii must be positive.  Keeps its own copy of the geometry. */
+int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const double* radii);
+
+/* Nodes of the current geometry: X, normals (3 planes of NP) and quadrature
+ * weights (NP), device outputs; any pointer may be NULL.  *np_out = NP. */
+int sps_nodes(sps_ctx* ctx, double* X, double* normals, double* weights, int* np_out);
+
+/* Layer operator (sps_op) applied to sigma (3 planes of NP, device) on the
+ * current geometry; out (3 planes) is overwritten.  Self part: VSH multipliers
+ * (Sec. 4.2); near pairs: VSH expansion of the source sphere (Sec. 4.2); all
+ * other pairs: direct quadrature (Sec. 5.1).  Precision follows prm.precision
+ * (SPS_MIXED: FP32 far field with compensated tile sums). */
+int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double* out);
+
+/* Contact set of Sec. 3.2 for spheres (pos, radii): all i < j with
+ * Phi = |c_i - c_j| - a_c,i - a_c,j <= delta, sorted by (i, j).  Kept in ctx;
+ * the count is written to *n_contacts (host int).  Bit-exact definition:
+ * d^2 = (dx*dx + dy*dy) + dz*dz rounded after every operation, d = sqrt(d^2),
+ * Phi = (d - R_i) - R_j, n = (c_j - c_i) / d. */
+int sps_build_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                       int* n_contacts);
+
+/* Copies the contact list out: ij (n_c x 2 int32), phi (n_c), normals
+ * (n_c x 3); device pointers, any may be NULL. */
+int sps_get_contacts(sps_ctx* ctx, int* ij, double* phi, double* normals);
+
+/* D gamma (eq. Dmatdef): FT (n x 6) = force -gamma n on sphere i and
+ * +gamma n on sphere j per contact; torques zero.  gamma: n_c (device). */
+int sps_contact_force(sps_ctx* ctx, const double* gamma, double* FT);
+
+/* D^T U (eq. Dtranspose): out_l = n_l . (U_j - U_i).  UO: n x 6 (device). */
+int sps_contact_rate(sps_ctx* ctx, const double* UO, double* out);
+
+/* Mobility problem of Sec. 4.1: U/Omega (n x 6) from force/torque FT (n x 6)
+ * for spheres (pos, radii): rho from FT, GMRES on eq. rigidbodyrho, u = S[rho
+ * + zeta] (eq. velS), averages over each sphere.  Sets the geometry.  stats
+ * may be NULL.  NOT_CONVERGED leaves the last iterate's velocities in UO. */
+int sps_mobility_apply(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                       const double* FT, double* UO, sps_stats* stats);
+
+/* One collision-resolved Euler step (Sec. 3.2): U_nc = M F_ext; contact set
+ * and D; BBPGD (Algorithm 1) for gamma with M = D^T M D and
+ * q = Phi/dt + D^T U_nc; U = U_nc + M D gamma; pos_out = pos + U dt.
+ * gamma: capacity gamma_cap (device), receives n_c values (CAPACITY if
+ * n_c > gamma_cap, nothing else written); UO (n x 6) and pos_out (n x 3) may
+ * alias nothing else; pos_out may be NULL. */
+int sps_resolve_collisions(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                           const double* FT_ext, double dt, double* gamma, int gamma_cap,
+                           double* UO, double* pos_out, sps_stats* stats);
+
+/* Same step with HOST arrays: copies the inputs to the device, runs the step
+ * and copies gamma, UO and pos_out back (stream ordered, synchronised before
+ * return).  *n_contacts_out receives n_c (host int, may be NULL). */
+int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                                const double* FT_ext, double dt, double* gamma, int gamma_cap,
+                                double* UO, double* pos_out, int* n_contacts_out,
+                                sps_stats* stats);
+
+/* Phase timers (CUDA events recorded on the context's stream around each
+ * kernel of a phase; the paper's Sec. 6.5 timing categories, refined). */
+typedef enum {
+  SPS_PH_FAR_K = 0,    /* far-field traction N-body kernel ("Far Traction")  */
+  SPS_PH_FAR_S = 1,    /* far-field single-layer N-body kernel ("Far SL")    */
+  SPS_PH_FAR_AUX = 2,  /* FP32 conversion and split reduction of the far field */
+  SPS_PH_NEAR_K = 3,   /* near-pair VSH traction ("Near Correction")         */
+  SPS_PH_NEAR_S = 4,   /* near-pair VSH velocity                             */
+  SPS_PH_SELF = 5,     /* VSH analysis, self synthesis, near coefficients    */
+  SPS_PH_KRYLOV = 6,   /* GMRES orthogonalisation and vector updates, L, rho */
+  SPS_PH_CONTACT = 7,  /* contact set, D, D^T                                */
+  SPS_PH_BBPGD = 8,    /* BBPGD vector kernels                               */
+  SPS_PH_GEOM = 9,     /* surface nodes and near lists ("Far/Near Setup")    */
+  SPS_PH_COUNT = 10
+} sps_phase;
+
+/* enable != 0 starts recording (and clears the totals); 0 stops. */
+int sps_profile(sps_ctx* ctx, int enable);
+/* Synchronises the stream and writes, per phase, the summed event time in
+ * milliseconds (ms[SPS_PH_COUNT]) and the number of kernel launches timed
+ * (launches[SPS_PH_COUNT]); either may be NULL. */
+int sps_profile_read(sps_ctx* ctx, double* ms, long long* launches);
+
+/* Host-only tables (no GPU needed), for checking the library's spherical
+ * harmonic set-up: P = (p+1)(2p+2) unit-sphere nodes and weights, and the
+ * real VSH analysis matrix (rows 6*NC, NC = (p+1)(p+2)/2, row index
+ * ((type*NC + n(n+1)/2 + m)*2 + re_im), type 0/1/2 = V/W/X, m >= 0; columns
+ * c*P + k).  Analysis gives the multipliers of V, W, X in eq. rhoshexp.
+ * Any output may be NULL. */
+int sps_unit_tables(int p, double* nodes /*3*P planes*/, double* weights /*P*/,
+                    double* analysis /*6NC x 3P row-major*/,
+                    double* synthesis /*3P x 6NC row-major*/);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPS_H */

@@ -1,0 +1,197 @@
+"""GB300-native collision-resolving Stokes suspensions of rigid spheres.
+
+Python front end of libsps.so (C ABI in include/sps.h).  Method: Yan, Corona,
+Malhotra, Veerapaneni & Shelley, arXiv 1909.06623 -- BBPGD collision
+resolution (Algorithm 1) around an indirect boundary-integral mobility solve
+(Sec. 4) with VSH self / near-singular quadrature and an all-pairs far field.
+
+The functions mirror the C entry points (same names without the ``sps_``
+prefix on the methods of :class:`Context`); they only marshal arguments:
+torch tensors provide device memory and the CUDA stream.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (SPS_FP64, SPS_MIXED, SPS_OP_A, SPS_OP_K, SPS_OP_S, SPSError, sps_params,
+                   sps_stats)
+
+__all__ = ["Context", "SPSError", "SPS_FP64", "SPS_MIXED", "SPS_OP_S", "SPS_OP_K", "SPS_OP_A",
+           "default_params", "unit_tables", "nodes_per_sphere"]
+
+
+def nodes_per_sphere(p):
+    return (p + 1) * (2 * p + 2)
+
+
+def default_params(**kw):
+    lib = _lib.load()
+    prm = sps_params()
+    lib.sps_default_params(ctypes.byref(prm))
+    for k, v in kw.items():
+        if not hasattr(prm, k):
+            raise KeyError(k)
+        setattr(prm, k, v)
+    return prm
+
+
+def _ptr(t, dtype=torch.float64, device=True):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if device and not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not device and t.is_cuda:
+        raise TypeError("expected a CPU tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def unit_tables(p):
+    """Host-only: unit nodes (3 x P), weights (P), analysis (6NC x 3P), synthesis (3P x 6NC)."""
+    import numpy as np
+    lib = _lib.load()
+    P = nodes_per_sphere(p)
+    NC = (p + 1) * (p + 2) // 2
+    nodes = np.zeros(3 * P)
+    w = np.zeros(P)
+    A = np.zeros(6 * NC * 3 * P)
+    S = np.zeros(3 * P * 6 * NC)
+    rc = lib.sps_unit_tables(p, nodes.ctypes.data, w.ctypes.data, A.ctypes.data, S.ctypes.data)
+    if rc:
+        raise SPSError(rc, "sps_unit_tables")
+    return nodes.reshape(3, P), w, A.reshape(6 * NC, 3 * P), S.reshape(3 * P, 6 * NC)
+
+
+class Context:
+    """Owns an sps_ctx (device scratch, contact list) bound to a CUDA stream."""
+
+    def __init__(self, stream=None, **params):
+        self.lib = _lib.load()
+        self.prm = default_params(**params)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.sps_create(ctypes.byref(self.prm), ctypes.c_void_p(stream.cuda_stream),
+                                 ctypes.byref(h))
+        if rc:
+            raise SPSError(rc, "sps_create")
+        self.h = h
+        self.last_stats = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != 0 and rc not in allow:
+            raise SPSError(rc, self.lib.sps_last_error(self.h).decode())
+        return rc
+
+    @property
+    def P(self):
+        return nodes_per_sphere(self.prm.p)
+
+    # ---- geometry and operators -------------------------------------------------
+    def set_geometry(self, pos, radii):
+        n = radii.numel()
+        self._check(self.lib.sps_set_geometry(self.h, n, _ptr(pos), _ptr(radii)))
+        self.n = n
+
+    def nodes(self):
+        NP = self.n * self.P
+        X = torch.empty(3, NP, dtype=torch.float64, device="cuda")
+        Nr = torch.empty_like(X)
+        W = torch.empty(NP, dtype=torch.float64, device="cuda")
+        np_out = ctypes.c_int()
+        self._check(self.lib.sps_nodes(self.h, _ptr(X), _ptr(Nr), _ptr(W), ctypes.byref(np_out)))
+        return X, Nr, W
+
+    def layer_apply(self, op, sigma, out=None):
+        if out is None:
+            out = torch.empty_like(sigma)
+        self._check(self.lib.sps_layer_apply(self.h, int(op), _ptr(sigma), _ptr(out)))
+        return out
+
+    def build_contacts(self, pos, radii):
+        nc = ctypes.c_int()
+        self._check(self.lib.sps_build_contacts(self.h, radii.numel(), _ptr(pos), _ptr(radii),
+                                                ctypes.byref(nc)))
+        self.n_c = nc.value
+        return nc.value
+
+    def get_contacts(self):
+        nc = self.n_c
+        ij = torch.empty(max(nc, 1), 2, dtype=torch.int32, device="cuda")
+        phi = torch.empty(max(nc, 1), dtype=torch.float64, device="cuda")
+        nrm = torch.empty(max(nc, 1), 3, dtype=torch.float64, device="cuda")
+        self._check(self.lib.sps_get_contacts(self.h, _ptr(ij, torch.int32), _ptr(phi), _ptr(nrm)))
+        return ij[:nc], phi[:nc], nrm[:nc]
+
+    def contact_force(self, gamma, n):
+        FT = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        self._check(self.lib.sps_contact_force(self.h, _ptr(gamma), _ptr(FT)))
+        return FT
+
+    def contact_rate(self, UO):
+        out = torch.empty(max(self.n_c, 1), dtype=torch.float64, device="cuda")
+        self._check(self.lib.sps_contact_rate(self.h, _ptr(UO), _ptr(out)))
+        return out[: self.n_c]
+
+    # ---- solves --------------------------------------------------------------------
+    def mobility_apply(self, pos, radii, FT, UO=None, allow_not_converged=False):
+        n = radii.numel()
+        if UO is None:
+            UO = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        st = sps_stats()
+        rc = self.lib.sps_mobility_apply(self.h, n, _ptr(pos), _ptr(radii), _ptr(FT), _ptr(UO),
+                                         ctypes.byref(st))
+        self._check(rc, allow=(4,) if allow_not_converged else ())
+        self.last_stats = st.as_dict()
+        return UO
+
+    def resolve_collisions(self, pos, radii, FT_ext, dt, gamma=None, UO=None, pos_out=None,
+                           gamma_cap=None, allow=()):
+        n = radii.numel()
+        if gamma_cap is None:
+            gamma_cap = 16 * n
+        if gamma is None:
+            gamma = torch.empty(max(gamma_cap, 1), dtype=torch.float64, device="cuda")
+        if UO is None:
+            UO = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        if pos_out is None:
+            pos_out = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+        st = sps_stats()
+        rc = self.lib.sps_resolve_collisions(self.h, n, _ptr(pos), _ptr(radii), _ptr(FT_ext),
+                                             float(dt), _ptr(gamma), int(gamma_cap), _ptr(UO),
+                                             _ptr(pos_out), ctypes.byref(st))
+        self._check(rc, allow=allow)
+        self.last_stats = st.as_dict()
+        return gamma[: st.n_contacts], UO, pos_out
+
+    def resolve_collisions_host(self, pos, radii, FT_ext, dt, gamma, UO, pos_out, allow=()):
+        """Same step on host (CPU, ideally pinned) tensors; copies happen inside."""
+        n = radii.numel()
+        nc = ctypes.c_int()
+        st = sps_stats()
+        rc = self.lib.sps_resolve_collisions_host(
+            self.h, n, _ptr(pos, device=False), _ptr(radii, device=False),
+            _ptr(FT_ext, device=False), float(dt), _ptr(gamma, device=False), gamma.numel(),
+            _ptr(UO, device=False), _ptr(pos_out, device=False), ctypes.byref(nc),
+            ctypes.byref(st))
+        self._check(rc, allow=allow)
+        self.last_stats = st.as_dict()
+        return nc.value

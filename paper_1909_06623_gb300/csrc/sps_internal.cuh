@@ -1,0 +1,179 @@
+// Internal declarations shared by the translation units of libsps.
+// Data layout in HBM (per context):
+//   geometry   pos (N x 3), rad (N) FP64; nodes X, normals Nrm as 3 planes of
+//              NP = N*P, weights W (NP); FP32 copies for the mixed far field.
+//   near lists CSR by target sphere (near_ptr N+1, near_idx sorted ascending).
+//   surface fields 3 planes of NP (FP64).
+//   VSH        coef: N x NR rows, NR = 6*NC real numbers per sphere
+//              (type V/W/X, n, m >= 0, re/im), the multipliers of eq. rhoshexp.
+//   near field per source sphere, E = (L+1)(L+2)/2 entries (n', m' >= 0,
+//              n' <= L = p+2, m'-major) x F fields, complex.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sps.h"
+
+#define SPS_PI 3.14159265358979323846
+
+namespace sps {
+
+constexpr int kFieldsK = 25;   // fields summed per target for the traction
+constexpr int kFieldsS = 10;   // fields summed per target for the velocity
+constexpr int kMaxP = 16;
+
+struct Tables {
+  int p = 0, P = 0, NC = 0, NR = 0, L = 0, E = 0;
+  std::vector<double> t, wgl;             // Gauss-Legendre nodes / weights
+  std::vector<double> unit_nrm;           // 3 planes of P
+  std::vector<double> unit_w;             // P
+  std::vector<double> anal;               // NR x 3P, row-major
+  std::vector<double> synth;              // 3P x NR, row-major
+  std::vector<double> multS, multK;       // NR (per row: self multipliers)
+  std::vector<double> kappa;              // NC: phi_nm = kappa * H_n^m
+};
+void build_tables(int p, Tables& T);
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace sps
+
+struct sps_ctx {
+  sps_params prm;
+  // phase timers
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
+  size_t ev_used = 0;
+  cudaStream_t stream = nullptr;
+  sps::Tables T;
+  std::string err;
+  long long launches = 0;
+
+  // unit tables on device
+  double *d_unit_nrm = nullptr, *d_unit_w = nullptr;
+  double *d_anal_t = nullptr;   // 3P x NR (column-major analysis: [col][row])
+  double *d_synthS_t = nullptr; // NR x 3P ([row r][col (c,k)]) synth * multS
+  double *d_synthK_t = nullptr; // NR x 3P synth * multK
+  double *d_kappa = nullptr;
+  float *d_anal_t32 = nullptr, *d_synthK_t32 = nullptr;
+
+  // geometry
+  int N = 0, NP = 0, capN = 0;
+  double *d_pos = nullptr, *d_rad = nullptr;
+  double *d_X = nullptr, *d_Nrm = nullptr, *d_W = nullptr;
+  float *d_X32 = nullptr, *d_N32 = nullptr, *d_W32 = nullptr;
+  int *d_near_ptr = nullptr, *d_near_idx = nullptr;
+  int n_near = 0, cap_near = 0;
+  bool have_geom = false;
+
+  // operator scratch
+  double *d_coef = nullptr;      // N x NR
+  double *d_fcoef = nullptr;     // N x E x kFieldsK x 2
+  double *d_mom = nullptr;       // N x 6 (per-sphere moments)
+  double *d_tmp3 = nullptr;      // 3NP scratch
+  float *d_sig32 = nullptr;      // 3NP FP32 density for the mixed far field
+  double *d_part = nullptr;      // far-field partial sums (splits x 3NP)
+  size_t cap_part = 0;
+
+  // GMRES
+  int gm_cap_n = 0, gm_cap_k = 0;
+  double *d_Q = nullptr;         // (k+1) x n Krylov basis
+  double *d_w = nullptr, *d_h = nullptr, *d_red = nullptr;
+  double *h_pinned = nullptr;    // pinned host scratch for scalars
+  double *d_rho = nullptr, *d_zeta = nullptr, *d_b = nullptr, *d_u = nullptr;
+  double *d_r = nullptr, *d_dz = nullptr;
+
+  // contacts
+  int n_c = 0, cap_c = 0, c_N = 0;   // contacts, capacity, spheres they refer to
+  int *d_cij = nullptr;          // n_c x 2
+  double *d_cphi = nullptr, *d_cn = nullptr;
+  int *d_ccount = nullptr, *d_cptr = nullptr;  // N+1
+  int *d_inc_ptr = nullptr, *d_inc = nullptr;  // incidence CSR by sphere (2 n_c)
+  void *d_cub = nullptr; size_t cub_bytes = 0;
+  int *d_keys = nullptr, *d_vals = nullptr, *d_keys2 = nullptr, *d_vals2 = nullptr;
+
+  // BBPGD vectors (n_c each)
+  double *d_gam = nullptr, *d_g = nullptr, *d_gam_new = nullptr, *d_g_new = nullptr;
+  double *d_q = nullptr, *d_Mg = nullptr;
+  double *d_FT = nullptr, *d_Unc = nullptr, *d_Uc = nullptr;
+  int cap_bb = 0;
+};
+
+// ---------------------------------------------------------------------------
+// error helpers
+// ---------------------------------------------------------------------------
+int sps_fail(sps_ctx* ctx, int code, const std::string& msg);
+#define SPS_CUDA(ctx, call)                                                   \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      return sps_fail(ctx, SPS_ERR_CUDA,                                      \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+#define SPS_LAUNCHED(ctx)                                                     \
+  do {                                                                        \
+    (ctx)->launches++;                                                        \
+    cudaError_t e_ = cudaGetLastError();                                      \
+    if (e_ != cudaSuccess)                                                    \
+      return sps_fail(ctx, SPS_ERR_CUDA,                                      \
+                      std::string("launch: ") + cudaGetErrorString(e_));      \
+  } while (0)
+#define SPS_TRY(x)            \
+  do {                        \
+    int rc_ = (x);            \
+    if (rc_ != SPS_OK) return rc_; \
+  } while (0)
+
+template <class T>
+int sps_grow(sps_ctx* ctx, T** p, size_t& cap_elems, size_t need_elems) {
+  if (need_elems <= cap_elems && *p) return SPS_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  size_t n = need_elems ? need_elems : 1;
+  if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    cap_elems = 0;
+    return sps_fail(ctx, SPS_ERR_OOM, "cudaMalloc failed");
+  }
+  cap_elems = n;
+  return SPS_OK;
+}
+
+// RAII phase timer: records an event pair around the enclosed launches
+struct SpsPhase {
+  sps_ctx* c;
+  int ph;
+  cudaEvent_t b = nullptr, e = nullptr;
+  SpsPhase(sps_ctx* ctx, int phase);
+  ~SpsPhase();
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each returns an sps_status)
+// ---------------------------------------------------------------------------
+// geometry / contacts (sps_geometry.cu)
+int sps_launch_grid(sps_ctx* ctx);
+int sps_launch_near_lists(sps_ctx* ctx);
+int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii);
+int sps_launch_D(sps_ctx* ctx, const double* gamma, double* FT);
+int sps_launch_DT(sps_ctx* ctx, const double* UO, double* out);
+int sps_launch_rho(sps_ctx* ctx, const double* FT, double* rho);
+int sps_launch_moments(sps_ctx* ctx, const double* f, double* mom);
+int sps_launch_add_L(sps_ctx* ctx, const double* mom, double* out);
+int sps_launch_extract(sps_ctx* ctx, const double* mom, double* UO);
+
+// layer operators (sps_vsh.cu, sps_nbody.cu)
+int sps_launch_analysis(sps_ctx* ctx, const double* sig);
+int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out);
+int sps_launch_near(sps_ctx* ctx, int op, double* out);
+int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
+int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
+
+// vector kernels (sps_solver.cu)
+int sps_dot(sps_ctx* ctx, const double* a, const double* b, long long n, double* host_out);

@@ -1,0 +1,844 @@
+// Context, mobility solve and collision resolution (C ABI of include/sps.h).
+//
+//  * Mobility (Sec. 4.1): rho from F, T; b = -(I/2 + K)[rho]; GMRES on
+//    (I/2 + K + L)[zeta] = b (eq. rigidbodyrho); u = S[rho + zeta] (eq. velS);
+//    U, Omega as averages of u over each sphere.
+//    GMRES: unrestarted, zero initial guess, classical Gram-Schmidt applied
+//    twice, Givens rotations on the host, FP64 everywhere; stop when
+//    ||r|| / ||b|| < gmres_tol.  Mixed precision: the far-field sums run in
+//    FP32 (compensated), the Krylov basis, orthogonalisation and residual in
+//    FP64; with ir_tol > 0 the solve is refined against the FP64 operator.
+//  * Collision step (Sec. 3.2, Algorithm 1): contacts, q = Phi/dt + D^T U_nc,
+//    BBPGD with gamma_0 = 0 (M gamma_0 = 0 needs no solve), alpha_0 =
+//    g^T g / g^T M g, projected steps, min-map residual test, BB1 or BB2
+//    step lengths; U = U_nc + M D gamma; pos += U dt.
+//  All reductions are deterministic (fixed block partition and order).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sps_internal.cuh"
+
+namespace {
+
+constexpr int kRedBlocks = 256;
+constexpr int kRedThreads = 256;
+constexpr int kChunk = 8;   // dot products per pass of the multi-dot kernel
+
+// partial[j][b] = sum over block b's slice of Q_j . w, for j in [j0, j0+nj)
+__global__ void __launch_bounds__(kRedThreads) k_multidot(long long n, const double* __restrict__ Q,
+                                                         long long ldq, int j0, int nj,
+                                                         const double* __restrict__ w,
+                                                         double* __restrict__ partial) {
+  __shared__ double red[kRedThreads / 32][kChunk];
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long a = blockIdx.x * per, b = min(n, a + per);
+  double acc[kChunk];
+#pragma unroll
+  for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
+  for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q)
+      if (q < nj) acc[q] = fma(Q[(long long)(j0 + q) * ldq + i], wi, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < kChunk; ++q)
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) red[warp][q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < nj) {
+    double s = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) s += red[k][threadIdx.x];
+    partial[(long long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_finish(int nj, int nb, const double* __restrict__ partial, double* __restrict__ h) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nj) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[(long long)j * nb + b];
+  h[j] = s;
+}
+
+// w -= sum_j h_j Q_j   (h on device)
+__global__ void k_sub_proj(long long n, const double* __restrict__ Q, long long ldq, int k,
+                           const double* __restrict__ h, double* __restrict__ w) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int j = 0; j < k; ++j) s = fma(-h[j], Q[(long long)j * ldq + i], s);
+    w[i] = s;
+  }
+}
+
+// x = sum_j y_j Q_j (+ x if accumulate)
+__global__ void k_combine(long long n, const double* __restrict__ Q, long long ldq, int k,
+                          const double* __restrict__ y, int accumulate, double* __restrict__ x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s = accumulate ? x[i] : 0.0;
+    for (int j = 0; j < k; ++j) s = fma(y[j], Q[(long long)j * ldq + i], s);
+    x[i] = s;
+  }
+}
+
+__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, double* __restrict__ z) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    z[i] = a * x[i] + b * (y ? y[i] : 0.0);
+}
+
+// BBPGD: gamma_new = max(gamma - alpha g, 0)
+__global__ void k_bb_step(int n, double alpha, const double* __restrict__ gam,
+                          const double* __restrict__ g, double* __restrict__ gnew) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) gnew[l] = fmax(gam[l] - alpha * g[l], 0.0);
+}
+
+// g = a + q
+__global__ void k_add(int n, const double* __restrict__ a, const double* __restrict__ q,
+                      double* __restrict__ g) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) g[l] = a[l] + q[l];
+}
+
+// q = phi/dt + D^T U_nc (D^T U_nc already in q)
+__global__ void k_q(int n, const double* __restrict__ phi, double idt, double* __restrict__ q) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) q[l] = phi[l] * idt + q[l];
+}
+
+// stats for Algorithm 1: [sum min(gn, gg)^2, s.s, s.y, y.y, g.g] with
+// s = gn - go, y = ggn - ggo.  One block, fixed order.
+__global__ void __launch_bounds__(1024) k_bb_stats(int n, const double* __restrict__ gam_new,
+                                                   const double* __restrict__ g_new,
+                                                   const double* __restrict__ gam_old,
+                                                   const double* __restrict__ g_old,
+                                                   double* __restrict__ out) {
+  __shared__ double red[32][5];
+  double a[5] = {0, 0, 0, 0, 0};
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    const double mn = fmin(gam_new[l], g_new[l]);
+    a[0] += mn * mn;
+    if (gam_old) {
+      const double s = gam_new[l] - gam_old[l], y = g_new[l] - g_old[l];
+      a[1] += s * s;
+      a[2] += s * y;
+      a[3] += y * y;
+    }
+    a[4] += g_new[l] * g_new[l];
+  }
+  for (int c = 0; c < 5; ++c)
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int c = 0; c < 5; ++c) red[threadIdx.x >> 5][c] = a[c];
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+__global__ void k_pos_update(int n, const double* __restrict__ pos, const double* __restrict__ UO,
+                             double dt, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * n) out[i] = pos[i] + dt * UO[6 * (i / 3) + (i % 3)];
+}
+
+inline int gblocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 8 * 152); }
+
+}  // namespace
+
+static cudaEvent_t pool_event(sps_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+SpsPhase::SpsPhase(sps_ctx* ctx, int phase) : c(ctx), ph(phase) {
+  if (!c->prof) return;
+  b = pool_event(c);
+  e = pool_event(c);
+  if (b) cudaEventRecord(b, c->stream);
+}
+
+SpsPhase::~SpsPhase() {
+  if (!c->prof || !b || !e) return;
+  cudaEventRecord(e, c->stream);
+  c->ev_rec.push_back({ph, {b, e}});
+}
+
+extern "C" int sps_profile(sps_ctx* ctx, int enable) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->prof = enable != 0;
+  ctx->ev_rec.clear();
+  ctx->ev_used = 0;
+  return SPS_OK;
+}
+
+extern "C" int sps_profile_read(sps_ctx* ctx, double* ms, long long* launches) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double t[SPS_PH_COUNT] = {0};
+  long long n[SPS_PH_COUNT] = {0};
+  for (auto& r : ctx->ev_rec) {
+    float x = 0.f;
+    SPS_CUDA(ctx, cudaEventElapsedTime(&x, r.second.first, r.second.second));
+    t[r.first] += x;
+    n[r.first] += 1;
+  }
+  if (ms) std::memcpy(ms, t, sizeof(t));
+  if (launches) std::memcpy(launches, n, sizeof(n));
+  return SPS_OK;
+}
+
+int sps_fail(sps_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+// h[0..k) = Q[0..k)^T w  -> device d_h and host hh
+static int multidot(sps_ctx* ctx, const double* Q, long long ldq, int k, const double* w,
+                    long long n, double* hh) {
+  for (int j0 = 0; j0 < k; j0 += kChunk) {
+    const int nj = std::min(kChunk, k - j0);
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_multidot<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(n, Q, ldq, j0, nj, w, ctx->d_red); }
+    SPS_LAUNCHED(ctx);
+  }
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_finish<<<(k + 127) / 128, 128, 0, ctx->stream>>>(k, kRedBlocks, ctx->d_red, ctx->d_h); }
+  SPS_LAUNCHED(ctx);
+  if (hh) {
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_h, sizeof(double) * k, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::memcpy(hh, ctx->h_pinned, sizeof(double) * k);
+  }
+  return SPS_OK;
+}
+
+int sps_dot(sps_ctx* ctx, const double* a, const double* b, long long n, double* out) {
+  return multidot(ctx, a, 0, 1, b, n, out);
+}
+
+static int ensure_gmres(sps_ctx* ctx, long long n, int kmax) {
+  if (n <= ctx->gm_cap_n && kmax <= ctx->gm_cap_k && ctx->d_Q) return SPS_OK;
+  cudaFree(ctx->d_Q);
+  cudaFree(ctx->d_w);
+  cudaFree(ctx->d_h);
+  cudaFree(ctx->d_red);
+  ctx->d_Q = ctx->d_w = ctx->d_h = ctx->d_red = nullptr;
+  size_t c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_Q, c, (size_t)(kmax + 1) * n));
+  c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_w, c, (size_t)n));
+  c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_h, c, (size_t)kmax + 8));
+  c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_red, c, (size_t)(kmax + 8) * kRedBlocks));
+  ctx->gm_cap_n = (int)n;
+  ctx->gm_cap_k = kmax;
+  return SPS_OK;
+}
+
+// operator application for GMRES: out = (I/2 + K + L) v
+static int apply_A(sps_ctx* ctx, const double* v, double* out, bool fp32) {
+  return sps_layer(ctx, SPS_OP_A, v, out, fp32);
+}
+
+// GMRES on A x = b, x0 = 0.  Returns SPS_OK or NOT_CONVERGED.
+static int gmres(sps_ctx* ctx, const double* b, double* x, double tol, int kmax, bool fp32,
+                 int* iters, double* relres) {
+  const long long n = 3LL * ctx->NP;
+  SPS_TRY(ensure_gmres(ctx, n, kmax));
+  double bb = 0.0;
+  SPS_TRY(sps_dot(ctx, b, b, n, &bb));
+  if (!std::isfinite(bb)) return sps_fail(ctx, SPS_ERR_NONFINITE, "GMRES right-hand side is not finite");
+  const double beta = std::sqrt(bb);
+  *iters = 0;
+  *relres = 0.0;
+  if (beta == 0.0) {
+    SPS_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+    return SPS_OK;
+  }
+  double* Q = ctx->d_Q;
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / beta, b, 0.0, nullptr, Q); }
+  SPS_LAUNCHED(ctx);
+  std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), g(kmax + 1, 0.0);
+  std::vector<double> h1(kmax + 1), h2(kmax + 1);
+  g[0] = beta;
+  int k = 0;
+  double res = 1.0;
+  auto Hc = [&](int r, int c) -> double& { return H[(size_t)c * (kmax + 1) + r]; };
+  for (k = 1; k <= kmax; ++k) {
+    double* w = ctx->d_w;
+    SPS_TRY(apply_A(ctx, Q + (long long)(k - 1) * n, w, fp32));
+    // classical Gram-Schmidt, twice
+    SPS_TRY(multidot(ctx, Q, n, k, w, n, h1.data()));
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, ctx->d_h, w); }
+    SPS_LAUNCHED(ctx);
+    SPS_TRY(multidot(ctx, Q, n, k, w, n, h2.data()));
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, ctx->d_h, w); }
+    SPS_LAUNCHED(ctx);
+    double ww = 0.0;
+    SPS_TRY(sps_dot(ctx, w, w, n, &ww));
+    if (!std::isfinite(ww)) return sps_fail(ctx, SPS_ERR_NONFINITE, "GMRES: non-finite Krylov vector");
+    const double hk = std::sqrt(ww);
+    for (int j = 0; j < k; ++j) Hc(j, k - 1) = h1[j] + h2[j];
+    Hc(k, k - 1) = hk;
+    if (hk > 0.0) {
+      { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+      k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / hk, w, 0.0, nullptr, Q + (long long)k * n); }
+      SPS_LAUNCHED(ctx);
+    }
+    for (int j = 0; j < k - 1; ++j) {
+      const double a = Hc(j, k - 1), bq = Hc(j + 1, k - 1);
+      Hc(j, k - 1) = cs[j] * a + sn[j] * bq;
+      Hc(j + 1, k - 1) = -sn[j] * a + cs[j] * bq;
+    }
+    const double a = Hc(k - 1, k - 1), bq = Hc(k, k - 1);
+    const double den = std::hypot(a, bq);
+    cs[k - 1] = a / den;
+    sn[k - 1] = bq / den;
+    Hc(k - 1, k - 1) = den;
+    Hc(k, k - 1) = 0.0;
+    g[k] = -sn[k - 1] * g[k - 1];
+    g[k - 1] = cs[k - 1] * g[k - 1];
+    res = std::fabs(g[k]) / beta;
+    if (res < tol || hk == 0.0) break;
+  }
+  if (k > kmax) k = kmax;
+  std::vector<double> y(k);
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int j = i + 1; j < k; ++j) s -= Hc(i, j) * y[j];
+    y[i] = s / Hc(i, i);
+  }
+  std::memcpy(ctx->h_pinned, y.data(), sizeof(double) * k);
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_h, ctx->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice,
+                                ctx->stream));
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, ctx->d_h, 0, x); }
+  SPS_LAUNCHED(ctx);
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *iters = k;
+  *relres = res;
+  return (res < tol) ? SPS_OK : SPS_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int sps_default_params(sps_params* o) {
+  if (!o) return SPS_ERR_INVALID_ARG;
+  o->p = 6;
+  o->beta = 1.75;
+  o->delta = 0.1;
+  o->a_c_scale = 1.0;
+  o->gmres_tol = 1e-10;
+  o->gmres_max = 200;
+  o->bbpgd_tol = 1e-8;
+  o->bbpgd_max = 10000;
+  o->precision = SPS_FP64;
+  o->bb_variant = 1;
+  o->ir_tol = 0.0;
+  o->ir_max = 10;
+  return SPS_OK;
+}
+
+template <class T>
+static int upload(sps_ctx* ctx, T** d, const std::vector<T>& h) {
+  SPS_CUDA(ctx, cudaMalloc((void**)d, sizeof(T) * std::max<size_t>(1, h.size())));
+  SPS_CUDA(ctx, cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return SPS_OK;
+}
+
+extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
+  if (!prm || !out) return SPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (prm->p < 1 || prm->p > sps::kMaxP || !(prm->beta > 1.0) || !(prm->gmres_tol > 0) ||
+      prm->gmres_max < 1 || !(prm->bbpgd_tol > 0) || prm->bbpgd_max < 1 ||
+      (prm->precision != SPS_FP64 && prm->precision != SPS_MIXED) ||
+      (prm->bb_variant != 1 && prm->bb_variant != 2) || !(prm->a_c_scale > 0) ||
+      !(prm->delta >= 0) || prm->ir_tol < 0 || prm->ir_max < 0)
+    return SPS_ERR_INVALID_ARG;
+  sps_ctx* ctx = new sps_ctx();
+  ctx->prm = *prm;
+  ctx->stream = (cudaStream_t)stream;
+  sps::build_tables(prm->p, ctx->T);
+  const sps::Tables& T = ctx->T;
+  const int P = T.P, NR = T.NR;
+  std::vector<double> anal_t((size_t)3 * P * NR), sS((size_t)NR * 3 * P), sK((size_t)NR * 3 * P);
+  for (int r = 0; r < NR; ++r)
+    for (int c = 0; c < 3 * P; ++c) {
+      anal_t[(size_t)c * NR + r] = T.anal[(size_t)r * 3 * P + c];
+      sS[(size_t)r * 3 * P + c] = T.synth[(size_t)c * NR + r] * T.multS[r];
+      sK[(size_t)r * 3 * P + c] = T.synth[(size_t)c * NR + r] * T.multK[r];
+    }
+  int rc = SPS_OK;
+  if ((rc = upload(ctx, &ctx->d_unit_nrm, T.unit_nrm)) || (rc = upload(ctx, &ctx->d_unit_w, T.unit_w)) ||
+      (rc = upload(ctx, &ctx->d_anal_t, anal_t)) || (rc = upload(ctx, &ctx->d_synthS_t, sS)) ||
+      (rc = upload(ctx, &ctx->d_synthK_t, sK)) || (rc = upload(ctx, &ctx->d_kappa, T.kappa))) {
+    sps_destroy(ctx);
+    return rc;
+  }
+  if (cudaMallocHost((void**)&ctx->h_pinned, sizeof(double) * 4096) != cudaSuccess) {
+    cudaGetLastError();
+    sps_destroy(ctx);
+    return SPS_ERR_CUDA;
+  }
+  *out = ctx;
+  return SPS_OK;
+}
+
+extern "C" int sps_destroy(sps_ctx* ctx) {
+  if (!ctx) return SPS_OK;
+  void* bufs[] = {ctx->d_unit_nrm, ctx->d_unit_w, ctx->d_anal_t, ctx->d_synthS_t, ctx->d_synthK_t,
+                  ctx->d_kappa, ctx->d_anal_t32, ctx->d_synthK_t32, ctx->d_pos, ctx->d_rad,
+                  ctx->d_X, ctx->d_Nrm, ctx->d_W, ctx->d_X32, ctx->d_N32, ctx->d_W32,
+                  ctx->d_near_ptr, ctx->d_near_idx, ctx->d_coef, ctx->d_fcoef, ctx->d_mom,
+                  ctx->d_tmp3, ctx->d_sig32, ctx->d_part, ctx->d_Q, ctx->d_w, ctx->d_h, ctx->d_red,
+                  ctx->d_rho, ctx->d_zeta, ctx->d_b, ctx->d_u, ctx->d_r, ctx->d_dz, ctx->d_cij,
+                  ctx->d_cphi, ctx->d_cn, ctx->d_ccount, ctx->d_cptr, ctx->d_inc_ptr, ctx->d_inc,
+                  ctx->d_cub, ctx->d_keys, ctx->d_vals, ctx->d_keys2, ctx->d_vals2, ctx->d_gam,
+                  ctx->d_g, ctx->d_gam_new, ctx->d_g_new, ctx->d_q, ctx->d_Mg, ctx->d_FT,
+                  ctx->d_Unc, ctx->d_Uc};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+  return SPS_OK;
+}
+
+extern "C" const char* sps_last_error(const sps_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+static int check_finite_host(sps_ctx* ctx, const double* d, long long n, const char* what) {
+  std::vector<double> h(n);
+  SPS_CUDA(ctx, cudaMemcpyAsync(h.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(h[i])) return sps_fail(ctx, SPS_ERR_NONFINITE, std::string(what) + " is not finite");
+  return SPS_OK;
+}
+
+extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const double* radii) {
+  if (!ctx || n < 1 || !pos || !radii) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "set_geometry: bad argument");
+  const int P = ctx->T.P;
+  const long long NP = (long long)n * P;
+  {
+    std::vector<double> h(4 * (size_t)n);
+    SPS_CUDA(ctx, cudaMemcpyAsync(h.data(), pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA(ctx, cudaMemcpyAsync(h.data() + 3 * n, radii, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < h.size(); ++i)
+      if (!std::isfinite(h[i])) return sps_fail(ctx, SPS_ERR_NONFINITE, "positions or radii not finite");
+    for (int i = 0; i < n; ++i)
+      if (!(h[3 * n + i] > 0)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "radii must be positive");
+  }
+  if (n > ctx->capN) {
+    double** d64[] = {&ctx->d_pos, &ctx->d_rad, &ctx->d_X, &ctx->d_Nrm, &ctx->d_W, &ctx->d_coef,
+                      &ctx->d_fcoef, &ctx->d_mom, &ctx->d_tmp3, &ctx->d_rho, &ctx->d_zeta, &ctx->d_b,
+                      &ctx->d_u, &ctx->d_r, &ctx->d_dz, &ctx->d_FT, &ctx->d_Unc, &ctx->d_Uc};
+    for (auto p : d64) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    float** d32[] = {&ctx->d_X32, &ctx->d_N32, &ctx->d_W32, &ctx->d_sig32};
+    for (auto p : d32) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    cudaFree(ctx->d_near_ptr);
+    ctx->d_near_ptr = nullptr;
+    size_t c;
+    const size_t E = ctx->T.E, NR = ctx->T.NR;
+    struct {
+      double** p;
+      size_t n;
+    } a64[] = {{&ctx->d_pos, 3 * (size_t)n}, {&ctx->d_rad, (size_t)n}, {&ctx->d_X, 3 * (size_t)NP},
+               {&ctx->d_Nrm, 3 * (size_t)NP}, {&ctx->d_W, (size_t)NP}, {&ctx->d_coef, (size_t)n * NR},
+               {&ctx->d_fcoef, (size_t)n * E * sps::kFieldsK * 2}, {&ctx->d_mom, 6 * (size_t)n},
+               {&ctx->d_tmp3, 3 * (size_t)NP}, {&ctx->d_rho, 3 * (size_t)NP},
+               {&ctx->d_zeta, 3 * (size_t)NP}, {&ctx->d_b, 3 * (size_t)NP}, {&ctx->d_u, 3 * (size_t)NP},
+               {&ctx->d_r, 3 * (size_t)NP}, {&ctx->d_dz, 3 * (size_t)NP}, {&ctx->d_FT, 6 * (size_t)n},
+               {&ctx->d_Unc, 6 * (size_t)n}, {&ctx->d_Uc, 6 * (size_t)n}};
+    for (auto& e : a64) {
+      c = 0;
+      SPS_TRY(sps_grow(ctx, e.p, c, e.n));
+    }
+    struct {
+      float** p;
+      size_t n;
+    } a32[] = {{&ctx->d_X32, 3 * (size_t)NP}, {&ctx->d_N32, 3 * (size_t)NP}, {&ctx->d_W32, (size_t)NP},
+               {&ctx->d_sig32, 3 * (size_t)NP}};
+    for (auto& e : a32) {
+      c = 0;
+      SPS_TRY(sps_grow(ctx, e.p, c, e.n));
+    }
+    c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_near_ptr, c, (size_t)n + 1));
+    ctx->capN = n;
+  }
+  ctx->N = n;
+  ctx->NP = (int)NP;
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_rad, radii, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  SPS_TRY(sps_launch_grid(ctx));
+  SPS_TRY(sps_launch_near_lists(ctx));
+  ctx->have_geom = true;
+  return SPS_OK;
+}
+
+extern "C" int sps_nodes(sps_ctx* ctx, double* X, double* normals, double* weights, int* np_out) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!ctx->have_geom) return sps_fail(ctx, SPS_ERR_NO_GEOMETRY, "no geometry");
+  const size_t NP = ctx->NP;
+  if (X) SPS_CUDA(ctx, cudaMemcpyAsync(X, ctx->d_X, 3 * NP * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (normals)
+    SPS_CUDA(ctx, cudaMemcpyAsync(normals, ctx->d_Nrm, 3 * NP * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (weights) SPS_CUDA(ctx, cudaMemcpyAsync(weights, ctx->d_W, NP * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (np_out) *np_out = (int)NP;
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+extern "C" int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double* out) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!ctx->have_geom) return sps_fail(ctx, SPS_ERR_NO_GEOMETRY, "no geometry");
+  if (op < SPS_OP_S || op > SPS_OP_A || !sigma || !out)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "layer_apply: bad argument");
+  SPS_TRY(sps_layer(ctx, op, sigma, out, ctx->prm.precision == SPS_MIXED));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mobility solve on the current geometry
+// ---------------------------------------------------------------------------
+static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats* st) {
+  const long long n = 3LL * ctx->NP;
+  const bool mixed = ctx->prm.precision == SPS_MIXED;
+  const bool refine = mixed && ctx->prm.ir_tol > 0;
+  SPS_TRY(sps_launch_rho(ctx, FT, ctx->d_rho));
+  // b = -(I/2 + K)[rho]
+  SPS_TRY(sps_layer(ctx, SPS_OP_K, ctx->d_rho, ctx->d_tmp3, mixed && !refine));
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, -0.5, ctx->d_rho, -1.0, ctx->d_tmp3, ctx->d_b); }
+  SPS_LAUNCHED(ctx);
+  int its = 0;
+  double res = 0.0;
+  int rc = gmres(ctx, ctx->d_b, ctx->d_zeta, ctx->prm.gmres_tol, ctx->prm.gmres_max, mixed, &its, &res);
+  if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+  int total_its = its;
+  double final_res = res;
+  if (refine) {
+    // iterative refinement against the FP64 operator: r = b - A zeta
+    double bb = 0.0;
+    SPS_TRY(sps_dot(ctx, ctx->d_b, ctx->d_b, n, &bb));
+    const double nb = std::sqrt(bb);
+    int sweep = 0;
+    for (; sweep < ctx->prm.ir_max; ++sweep) {
+      SPS_TRY(apply_A(ctx, ctx->d_zeta, ctx->d_r, false));
+      { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+      k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_b, -1.0, ctx->d_r, ctx->d_r); }
+      SPS_LAUNCHED(ctx);
+      double rr = 0.0;
+      SPS_TRY(sps_dot(ctx, ctx->d_r, ctx->d_r, n, &rr));
+      final_res = nb > 0 ? std::sqrt(rr) / nb : 0.0;
+      if (final_res < ctx->prm.ir_tol) break;
+      int its2 = 0;
+      double res2 = 0;
+      int rc2 = gmres(ctx, ctx->d_r, ctx->d_dz, ctx->prm.gmres_tol, ctx->prm.gmres_max, true, &its2, &res2);
+      if (rc2 != SPS_OK && rc2 != SPS_ERR_NOT_CONVERGED) return rc2;
+      total_its += its2;
+      { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+      k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_zeta, 1.0, ctx->d_dz, ctx->d_zeta); }
+      SPS_LAUNCHED(ctx);
+    }
+    if (st) st->ir_sweeps += sweep;
+    rc = (final_res < ctx->prm.ir_tol) ? SPS_OK : SPS_ERR_NOT_CONVERGED;
+  }
+  // u = S[rho + zeta]
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_rho, 1.0, ctx->d_zeta, ctx->d_tmp3); }
+  SPS_LAUNCHED(ctx);
+  SPS_TRY(sps_layer(ctx, SPS_OP_S, ctx->d_tmp3, ctx->d_u, mixed && !refine));
+  SPS_TRY(sps_launch_moments(ctx, ctx->d_u, ctx->d_mom));
+  SPS_TRY(sps_launch_extract(ctx, ctx->d_mom, UO));
+  if (st) {
+    st->mobility_solves += 1;
+    st->gmres_iters += total_its;
+    st->gmres_iters_max = std::max(st->gmres_iters_max, total_its);
+    st->gmres_res_max = std::max(st->gmres_res_max, final_res);
+  }
+  return rc;
+}
+
+static void stats_begin(sps_ctx* ctx, sps_stats* st, long long* l0) {
+  if (st) std::memset(st, 0, sizeof(*st));
+  *l0 = ctx->launches;
+}
+static int stats_end(sps_ctx* ctx, sps_stats* st, long long l0, int rc) {
+  if (st) {
+    st->status = rc;
+    st->kernel_launches = ctx->launches - l0;
+    st->n_near_pairs = ctx->n_near;
+  }
+  return rc;
+}
+
+extern "C" int sps_mobility_apply(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                                  const double* FT, double* UO, sps_stats* st) {
+  if (!ctx || !FT || !UO) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "mobility_apply: bad argument");
+  long long l0;
+  stats_begin(ctx, st, &l0);
+  int rc = sps_set_geometry(ctx, n, pos, radii);
+  if (rc == SPS_OK) rc = check_finite_host(ctx, FT, 6LL * n, "force/torque");
+  if (rc == SPS_OK) rc = mobility_solve(ctx, FT, UO, st);
+  if (rc == SPS_OK || rc == SPS_ERR_NOT_CONVERGED) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return stats_end(ctx, st, l0, rc);
+}
+
+extern "C" int sps_build_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                                  int* n_contacts) {
+  if (!ctx || n < 1 || !pos || !radii) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "build_contacts: bad argument");
+  SPS_TRY(sps_launch_contacts(ctx, n, pos, radii));
+  ctx->c_N = n;
+  if (n_contacts) *n_contacts = ctx->n_c;
+  return SPS_OK;
+}
+
+extern "C" int sps_get_contacts(sps_ctx* ctx, int* ij, double* phi, double* normals) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  const size_t nc = ctx->n_c;
+  if (nc == 0) return SPS_OK;
+  if (ij) SPS_CUDA(ctx, cudaMemcpyAsync(ij, ctx->d_cij, nc * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (phi) SPS_CUDA(ctx, cudaMemcpyAsync(phi, ctx->d_cphi, nc * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (normals)
+    SPS_CUDA(ctx, cudaMemcpyAsync(normals, ctx->d_cn, nc * 24, cudaMemcpyDeviceToDevice, ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+extern "C" int sps_contact_force(sps_ctx* ctx, const double* gamma, double* FT) {
+  if (!ctx || !FT || (ctx->n_c && !gamma)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "contact_force");
+  if (ctx->c_N == 0) return sps_fail(ctx, SPS_ERR_NO_GEOMETRY, "no contact list");
+  SPS_TRY(sps_launch_D(ctx, gamma, FT));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+extern "C" int sps_contact_rate(sps_ctx* ctx, const double* UO, double* out) {
+  if (!ctx || !UO || (ctx->n_c && !out)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "contact_rate");
+  SPS_TRY(sps_launch_DT(ctx, UO, out));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// collision-resolved step
+// ---------------------------------------------------------------------------
+static int ensure_bb(sps_ctx* ctx, int nc) {
+  if (nc <= ctx->cap_bb && ctx->d_gam) return SPS_OK;
+  double** v[] = {&ctx->d_gam, &ctx->d_g, &ctx->d_gam_new, &ctx->d_g_new, &ctx->d_q, &ctx->d_Mg};
+  for (auto p : v) {
+    cudaFree(*p);
+    *p = nullptr;
+    size_t c = 0;
+    SPS_TRY(sps_grow(ctx, p, c, (size_t)std::max(nc, 1)));
+  }
+  ctx->cap_bb = std::max(nc, 1);
+  return SPS_OK;
+}
+
+// out = M gamma = D^T M D gamma; leaves M D gamma in d_Uc
+static int apply_M(sps_ctx* ctx, const double* gam, double* out, sps_stats* st) {
+  SPS_TRY(sps_launch_D(ctx, gam, ctx->d_FT));
+  int rc = mobility_solve(ctx, ctx->d_FT, ctx->d_Uc, st);
+  if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+  if (st) st->mvops += 1;
+  SPS_TRY(sps_launch_DT(ctx, ctx->d_Uc, out));
+  return rc;
+}
+
+static int bb_stats(sps_ctx* ctx, const double* gn, const double* ggn, const double* go,
+                    const double* ggo, double out[5]) {
+  { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+  k_bb_stats<<<1, 1024, 0, ctx->stream>>>(ctx->n_c, gn, ggn, go, ggo, ctx->d_h); }
+  SPS_LAUNCHED(ctx);
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_h, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::memcpy(out, ctx->h_pinned, 5 * sizeof(double));
+  for (int i = 0; i < 5; ++i)
+    if (!std::isfinite(out[i])) return sps_fail(ctx, SPS_ERR_NONFINITE, "BBPGD: non-finite residual");
+  return SPS_OK;
+}
+
+static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, const double* FT_ext,
+                   double dt, double* gamma, int gamma_cap, double* UO, double* pos_out, sps_stats* st) {
+  if (!(dt > 0)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "dt must be positive");
+  SPS_TRY(sps_set_geometry(ctx, n, pos, radii));
+  SPS_TRY(check_finite_host(ctx, FT_ext, 6LL * n, "external force/torque"));
+  // 1. U_nc
+  int rc = mobility_solve(ctx, FT_ext, ctx->d_Unc, st);
+  if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+  int worst = rc;
+  // 2. contacts and D
+  SPS_TRY(sps_launch_contacts(ctx, n, ctx->d_pos, ctx->d_rad));
+  ctx->c_N = n;
+  const int nc = ctx->n_c;
+  if (st) st->n_contacts = nc;
+  if (nc > gamma_cap) return sps_fail(ctx, SPS_ERR_CAPACITY, "gamma capacity smaller than the contact count");
+  SPS_TRY(ensure_bb(ctx, nc));
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
+  int bb_rc = SPS_OK;
+  if (nc > 0) {
+    // 3. q = Phi/dt + D^T U_nc; BBPGD (Algorithm 1) from gamma_0 = 0
+    SPS_TRY(sps_launch_DT(ctx, ctx->d_Unc, ctx->d_q));
+    const int tb = (nc + 255) / 256;
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_q<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_cphi, 1.0 / dt, ctx->d_q); }
+    SPS_LAUNCHED(ctx);
+    SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+    double s5[5];
+    SPS_TRY(bb_stats(ctx, ctx->d_gam, ctx->d_g, nullptr, nullptr, s5));
+    double phi = std::sqrt(s5[0]);
+    const double tol = ctx->prm.bbpgd_tol;
+    int iters = 0;
+    if (!(phi < tol)) {
+      // alpha_0 = g^T g / g^T M g
+      rc = apply_M(ctx, ctx->d_g, ctx->d_Mg, st);
+      if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+      if (rc) worst = rc;
+      double gMg = 0.0;
+      SPS_TRY(sps_dot(ctx, ctx->d_g, ctx->d_Mg, nc, &gMg));
+      double alpha = (gMg > 0) ? s5[4] / gMg : 0.0;
+      if (!(gMg > 0)) bb_rc = SPS_ERR_BREAKDOWN;
+      for (int j = 1; bb_rc == SPS_OK && j <= ctx->prm.bbpgd_max; ++j) {
+        { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+        k_bb_step<<<tb, 256, 0, ctx->stream>>>(nc, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new); }
+        SPS_LAUNCHED(ctx);
+        rc = apply_M(ctx, ctx->d_gam_new, ctx->d_Mg, st);
+        if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+        if (rc) worst = rc;
+        { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+        k_add<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_Mg, ctx->d_q, ctx->d_g_new); }
+        SPS_LAUNCHED(ctx);
+        SPS_TRY(bb_stats(ctx, ctx->d_gam_new, ctx->d_g_new, ctx->d_gam, ctx->d_g, s5));
+        std::swap(ctx->d_gam, ctx->d_gam_new);
+        std::swap(ctx->d_g, ctx->d_g_new);
+        iters = j;
+        phi = std::sqrt(s5[0]);
+        if (phi < tol) break;
+        if (ctx->prm.bb_variant == 1) {
+          if (!(s5[2] > 0)) bb_rc = SPS_ERR_BREAKDOWN;
+          else alpha = s5[1] / s5[2];
+        } else {
+          if (!(s5[2] > 0 && s5[3] > 0)) bb_rc = SPS_ERR_BREAKDOWN;
+          else alpha = s5[2] / s5[3];
+        }
+      }
+      if (bb_rc == SPS_OK && !(phi < tol)) bb_rc = SPS_ERR_NOT_CONVERGED;
+      if (iters == 0) SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
+    }
+    if (st) {
+      st->bbpgd_iters = iters;
+      st->final_phi = phi;
+    }
+    SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (st) {
+      std::vector<double> hg(nc);
+      SPS_CUDA(ctx, cudaMemcpyAsync(hg.data(), ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+      SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      int na = 0;
+      for (double v : hg) na += v > 0;
+      st->n_active = na;
+    }
+  }
+  // 4. U = U_nc + U_c, pos += U dt
+  const long long n6 = 6LL * n;
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_axpby<<<gblocks(n6), 256, 0, ctx->stream>>>(n6, 1.0, ctx->d_Unc, 1.0, ctx->d_Uc, UO); }
+  SPS_LAUNCHED(ctx);
+  if (pos_out) {
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_pos_update<<<(3 * n + 255) / 256, 256, 0, ctx->stream>>>(n, pos, UO, dt, pos_out); }
+    SPS_LAUNCHED(ctx);
+  }
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (bb_rc != SPS_OK) return sps_fail(ctx, bb_rc, bb_rc == SPS_ERR_BREAKDOWN ? "BBPGD breakdown" : "BBPGD not converged");
+  if (worst != SPS_OK) return sps_fail(ctx, worst, "a mobility solve did not converge");
+  return SPS_OK;
+}
+
+extern "C" int sps_resolve_collisions(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                                      const double* FT_ext, double dt, double* gamma, int gamma_cap,
+                                      double* UO, double* pos_out, sps_stats* st) {
+  if (!ctx || n < 1 || !pos || !radii || !FT_ext || !UO || gamma_cap < 0 || (gamma_cap > 0 && !gamma))
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "resolve_collisions: bad argument");
+  long long l0;
+  stats_begin(ctx, st, &l0);
+  const int rc = resolve(ctx, n, pos, radii, FT_ext, dt, gamma, gamma_cap, UO, pos_out, st);
+  return stats_end(ctx, st, l0, rc);
+}
+
+extern "C" int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                                           const double* FT_ext, double dt, double* gamma, int gamma_cap,
+                                           double* UO, double* pos_out, int* n_contacts_out,
+                                           sps_stats* st) {
+  if (!ctx || n < 1 || !pos || !radii || !FT_ext || !UO || gamma_cap < 0 || (gamma_cap > 0 && !gamma))
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "resolve_collisions_host: bad argument");
+  // device staging: pos, radii, FT in, UO, pos_out, gamma out
+  double *d = nullptr;
+  const size_t need = 3 * (size_t)n + n + 6 * (size_t)n + 6 * (size_t)n + 3 * (size_t)n +
+                      (size_t)std::max(gamma_cap, 1);
+  SPS_CUDA(ctx, cudaMallocAsync((void**)&d, need * sizeof(double), ctx->stream));
+  double *dp = d, *dr = dp + 3 * n, *dF = dr + n, *dU = dF + 6 * n, *dpo = dU + 6 * n, *dg = dpo + 3 * n;
+  SPS_CUDA(ctx, cudaMemcpyAsync(dp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpyAsync(dr, radii, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpyAsync(dF, FT_ext, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, ctx->stream));
+  long long l0;
+  stats_begin(ctx, st, &l0);
+  int rc = resolve(ctx, n, dp, dr, dF, dt, dg, gamma_cap, dU, pos_out ? dpo : nullptr, st);
+  if (rc == SPS_OK || rc == SPS_ERR_NOT_CONVERGED || rc == SPS_ERR_BREAKDOWN) {
+    cudaMemcpyAsync(UO, dU, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (pos_out) cudaMemcpyAsync(pos_out, dpo, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (ctx->n_c > 0 && ctx->n_c <= gamma_cap)
+      cudaMemcpyAsync(gamma, dg, sizeof(double) * ctx->n_c, cudaMemcpyDeviceToHost, ctx->stream);
+  }
+  if (n_contacts_out) *n_contacts_out = ctx->n_c;
+  cudaFreeAsync(d, ctx->stream);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess && rc == SPS_OK) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
+  return stats_end(ctx, st, l0, rc);
+}

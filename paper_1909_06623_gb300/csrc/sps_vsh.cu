@@ -1,0 +1,429 @@
+// Spectral (VSH) parts of the layer operators (Sec. 4.2, 5.4).
+//
+//  analysis   coef_s = A sigma_s: the multipliers of V, W, X in eq. rhoshexp for
+//             every sphere, one small dense product per sphere (batched).
+//  self       S_self = a_s Synth diag(multS) coef_s (eq. ssgext at r = 1);
+//             K_self = Synth diag(multK) coef_s, the on-surface principal value
+//             (exterior traction at r -> 1+ plus half the band-limited density).
+//  near       for every near pair (target sphere i, source sphere j): the exterior
+//             single layer of sphere j (eq. ssgshexp / ssgext) evaluated at the
+//             nodes of sphere i, its velocity (S) or its traction
+//             (-p I + grad u + grad u^T) n(x) (K, Sec. 4.2).
+//
+// Near field.  On the unit sphere the exterior field of eq. ssgext is, in
+// Cartesian form (Lamb's representation with decaying solid harmonics
+// phi_nm = r^{-(n+1)} Y_n^m),
+//    u = grad Phi_a + x x grad Phi_d + r^2 grad Phi_alpha + x Phi_beta,
+//    p = Phi_P,  Phi_* = sum_nm c*_nm phi_nm,
+// with a = n sV/((2n+1)(2n+3)) + n sW/(2(2n+1)), d = sX/(2n+1),
+// alpha = (2-n) sW/(2(2n-1)), beta = (n+1) sW/(2n-1), P = n sW, where
+// sV, sW, sX are the expansion multipliers of the density.  This reproduces
+// eq. ssgext's f^X, f^W and g exactly and f^V with the rho^W factor n/(4n+2)
+// (the value that satisfies the Stokes equations; the paper prints (n+1)/(4n+2)).
+// phi_nm = kappa_nm H_n^m with H_n^m = (d_x + i d_y)^m d_z^{n-m} (1/r), which obey
+//    d_z H_n^m = H_{n+1}^m,  (d_x + i d_y) H_n^m = H_{n+1}^{m+1},
+//    (d_x - i d_y) H_n^m = -H_{n+1}^{m-1},   H_n^{-m} = (-1)^m conj(H_n^m),
+// so every derivative of a potential is again a sum over H with shifted
+// coefficients, precomputed per source sphere ("fields").  Per target only the
+// recurrences
+//    H_m^m = -(2m-1) (x + i y) H_{m-1}^{m-1} / r^2,
+//    H_{n+1}^m = -((2n+1) z H_n^m + (n^2 - m^2) H_{n-1}^m) / r^2
+// and one complex multiply-add per field and (n, m >= 0) remain; nothing is
+// singular at the poles.  The traction needs only the symmetric part of
+// grad u, whose grad Phi_d term cancels, leaving 25 fields (6+6 Hessian
+// components of Phi_a, Phi_d; grad and Hessian of Phi_alpha; grad Phi_beta;
+// 2 Phi_beta - Phi_P); the velocity needs 10.
+#include "sps_internal.cuh"
+
+namespace {
+
+constexpr int kGA = 8;  // spheres per block in the batched products
+
+// coef[s][r] = sum_col A_t[col][r] sig_col(s); col = c*P + k
+__global__ void k_analysis(int N, int P, int NR, const double* __restrict__ At,
+                           const double* __restrict__ sig, double* __restrict__ coef) {
+  extern __shared__ double sm[];
+  const long long NP = (long long)N * P;
+  const int s0 = blockIdx.x * kGA;
+  const int ns = min(kGA, N - s0);
+  const int C = 3 * P;
+  for (int e = threadIdx.x; e < kGA * C; e += blockDim.x) {
+    const int g = e / C, col = e - g * C, c = col / P, k = col - c * P;
+    sm[e] = (g < ns) ? sig[c * NP + (long long)(s0 + g) * P + k] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    double acc[kGA];
+#pragma unroll
+    for (int g = 0; g < kGA; ++g) acc[g] = 0.0;
+    for (int col = 0; col < C; ++col) {
+      const double a = At[(long long)col * NR + r];
+#pragma unroll
+      for (int g = 0; g < kGA; ++g) acc[g] = fma(a, sm[g * C + col], acc[g]);
+    }
+    for (int g = 0; g < ns; ++g) coef[(long long)(s0 + g) * NR + r] = acc[g];
+  }
+}
+
+// out_col(s) = scale_s * sum_r St[r][col] coef[s][r] (+ 0.5 sig if half)
+__global__ void k_self(int N, int P, int NR, const double* __restrict__ St,
+                       const double* __restrict__ coef, const double* __restrict__ rad,
+                       int scale_by_radius, const double* __restrict__ sig, int half,
+                       double* __restrict__ out) {
+  extern __shared__ double sm[];
+  const long long NP = (long long)N * P;
+  const int s0 = blockIdx.x * kGA;
+  const int ns = min(kGA, N - s0);
+  for (int e = threadIdx.x; e < kGA * NR; e += blockDim.x) {
+    const int g = e / NR;
+    sm[e] = (g < ns) ? coef[(long long)(s0 + g) * NR + (e - g * NR)] : 0.0;
+  }
+  __syncthreads();
+  const int C = 3 * P;
+  for (int col = threadIdx.x; col < C; col += blockDim.x) {
+    double acc[kGA];
+#pragma unroll
+    for (int g = 0; g < kGA; ++g) acc[g] = 0.0;
+    for (int r = 0; r < NR; ++r) {
+      const double m = St[(long long)r * C + col];
+#pragma unroll
+      for (int g = 0; g < kGA; ++g) acc[g] = fma(m, sm[g * NR + r], acc[g]);
+    }
+    const int c = col / P, k = col - c * P;
+    for (int g = 0; g < ns; ++g) {
+      const long long idx = c * NP + (long long)(s0 + g) * P + k;
+      double v = scale_by_radius ? rad[s0 + g] * acc[g] : acc[g];
+      if (half) v += 0.5 * sig[idx];
+      out[idx] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// near-field coefficient builder
+// ---------------------------------------------------------------------------
+enum Pot { POT_A = 0, POT_D = 1, POT_AL = 2, POT_BE = 3, POT_Q = 4 };
+enum Der { D1 = 0, DX, DY, DZ, DXX, DXY, DXZ, DYY, DYZ, DZZ };
+
+struct Field {
+  unsigned char pot, der;
+};
+
+__constant__ Field c_fieldsK[sps::kFieldsK] = {
+    {POT_A, DXX},  {POT_A, DXY},  {POT_A, DXZ},  {POT_A, DYY},  {POT_A, DYZ},
+    {POT_A, DZZ},  {POT_D, DXX},  {POT_D, DXY},  {POT_D, DXZ},  {POT_D, DYY},
+    {POT_D, DYZ},  {POT_D, DZZ},  {POT_AL, DX},  {POT_AL, DY},  {POT_AL, DZ},
+    {POT_AL, DXX}, {POT_AL, DXY}, {POT_AL, DXZ}, {POT_AL, DYY}, {POT_AL, DYZ},
+    {POT_AL, DZZ}, {POT_BE, DX},  {POT_BE, DY},  {POT_BE, DZ},  {POT_Q, D1}};
+__constant__ Field c_fieldsS[sps::kFieldsS] = {
+    {POT_A, DX},  {POT_A, DY},  {POT_A, DZ},  {POT_D, DX},  {POT_D, DY},
+    {POT_D, DZ},  {POT_AL, DX}, {POT_AL, DY}, {POT_AL, DZ}, {POT_BE, D1}};
+
+// potential coefficient c_pot(n, m) for signed m (zero outside 0 <= |m| <= n <= p)
+__device__ double2 pot_coef(const double* __restrict__ cs, const double* __restrict__ kappa,
+                            int p, int NC, int pot, int n, int m) {
+  if (n < 0 || n > p || m > n || -m > n) return make_double2(0.0, 0.0);
+  const int mm = m < 0 ? -m : m;
+  const int ci = n * (n + 1) / 2 + mm;
+  const double vr = cs[(0 * NC + ci) * 2], vi = cs[(0 * NC + ci) * 2 + 1];
+  const double wr = cs[(1 * NC + ci) * 2], wi = cs[(1 * NC + ci) * 2 + 1];
+  const double xr = cs[(2 * NC + ci) * 2], xi = cs[(2 * NC + ci) * 2 + 1];
+  const double dn = n;
+  double re, im;
+  switch (pot) {
+    case POT_A: {
+      const double fv = dn / ((2 * dn + 1) * (2 * dn + 3)), fw = dn / (2 * (2 * dn + 1));
+      re = fv * vr + fw * wr;
+      im = fv * vi + fw * wi;
+      break;
+    }
+    case POT_D: {
+      const double f = 1.0 / (2 * dn + 1);
+      re = f * xr;
+      im = f * xi;
+      break;
+    }
+    case POT_AL: {
+      const double f = (2 - dn) / (2 * (2 * dn - 1));
+      re = f * wr;
+      im = f * wi;
+      break;
+    }
+    case POT_BE: {
+      const double f = (dn + 1) / (2 * dn - 1);
+      re = f * wr;
+      im = f * wi;
+      break;
+    }
+    default: {  // POT_Q: 2 beta - P
+      const double f = 2 * (dn + 1) / (2 * dn - 1) - dn;
+      re = f * wr;
+      im = f * wi;
+      break;
+    }
+  }
+  const double k = kappa[ci];
+  re *= k;
+  im *= k;
+  if (m < 0) {  // c_{n,-m} = (-1)^m conj(c_{n,m})
+    const double sg = (mm & 1) ? -1.0 : 1.0;
+    re = sg * re;
+    im = -sg * im;
+  }
+  return make_double2(re, im);
+}
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b, double sa, double sb) {
+  return make_double2(sa * a.x + sb * b.x, sa * a.y + sb * b.y);
+}
+__device__ __forceinline__ double2 mul_i(double2 a, double s) {  // s * i * a
+  return make_double2(-s * a.y, s * a.x);
+}
+
+__device__ double2 field_coef(const double* cs, const double* kappa, int p, int NC, Field f, int n,
+                              int m) {
+  const int pot = f.pot;
+  auto c = [&](int nn, int mm) { return pot_coef(cs, kappa, p, NC, pot, nn, mm); };
+  switch (f.der) {
+    case D1: return c(n, m);
+    case DX: return cadd(c(n - 1, m - 1), c(n - 1, m + 1), 0.5, -0.5);
+    case DY: return mul_i(cadd(c(n - 1, m - 1), c(n - 1, m + 1), 1.0, 1.0), -0.5);
+    case DZ: return c(n - 1, m);
+    case DXX: {
+      double2 a = cadd(c(n - 2, m - 2), c(n - 2, m + 2), 0.25, 0.25);
+      return cadd(a, c(n - 2, m), 1.0, -0.5);
+    }
+    case DYY: {
+      double2 a = cadd(c(n - 2, m - 2), c(n - 2, m + 2), -0.25, -0.25);
+      return cadd(a, c(n - 2, m), 1.0, -0.5);
+    }
+    case DXY: return mul_i(cadd(c(n - 2, m - 2), c(n - 2, m + 2), -0.25, 0.25), 1.0);
+    case DXZ: return cadd(c(n - 2, m - 1), c(n - 2, m + 1), 0.5, -0.5);
+    case DYZ: return mul_i(cadd(c(n - 2, m - 1), c(n - 2, m + 1), 1.0, 1.0), -0.5);
+    default: return c(n - 2, m);  // DZZ
+  }
+}
+
+// fcoef[s][e][f] (complex), entries e in m'-major order, n' = m'..L
+template <int F>
+__global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
+                            const double* __restrict__ coef, const double* __restrict__ kappa,
+                            double* __restrict__ fcoef) {
+  const int s = blockIdx.x;
+  const double* cs = coef + (long long)s * NR;
+  const Field* fl = (F == sps::kFieldsK) ? c_fieldsK : c_fieldsS;
+  for (int q = threadIdx.x; q < E * F; q += blockDim.x) {
+    const int e = q / F, f = q - e * F;
+    // decode entry e -> (m', n')
+    int m = 0, off = 0;
+    while (off + (L + 1 - m) <= e) {
+      off += L + 1 - m;
+      ++m;
+    }
+    const int n = m + (e - off);
+    double2 v = field_coef(cs, kappa, p, NC, fl[f], n, m);
+    const double eps = (m == 0) ? 1.0 : 2.0;
+    fcoef[((long long)s * E + e) * F * 2 + 2 * f] = eps * v.x;
+    fcoef[((long long)s * E + e) * F * 2 + 2 * f + 1] = eps * v.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// near-field evaluation: one block per target sphere, one thread per node
+// ---------------------------------------------------------------------------
+template <int F>
+__global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict__ pos,
+                            const double* __restrict__ rad, const double* __restrict__ X,
+                            const double* __restrict__ Nr, const int* __restrict__ near_ptr,
+                            const int* __restrict__ near_idx, const double* __restrict__ fcoef,
+                            double* __restrict__ out) {
+  extern __shared__ double sc[];
+  const int i = blockIdx.x;
+  const long long NP = (long long)N * P;
+  const int k = threadIdx.x;
+  const bool valid = k < P;
+  const long long g = (long long)i * P + (valid ? k : 0);
+  const double gx = X[g], gy = X[NP + g], gz = X[2 * NP + g];
+  double vx = 0, vy = 0, vz = 0;
+  if (F == sps::kFieldsK) {
+    vx = Nr[g];
+    vy = Nr[NP + g];
+    vz = Nr[2 * NP + g];
+  }
+  double ox = 0, oy = 0, oz = 0;
+  for (int q = near_ptr[i]; q < near_ptr[i + 1]; ++q) {
+    const int j = near_idx[q];
+    __syncthreads();
+    const double* src = fcoef + (long long)j * E * F * 2;
+    for (int e = threadIdx.x; e < E * F * 2; e += blockDim.x) sc[e] = src[e];
+    __syncthreads();
+    const double aj = rad[j], ia = 1.0 / aj;
+    const double x = (gx - pos[3 * j]) * ia, y = (gy - pos[3 * j + 1]) * ia,
+                 z = (gz - pos[3 * j + 2]) * ia;
+    const double r2 = x * x + y * y + z * z, ir2 = 1.0 / r2;
+    double acc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = 0.0;
+    double dre = 1.0 / sqrt(r2), dim = 0.0;  // H_m^m
+    int e = 0;
+    for (int m = 0; m <= L; ++m) {
+      if (m > 0) {
+        const double fm = -(2.0 * m - 1.0) * ir2;
+        const double re = fm * (x * dre - y * dim), im = fm * (x * dim + y * dre);
+        dre = re;
+        dim = im;
+      }
+      double hre = dre, him = dim, pre = 0.0, pim = 0.0;
+      for (int n = m; n <= L; ++n, ++e) {
+        const double* cf = sc + e * F * 2;
+#pragma unroll
+        for (int f = 0; f < F; ++f) acc[f] = fma(cf[2 * f], hre, fma(-cf[2 * f + 1], him, acc[f]));
+        const double f1 = (2.0 * n + 1.0) * z, f2 = (double)(n * n - m * m);
+        const double nre = -(f1 * hre + f2 * pre) * ir2, nim = -(f1 * him + f2 * pim) * ir2;
+        pre = hre;
+        pim = him;
+        hre = nre;
+        him = nim;
+      }
+    }
+    if (F == sps::kFieldsK) {
+      // Hessians: [xx, xy, xz, yy, yz, zz]
+      const double* HA = acc;
+      const double* HD = acc + 6;
+      const double* GL = acc + 12;
+      const double* HL = acc + 15;
+      const double* GB = acc + 21;
+      const double Qs = acc[24];
+      auto hv = [](const double* H, double a, double b, double c, double& o0, double& o1,
+                   double& o2) {
+        o0 = H[0] * a + H[1] * b + H[2] * c;
+        o1 = H[1] * a + H[3] * b + H[4] * c;
+        o2 = H[2] * a + H[4] * b + H[5] * c;
+      };
+      double t0, t1, t2, u0, u1, u2;
+      // Q v + 2 HA v
+      hv(HA, vx, vy, vz, t0, t1, t2);
+      double tx = Qs * vx + 2 * t0, ty = Qs * vy + 2 * t1, tz = Qs * vz + 2 * t2;
+      // x x (HD v) + HD (v x x)
+      hv(HD, vx, vy, vz, u0, u1, u2);
+      tx += y * u2 - z * u1;
+      ty += z * u0 - x * u2;
+      tz += x * u1 - y * u0;
+      const double cx = vy * z - vz * y, cy = vz * x - vx * z, cz = vx * y - vy * x;
+      hv(HD, cx, cy, cz, u0, u1, u2);
+      tx += u0;
+      ty += u1;
+      tz += u2;
+      // 2 (GL (x.v) + x (GL.v)) + 2 r^2 HL v + x (GB.v) + GB (x.v)
+      const double xv = x * vx + y * vy + z * vz;
+      const double glv = GL[0] * vx + GL[1] * vy + GL[2] * vz;
+      const double gbv = GB[0] * vx + GB[1] * vy + GB[2] * vz;
+      hv(HL, vx, vy, vz, u0, u1, u2);
+      tx += 2 * (GL[0] * xv + x * glv) + 2 * r2 * u0 + x * gbv + GB[0] * xv;
+      ty += 2 * (GL[1] * xv + y * glv) + 2 * r2 * u1 + y * gbv + GB[1] * xv;
+      tz += 2 * (GL[2] * xv + z * glv) + 2 * r2 * u2 + z * gbv + GB[2] * xv;
+      ox += tx;
+      oy += ty;
+      oz += tz;
+    } else {
+      const double* GA = acc;
+      const double* GD = acc + 3;
+      const double* GL = acc + 6;
+      const double Be = acc[9];
+      const double ux = GA[0] + (y * GD[2] - z * GD[1]) + r2 * GL[0] + x * Be;
+      const double uy = GA[1] + (z * GD[0] - x * GD[2]) + r2 * GL[1] + y * Be;
+      const double uz = GA[2] + (x * GD[1] - y * GD[0]) + r2 * GL[2] + z * Be;
+      ox += aj * ux;
+      oy += aj * uy;
+      oz += aj * uz;
+    }
+  }
+  if (valid) {
+    out[g] += ox;
+    out[NP + g] += oy;
+    out[2 * NP + g] += oz;
+  }
+}
+
+}  // namespace
+
+int sps_launch_analysis(sps_ctx* ctx, const double* sig) {
+  SpsPhase timer(ctx, SPS_PH_SELF);
+  const int N = ctx->N, P = ctx->T.P, NR = ctx->T.NR;
+  const size_t sm = sizeof(double) * kGA * 3 * P;
+  if (sm > 48 * 1024)
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_analysis<<<(N + kGA - 1) / kGA, 128, sm, ctx->stream>>>(N, P, NR, ctx->d_anal_t, sig, ctx->d_coef);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out) {
+  SpsPhase timer(ctx, SPS_PH_SELF);
+  const int N = ctx->N, P = ctx->T.P, NR = ctx->T.NR;
+  const size_t sm = sizeof(double) * kGA * NR;
+  if (sm > 48 * 1024)
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_self, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const bool S = (op == SPS_OP_S);
+  k_self<<<(N + kGA - 1) / kGA, 128, sm, ctx->stream>>>(N, P, NR, S ? ctx->d_synthS_t : ctx->d_synthK_t,
+                                                        ctx->d_coef, ctx->d_rad, S ? 1 : 0, sig,
+                                                        op == SPS_OP_A ? 1 : 0, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_near(sps_ctx* ctx, int op, double* out) {
+  if (ctx->n_near == 0) return SPS_OK;
+  const int N = ctx->N, P = ctx->T.P, NR = ctx->T.NR, NC = ctx->T.NC, L = ctx->T.L, E = ctx->T.E;
+  const int p = ctx->T.p;
+  const int threads = ((P + 31) / 32) * 32;
+  if (op == SPS_OP_S) {
+    constexpr int F = sps::kFieldsS;
+    {
+      SpsPhase timer(ctx, SPS_PH_SELF);
+      k_near_coef<F><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef, ctx->d_kappa,
+                                                 ctx->d_fcoef);
+      SPS_LAUNCHED(ctx);
+    }
+    SpsPhase timer(ctx, F == sps::kFieldsK ? SPS_PH_NEAR_K : SPS_PH_NEAR_S);
+    const size_t sm = sizeof(double) * E * F * 2;
+    if (sm > 48 * 1024)
+      SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_eval<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm));
+    k_near_eval<F><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
+                                                    ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
+                                                    ctx->d_fcoef, out);
+    SPS_LAUNCHED(ctx);
+  } else {
+    constexpr int F = sps::kFieldsK;
+    {
+      SpsPhase timer(ctx, SPS_PH_SELF);
+      k_near_coef<F><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef, ctx->d_kappa,
+                                                 ctx->d_fcoef);
+      SPS_LAUNCHED(ctx);
+    }
+    SpsPhase timer(ctx, F == sps::kFieldsK ? SPS_PH_NEAR_K : SPS_PH_NEAR_S);
+    const size_t sm = sizeof(double) * E * F * 2;
+    if (sm > 48 * 1024)
+      SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_eval<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm));
+    k_near_eval<F><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
+                                                    ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
+                                                    ctx->d_fcoef, out);
+    SPS_LAUNCHED(ctx);
+  }
+  return SPS_OK;
+}
+
+int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32) {
+  SPS_TRY(sps_launch_analysis(ctx, sig));
+  SPS_TRY(sps_launch_self(ctx, op, sig, out));
+  const int kop = (op == SPS_OP_S) ? SPS_OP_S : SPS_OP_K;
+  SPS_TRY(sps_launch_near(ctx, kop, out));
+  SPS_TRY(sps_launch_far(ctx, kop, sig, out, fp32));
+  if (op == SPS_OP_A) {
+    SPS_TRY(sps_launch_moments(ctx, sig, ctx->d_mom));
+    SPS_TRY(sps_launch_add_L(ctx, ctx->d_mom, out));
+  }
+  return SPS_OK;
+}

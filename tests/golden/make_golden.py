@@ -1,0 +1,110 @@
+"""Writes the oracle reference files used by the GPU parity tests.
+
+Calls only the CPU oracle (oracle/) and the seeded input generators
+(paper_1909_06623_gb300.workloads); every stored expected value is an oracle
+output.  Each file also stores its inputs, so the tests feed the CUDA path
+exactly what the oracle saw.
+
+    python tests/golden/make_golden.py            # all files
+    python tests/golden/make_golden.py cfg1       # one file
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from oracle import lcp, mobility, sph  # noqa: E402
+from oracle.layer import Suspension  # noqa: E402
+from paper_1909_06623_gb300 import workloads  # noqa: E402
+
+
+def _step(name, C, R, FT, dt, p, **kw):
+    out = lcp.resolve_collisions(C, R, FT, dt, p, **kw)
+    info = out["info"]
+    np.savez_compressed(
+        os.path.join(HERE, name + ".npz"), centers=C, radii=R, FT=FT, dt=dt, p=p,
+        params=np.array([kw.get("beta", 1.75), kw.get("delta", 0.1), kw.get("a_c_scale", 1.0),
+                         kw["gmres_tol"], kw["bbpgd_tol"]]),
+        ij=out["ij"], phi=out["phi"], normals=out["normals"], gamma=out["gamma"], q=out["q"],
+        U=out["U"], U_nc=out["U_nc"], centers_new=out["centers_new"],
+        n_active=info["n_active"], bbpgd_iters=info["iters"])
+    print(name, info)
+
+
+def cfg1():
+    """Config 1: 8 unit spheres, p = 8, one step (FP64 parity)."""
+    w = workloads.config1()
+    _step("cfg1_step", w.centers, w.radii, w.FT, w.dt, w.p, delta=0.1, gmres_tol=1e-13,
+          bbpgd_tol=1e-12)
+
+
+def active():
+    """Five spheres pushed together: several active contacts, p = 4."""
+    C = np.array([[0, 0, 0], [2.02, 0.1, 0], [1.0, 1.78, 0.05], [4.1, 0.3, 0.2],
+                  [1.1, 0.6, 1.85]])
+    R = np.array([1.0, 1.0, 0.95, 1.0, 0.8])
+    FT = np.zeros((5, 6))
+    FT[:, :3] = 20.0 * np.array([[1.0, 0.3, 0.2], [-1.0, 0.2, 0.0], [0.0, -1.0, 0.1],
+                                 [-0.9, 0, 0], [0.1, 0.0, -1.0]])
+    FT[:, 3:] = [[0.5, 0, 0], [0, 0, 0], [0, 0.3, 0], [0, 0, 0], [0, 0, -0.4]]
+    _step("active_step_p4", C, R, FT, 0.05, 4, delta=0.1, a_c_scale=1.05, gmres_tol=1e-13,
+          bbpgd_tol=1e-12)
+
+
+def cfg2_sample():
+    """Config 2 geometry (1,000 spheres, p = 6): contacts, near lists and the
+    layer operators S, K, I/2+K+L of a seeded random density on a sample of
+    target spheres (the oracle evaluates only those)."""
+    w = workloads.config2()
+    sus = Suspension(w.centers, w.radii, w.p)
+    rng = np.random.default_rng(workloads.SEED_BASE + 20)
+    sig = rng.standard_normal((sus.N * sus.P, 3))
+    nn = np.array([len(x) for x in sus.near])
+    # targets: the sphere with most near neighbours, two close-pair members, random ones
+    ij, phi, nrm = lcp.build_contacts(w.centers, w.radii, 0.1)
+    tg = [int(np.argmax(nn)), int(ij[np.argmin(phi), 0]), int(ij[np.argmin(phi), 1])]
+    tg += [int(x) for x in rng.choice(sus.N, 5, replace=False)]
+    tg = sorted(set(tg))
+    t0 = time.time()
+    S = sus.apply("S", sig, targets=tg)
+    K = sus.apply("K", sig, targets=tg)
+    A = 0.5 * sig + K + mobility.apply_L(sus, sig)
+    sl = np.concatenate([np.arange(i * sus.P, (i + 1) * sus.P) for i in tg])
+    np.savez_compressed(os.path.join(HERE, "cfg2_sample.npz"), centers=w.centers, radii=w.radii,
+                        FT=w.FT, p=w.p, sigma=sig, targets=np.array(tg), S=S[sl], K=K[sl],
+                        A=A[sl], ij=ij, phi=phi, normals=nrm,
+                        near_count=nn)
+    print("cfg2_sample", tg, f"{time.time() - t0:.1f}s")
+
+
+def tiny_layers():
+    """Small polydisperse cases (p = 3, 4, 5) with close pairs: full operators."""
+    out = {}
+    for seed, N, p in ((1, 6, 4), (2, 9, 3), (3, 5, 5)):
+        w = workloads.tiny(seed, N, p, phi=0.08, gap=5e-3)
+        sus = Suspension(w.centers, w.radii, p)
+        rng = np.random.default_rng(seed + 100)
+        sig = rng.standard_normal((sus.N * sus.P, 3))
+        out[f"c{seed}_centers"] = w.centers
+        out[f"c{seed}_radii"] = w.radii
+        out[f"c{seed}_p"] = p
+        out[f"c{seed}_sigma"] = sig
+        out[f"c{seed}_S"] = sus.apply("S", sig)
+        out[f"c{seed}_K"] = sus.apply("K", sig)
+        out[f"c{seed}_A"] = 0.5 * sig + out[f"c{seed}_K"] + mobility.apply_L(sus, sig)
+        out[f"c{seed}_FT"] = w.FT
+        out[f"c{seed}_U"] = mobility.mobility_apply(sus, w.FT, 1e-13, 300)
+    np.savez_compressed(os.path.join(HERE, "tiny_layers.npz"), **out)
+    print("tiny_layers")
+
+
+ALL = {"cfg1": cfg1, "active": active, "cfg2": cfg2_sample, "tiny": tiny_layers}
+
+if __name__ == "__main__":
+    for k in (sys.argv[1:] or ALL):
+        ALL[k]()

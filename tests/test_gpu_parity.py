@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated by the workloads this library is built for): contacts and
+indices bit-exact; FP64 path <= 1e-10 relative (max-norm over the compared
+array, relative to its largest entry); mixed path <= 1e-5 relative.  The
+oracle values come from tests/golden/*.npz (written by make_golden.py, which
+calls only oracle/) or are computed live for small cases."""
+import os
+from math import pi
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lcp, mobility, sph
+from oracle.layer import Suspension
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden")
+TOL64 = 1e-10
+TOLMX = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sps():
+    from paper_1909_06623_gb300 import build
+    build.build()
+    import paper_1909_06623_gb300 as m
+    return m
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def planes(a):  # (NP, 3) -> (3, NP) device
+    return dev(np.ascontiguousarray(np.asarray(a).T))
+
+
+def relerr(got, ref):
+    got, ref = np.asarray(got), np.asarray(ref)
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+def load(name):
+    return np.load(os.path.join(GOLD, name), allow_pickle=False)
+
+
+# ---------------------------------------------------------------------------
+# geometry
+# ---------------------------------------------------------------------------
+def test_nodes_match_oracle(sps):
+    d = load("tiny_layers.npz")
+    C, R, p = d["c1_centers"], d["c1_radii"], int(d["c1_p"])
+    ctx = sps.Context(p=p)
+    ctx.set_geometry(dev(C), dev(R))
+    X, Nr, W = ctx.nodes()
+    Xo, No, Wo = sph.sphere_nodes(C, R, p)
+    assert np.abs(X.cpu().numpy().T - Xo).max() < 1e-14 * np.abs(Xo).max() * 10
+    assert np.abs(Nr.cpu().numpy().T - No).max() < 1e-14
+    assert np.abs(W.cpu().numpy() - Wo).max() < 1e-14
+
+
+@pytest.mark.parametrize("name,acs", [("cfg2_sample.npz", 1.0), ("cfg1_step.npz", 1.0),
+                                      ("active_step_p4.npz", 1.05)])
+def test_contacts_bit_exact(sps, name, acs):
+    d = load(name)
+    ctx = sps.Context(p=4, delta=0.1, a_c_scale=acs)
+    nc = ctx.build_contacts(dev(d["centers"]), dev(d["radii"]))
+    assert nc == len(d["ij"])
+    ij, phi, nrm = ctx.get_contacts()
+    assert np.array_equal(ij.cpu().numpy(), d["ij"])
+    assert np.array_equal(phi.cpu().numpy().view(np.uint64), d["phi"].view(np.uint64))
+    assert np.array_equal(nrm.cpu().numpy().view(np.uint64), d["normals"].view(np.uint64))
+
+
+def test_contacts_large_delta_and_edges(sps):
+    rng = np.random.default_rng(5)
+    C = rng.random((300, 3)) * 12
+    R = 0.3 + 0.4 * rng.random(300)          # overlaps allowed
+    ctx = sps.Context(p=2, delta=0.7)
+    nc = ctx.build_contacts(dev(C), dev(R))
+    ij, phi, nrm = lcp.build_contacts(C, R, 0.7)
+    g_ij, g_phi, g_n = ctx.get_contacts()
+    assert nc == len(ij) and np.array_equal(g_ij.cpu().numpy(), ij)
+    assert np.array_equal(g_phi.cpu().numpy(), phi) and np.array_equal(g_n.cpu().numpy(), nrm)
+    # one sphere: empty list
+    assert ctx.build_contacts(dev(C[:1]), dev(R[:1])) == 0
+
+
+def test_D_and_DT_match_oracle(sps):
+    d = load("active_step_p4.npz")
+    C, R = d["centers"], d["radii"]
+    ctx = sps.Context(p=4, delta=0.3, a_c_scale=1.05)
+    ctx.build_contacts(dev(C), dev(R))
+    ij, phi, nrm = lcp.build_contacts(C, R, 0.3, 1.05)
+    rng = np.random.default_rng(0)
+    gam = rng.random(len(ij))
+    U = rng.standard_normal((len(R), 6))
+    FT = ctx.contact_force(dev(gam), len(R)).cpu().numpy()
+    assert relerr(FT, lcp.D_apply(len(R), ij, nrm, gam)) < 1e-15
+    rate = ctx.contact_rate(dev(U)).cpu().numpy()
+    assert relerr(rate, lcp.DT_apply(ij, nrm, U)) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# layer operators
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["c1", "c2", "c3"])
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX)])
+def test_layer_operators_tiny(sps, case, precision, tol):
+    d = load("tiny_layers.npz")
+    C, R, p, sig = d[f"{case}_centers"], d[f"{case}_radii"], int(d[f"{case}_p"]), d[f"{case}_sigma"]
+    ctx = sps.Context(p=p, precision=precision)
+    ctx.set_geometry(dev(C), dev(R))
+    s = planes(sig)
+    for op, key in ((sps.SPS_OP_S, "S"), (sps.SPS_OP_K, "K"), (sps.SPS_OP_A, "A")):
+        out = ctx.layer_apply(op, s).cpu().numpy().T
+        assert relerr(out, d[f"{case}_{key}"]) < tol, (case, key)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX)])
+def test_layer_operators_cfg2_sampled(sps, precision, tol):
+    """Full-size geometry (1,000 spheres, p = 6) in the launch shape the bench
+    uses; the oracle evaluated S, K and I/2+K+L on a sample of target spheres."""
+    d = load("cfg2_sample.npz")
+    p = int(d["p"])
+    P = (p + 1) * (2 * p + 2)
+    ctx = sps.Context(p=p, precision=precision)
+    ctx.set_geometry(dev(d["centers"]), dev(d["radii"]))
+    s = planes(d["sigma"])
+    sl = np.concatenate([np.arange(i * P, (i + 1) * P) for i in d["targets"]])
+    for op, key in ((sps.SPS_OP_S, "S"), (sps.SPS_OP_K, "K"), (sps.SPS_OP_A, "A")):
+        out = ctx.layer_apply(op, s).cpu().numpy().T[sl]
+        assert relerr(out, d[key]) < tol, key
+
+
+# ---------------------------------------------------------------------------
+# mobility
+# ---------------------------------------------------------------------------
+def test_single_sphere_drag(sps):
+    ctx = sps.Context(p=6, gmres_tol=1e-13)
+    FT = np.array([[0.3, -1.0, 0.5, 0.2, 0.7, -0.4]])
+    for a in (1.0, 0.6):
+        U = ctx.mobility_apply(dev([[1.0, 2.0, -3.0]]), dev([a]), dev(FT)).cpu().numpy()
+        assert np.abs(U[0, :3] - FT[0, :3] / (6 * pi * a)).max() < 1e-13
+        assert np.abs(U[0, 3:] - FT[0, 3:] / (8 * pi * a ** 3)).max() < 1e-13 / a ** 3
+
+
+@pytest.mark.parametrize("case", ["c1", "c2", "c3"])
+def test_mobility_tiny_fp64(sps, case):
+    d = load("tiny_layers.npz")
+    C, R, p = d[f"{case}_centers"], d[f"{case}_radii"], int(d[f"{case}_p"])
+    ctx = sps.Context(p=p, gmres_tol=1e-13, gmres_max=300)
+    U = ctx.mobility_apply(dev(C), dev(R), dev(d[f"{case}_FT"])).cpu().numpy()
+    assert relerr(U, d[f"{case}_U"]) < TOL64
+
+
+@pytest.mark.parametrize("case", ["c1", "c3"])
+def test_mobility_tiny_mixed(sps, case):
+    d = load("tiny_layers.npz")
+    C, R, p = d[f"{case}_centers"], d[f"{case}_radii"], int(d[f"{case}_p"])
+    ctx = sps.Context(p=p, gmres_tol=1e-9, gmres_max=300, precision=1)
+    U = ctx.mobility_apply(dev(C), dev(R), dev(d[f"{case}_FT"])).cpu().numpy()
+    assert relerr(U, d[f"{case}_U"]) < TOLMX
+    # refinement against the FP64 residual recovers the FP64 answer
+    ctx = sps.Context(p=p, gmres_tol=1e-7, gmres_max=300, precision=1, ir_tol=1e-13)
+    U = ctx.mobility_apply(dev(C), dev(R), dev(d[f"{case}_FT"])).cpu().numpy()
+    assert relerr(U, d[f"{case}_U"]) < 1e-10
+    assert ctx.last_stats["ir_sweeps"] >= 1
+
+
+def test_zero_force_and_nonfinite(sps):
+    ctx = sps.Context(p=4)
+    C = dev([[0, 0, 0], [3.0, 0, 0]])
+    R = dev([1.0, 1.0])
+    U = ctx.mobility_apply(C, R, dev(np.zeros((2, 6)))).cpu().numpy()
+    assert not U.any() and ctx.last_stats["gmres_iters"] == 0
+    bad = np.zeros((2, 6))
+    bad[0, 0] = np.nan
+    with pytest.raises(sps.SPSError) as e:
+        ctx.mobility_apply(C, R, dev(bad))
+    assert e.value.code == 8
+
+
+# ---------------------------------------------------------------------------
+# collision-resolved step
+# ---------------------------------------------------------------------------
+def _check_step(d, gamma, U, pos_new, tol):
+    q = d["q"]
+    gref = d["gamma"]
+    if np.abs(gref).max() > 0:
+        assert relerr(gamma, gref) < tol
+    else:
+        assert np.abs(gamma).max() <= tol * max(np.abs(q).max(), 1.0)
+    assert relerr(U, d["U"]) < tol
+    assert np.abs(pos_new - d["centers_new"]).max() < tol * np.abs(d["U"]).max() * float(d["dt"]) + 1e-15
+
+
+@pytest.mark.parametrize("name,acs", [("cfg1_step.npz", 1.0), ("active_step_p4.npz", 1.05)])
+def test_step_fp64(sps, name, acs):
+    d = load(name)
+    p = int(d["p"])
+    ctx = sps.Context(p=p, delta=0.1, a_c_scale=acs, gmres_tol=1e-13, gmres_max=300,
+                      bbpgd_tol=1e-12)
+    gam, U, pn = ctx.resolve_collisions(dev(d["centers"]), dev(d["radii"]), dev(d["FT"]),
+                                        float(d["dt"]))
+    st = ctx.last_stats
+    assert st["n_contacts"] == len(d["ij"]) and st["n_active"] == int(d["n_active"])
+    assert st["bbpgd_iters"] == int(d["bbpgd_iters"])
+    _check_step(d, gam.cpu().numpy(), U.cpu().numpy(), pn.cpu().numpy(), TOL64)
+
+
+def test_step_mixed_and_host_api(sps):
+    d = load("active_step_p4.npz")
+    p = int(d["p"])
+    # an FP32 far field puts ~1e-7 relative noise on M gamma: eps_tol 1e-6 is reachable
+    kw = dict(p=p, delta=0.1, a_c_scale=1.05, gmres_tol=1e-9, gmres_max=300, bbpgd_tol=1e-6,
+              precision=1)
+    ctx = sps.Context(**kw)
+    gam, U, pn = ctx.resolve_collisions(dev(d["centers"]), dev(d["radii"]), dev(d["FT"]),
+                                        float(d["dt"]))
+    _check_step(d, gam.cpu().numpy(), U.cpu().numpy(), pn.cpu().numpy(), TOLMX)
+    n = len(d["radii"])
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
+    g_h = torch.zeros(64, dtype=torch.float64).pin_memory()
+    U_h = torch.zeros(n, 6, dtype=torch.float64).pin_memory()
+    p_h = torch.zeros(n, 3, dtype=torch.float64).pin_memory()
+    nc = ctx.resolve_collisions_host(pin(d["centers"]), pin(d["radii"]), pin(d["FT"]),
+                                     float(d["dt"]), g_h, U_h, p_h)
+    assert nc == len(d["ij"])
+    assert np.array_equal(g_h[:nc].numpy(), gam.cpu().numpy())
+    assert np.array_equal(U_h.numpy(), U.cpu().numpy())
+
+
+def test_step_capacity_and_single_sphere(sps):
+    d = load("active_step_p4.npz")
+    ctx = sps.Context(p=4, delta=0.1, a_c_scale=1.05)
+    with pytest.raises(sps.SPSError) as e:
+        ctx.resolve_collisions(dev(d["centers"]), dev(d["radii"]), dev(d["FT"]), 0.05, gamma_cap=2)
+    assert e.value.code == 6
+    gam, U, pn = ctx.resolve_collisions(dev([[0.0, 0, 0]]), dev([1.0]),
+                                        dev([[0, 0, -1.0, 0, 0, 0]]), 0.1)
+    assert len(gam) == 0
+    assert abs(U[0, 2].item() + 1 / (6 * pi)) < 1e-12
