@@ -57,11 +57,11 @@ struct sps_ctx {
 
   // unit tables on device
   double *d_unit_nrm = nullptr, *d_unit_w = nullptr;
-  double *d_anal_t = nullptr;   // 3P x NR (column-major analysis: [col][row])
-  double *d_synthS_t = nullptr; // NR x 3P ([row r][col (c,k)]) synth * multS
-  double *d_synthK_t = nullptr; // NR x 3P synth * multK
+  double *d_anal = nullptr;     // NR x 3P row-major analysis
+  double *d_synthS = nullptr;   // 3P x NR row-major synthesis * multS
+  double *d_synthK = nullptr;   // 3P x NR row-major synthesis * multK
   double *d_kappa = nullptr;
-  float *d_anal_t32 = nullptr, *d_synthK_t32 = nullptr;
+  float *d_anal32 = nullptr, *d_synthS32 = nullptr, *d_synthK32 = nullptr;
 
   // geometry
   int N = 0, NP = 0, capN = 0;
@@ -169,9 +169,9 @@ int sps_launch_add_L(sps_ctx* ctx, const double* mom, double* out);
 int sps_launch_extract(sps_ctx* ctx, const double* mom, double* UO);
 
 // layer operators (sps_vsh.cu, sps_nbody.cu)
-int sps_launch_analysis(sps_ctx* ctx, const double* sig);
-int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out);
-int sps_launch_near(sps_ctx* ctx, int op, double* out);
+int sps_launch_analysis(sps_ctx* ctx, const double* sig, bool fp32);
+int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
+int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32);
 int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
 int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
 

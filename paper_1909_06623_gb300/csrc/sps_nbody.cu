@@ -295,7 +295,32 @@ int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp
   SPS_LAUNCHED(ctx);
   }
   const int bx = (int)((NP + kT32 * kTPT - 1) / (kT32 * kTPT));
-  int splits = (int)std::max<long long>(1, std::min<long long>(16, (8LL * 152 + bx - 1) / bx));
+  // Source splits chosen so that the grid fills whole waves of resident blocks
+  // (every block does the same work, so a partial last wave idles SMs).
+  static int resident = 0;
+  if (!resident) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far32<SPS_OP_K>, kT32, 0);
+    resident = std::max(1, per_sm) * std::max(1, sms);
+  }
+  int splits = 1;
+  double best = 0.0;
+  for (int s = 1; s <= 32; ++s) {
+    long long per_s = (NP + s - 1) / s;
+    per_s = ((per_s + kTS32 - 1) / kTS32) * kTS32;
+    const int s_eff = (int)((NP + per_s - 1) / per_s);
+    const long long blocks = (long long)bx * s_eff;
+    const long long waves = (blocks + resident - 1) / resident;
+    const double eff = (double)blocks / (double)(waves * resident);
+    // prefer fewer splits unless a larger count fills the machine clearly better
+    if (eff > best + 0.02) {
+      best = eff;
+      splits = s_eff;
+    }
+    if (blocks >= 4LL * resident) break;
+  }
   long long per = (NP + splits - 1) / splits;
   per = ((per + kTS32 - 1) / kTS32) * kTS32;
   splits = (int)((NP + per - 1) / per);

@@ -387,17 +387,19 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
   sps::build_tables(prm->p, ctx->T);
   const sps::Tables& T = ctx->T;
   const int P = T.P, NR = T.NR;
-  std::vector<double> anal_t((size_t)3 * P * NR), sS((size_t)NR * 3 * P), sK((size_t)NR * 3 * P);
-  for (int r = 0; r < NR; ++r)
-    for (int c = 0; c < 3 * P; ++c) {
-      anal_t[(size_t)c * NR + r] = T.anal[(size_t)r * 3 * P + c];
-      sS[(size_t)r * 3 * P + c] = T.synth[(size_t)c * NR + r] * T.multS[r];
-      sK[(size_t)r * 3 * P + c] = T.synth[(size_t)c * NR + r] * T.multK[r];
+  std::vector<double> sS((size_t)3 * P * NR), sK((size_t)3 * P * NR);
+  for (int c = 0; c < 3 * P; ++c)
+    for (int r = 0; r < NR; ++r) {
+      sS[(size_t)c * NR + r] = T.synth[(size_t)c * NR + r] * T.multS[r];
+      sK[(size_t)c * NR + r] = T.synth[(size_t)c * NR + r] * T.multK[r];
     }
+  auto f32 = [](const std::vector<double>& a) { return std::vector<float>(a.begin(), a.end()); };
   int rc = SPS_OK;
   if ((rc = upload(ctx, &ctx->d_unit_nrm, T.unit_nrm)) || (rc = upload(ctx, &ctx->d_unit_w, T.unit_w)) ||
-      (rc = upload(ctx, &ctx->d_anal_t, anal_t)) || (rc = upload(ctx, &ctx->d_synthS_t, sS)) ||
-      (rc = upload(ctx, &ctx->d_synthK_t, sK)) || (rc = upload(ctx, &ctx->d_kappa, T.kappa))) {
+      (rc = upload(ctx, &ctx->d_anal, T.anal)) || (rc = upload(ctx, &ctx->d_synthS, sS)) ||
+      (rc = upload(ctx, &ctx->d_synthK, sK)) || (rc = upload(ctx, &ctx->d_kappa, T.kappa)) ||
+      (rc = upload(ctx, &ctx->d_anal32, f32(T.anal))) || (rc = upload(ctx, &ctx->d_synthS32, f32(sS))) ||
+      (rc = upload(ctx, &ctx->d_synthK32, f32(sK)))) {
     sps_destroy(ctx);
     return rc;
   }
@@ -412,8 +414,8 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
 
 extern "C" int sps_destroy(sps_ctx* ctx) {
   if (!ctx) return SPS_OK;
-  void* bufs[] = {ctx->d_unit_nrm, ctx->d_unit_w, ctx->d_anal_t, ctx->d_synthS_t, ctx->d_synthK_t,
-                  ctx->d_kappa, ctx->d_anal_t32, ctx->d_synthK_t32, ctx->d_pos, ctx->d_rad,
+  void* bufs[] = {ctx->d_unit_nrm, ctx->d_unit_w, ctx->d_anal, ctx->d_synthS, ctx->d_synthK,
+                  ctx->d_kappa, ctx->d_anal32, ctx->d_synthS32, ctx->d_synthK32, ctx->d_pos, ctx->d_rad,
                   ctx->d_X, ctx->d_Nrm, ctx->d_W, ctx->d_X32, ctx->d_N32, ctx->d_W32,
                   ctx->d_near_ptr, ctx->d_near_idx, ctx->d_coef, ctx->d_fcoef, ctx->d_mom,
                   ctx->d_tmp3, ctx->d_sig32, ctx->d_part, ctx->d_Q, ctx->d_w, ctx->d_h, ctx->d_red,

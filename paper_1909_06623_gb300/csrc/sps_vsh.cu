@@ -37,66 +37,73 @@
 
 namespace {
 
-constexpr int kGA = 8;  // spheres per block in the batched products
+// Batched small products out(s, r) = sum_c M[r][c] in(s, c), one sphere s per
+// row of a GEMM [N x C] x [C x R]: 32 spheres x 32 rows per block, the inner
+// dimension staged through shared memory in chunks of 32.
+//   MODE_ANALYSIS: in = density planes (c = comp*P + node), out = coef rows.
+//   MODE_SYNTH:    in = coef rows (c = VSH row), out = field planes,
+//                  times a_s if scale_by_radius, plus sig/2 if half.
+enum { MODE_ANALYSIS = 0, MODE_SYNTH = 1 };
+constexpr int kTB = 32;
 
-// coef[s][r] = sum_col A_t[col][r] sig_col(s); col = c*P + k
-__global__ void k_analysis(int N, int P, int NR, const double* __restrict__ At,
-                           const double* __restrict__ sig, double* __restrict__ coef) {
-  extern __shared__ double sm[];
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_batched(int N, int P, int R, int C, const T* __restrict__ M,
+                                                 const double* __restrict__ in,
+                                                 double* __restrict__ out,
+                                                 const double* __restrict__ rad,
+                                                 int scale_by_radius,
+                                                 const double* __restrict__ sig, int half) {
+  __shared__ T sIn[kTB][kTB + 1];
+  __shared__ T sM[kTB][kTB + 1];
   const long long NP = (long long)N * P;
-  const int s0 = blockIdx.x * kGA;
-  const int ns = min(kGA, N - s0);
-  const int C = 3 * P;
-  for (int e = threadIdx.x; e < kGA * C; e += blockDim.x) {
-    const int g = e / C, col = e - g * C, c = col / P, k = col - c * P;
-    sm[e] = (g < ns) ? sig[c * NP + (long long)(s0 + g) * P + k] : 0.0;
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
-    double acc[kGA];
-#pragma unroll
-    for (int g = 0; g < kGA; ++g) acc[g] = 0.0;
-    for (int col = 0; col < C; ++col) {
-      const double a = At[(long long)col * NR + r];
-#pragma unroll
-      for (int g = 0; g < kGA; ++g) acc[g] = fma(a, sm[g * C + col], acc[g]);
+  const int s0 = blockIdx.x * kTB, r0 = blockIdx.y * kTB;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+  for (int c0 = 0; c0 < C; c0 += kTB) {
+    for (int e = threadIdx.x; e < kTB * kTB; e += 256) {
+      const int a = e / kTB, b = e - a * kTB;
+      const int s = s0 + a, c = c0 + b, r = r0 + a;
+      T v = T(0);
+      if (s < N && c < C) {
+        if (MODE == MODE_ANALYSIS) {
+          const int comp = c / P, k = c - comp * P;
+          v = (T)in[comp * NP + (long long)s * P + k];
+        } else {
+          v = (T)in[(long long)s * C + c];
+        }
+      }
+      sIn[a][b] = v;
+      sM[a][b] = (r < R && c < C) ? M[(long long)r * C + c] : T(0);
     }
-    for (int g = 0; g < ns; ++g) coef[(long long)(s0 + g) * NR + r] = acc[g];
-  }
-}
-
-// out_col(s) = scale_s * sum_r St[r][col] coef[s][r] (+ 0.5 sig if half)
-__global__ void k_self(int N, int P, int NR, const double* __restrict__ St,
-                       const double* __restrict__ coef, const double* __restrict__ rad,
-                       int scale_by_radius, const double* __restrict__ sig, int half,
-                       double* __restrict__ out) {
-  extern __shared__ double sm[];
-  const long long NP = (long long)N * P;
-  const int s0 = blockIdx.x * kGA;
-  const int ns = min(kGA, N - s0);
-  for (int e = threadIdx.x; e < kGA * NR; e += blockDim.x) {
-    const int g = e / NR;
-    sm[e] = (g < ns) ? coef[(long long)(s0 + g) * NR + (e - g * NR)] : 0.0;
-  }
-  __syncthreads();
-  const int C = 3 * P;
-  for (int col = threadIdx.x; col < C; col += blockDim.x) {
-    double acc[kGA];
-#pragma unroll
-    for (int g = 0; g < kGA; ++g) acc[g] = 0.0;
-    for (int r = 0; r < NR; ++r) {
-      const double m = St[(long long)r * C + col];
-#pragma unroll
-      for (int g = 0; g < kGA; ++g) acc[g] = fma(m, sm[g * NR + r], acc[g]);
+    __syncthreads();
+#pragma unroll 8
+    for (int b = 0; b < kTB; ++b) {
+      const T i0 = sIn[2 * ty][b], i1 = sIn[2 * ty + 1][b];
+      const T m0 = sM[2 * tx][b], m1 = sM[2 * tx + 1][b];
+      acc[0][0] = fma(i0, m0, acc[0][0]);
+      acc[0][1] = fma(i0, m1, acc[0][1]);
+      acc[1][0] = fma(i1, m0, acc[1][0]);
+      acc[1][1] = fma(i1, m1, acc[1][1]);
     }
-    const int c = col / P, k = col - c * P;
-    for (int g = 0; g < ns; ++g) {
-      const long long idx = c * NP + (long long)(s0 + g) * P + k;
-      double v = scale_by_radius ? rad[s0 + g] * acc[g] : acc[g];
-      if (half) v += 0.5 * sig[idx];
-      out[idx] = v;
-    }
+    __syncthreads();
   }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int s = s0 + 2 * ty + u, r = r0 + 2 * tx + v;
+      if (s >= N || r >= R) continue;
+      if (MODE == MODE_ANALYSIS) {
+        out[(long long)s * R + r] = (double)acc[u][v];
+      } else {
+        const int comp = r / P, k = r - comp * P;
+        const long long idx = comp * NP + (long long)s * P + k;
+        double val = (double)acc[u][v];
+        if (scale_by_radius) val *= rad[s];
+        if (half) val += 0.5 * sig[idx];
+        out[idx] = val;
+      }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -231,55 +238,56 @@ __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
 // ---------------------------------------------------------------------------
 // near-field evaluation: one block per target sphere, one thread per node
 // ---------------------------------------------------------------------------
-template <int F>
+template <int F, typename T>
 __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict__ pos,
                             const double* __restrict__ rad, const double* __restrict__ X,
                             const double* __restrict__ Nr, const int* __restrict__ near_ptr,
                             const int* __restrict__ near_idx, const double* __restrict__ fcoef,
                             double* __restrict__ out) {
-  extern __shared__ double sc[];
+  extern __shared__ __align__(16) unsigned char sraw[];
+  T* sc = reinterpret_cast<T*>(sraw);
   const int i = blockIdx.x;
   const long long NP = (long long)N * P;
   const int k = threadIdx.x;
   const bool valid = k < P;
   const long long g = (long long)i * P + (valid ? k : 0);
   const double gx = X[g], gy = X[NP + g], gz = X[2 * NP + g];
-  double vx = 0, vy = 0, vz = 0;
+  T vx = 0, vy = 0, vz = 0;
   if (F == sps::kFieldsK) {
-    vx = Nr[g];
-    vy = Nr[NP + g];
-    vz = Nr[2 * NP + g];
+    vx = (T)Nr[g];
+    vy = (T)Nr[NP + g];
+    vz = (T)Nr[2 * NP + g];
   }
   double ox = 0, oy = 0, oz = 0;
   for (int q = near_ptr[i]; q < near_ptr[i + 1]; ++q) {
     const int j = near_idx[q];
     __syncthreads();
     const double* src = fcoef + (long long)j * E * F * 2;
-    for (int e = threadIdx.x; e < E * F * 2; e += blockDim.x) sc[e] = src[e];
+    for (int e = threadIdx.x; e < E * F * 2; e += blockDim.x) sc[e] = (T)src[e];
     __syncthreads();
     const double aj = rad[j], ia = 1.0 / aj;
-    const double x = (gx - pos[3 * j]) * ia, y = (gy - pos[3 * j + 1]) * ia,
-                 z = (gz - pos[3 * j + 2]) * ia;
-    const double r2 = x * x + y * y + z * z, ir2 = 1.0 / r2;
-    double acc[F];
+    const T x = (T)((gx - pos[3 * j]) * ia), y = (T)((gy - pos[3 * j + 1]) * ia),
+            z = (T)((gz - pos[3 * j + 2]) * ia);
+    const T r2 = x * x + y * y + z * z, ir2 = T(1) / r2;
+    T acc[F];
 #pragma unroll
-    for (int f = 0; f < F; ++f) acc[f] = 0.0;
-    double dre = 1.0 / sqrt(r2), dim = 0.0;  // H_m^m
+    for (int f = 0; f < F; ++f) acc[f] = T(0);
+    T dre = T(1) / sqrt(r2), dim = T(0);  // H_m^m
     int e = 0;
     for (int m = 0; m <= L; ++m) {
       if (m > 0) {
-        const double fm = -(2.0 * m - 1.0) * ir2;
-        const double re = fm * (x * dre - y * dim), im = fm * (x * dim + y * dre);
+        const T fm = -(T)(2 * m - 1) * ir2;
+        const T re = fm * (x * dre - y * dim), im = fm * (x * dim + y * dre);
         dre = re;
         dim = im;
       }
-      double hre = dre, him = dim, pre = 0.0, pim = 0.0;
+      T hre = dre, him = dim, pre = T(0), pim = T(0);
       for (int n = m; n <= L; ++n, ++e) {
-        const double* cf = sc + e * F * 2;
+        const T* cf = sc + e * F * 2;
 #pragma unroll
         for (int f = 0; f < F; ++f) acc[f] = fma(cf[2 * f], hre, fma(-cf[2 * f + 1], him, acc[f]));
-        const double f1 = (2.0 * n + 1.0) * z, f2 = (double)(n * n - m * m);
-        const double nre = -(f1 * hre + f2 * pre) * ir2, nim = -(f1 * him + f2 * pim) * ir2;
+        const T f1 = (T)(2 * n + 1) * z, f2 = (T)(n * n - m * m);
+        const T nre = -(f1 * hre + f2 * pre) * ir2, nim = -(f1 * him + f2 * pim) * ir2;
         pre = hre;
         pim = him;
         hre = nre;
@@ -288,54 +296,53 @@ __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict
     }
     if (F == sps::kFieldsK) {
       // Hessians: [xx, xy, xz, yy, yz, zz]
-      const double* HA = acc;
-      const double* HD = acc + 6;
-      const double* GL = acc + 12;
-      const double* HL = acc + 15;
-      const double* GB = acc + 21;
-      const double Qs = acc[24];
-      auto hv = [](const double* H, double a, double b, double c, double& o0, double& o1,
-                   double& o2) {
+      const T* HA = acc;
+      const T* HD = acc + 6;
+      const T* GL = acc + 12;
+      const T* HL = acc + 15;
+      const T* GB = acc + 21;
+      const T Qs = acc[24];
+      auto hv = [](const T* H, T a, T b, T c, T& o0, T& o1, T& o2) {
         o0 = H[0] * a + H[1] * b + H[2] * c;
         o1 = H[1] * a + H[3] * b + H[4] * c;
         o2 = H[2] * a + H[4] * b + H[5] * c;
       };
-      double t0, t1, t2, u0, u1, u2;
+      T t0, t1, t2, u0, u1, u2;
       // Q v + 2 HA v
       hv(HA, vx, vy, vz, t0, t1, t2);
-      double tx = Qs * vx + 2 * t0, ty = Qs * vy + 2 * t1, tz = Qs * vz + 2 * t2;
+      T tx = Qs * vx + 2 * t0, ty = Qs * vy + 2 * t1, tz = Qs * vz + 2 * t2;
       // x x (HD v) + HD (v x x)
       hv(HD, vx, vy, vz, u0, u1, u2);
       tx += y * u2 - z * u1;
       ty += z * u0 - x * u2;
       tz += x * u1 - y * u0;
-      const double cx = vy * z - vz * y, cy = vz * x - vx * z, cz = vx * y - vy * x;
+      const T cx = vy * z - vz * y, cy = vz * x - vx * z, cz = vx * y - vy * x;
       hv(HD, cx, cy, cz, u0, u1, u2);
       tx += u0;
       ty += u1;
       tz += u2;
       // 2 (GL (x.v) + x (GL.v)) + 2 r^2 HL v + x (GB.v) + GB (x.v)
-      const double xv = x * vx + y * vy + z * vz;
-      const double glv = GL[0] * vx + GL[1] * vy + GL[2] * vz;
-      const double gbv = GB[0] * vx + GB[1] * vy + GB[2] * vz;
+      const T xv = x * vx + y * vy + z * vz;
+      const T glv = GL[0] * vx + GL[1] * vy + GL[2] * vz;
+      const T gbv = GB[0] * vx + GB[1] * vy + GB[2] * vz;
       hv(HL, vx, vy, vz, u0, u1, u2);
       tx += 2 * (GL[0] * xv + x * glv) + 2 * r2 * u0 + x * gbv + GB[0] * xv;
       ty += 2 * (GL[1] * xv + y * glv) + 2 * r2 * u1 + y * gbv + GB[1] * xv;
       tz += 2 * (GL[2] * xv + z * glv) + 2 * r2 * u2 + z * gbv + GB[2] * xv;
-      ox += tx;
-      oy += ty;
-      oz += tz;
+      ox += (double)tx;
+      oy += (double)ty;
+      oz += (double)tz;
     } else {
-      const double* GA = acc;
-      const double* GD = acc + 3;
-      const double* GL = acc + 6;
-      const double Be = acc[9];
-      const double ux = GA[0] + (y * GD[2] - z * GD[1]) + r2 * GL[0] + x * Be;
-      const double uy = GA[1] + (z * GD[0] - x * GD[2]) + r2 * GL[1] + y * Be;
-      const double uz = GA[2] + (x * GD[1] - y * GD[0]) + r2 * GL[2] + z * Be;
-      ox += aj * ux;
-      oy += aj * uy;
-      oz += aj * uz;
+      const T* GA = acc;
+      const T* GD = acc + 3;
+      const T* GL = acc + 6;
+      const T Be = acc[9];
+      const T ux = GA[0] + (y * GD[2] - z * GD[1]) + r2 * GL[0] + x * Be;
+      const T uy = GA[1] + (z * GD[0] - x * GD[2]) + r2 * GL[1] + y * Be;
+      const T uz = GA[2] + (x * GD[1] - y * GD[0]) + r2 * GL[2] + z * Be;
+      ox += aj * (double)ux;
+      oy += aj * (double)uy;
+      oz += aj * (double)uz;
     }
   }
   if (valid) {
@@ -345,81 +352,82 @@ __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict
   }
 }
 
+template <int F, typename T>
+int launch_near_eval(sps_ctx* ctx, double* out) {
+  const int N = ctx->N, P = ctx->T.P, L = ctx->T.L, E = ctx->T.E;
+  const int threads = ((P + 31) / 32) * 32;
+  const size_t sm = sizeof(T) * E * F * 2;
+  if (sm > 48 * 1024)
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_eval<F, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm));
+  k_near_eval<F, T><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
+                                                      ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
+                                                      ctx->d_fcoef, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
 }  // namespace
 
-int sps_launch_analysis(sps_ctx* ctx, const double* sig) {
+int sps_launch_analysis(sps_ctx* ctx, const double* sig, bool fp32) {
   SpsPhase timer(ctx, SPS_PH_SELF);
   const int N = ctx->N, P = ctx->T.P, NR = ctx->T.NR;
-  const size_t sm = sizeof(double) * kGA * 3 * P;
-  if (sm > 48 * 1024)
-    SPS_CUDA(ctx, cudaFuncSetAttribute(k_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_analysis<<<(N + kGA - 1) / kGA, 128, sm, ctx->stream>>>(N, P, NR, ctx->d_anal_t, sig, ctx->d_coef);
+  dim3 grid((N + kTB - 1) / kTB, (NR + kTB - 1) / kTB);
+  if (fp32)
+    k_batched<float, MODE_ANALYSIS><<<grid, 256, 0, ctx->stream>>>(N, P, NR, 3 * P, ctx->d_anal32, sig,
+                                                                    ctx->d_coef, nullptr, 0, nullptr, 0);
+  else
+    k_batched<double, MODE_ANALYSIS><<<grid, 256, 0, ctx->stream>>>(N, P, NR, 3 * P, ctx->d_anal, sig,
+                                                                     ctx->d_coef, nullptr, 0, nullptr, 0);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
 
-int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out) {
+int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32) {
   SpsPhase timer(ctx, SPS_PH_SELF);
   const int N = ctx->N, P = ctx->T.P, NR = ctx->T.NR;
-  const size_t sm = sizeof(double) * kGA * NR;
-  if (sm > 48 * 1024)
-    SPS_CUDA(ctx, cudaFuncSetAttribute(k_self, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   const bool S = (op == SPS_OP_S);
-  k_self<<<(N + kGA - 1) / kGA, 128, sm, ctx->stream>>>(N, P, NR, S ? ctx->d_synthS_t : ctx->d_synthK_t,
-                                                        ctx->d_coef, ctx->d_rad, S ? 1 : 0, sig,
-                                                        op == SPS_OP_A ? 1 : 0, out);
+  dim3 grid((N + kTB - 1) / kTB, (3 * P + kTB - 1) / kTB);
+  const int half = (op == SPS_OP_A) ? 1 : 0;
+  if (fp32)
+    k_batched<float, MODE_SYNTH><<<grid, 256, 0, ctx->stream>>>(
+        N, P, 3 * P, NR, S ? ctx->d_synthS32 : ctx->d_synthK32, ctx->d_coef, out, ctx->d_rad, S ? 1 : 0,
+        sig, half);
+  else
+    k_batched<double, MODE_SYNTH><<<grid, 256, 0, ctx->stream>>>(
+        N, P, 3 * P, NR, S ? ctx->d_synthS : ctx->d_synthK, ctx->d_coef, out, ctx->d_rad, S ? 1 : 0,
+        sig, half);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
 
-int sps_launch_near(sps_ctx* ctx, int op, double* out) {
+int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
   if (ctx->n_near == 0) return SPS_OK;
-  const int N = ctx->N, P = ctx->T.P, NR = ctx->T.NR, NC = ctx->T.NC, L = ctx->T.L, E = ctx->T.E;
+  const int N = ctx->N, NR = ctx->T.NR, NC = ctx->T.NC, L = ctx->T.L, E = ctx->T.E;
   const int p = ctx->T.p;
-  const int threads = ((P + 31) / 32) * 32;
-  if (op == SPS_OP_S) {
-    constexpr int F = sps::kFieldsS;
-    {
-      SpsPhase timer(ctx, SPS_PH_SELF);
-      k_near_coef<F><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef, ctx->d_kappa,
-                                                 ctx->d_fcoef);
-      SPS_LAUNCHED(ctx);
-    }
-    SpsPhase timer(ctx, F == sps::kFieldsK ? SPS_PH_NEAR_K : SPS_PH_NEAR_S);
-    const size_t sm = sizeof(double) * E * F * 2;
-    if (sm > 48 * 1024)
-      SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_eval<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm));
-    k_near_eval<F><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
-                                                    ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
-                                                    ctx->d_fcoef, out);
-    SPS_LAUNCHED(ctx);
-  } else {
-    constexpr int F = sps::kFieldsK;
-    {
-      SpsPhase timer(ctx, SPS_PH_SELF);
-      k_near_coef<F><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef, ctx->d_kappa,
-                                                 ctx->d_fcoef);
-      SPS_LAUNCHED(ctx);
-    }
-    SpsPhase timer(ctx, F == sps::kFieldsK ? SPS_PH_NEAR_K : SPS_PH_NEAR_S);
-    const size_t sm = sizeof(double) * E * F * 2;
-    if (sm > 48 * 1024)
-      SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_eval<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm));
-    k_near_eval<F><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
-                                                    ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
-                                                    ctx->d_fcoef, out);
+  const bool S = (op == SPS_OP_S);
+  {
+    SpsPhase timer(ctx, SPS_PH_SELF);
+    if (S)
+      k_near_coef<sps::kFieldsS><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef,
+                                                             ctx->d_kappa, ctx->d_fcoef);
+    else
+      k_near_coef<sps::kFieldsK><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef,
+                                                             ctx->d_kappa, ctx->d_fcoef);
     SPS_LAUNCHED(ctx);
   }
-  return SPS_OK;
+  SpsPhase timer(ctx, S ? SPS_PH_NEAR_S : SPS_PH_NEAR_K);
+  if (S) return fp32 ? launch_near_eval<sps::kFieldsS, float>(ctx, out)
+                     : launch_near_eval<sps::kFieldsS, double>(ctx, out);
+  return fp32 ? launch_near_eval<sps::kFieldsK, float>(ctx, out)
+              : launch_near_eval<sps::kFieldsK, double>(ctx, out);
 }
 
 int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32) {
-  SPS_TRY(sps_launch_analysis(ctx, sig));
-  SPS_TRY(sps_launch_self(ctx, op, sig, out));
+  SPS_TRY(sps_launch_analysis(ctx, sig, fp32));
+  SPS_TRY(sps_launch_self(ctx, op, sig, out, fp32));
   const int kop = (op == SPS_OP_S) ? SPS_OP_S : SPS_OP_K;
-  SPS_TRY(sps_launch_near(ctx, kop, out));
+  SPS_TRY(sps_launch_near(ctx, kop, out, fp32));
   SPS_TRY(sps_launch_far(ctx, kop, sig, out, fp32));
   if (op == SPS_OP_A) {
     SPS_TRY(sps_launch_moments(ctx, sig, ctx->d_mom));
