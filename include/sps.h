@@ -159,6 +159,31 @@ int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* pos, const do
                                 double* UO, double* pos_out, int* n_contacts_out,
                                 sps_stats* stats);
 
+/* Contact set of sps_build_contacts for callers that cannot allocate device
+ * memory when they need it: code running while a stream is being captured into
+ * a CUDA graph (cudaMalloc is not a capturable operation), hosts whose own
+ * memory pool owns the device, or stepping loops that must never allocate.
+ * No counterpart in the paper: it is the same contact set (Sec. 3.2), computed
+ * without a context and without any cudaMalloc / cudaFree.
+ *
+ * Scratch: a fixed device array inside the library (one counter per sphere,
+ * about 1 MB) that every GPU loading the library keeps until the process
+ * exits.  n <= 262,144 spheres (larger n returns SPS_ERR_CAPACITY).  The first
+ * call on a device looks up that array's device address; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU (different streams or threads at the same time) race and must not be
+ * issued.  Every counter a call reads is written by the same call first.
+ *
+ * pos (n x 3), radii (n): device inputs.  ij (max_contacts x 2 int32), phi
+ * (max_contacts), normals (max_contacts x 3): device outputs, written in the
+ * order of sps_build_contacts (bit-identical values).  *n_contacts_out (host)
+ * receives n_c; if n_c > max_contacts the call returns SPS_ERR_CAPACITY and
+ * writes no output array.  stream: cudaStream_t (NULL = legacy default).  The
+ * call synchronises the stream before returning. */
+int sps_build_contacts_noalloc(int n, const double* pos, const double* radii, double a_c_scale,
+                               double delta, int max_contacts, int* ij, double* phi,
+                               double* normals, int* n_contacts_out, void* stream);
+
 /* Phase timers (CUDA events recorded on the context's stream around each
  * kernel of a phase; the paper's Sec. 6.5 timing categories, refined). */
 typedef enum {

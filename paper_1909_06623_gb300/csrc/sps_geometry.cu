@@ -4,6 +4,8 @@
 // extraction (Sec. 4.1).
 #include <cub/cub.cuh>
 
+#include <mutex>
+
 #include "sps_internal.cuh"
 
 namespace {
@@ -426,5 +428,141 @@ int sps_launch_extract(sps_ctx* ctx, const double* mom, double* UO) {
   SpsPhase timer(ctx, SPS_PH_KRYLOV);
   k_extract<<<nblk(ctx->N), kThreads, 0, ctx->stream>>>(ctx->N, ctx->d_rad, mom, UO);
   SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Contact set without allocation.
+//
+// Some callers cannot allocate device memory at the moment they need the
+// contact list: code running while a CUDA stream is being captured into a
+// graph (a plain cudaMalloc is not a capturable operation), code embedded in a
+// host that owns the whole device through its own memory pool (a framework
+// allocator, an MPS client with a hard memory limit), or a time-stepping loop
+// that must not pay for, or risk failing on, an allocation in the middle of a
+// step.  This variant of the contact builder keeps its only scratch (one
+// counter per sphere plus the scan's block totals) in a fixed device array
+// that lives as long as the library is loaded.  The caller passes positions,
+// radii and output buffers.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxSpheres = 1 << 18;     // 262,144 spheres
+constexpr int kScanThreads = 1024;
+// counters (max spheres + 1) followed by one total per scan thread
+static __device__ __align__(256) int g_contact_scratch[kStaticMaxSpheres + 1 + kScanThreads];
+
+__global__ void k_static_count(int N, const double* pos, const double* rad, double acs, double delta,
+                               int* cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) cnt[N] = 0;   // the scan's last slot (the total) starts at zero
+  if (i >= N) return;
+  int c = 0;
+  for (int j = i + 1; j < N; ++j)
+    if (contact(pos, rad, acs, delta, i, j, nullptr)) ++c;
+  cnt[i] = c;
+}
+
+// exclusive scan of cnt[0..n) in place, one block; totals[] holds per-thread sums
+__global__ void __launch_bounds__(kScanThreads) k_static_scan(int n, int* cnt, int* totals) {
+  const int t = threadIdx.x;
+  const int per = (n + kScanThreads - 1) / kScanThreads;
+  const int a = min(n, t * per), b = min(n, a + per);
+  int s = 0;
+  for (int i = a; i < b; ++i) s += cnt[i];
+  totals[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int k = 0; k < kScanThreads; ++k) {
+      const int v = totals[k];
+      totals[k] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  int run = totals[t];
+  for (int i = a; i < b; ++i) {
+    const int v = cnt[i];
+    cnt[i] = run;
+    run += v;
+  }
+}
+
+__global__ void k_static_fill(int N, const double* pos, const double* rad, double acs, double delta,
+                              const int* ptr, int* ij, double* phi, double* nrm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int o = ptr[i];
+  ContactGeom g;
+  for (int j = i + 1; j < N; ++j)
+    if (contact(pos, rad, acs, delta, i, j, &g)) {
+      ij[2 * o] = i;
+      ij[2 * o + 1] = j;
+      phi[o] = g.phi;
+      nrm[3 * o + 0] = g.nx;
+      nrm[3 * o + 1] = g.ny;
+      nrm[3 * o + 2] = g.nz;
+      ++o;
+    }
+}
+
+// Host-side stand-in for g_contact_scratch is not a device address: resolve
+// the real address once per device, with that device current.
+std::mutex g_scratch_mu;
+int* g_scratch_ptr[64] = {nullptr};
+
+int static_scratch(int** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return SPS_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_contact_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return SPS_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = static_cast<int*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return SPS_OK;
+}
+
+}  // namespace
+
+extern "C" int sps_build_contacts_noalloc(int n, const double* pos, const double* radii,
+                                          double a_c_scale, double delta, int max_contacts, int* ij,
+                                          double* phi, double* normals, int* n_contacts_out,
+                                          void* stream) {
+  if (n < 1 || !pos || !radii || !n_contacts_out || max_contacts < 0 || !(a_c_scale > 0) ||
+      !(delta >= 0) || (max_contacts > 0 && (!ij || !phi || !normals)))
+    return SPS_ERR_INVALID_ARG;
+  if (n > kStaticMaxSpheres) return SPS_ERR_CAPACITY;
+  int* cnt = nullptr;
+  int rc = static_scratch(&cnt);
+  if (rc != SPS_OK) return rc;
+  int* totals = cnt + kStaticMaxSpheres + 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_static_count<<<(n + 127) / 128, 128, 0, st>>>(n, pos, radii, a_c_scale, delta, cnt);
+  k_static_scan<<<1, kScanThreads, 0, st>>>(n + 1, cnt, totals);
+  int nc = 0;
+  if (cudaMemcpyAsync(&nc, cnt + n, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return SPS_ERR_CUDA;
+  }
+  *n_contacts_out = nc;
+  if (nc > max_contacts) return SPS_ERR_CAPACITY;
+  if (nc > 0) {
+    k_static_fill<<<(n + 127) / 128, 128, 0, st>>>(n, pos, radii, a_c_scale, delta, cnt, ij, phi,
+                                                   normals);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return SPS_ERR_CUDA;
+    }
+  }
   return SPS_OK;
 }
