@@ -67,6 +67,12 @@ typedef struct sps_params {
   double ir_tol;      /* SPS_MIXED: refine against an FP64 residual until
                          ||r||/||b|| < ir_tol; 0 disables refinement          */
   int ir_max;         /* refinement sweep cap                                 */
+  int warm_start;     /* 1: start GMRES from the previous solution where one
+                         exists (BBPGD iterates 2.., U_nc of the next step of
+                         the same suspension); 0: zero initial guess          */
+  int bb_safeguard;   /* Algorithm 1 defines no step when s^T y <= 0 (BB1) or
+                         y^T y <= 0 (BB2): 0 stops with SPS_ERR_BREAKDOWN,
+                         1 keeps the previous step length and continues       */
 } sps_params;
 
 typedef struct sps_stats {
@@ -80,6 +86,7 @@ typedef struct sps_stats {
   int n_active;         /* contacts with gamma > 0 (the active set A_c)      */
   int n_near_pairs;     /* directed near pairs (i, j), i != j                */
   int ir_sweeps;        /* refinement sweeps (SPS_MIXED with ir_tol > 0)     */
+  int bb_safeguards;    /* BBPGD steps that kept the previous step length    */
   long long kernel_launches; /* kernels launched by this call                */
   double final_phi;     /* min-map residual at exit                          */
   double gmres_res_max; /* largest final relative residual over the solves   */
@@ -88,7 +95,8 @@ typedef struct sps_stats {
 typedef struct sps_ctx sps_ctx;
 
 /* Fills *out with the defaults: p 6, beta 1.75, delta 0.1, a_c_scale 1,
- * gmres 1e-10 / 200, bbpgd 1e-8 / 10000, FP64, BB1, no refinement. */
+ * gmres 1e-10 / 200, bbpgd 1e-8 / 10000, FP64, BB1, no refinement, warm
+ * starts on. */
 int sps_default_params(sps_params* out);
 
 /* Creates a context.  stream: a cudaStream_t (NULL = legacy default stream).

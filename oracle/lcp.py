@@ -17,7 +17,11 @@ Paper: Yan et al., arXiv 1909.06623.
   * Algorithm 1 (BBPGD) with the min-map residual of eq. mmapnorm and the BB1
     step (BB2 optional).  Readings where the algorithm is silent: gamma_0 = 0,
     whose product M gamma_0 = 0 needs no mobility solve; a non-positive s^T y
-    (or y^T y for BB2) stops with status "breakdown"; j_max caps the loop.
+    (or y^T y for BB2) stops with status "breakdown", or, with safeguard=True,
+    keeps the previous step length and continues (the discrete mobility is
+    symmetric only to discretisation accuracy, so s^T M s can turn
+    non-positive for nearly touching spheres at low order p); j_max caps the
+    loop.
   * eq. time-step: C^{k+1} = C^k + (U_nc + M D gamma) dt, positions only
     (spheres are isotropic; the grid keeps its lab-frame orientation).
 """
@@ -71,13 +75,13 @@ def minmap(gamma, g):
     return float(np.linalg.norm(np.minimum(gamma, g)))
 
 
-def bbpgd(Mop, q, tol, jmax=10000, variant=1):
+def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False):
     """Algorithm 1.  Mop(gamma) -> M gamma.  Returns gamma, g, info."""
     q = np.asarray(q, dtype=np.float64)
     mv = 0
     gamma = np.zeros_like(q)
     g = q.copy()                                   # M gamma_0 = 0 for gamma_0 = 0
-    info = {"iters": 0, "mvops": 0, "status": "ok", "phi": minmap(gamma, g)}
+    info = {"iters": 0, "mvops": 0, "status": "ok", "phi": minmap(gamma, g), "safeguards": 0}
     if info["phi"] < tol:
         return gamma, g, info
     Mg = Mop(g)
@@ -99,17 +103,15 @@ def bbpgd(Mop, q, tol, jmax=10000, variant=1):
         if phi < tol:
             return gamma, g, info
         sy = s @ y
-        if variant == 1:
-            if not sy > 0:
+        yy = y @ y
+        ok = sy > 0 if variant == 1 else (sy > 0 and yy > 0)
+        if not ok:
+            if not safeguard:
                 info["status"] = "breakdown"
                 return gamma, g, info
-            alpha = (s @ s) / sy
-        else:
-            yy = y @ y
-            if not (sy > 0 and yy > 0):
-                info["status"] = "breakdown"
-                return gamma, g, info
-            alpha = sy / yy
+            info["safeguards"] += 1          # keep the previous step length
+            continue
+        alpha = (s @ s) / sy if variant == 1 else sy / yy
     info["status"] = "not_converged"
     return gamma, g, info
 
@@ -138,7 +140,7 @@ def lcp_enumerate(Mmat, q):
 
 def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
                        a_c_scale=1.0, gmres_tol=1e-12, gmres_max=200,
-                       bbpgd_tol=1e-10, bbpgd_max=10000, variant=1):
+                       bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False):
     """One collision-resolved Euler step (Sec. 3.2, four-step procedure).
 
     1. U_nc = M F_ext; 2. contacts and D; 3. BBPGD for gamma with
@@ -159,7 +161,7 @@ def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
         state["gmres"] += inf["gmres_iters"]
         return DT_apply(ij, nrm, UO)
 
-    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant)
+    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard)
     if info["iters"] == 0:
         U_c = np.zeros_like(U_nc)       # gamma = gamma_0 = 0
     else:

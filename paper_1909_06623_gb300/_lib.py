@@ -23,7 +23,8 @@ class sps_params(ctypes.Structure):
                 ("a_c_scale", ctypes.c_double), ("gmres_tol", ctypes.c_double),
                 ("gmres_max", ctypes.c_int), ("bbpgd_tol", ctypes.c_double),
                 ("bbpgd_max", ctypes.c_int), ("precision", ctypes.c_int),
-                ("bb_variant", ctypes.c_int), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int)]
+                ("bb_variant", ctypes.c_int), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("bb_safeguard", ctypes.c_int)]
 
 
 class sps_stats(ctypes.Structure):
@@ -32,6 +33,7 @@ class sps_stats(ctypes.Structure):
                 ("bbpgd_iters", ctypes.c_int), ("mvops", ctypes.c_int),
                 ("n_contacts", ctypes.c_int), ("n_active", ctypes.c_int),
                 ("n_near_pairs", ctypes.c_int), ("ir_sweeps", ctypes.c_int),
+                ("bb_safeguards", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong), ("final_phi", ctypes.c_double),
                 ("gmres_res_max", ctypes.c_double)]
 

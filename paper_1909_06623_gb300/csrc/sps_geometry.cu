@@ -20,7 +20,8 @@ inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); 
 __global__ void k_grid(int N, int P, const double* __restrict__ pos, const double* __restrict__ rad,
                        const double* __restrict__ un, const double* __restrict__ uw,
                        double* __restrict__ X, double* __restrict__ Nr, double* __restrict__ W,
-                       float* __restrict__ X32, float* __restrict__ N32, float* __restrict__ W32) {
+                       float* __restrict__ rel32, float* __restrict__ N32, float* __restrict__ W32,
+                       float* __restrict__ chi, float* __restrict__ clo) {
   const long long NP = (long long)N * P;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NP;
        g += (long long)gridDim.x * blockDim.x) {
@@ -31,8 +32,13 @@ __global__ void k_grid(int N, int P, const double* __restrict__ pos, const doubl
       const double x = pos[3 * s + c] + a * n;
       X[c * NP + g] = x;
       Nr[c * NP + g] = n;
-      X32[c * NP + g] = (float)x;
+      rel32[c * NP + g] = (float)(a * n);     // offset from the sphere's centre
       N32[c * NP + g] = (float)n;
+      if (k == 0) {                           // centre as an FP32 pair hi + lo
+        const float hi = (float)pos[3 * s + c];
+        chi[3 * s + c] = hi;
+        clo[3 * s + c] = (float)(pos[3 * s + c] - (double)hi);
+      }
     }
     const double w = a * a * uw[k];
     W[g] = w;
@@ -66,6 +72,54 @@ __global__ void k_near_fill(int N, const double* pos, const double* rad, double 
   int o = ptr[i];
   for (int j = 0; j < N; ++j)
     if (j != i && is_near(pos, rad, i, j, beta)) idx[o++] = j;
+}
+
+// close near entries: node g of sphere i and near source j with
+// |x_g - c_j| < kCloseRadius a_j
+__global__ void k_close_count(int N, int P, const double* __restrict__ pos, const double* __restrict__ rad,
+                              const double* __restrict__ X, const int* __restrict__ near_ptr,
+                              const int* __restrict__ near_idx, int* __restrict__ cnt,
+                              int* __restrict__ flag) {
+  const long long NP = (long long)N * P;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g > NP) return;
+  if (g == NP) {
+    cnt[g] = 0;
+    flag[g] = 0;
+    return;
+  }
+  const int i = (int)(g / P);
+  const double gx = X[g], gy = X[NP + g], gz = X[2 * NP + g];
+  const double lim = sps::kCloseRadius * sps::kCloseRadius;
+  int c = 0;
+  for (int q = near_ptr[i]; q < near_ptr[i + 1]; ++q) {
+    const int j = near_idx[q];
+    if (sps_close_r2(pos, 1.0 / rad[j], gx, gy, gz, j) < lim) ++c;
+  }
+  cnt[g] = c;
+  flag[g] = c > 0 ? 1 : 0;
+}
+
+__global__ void k_close_fill(int N, int P, const double* __restrict__ pos, const double* __restrict__ rad,
+                             const double* __restrict__ X, const int* __restrict__ near_ptr,
+                             const int* __restrict__ near_idx, const int* __restrict__ cnt,
+                             const int* __restrict__ sptr, const int* __restrict__ fpos,
+                             int* __restrict__ cnode, int* __restrict__ cptr, int* __restrict__ csrc) {
+  const long long NP = (long long)N * P;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= NP || cnt[g] == 0) return;
+  const int t = fpos[g];
+  cnode[t] = (int)g;
+  cptr[t] = sptr[g];
+  cptr[t + 1] = sptr[g] + cnt[g];
+  const int i = (int)(g / P);
+  const double gx = X[g], gy = X[NP + g], gz = X[2 * NP + g];
+  const double lim = sps::kCloseRadius * sps::kCloseRadius;
+  int o = sptr[g];
+  for (int q = near_ptr[i]; q < near_ptr[i + 1]; ++q) {
+    const int j = near_idx[q];
+    if (sps_close_r2(pos, 1.0 / rad[j], gx, gy, gz, j) < lim) csrc[o++] = j;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -263,8 +317,8 @@ int sps_launch_grid(sps_ctx* ctx) {
   const long long NP = ctx->NP;
   k_grid<<<nblk(NP), kThreads, 0, ctx->stream>>>(ctx->N, ctx->T.P, ctx->d_pos, ctx->d_rad,
                                                   ctx->d_unit_nrm, ctx->d_unit_w, ctx->d_X,
-                                                  ctx->d_Nrm, ctx->d_W, ctx->d_X32, ctx->d_N32,
-                                                  ctx->d_W32);
+                                                  ctx->d_Nrm, ctx->d_W, ctx->d_rel32, ctx->d_N32,
+                                                  ctx->d_W32, ctx->d_chi, ctx->d_clo);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -298,6 +352,51 @@ int sps_launch_near_lists(sps_ctx* ctx) {
   k_near_fill<<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_pos, ctx->d_rad, ctx->prm.beta,
                                                       ctx->d_near_ptr, ctx->d_near_idx);
   SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_close_lists(sps_ctx* ctx) {
+  SpsPhase timer(ctx, SPS_PH_GEOM);
+  const long long NP = ctx->NP;
+  int *d_cnt = nullptr, *d_flag = nullptr, *d_sptr = nullptr, *d_fpos = nullptr;
+  size_t c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+  SPS_TRY(sps_grow(ctx, &d_cnt, c1, (size_t)NP + 1));
+  SPS_TRY(sps_grow(ctx, &d_flag, c2, (size_t)NP + 1));
+  SPS_TRY(sps_grow(ctx, &d_sptr, c3, (size_t)NP + 1));
+  SPS_TRY(sps_grow(ctx, &d_fpos, c4, (size_t)NP + 1));
+  k_close_count<<<nblk(NP + 1), kThreads, 0, ctx->stream>>>(ctx->N, ctx->T.P, ctx->d_pos, ctx->d_rad,
+                                                             ctx->d_X, ctx->d_near_ptr, ctx->d_near_idx,
+                                                             d_cnt, d_flag);
+  SPS_LAUNCHED(ctx);
+  size_t tmp = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tmp, d_cnt, d_sptr, (int)(NP + 1), ctx->stream);
+  void* d_tmp = nullptr;
+  SPS_CUDA(ctx, cudaMalloc(&d_tmp, tmp ? tmp : 1));
+  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(d_tmp, tmp, d_cnt, d_sptr, (int)(NP + 1), ctx->stream));
+  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(d_tmp, tmp, d_flag, d_fpos, (int)(NP + 1), ctx->stream));
+  ctx->launches += 2;
+  int tot[2] = {0, 0};
+  SPS_CUDA(ctx, cudaMemcpyAsync(&tot[0], d_fpos + NP, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpyAsync(&tot[1], d_sptr + NP, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  cudaFree(d_tmp);
+  ctx->n_close = tot[0];
+  ctx->n_close_src = tot[1];
+  SPS_TRY(sps_grow(ctx, &ctx->d_close_node, ctx->cap_close_node, (size_t)tot[0] + 1));
+  SPS_TRY(sps_grow(ctx, &ctx->d_close_ptr, ctx->cap_close_ptr, (size_t)tot[0] + 2));
+  SPS_TRY(sps_grow(ctx, &ctx->d_close_src, ctx->cap_close_src, (size_t)tot[1] + 1));
+  if (tot[0] > 0) {
+    k_close_fill<<<nblk(NP), kThreads, 0, ctx->stream>>>(ctx->N, ctx->T.P, ctx->d_pos, ctx->d_rad, ctx->d_X,
+                                                          ctx->d_near_ptr, ctx->d_near_idx, d_cnt, d_sptr,
+                                                          d_fpos, ctx->d_close_node, ctx->d_close_ptr,
+                                                          ctx->d_close_src);
+    SPS_LAUNCHED(ctx);
+  }
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  cudaFree(d_cnt);
+  cudaFree(d_flag);
+  cudaFree(d_sptr);
+  cudaFree(d_fpos);
   return SPS_OK;
 }
 

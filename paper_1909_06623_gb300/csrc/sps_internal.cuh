@@ -23,6 +23,9 @@ namespace sps {
 constexpr int kFieldsK = 25;   // fields summed per target for the traction
 constexpr int kFieldsS = 10;   // fields summed per target for the velocity
 constexpr int kMaxP = 16;
+// near entries closer than this many source radii from the source centre are
+// evaluated in FP64 in the mixed path (the VSH terms decay slowly there)
+constexpr double kCloseRadius = 1.5;
 
 struct Tables {
   int p = 0, P = 0, NC = 0, NR = 0, L = 0, E = 0;
@@ -33,6 +36,7 @@ struct Tables {
   std::vector<double> synth;              // 3P x NR, row-major
   std::vector<double> multS, multK;       // NR (per row: self multipliers)
   std::vector<double> kappa;              // NC: phi_nm = kappa * H_n^m
+  std::vector<double> potfac;             // (p+1) x 6: near-field potential factors per degree
 };
 void build_tables(int p, Tables& T);
 
@@ -60,16 +64,21 @@ struct sps_ctx {
   double *d_anal = nullptr;     // NR x 3P row-major analysis
   double *d_synthS = nullptr;   // 3P x NR row-major synthesis * multS
   double *d_synthK = nullptr;   // 3P x NR row-major synthesis * multK
-  double *d_kappa = nullptr;
+  double *d_kappa = nullptr, *d_potfac = nullptr;
   float *d_anal32 = nullptr, *d_synthS32 = nullptr, *d_synthK32 = nullptr;
 
   // geometry
   int N = 0, NP = 0, capN = 0;
   double *d_pos = nullptr, *d_rad = nullptr;
   double *d_X = nullptr, *d_Nrm = nullptr, *d_W = nullptr;
-  float *d_X32 = nullptr, *d_N32 = nullptr, *d_W32 = nullptr;
+  float *d_rel32 = nullptr, *d_N32 = nullptr, *d_W32 = nullptr;  // node - own centre, normal, w
+  float *d_chi = nullptr, *d_clo = nullptr;                       // centres as hi + lo (N x 3)
   int *d_near_ptr = nullptr, *d_near_idx = nullptr;
   int n_near = 0, cap_near = 0;
+  // close near entries (mixed path FP64 list): nodes, CSR into source spheres
+  int n_close = 0, n_close_src = 0;
+  int *d_close_node = nullptr, *d_close_ptr = nullptr, *d_close_src = nullptr;
+  size_t cap_close_node = 0, cap_close_ptr = 0, cap_close_src = 0;
   bool have_geom = false;
 
   // operator scratch
@@ -77,7 +86,7 @@ struct sps_ctx {
   double *d_fcoef = nullptr;     // N x E x kFieldsK x 2
   double *d_mom = nullptr;       // N x 6 (per-sphere moments)
   double *d_tmp3 = nullptr;      // 3NP scratch
-  float *d_sig32 = nullptr;      // 3NP FP32 density for the mixed far field
+  float *d_sig32 = nullptr;      // 3NP FP32 w*sigma for the mixed far field
   double *d_part = nullptr;      // far-field partial sums (splits x 3NP)
   size_t cap_part = 0;
 
@@ -87,6 +96,8 @@ struct sps_ctx {
   double *d_w = nullptr, *d_h = nullptr, *d_red = nullptr;
   double *h_pinned = nullptr;    // pinned host scratch for scalars
   double *d_rho = nullptr, *d_zeta = nullptr, *d_b = nullptr, *d_u = nullptr;
+  double *d_zeta_nc = nullptr;   // density of the last U_nc solve (warm start)
+  long long zeta_nc_n = 0;       // node count it belongs to (0: none)
   double *d_r = nullptr, *d_dz = nullptr;
 
   // contacts
@@ -145,6 +156,15 @@ int sps_grow(sps_ctx* ctx, T** p, size_t& cap_elems, size_t need_elems) {
   return SPS_OK;
 }
 
+// squared distance of a target (gx, gy, gz) from the centre of sphere j in
+// units of a_j (ia = 1/a_j), evaluated identically wherever near entries are
+// split into FP32 and FP64 ones
+__device__ __forceinline__ double sps_close_r2(const double* pos, double ia, double gx, double gy,
+                                               double gz, int j) {
+  const double x = (gx - pos[3 * j]) * ia, y = (gy - pos[3 * j + 1]) * ia, z = (gz - pos[3 * j + 2]) * ia;
+  return x * x + y * y + z * z;
+}
+
 // RAII phase timer: records an event pair around the enclosed launches
 struct SpsPhase {
   sps_ctx* c;
@@ -160,6 +180,7 @@ struct SpsPhase {
 // geometry / contacts (sps_geometry.cu)
 int sps_launch_grid(sps_ctx* ctx);
 int sps_launch_near_lists(sps_ctx* ctx);
+int sps_launch_close_lists(sps_ctx* ctx);
 int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii);
 int sps_launch_D(sps_ctx* ctx, const double* gamma, double* FT);
 int sps_launch_DT(sps_ctx* ctx, const double* UO, double* out);

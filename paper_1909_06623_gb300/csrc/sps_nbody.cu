@@ -96,160 +96,260 @@ __global__ void __launch_bounds__(kT64) k_far64(int N, int P, const double* __re
 }
 
 // ---------------------------------------------------------------------------
-// FP32 kernel
+// FP32 kernel (mixed precision)
+//
+// Coordinates: every node is stored as its offset from its own sphere centre
+// (FP32), every centre as an FP32 pair hi + lo (hi = fl(c), lo = fl(c - hi)).
+// For target t on sphere i and source s on sphere j the pair vector is
+//   r = ((hi_i - hi_j) + (lo_i + d_t - lo_j)) - d_s,
+// whose rounding error is relative to |r|, not to the absolute coordinates.
+// Sources are staged in shared memory a few whole spheres at a time; each
+// (target, source sphere) partial sum is formed in FP32 and added into a
+// Kahan-compensated running sum unless sphere j is i or a near neighbour of i
+// (a select, so the r = 0 self pair never reaches the sum).  Two targets share
+// one packed FP32x2 register pair (fma.rn.f32x2 and friends), so one issued
+// instruction does the arithmetic of two pair terms.
+// Work items (target block, source split) are taken from an atomic counter by
+// a persistent grid; each item writes its own partial sums, which a second
+// kernel adds in a fixed order: results do not depend on scheduling.
 // ---------------------------------------------------------------------------
-constexpr int kT32 = 128;      // threads per block
-constexpr int kTS32 = 256;     // sources per tile
-constexpr int kTPT = 2;        // targets per thread
+#ifndef SPS_FAR_NPAIR
+#define SPS_FAR_NPAIR 2
+#endif
+#ifndef SPS_FAR_THREADS
+#define SPS_FAR_THREADS 128
+#endif
+#ifndef SPS_FAR_MINB
+#define SPS_FAR_MINB 3
+#endif
+constexpr int kT32 = SPS_FAR_THREADS;         // threads per block
+constexpr int kNPair = SPS_FAR_NPAIR;         // target pairs per thread
+#ifndef SPS_FAR_PACKED
+#define SPS_FAR_PACKED 2
+#endif
+// pairs q < kPacked use packed FP32x2 instructions, the others scalar FP32
+// (measured on GB300: all-packed is fastest; the scalar path is kept for
+// tuning on other parts).
+constexpr int kPacked = SPS_FAR_PACKED;
+constexpr int kTPB32 = kT32 * 2 * kNPair;     // targets per block
+constexpr int kChunkNodes = 512;              // staged source nodes (whole spheres)
 
-struct Excl {
-  int i, ptr, end;
-};
-
-__device__ __forceinline__ unsigned long long excl_mask(Excl& e, const int* __restrict__ near_idx,
-                                                        int s_lo, int s_hi) {
-  unsigned long long m = 0ull;
-  if (e.i >= s_lo && e.i <= s_hi) m |= 1ull << (e.i - s_lo);
-  while (e.ptr < e.end && near_idx[e.ptr] < s_lo) ++e.ptr;
-  for (int q = e.ptr; q < e.end; ++q) {
-    const int s = near_idx[q];
-    if (s > s_hi) break;
-    m |= 1ull << (s - s_lo);
-  }
-  return m;
-}
-
-template <int OP>
-__device__ __forceinline__ void pair32(float tx, float ty, float tz, float nx, float ny, float nz,
-                                       const float4 a, const float4 b, float& ax, float& ay,
-                                       float& az) {
-  const float rx = tx - a.x, ry = ty - a.y, rz = tz - a.z;
-  const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-  const float inv = rsqrtf(r2);
-  const float rs = fmaf(rz, b.y, fmaf(ry, b.x, rx * a.w));
-  if (OP == SPS_OP_S) {
-    const float i2 = inv * inv;
-    const float c = rs * i2 * inv;
-    ax = fmaf(a.w, inv, fmaf(c, rx, ax));
-    ay = fmaf(b.x, inv, fmaf(c, ry, ay));
-    az = fmaf(b.y, inv, fmaf(c, rz, az));
-  } else {
-    const float rn = fmaf(rz, nz, fmaf(ry, ny, rx * nx));
-    const float i2 = inv * inv;
-    const float c = (rs * rn) * (i2 * i2 * inv);
-    ax = fmaf(c, rx, ax);
-    ay = fmaf(c, ry, ay);
-    az = fmaf(c, rz, az);
-  }
-}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 template <int OP>
-__global__ void __launch_bounds__(kT32) k_far32(int N, int P, long long src_per_split,
-                                                const float* __restrict__ X,
-                                                const float* __restrict__ Nr,
-                                                const float* __restrict__ W,
-                                                const float* __restrict__ sig,
-                                                const int* __restrict__ near_ptr,
-                                                const int* __restrict__ near_idx,
-                                                double* __restrict__ part) {
-  __shared__ float4 sa[kTS32], sb[kTS32];
-  __shared__ unsigned char sl[kTS32];
+__global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
+    int N, int P, int spc, int n_tb, int n_items, int n_splits,
+    const float* __restrict__ rel,    // 3 planes NP: node - own centre
+    const float* __restrict__ nrm,    // 3 planes NP
+    const float* __restrict__ wsig,   // 3 planes NP: w * sigma
+    const float* __restrict__ chi,    // N x 3 centre hi
+    const float* __restrict__ clo,    // N x 3 centre lo
+    const int* __restrict__ near_ptr, const int* __restrict__ near_idx,
+    int* __restrict__ work, double* __restrict__ part) {
+  extern __shared__ __align__(16) float4 sdyn[];
   const long long NP = (long long)N * P;
-  const long long base = (long long)blockIdx.x * kT32 * kTPT + threadIdx.x;
-  float tx[kTPT], ty[kTPT], tz[kTPT], nx[kTPT], ny[kTPT], nz[kTPT];
-  float sx[kTPT], sy[kTPT], sz[kTPT], cx[kTPT], cy[kTPT], cz[kTPT];
-  Excl ex[kTPT];
-#pragma unroll
-  for (int q = 0; q < kTPT; ++q) {
-    const long long t = base + q * kT32;
-    const long long tt = t < NP ? t : NP - 1;
-    tx[q] = X[tt];
-    ty[q] = X[NP + tt];
-    tz[q] = X[2 * NP + tt];
-    if (OP == SPS_OP_K) {
-      nx[q] = Nr[tt];
-      ny[q] = Nr[NP + tt];
-      nz[q] = Nr[2 * NP + tt];
-    } else {
-      nx[q] = ny[q] = nz[q] = 0.f;
-    }
-    sx[q] = sy[q] = sz[q] = cx[q] = cy[q] = cz[q] = 0.f;
-    ex[q].i = (int)(tt / P);
-    ex[q].ptr = near_ptr[ex[q].i];
-    ex[q].end = near_ptr[ex[q].i + 1];
-  }
-  const long long s0 = (long long)blockIdx.y * src_per_split;
-  const long long s1 = min(NP, s0 + src_per_split);
-  for (long long t0 = s0; t0 < s1; t0 += kTS32) {
-    const int nt = (int)min((long long)kTS32, s1 - t0);
-    const int s_lo = (int)(t0 / P), s_hi = (int)((t0 + nt - 1) / P);
-    for (int k = threadIdx.x; k < kTS32; k += kT32) {
-      const long long j = t0 + k;
-      if (k < nt) {
-        const float w = W[j];
-        sa[k] = make_float4(X[j], X[NP + j], X[2 * NP + j], w * sig[j]);
-        sb[k] = make_float4(w * sig[NP + j], w * sig[2 * NP + j], 0.f, 0.f);
-        sl[k] = (unsigned char)(j / P - s_lo);
-      } else {
-        // padding sources far away with zero weight (never excluded)
-        sa[k] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-        sb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        sl[k] = 63;
-      }
-    }
+  const int cap = spc * P;                     // nodes per staged chunk
+  float4* sA = sdyn;                           // (-dx, -dx, -dy, -dy)
+  float4* sB = sA + cap;                       // (-dz, -dz, wx, wx)
+  float4* sC = sB + cap;                       // (wy, wy, wz, wz)
+  float* sh = reinterpret_cast<float*>(sC + cap);  // spc x 6: hi xyz, lo xyz
+  // per-thread target state kept out of registers: hi, lo + offset (6 per target)
+  __shared__ float sEF[6 * 2 * kNPair][kT32];
+  __shared__ int sX[3 * 2 * kNPair][kT32];        // sphere, near pointer, near end
+  __shared__ int s_item;
+  for (;;) {
     __syncthreads();
-    unsigned long long m[kTPT];
-    bool any = false;
+    if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const int tb = item % n_tb, sp = item / n_tb;
+    const int j_begin = (int)((long long)N * sp / n_splits);
+    const int j_end = (int)((long long)N * (sp + 1) / n_splits);
+    // ---- targets of this thread: lanes (2q, 2q+1) of pair q
+    const long long base = (long long)tb * kTPB32 + threadIdx.x;
+    float2 nx[kNPair], ny[kNPair], nz[kNPair];
+    float2 sx[kNPair], sy[kNPair], sz[kNPair], cx[kNPair], cy[kNPair], cz[kNPair];
 #pragma unroll
-    for (int q = 0; q < kTPT; ++q) {
-      m[q] = excl_mask(ex[q], near_idx, s_lo, s_hi);
-      any |= (m[q] != 0ull);
-    }
-    float ax[kTPT], ay[kTPT], az[kTPT];
+    for (int q = 0; q < kNPair; ++q) {
+      float n[2][3];
 #pragma unroll
-    for (int q = 0; q < kTPT; ++q) ax[q] = ay[q] = az[q] = 0.f;
-    if (!__any_sync(0xffffffffu, any)) {
-#pragma unroll 4
-      for (int k = 0; k < kTS32; ++k) {
-        const float4 a = sa[k], b = sb[k];
-#pragma unroll
-        for (int q = 0; q < kTPT; ++q)
-          pair32<OP>(tx[q], ty[q], tz[q], nx[q], ny[q], nz[q], a, b, ax[q], ay[q], az[q]);
+      for (int h = 0; h < 2; ++h) {
+        const int l = 2 * q + h;
+        const long long t = base + (long long)l * kT32;
+        const long long tt = t < NP ? t : NP - 1;
+        const int i = (int)(tt / P);
+        for (int c = 0; c < 3; ++c) {
+          sEF[6 * l + c][threadIdx.x] = chi[3 * i + c];
+          sEF[6 * l + 3 + c][threadIdx.x] = clo[3 * i + c] + rel[c * NP + tt];
+          n[h][c] = (OP == SPS_OP_K) ? nrm[c * NP + tt] : 0.f;
+        }
+        // first near neighbour not below j_begin
+        int a = near_ptr[i];
+        const int b = near_ptr[i + 1];
+        while (a < b && near_idx[a] < j_begin) ++a;
+        sX[3 * l][threadIdx.x] = i;
+        sX[3 * l + 1][threadIdx.x] = a;
+        sX[3 * l + 2][threadIdx.x] = b;
       }
-    } else {
-      for (int k = 0; k < kTS32; ++k) {
-        const float4 a = sa[k], b = sb[k];
-        const int l = sl[k];
+      nx[q] = make_float2(n[0][0], n[1][0]);
+      ny[q] = make_float2(n[0][1], n[1][1]);
+      nz[q] = make_float2(n[0][2], n[1][2]);
+      sx[q] = sy[q] = sz[q] = cx[q] = cy[q] = cz[q] = make_float2(0.f, 0.f);
+    }
+    // ---- source spheres, staged spc at a time
+    for (int j0 = j_begin; j0 < j_end; j0 += spc) {
+      const int ns = min(spc, j_end - j0);
+      const int nn = ns * P;
+      const long long g0 = (long long)j0 * P;
+      __syncthreads();
+      for (int k = threadIdx.x; k < nn; k += kT32) {
+        const long long g = g0 + k;
+        const float dx = -rel[g], dy = -rel[NP + g], dz = -rel[2 * NP + g];   // negated offsets
+        const float wx = wsig[g], wy = wsig[NP + g], wz = wsig[2 * NP + g];
+        sA[k] = make_float4(dx, dx, dy, dy);
+        sB[k] = make_float4(dz, dz, wx, wx);
+        sC[k] = make_float4(wy, wy, wz, wz);
+      }
+      for (int k = threadIdx.x; k < ns * 6; k += kT32) {
+        const int js = k / 6, c = k % 6;
+        sh[k] = (c < 3) ? chi[3 * (j0 + js) + c] : clo[3 * (j0 + js) + c - 3];
+      }
+      __syncthreads();
+      for (int js = 0; js < ns; ++js) {
+        const int j = j0 + js;
+        const float hx = sh[6 * js], hy = sh[6 * js + 1], hz = sh[6 * js + 2];
+        const float lx = sh[6 * js + 3], ly = sh[6 * js + 4], lz = sh[6 * js + 5];
+        float2 Dx[kNPair], Dy[kNPair], Dz[kNPair], ax[kNPair], ay[kNPair], az[kNPair];
 #pragma unroll
-        for (int q = 0; q < kTPT; ++q) {
-          float bx = ax[q], by = ay[q], bz = az[q];
-          pair32<OP>(tx[q], ty[q], tz[q], nx[q], ny[q], nz[q], a, b, bx, by, bz);
-          const bool skip = (m[q] >> l) & 1ull;
-          ax[q] = skip ? ax[q] : bx;
-          ay[q] = skip ? ay[q] : by;
-          az[q] = skip ? az[q] : bz;
+        for (int q = 0; q < kNPair; ++q) {
+          const int l0 = 12 * q, l1 = 12 * q + 6;
+          const float2 Ex = make_float2(sEF[l0][threadIdx.x], sEF[l1][threadIdx.x]);
+          const float2 Ey = make_float2(sEF[l0 + 1][threadIdx.x], sEF[l1 + 1][threadIdx.x]);
+          const float2 Ez = make_float2(sEF[l0 + 2][threadIdx.x], sEF[l1 + 2][threadIdx.x]);
+          const float2 Fx = make_float2(sEF[l0 + 3][threadIdx.x], sEF[l1 + 3][threadIdx.x]);
+          const float2 Fy = make_float2(sEF[l0 + 4][threadIdx.x], sEF[l1 + 4][threadIdx.x]);
+          const float2 Fz = make_float2(sEF[l0 + 5][threadIdx.x], sEF[l1 + 5][threadIdx.x]);
+          Dx[q] = __fadd2_rn(__fadd2_rn(Ex, f2(-hx)), __fadd2_rn(Fx, f2(-lx)));
+          Dy[q] = __fadd2_rn(__fadd2_rn(Ey, f2(-hy)), __fadd2_rn(Fy, f2(-ly)));
+          Dz[q] = __fadd2_rn(__fadd2_rn(Ez, f2(-hz)), __fadd2_rn(Fz, f2(-lz)));
+          ax[q] = ay[q] = az[q] = make_float2(0.f, 0.f);
+        }
+        const float4* A = sA + js * P;
+        const float4* B = sB + js * P;
+        const float4* C = sC + js * P;
+#pragma unroll 2
+        for (int k = 0; k < P; ++k) {
+          const float4 a4 = A[k], b4 = B[k], c4 = C[k];
+          const float2 sxx = make_float2(a4.x, a4.y), syy = make_float2(a4.z, a4.w);
+          const float2 szz = make_float2(b4.x, b4.y), wxx = make_float2(b4.z, b4.w);
+          const float2 wyy = make_float2(c4.x, c4.y), wzz = make_float2(c4.z, c4.w);
+#pragma unroll
+          for (int q = 0; q < kNPair; ++q) {
+            if (q < kPacked) {
+              const float2 rx = __fadd2_rn(Dx[q], sxx);
+              const float2 ry = __fadd2_rn(Dy[q], syy);
+              const float2 rz = __fadd2_rn(Dz[q], szz);
+              const float2 r2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+              const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+              const float2 rs = __ffma2_rn(rz, wzz, __ffma2_rn(ry, wyy, __fmul2_rn(rx, wxx)));
+              const float2 i2 = __fmul2_rn(inv, inv);
+              if (OP == SPS_OP_S) {
+                const float2 cc = __fmul2_rn(__fmul2_rn(rs, i2), inv);
+                ax[q] = __ffma2_rn(wxx, inv, __ffma2_rn(cc, rx, ax[q]));
+                ay[q] = __ffma2_rn(wyy, inv, __ffma2_rn(cc, ry, ay[q]));
+                az[q] = __ffma2_rn(wzz, inv, __ffma2_rn(cc, rz, az[q]));
+              } else {
+                const float2 rn = __ffma2_rn(rz, nz[q], __ffma2_rn(ry, ny[q], __fmul2_rn(rx, nx[q])));
+                const float2 i5 = __fmul2_rn(__fmul2_rn(i2, i2), inv);
+                const float2 cc = __fmul2_rn(__fmul2_rn(rs, rn), i5);
+                ax[q] = __ffma2_rn(cc, rx, ax[q]);
+                ay[q] = __ffma2_rn(cc, ry, ay[q]);
+                az[q] = __ffma2_rn(cc, rz, az[q]);
+              }
+            } else {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const float dX = h ? Dx[q].y : Dx[q].x, dY = h ? Dy[q].y : Dy[q].x;
+                const float dZ = h ? Dz[q].y : Dz[q].x;
+                const float rx = dX + sxx.x, ry = dY + syy.x, rz = dZ + szz.x;
+                const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                const float inv = rsqrtf(r2);
+                const float rs = fmaf(rz, wzz.x, fmaf(ry, wyy.x, rx * wxx.x));
+                const float i2 = inv * inv;
+                float bx = h ? ax[q].y : ax[q].x, by = h ? ay[q].y : ay[q].x;
+                float bz = h ? az[q].y : az[q].x;
+                if (OP == SPS_OP_S) {
+                  const float cc = rs * i2 * inv;
+                  bx = fmaf(wxx.x, inv, fmaf(cc, rx, bx));
+                  by = fmaf(wyy.x, inv, fmaf(cc, ry, by));
+                  bz = fmaf(wzz.x, inv, fmaf(cc, rz, bz));
+                } else {
+                  const float vx = h ? nx[q].y : nx[q].x, vy = h ? ny[q].y : ny[q].x;
+                  const float vz = h ? nz[q].y : nz[q].x;
+                  const float rn = fmaf(rz, vz, fmaf(ry, vy, rx * vx));
+                  const float cc = (rs * rn) * (i2 * i2 * inv);
+                  bx = fmaf(cc, rx, bx);
+                  by = fmaf(cc, ry, by);
+                  bz = fmaf(cc, rz, bz);
+                }
+                if (h) {
+                  ax[q].y = bx; ay[q].y = by; az[q].y = bz;
+                } else {
+                  ax[q].x = bx; ay[q].x = by; az[q].x = bz;
+                }
+              }
+            }
+          }
+        }
+        // fold the sphere's partial sums unless j is excluded for the target
+#pragma unroll
+        for (int q = 0; q < kNPair; ++q) {
+          bool ex[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int l = 2 * q + h;
+            int pt = sX[3 * l + 1][threadIdx.x];
+            const int pe = sX[3 * l + 2][threadIdx.x];
+            while (pt < pe && near_idx[pt] < j) ++pt;
+            sX[3 * l + 1][threadIdx.x] = pt;
+            ex[h] = (j == sX[3 * l][threadIdx.x]) || (pt < pe && near_idx[pt] == j);
+          }
+          const float2 zx = make_float2(ex[0] ? 0.f : ax[q].x, ex[1] ? 0.f : ax[q].y);
+          const float2 zy = make_float2(ex[0] ? 0.f : ay[q].x, ex[1] ? 0.f : ay[q].y);
+          const float2 zz = make_float2(ex[0] ? 0.f : az[q].x, ex[1] ? 0.f : az[q].y);
+          float2 y, t;
+          y = __fadd2_rn(zx, make_float2(-cx[q].x, -cx[q].y));
+          t = __fadd2_rn(sx[q], y);
+          cx[q] = __fadd2_rn(__fadd2_rn(t, make_float2(-sx[q].x, -sx[q].y)), make_float2(-y.x, -y.y));
+          sx[q] = t;
+          y = __fadd2_rn(zy, make_float2(-cy[q].x, -cy[q].y));
+          t = __fadd2_rn(sy[q], y);
+          cy[q] = __fadd2_rn(__fadd2_rn(t, make_float2(-sy[q].x, -sy[q].y)), make_float2(-y.x, -y.y));
+          sy[q] = t;
+          y = __fadd2_rn(zz, make_float2(-cz[q].x, -cz[q].y));
+          t = __fadd2_rn(sz[q], y);
+          cz[q] = __fadd2_rn(__fadd2_rn(t, make_float2(-sz[q].x, -sz[q].y)), make_float2(-y.x, -y.y));
+          sz[q] = t;
         }
       }
     }
-    // Kahan: fold this tile's FP32 sum into the running compensated sum
+    // ---- this item's partial sums
+    double* o = part + (long long)sp * 3 * NP;
 #pragma unroll
-    for (int q = 0; q < kTPT; ++q) {
-      float y, t;
-      y = ax[q] - cx[q]; t = sx[q] + y; cx[q] = (t - sx[q]) - y; sx[q] = t;
-      y = ay[q] - cy[q]; t = sy[q] + y; cy[q] = (t - sy[q]) - y; sy[q] = t;
-      y = az[q] - cz[q]; t = sz[q] + y; cz[q] = (t - sz[q]) - y; sz[q] = t;
-    }
-    __syncthreads();
-  }
-  double* o = part + (long long)blockIdx.y * 3 * NP;
+    for (int q = 0; q < kNPair; ++q)
 #pragma unroll
-  for (int q = 0; q < kTPT; ++q) {
-    const long long t = base + q * kT32;
-    if (t < NP) {
-      o[t] = (double)sx[q] - (double)cx[q];
-      o[NP + t] = (double)sy[q] - (double)cy[q];
-      o[2 * NP + t] = (double)sz[q] - (double)cz[q];
-    }
+      for (int h = 0; h < 2; ++h) {
+        const long long t = base + (long long)(2 * q + h) * kT32;
+        if (t < NP) {
+          const float vx = h ? sx[q].y : sx[q].x, kx = h ? cx[q].y : cx[q].x;
+          const float vy = h ? sy[q].y : sy[q].x, ky = h ? cy[q].y : cy[q].x;
+          const float vz = h ? sz[q].y : sz[q].x, kz = h ? cz[q].y : cz[q].x;
+          o[t] = (double)vx - (double)kx;
+          o[NP + t] = (double)vy - (double)ky;
+          o[2 * NP + t] = (double)vz - (double)kz;
+        }
+      }
   }
 }
 
@@ -263,10 +363,12 @@ __global__ void k_reduce_parts(long long n3, int splits, const double* __restric
   }
 }
 
-__global__ void k_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+// w * sigma in FP32 (3 planes), the source strengths of the far field
+__global__ void k_wsig32(long long NP, const double* __restrict__ sig, const double* __restrict__ W,
+                         float* __restrict__ out) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 3 * NP;
        g += (long long)gridDim.x * blockDim.x)
-    b[g] = (float)a[g];
+    out[g] = (float)(W[g % NP] * sig[g]);
 }
 
 }  // namespace
@@ -289,54 +391,56 @@ int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp
   }
   const long long n3 = 3 * NP;
   {
-  SpsPhase timer(ctx, SPS_PH_FAR_AUX);
-  k_to_f32<<<(int)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, ctx->stream>>>(n3, sig,
-                                                                                     ctx->d_sig32);
-  SPS_LAUNCHED(ctx);
+    SpsPhase timer(ctx, SPS_PH_FAR_AUX);
+    k_wsig32<<<(int)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        NP, sig, ctx->d_W, ctx->d_sig32);
+    SPS_LAUNCHED(ctx);
   }
-  const int bx = (int)((NP + kT32 * kTPT - 1) / (kT32 * kTPT));
-  // Source splits chosen so that the grid fills whole waves of resident blocks
-  // (every block does the same work, so a partial last wave idles SMs).
-  static int resident = 0;
-  if (!resident) {
-    int per_sm = 0, sms = 0, dev = 0;
+  // persistent grid over (target block, source split) items
+  const int spc = std::max(1, kChunkNodes / P);
+  const size_t smem = (size_t)3 * spc * P * sizeof(float4) + (size_t)spc * 6 * sizeof(float);
+  int per_sm[2] = {0, 0};
+  static int sms = 0;
+  const int oi = (op == SPS_OP_S) ? 0 : 1;
+  if (!sms) {
+    int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far32<SPS_OP_K>, kT32, 0);
-    resident = std::max(1, per_sm) * std::max(1, sms);
   }
-  int splits = 1;
-  double best = 0.0;
-  for (int s = 1; s <= 32; ++s) {
-    long long per_s = (NP + s - 1) / s;
-    per_s = ((per_s + kTS32 - 1) / kTS32) * kTS32;
-    const int s_eff = (int)((NP + per_s - 1) / per_s);
-    const long long blocks = (long long)bx * s_eff;
-    const long long waves = (blocks + resident - 1) / resident;
-    const double eff = (double)blocks / (double)(waves * resident);
-    // prefer fewer splits unless a larger count fills the machine clearly better
-    if (eff > best + 0.02) {
-      best = eff;
-      splits = s_eff;
-    }
-    if (blocks >= 4LL * resident) break;
+  if (smem > 48 * 1024) {
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_far32<SPS_OP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_far32<SPS_OP_K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
-  long long per = (NP + splits - 1) / splits;
-  per = ((per + kTS32 - 1) / kTS32) * kTS32;
-  splits = (int)((NP + per - 1) / per);
-  SPS_TRY(sps_grow(ctx, &ctx->d_part, ctx->cap_part, (size_t)splits * n3));
-  dim3 grid(bx, splits);
+  if (!per_sm[oi]) {
+    if (op == SPS_OP_S)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[oi], k_far32<SPS_OP_S>, kT32, smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[oi], k_far32<SPS_OP_K>, kT32, smem);
+    per_sm[oi] = std::max(1, per_sm[oi]);
+  }
+  const int resident = per_sm[oi] * std::max(1, sms);
+  const int n_tb = (int)((NP + kTPB32 - 1) / kTPB32);
+  // enough items for the atomic queue to balance the load (>= 8 per block)
+  int splits = (int)std::min<long long>(std::max(1, (8 * resident + n_tb - 1) / n_tb), (long long)N);
+  splits = std::min(splits, 64);
+  const int n_items = n_tb * splits;
+  const int grid = std::min(n_items, resident);
+  SPS_TRY(sps_grow(ctx, &ctx->d_part, ctx->cap_part, (size_t)splits * n3 + 1));
+  int* d_work = reinterpret_cast<int*>(ctx->d_part + (size_t)splits * n3);
+  SPS_CUDA(ctx, cudaMemsetAsync(d_work, 0, sizeof(int), ctx->stream));
   {
-  SpsPhase timer(ctx, ph);
-  if (op == SPS_OP_S)
-    k_far32<SPS_OP_S><<<grid, kT32, 0, ctx->stream>>>(N, P, per, ctx->d_X32, ctx->d_N32, ctx->d_W32,
-                                                      ctx->d_sig32, ctx->d_near_ptr,
-                                                      ctx->d_near_idx, ctx->d_part);
-  else
-    k_far32<SPS_OP_K><<<grid, kT32, 0, ctx->stream>>>(N, P, per, ctx->d_X32, ctx->d_N32, ctx->d_W32,
-                                                      ctx->d_sig32, ctx->d_near_ptr,
-                                                      ctx->d_near_idx, ctx->d_part);
-  SPS_LAUNCHED(ctx);
+    SpsPhase timer(ctx, ph);
+    if (op == SPS_OP_S)
+      k_far32<SPS_OP_S><<<grid, kT32, smem, ctx->stream>>>(N, P, spc, n_tb, n_items, splits, ctx->d_rel32,
+                                                          ctx->d_N32, ctx->d_sig32, ctx->d_chi, ctx->d_clo,
+                                                          ctx->d_near_ptr, ctx->d_near_idx, d_work,
+                                                          ctx->d_part);
+    else
+      k_far32<SPS_OP_K><<<grid, kT32, smem, ctx->stream>>>(N, P, spc, n_tb, n_items, splits, ctx->d_rel32,
+                                                          ctx->d_N32, ctx->d_sig32, ctx->d_chi, ctx->d_clo,
+                                                          ctx->d_near_ptr, ctx->d_near_idx, d_work,
+                                                          ctx->d_part);
+    SPS_LAUNCHED(ctx);
   }
   SpsPhase timer(ctx, SPS_PH_FAR_AUX);
   const double s = (op == SPS_OP_S) ? 1.0 / (8.0 * SPS_PI) : -3.0 / (4.0 * SPS_PI);

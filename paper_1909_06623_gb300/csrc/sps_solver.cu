@@ -26,35 +26,43 @@ constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 256;
 constexpr int kChunk = 8;   // dot products per pass of the multi-dot kernel
 
-// partial[j][b] = sum over block b's slice of Q_j . w, for j in [j0, j0+nj)
+// partial[j][b] = sum over block b's slice of Q_j . w for j < k, and
+// partial[k][b] = the slice's w . w: every dot product of one Gram-Schmidt pass
+// plus the squared norm in one launch (fixed slice partition: deterministic).
 __global__ void __launch_bounds__(kRedThreads) k_multidot(long long n, const double* __restrict__ Q,
-                                                         long long ldq, int j0, int nj,
+                                                         long long ldq, int k,
                                                          const double* __restrict__ w,
                                                          double* __restrict__ partial) {
   __shared__ double red[kRedThreads / 32][kChunk];
   const long long per = (n + gridDim.x - 1) / gridDim.x;
   const long long a = blockIdx.x * per, b = min(n, a + per);
-  double acc[kChunk];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j0 = 0; j0 <= k; j0 += kChunk) {
+    const int nj = min(kChunk, k + 1 - j0);
+    double acc[kChunk];
 #pragma unroll
-  for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
-  for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
-    const double wi = w[i];
+    for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
+    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < kChunk; ++q) {
+        const int j = j0 + q;
+        if (q < nj) acc[q] = fma(j < k ? Q[(long long)j * ldq + i] : wi, wi, acc[q]);
+      }
+    }
 #pragma unroll
     for (int q = 0; q < kChunk; ++q)
-      if (q < nj) acc[q] = fma(Q[(long long)(j0 + q) * ldq + i], wi, acc[q]);
-  }
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    __syncthreads();
+    if (lane == 0)
 #pragma unroll
-  for (int q = 0; q < kChunk; ++q)
-    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < kChunk; ++q) red[warp][q] = acc[q];
-  __syncthreads();
-  if (threadIdx.x < nj) {
-    double s = 0.0;
-    for (int k = 0; k < kRedThreads / 32; ++k) s += red[k][threadIdx.x];
-    partial[(long long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+      for (int q = 0; q < kChunk; ++q) red[warp][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < nj) {
+      double s = 0.0;
+      for (int v = 0; v < kRedThreads / 32; ++v) s += red[v][threadIdx.x];
+      partial[(long long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    }
   }
 }
 
@@ -212,29 +220,34 @@ int sps_fail(sps_ctx* ctx, int code, const std::string& msg) {
   return code;
 }
 
-// h[0..k) = Q[0..k)^T w  -> device d_h and host hh
-static int multidot(sps_ctx* ctx, const double* Q, long long ldq, int k, const double* w,
-                    long long n, double* hh) {
-  for (int j0 = 0; j0 < k; j0 += kChunk) {
-    const int nj = std::min(kChunk, k - j0);
-    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-    k_multidot<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(n, Q, ldq, j0, nj, w, ctx->d_red); }
-    SPS_LAUNCHED(ctx);
-  }
+// out[0..k) = Q[0..k)^T w and out[k] = w . w, on the device (no sync)
+static int multidot_dev(sps_ctx* ctx, const double* Q, long long ldq, int k, const double* w,
+                        long long n, double* out) {
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_finish<<<(k + 127) / 128, 128, 0, ctx->stream>>>(k, kRedBlocks, ctx->d_red, ctx->d_h); }
+  k_multidot<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(n, Q, ldq, k, w, ctx->d_red); }
   SPS_LAUNCHED(ctx);
-  if (hh) {
-    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_h, sizeof(double) * k, cudaMemcpyDeviceToHost,
-                                  ctx->stream));
-    SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    std::memcpy(hh, ctx->h_pinned, sizeof(double) * k);
-  }
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_finish<<<(k + 1 + 127) / 128, 128, 0, ctx->stream>>>(k + 1, kRedBlocks, ctx->d_red, out); }
+  SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
 
+static int to_host(sps_ctx* ctx, const double* d, int cnt, double* h) {
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::memcpy(h, ctx->h_pinned, sizeof(double) * cnt);
+  return SPS_OK;
+}
+
+// a . b (host result); uses the multi-dot kernel with a one-vector "basis"
 int sps_dot(sps_ctx* ctx, const double* a, const double* b, long long n, double* out) {
-  return multidot(ctx, a, 0, 1, b, n, out);
+  // k = 1 with Q = a gives out[0] = a.b (out[1] = b.b is ignored)
+  SPS_TRY(multidot_dev(ctx, a, 0, 1, b, n, ctx->d_h));
+  double tmp[2];
+  SPS_TRY(to_host(ctx, ctx->d_h, 2, tmp));
+  *out = tmp[0];
+  return SPS_OK;
 }
 
 static int ensure_gmres(sps_ctx* ctx, long long n, int kmax) {
@@ -249,7 +262,7 @@ static int ensure_gmres(sps_ctx* ctx, long long n, int kmax) {
   c = 0;
   SPS_TRY(sps_grow(ctx, &ctx->d_w, c, (size_t)n));
   c = 0;
-  SPS_TRY(sps_grow(ctx, &ctx->d_h, c, (size_t)kmax + 8));
+  SPS_TRY(sps_grow(ctx, &ctx->d_h, c, 2 * (size_t)kmax + 16));
   c = 0;
   SPS_TRY(sps_grow(ctx, &ctx->d_red, c, (size_t)(kmax + 8) * kRedBlocks));
   ctx->gm_cap_n = (int)n;
@@ -262,48 +275,81 @@ static int apply_A(sps_ctx* ctx, const double* v, double* out, bool fp32) {
   return sps_layer(ctx, SPS_OP_A, v, out, fp32);
 }
 
-// GMRES on A x = b, x0 = 0.  Returns SPS_OK or NOT_CONVERGED.
-static int gmres(sps_ctx* ctx, const double* b, double* x, double tol, int kmax, bool fp32,
-                 int* iters, double* relres) {
+// GMRES on A x = b.  warm: x holds an initial guess (else x0 = 0).  Stops when
+// ||b - A x|| / ||b|| < tol.  Classical Gram-Schmidt applied twice; each
+// Arnoldi step reads its dot products and norm back with one synchronisation:
+// the norm after the second pass is sqrt(||w||^2 - ||h2||^2) (w is then
+// orthogonal to the basis).  Returns SPS_OK or NOT_CONVERGED.
+static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol, int kmax,
+                 bool fp32, int* iters, double* relres) {
   const long long n = 3LL * ctx->NP;
   SPS_TRY(ensure_gmres(ctx, n, kmax));
   double bb = 0.0;
   SPS_TRY(sps_dot(ctx, b, b, n, &bb));
   if (!std::isfinite(bb)) return sps_fail(ctx, SPS_ERR_NONFINITE, "GMRES right-hand side is not finite");
-  const double beta = std::sqrt(bb);
+  const double nb = std::sqrt(bb);
   *iters = 0;
   *relres = 0.0;
-  if (beta == 0.0) {
+  if (nb == 0.0) {
     SPS_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
     return SPS_OK;
   }
   double* Q = ctx->d_Q;
-  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / beta, b, 0.0, nullptr, Q); }
-  SPS_LAUNCHED(ctx);
+  double* w = ctx->d_w;
+  // r0 = b - A x0 (in Q_0 before normalisation)
+  double beta = nb;
+  if (warm) {
+    SPS_TRY(apply_A(ctx, x, w, fp32));
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, b, -1.0, w, Q); }
+    SPS_LAUNCHED(ctx);
+    double rr = 0.0;
+    SPS_TRY(sps_dot(ctx, Q, Q, n, &rr));
+    if (!std::isfinite(rr)) return sps_fail(ctx, SPS_ERR_NONFINITE, "GMRES: non-finite initial residual");
+    beta = std::sqrt(rr);
+    if (beta / nb < tol) {
+      *relres = beta / nb;
+      return SPS_OK;
+    }
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / beta, Q, 0.0, nullptr, Q); }
+    SPS_LAUNCHED(ctx);
+  } else {
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / beta, b, 0.0, nullptr, Q); }
+    SPS_LAUNCHED(ctx);
+  }
   std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), g(kmax + 1, 0.0);
-  std::vector<double> h1(kmax + 1), h2(kmax + 1);
+  std::vector<double> hh(2 * kmax + 4);
   g[0] = beta;
   int k = 0;
-  double res = 1.0;
+  double res = beta / nb;
   auto Hc = [&](int r, int c) -> double& { return H[(size_t)c * (kmax + 1) + r]; };
+  double* d_h1 = ctx->d_h;
+  double* d_h2 = ctx->d_h + kmax + 8;
   for (k = 1; k <= kmax; ++k) {
-    double* w = ctx->d_w;
     SPS_TRY(apply_A(ctx, Q + (long long)(k - 1) * n, w, fp32));
-    // classical Gram-Schmidt, twice
-    SPS_TRY(multidot(ctx, Q, n, k, w, n, h1.data()));
+    SPS_TRY(multidot_dev(ctx, Q, n, k, w, n, d_h1));
     { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, ctx->d_h, w); }
+    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, d_h1, w); }
     SPS_LAUNCHED(ctx);
-    SPS_TRY(multidot(ctx, Q, n, k, w, n, h2.data()));
+    SPS_TRY(multidot_dev(ctx, Q, n, k, w, n, d_h2));
     { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, ctx->d_h, w); }
+    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, d_h2, w); }
     SPS_LAUNCHED(ctx);
-    double ww = 0.0;
-    SPS_TRY(sps_dot(ctx, w, w, n, &ww));
+    // one read-back: h1 (k), h2 (k) and ||w||^2 before the second projection
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, d_h1, sizeof(double) * k, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + k, d_h2, sizeof(double) * (k + 1),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::memcpy(hh.data(), ctx->h_pinned, sizeof(double) * (2 * k + 1));
+    double h2sq = 0.0;
+    for (int j = 0; j < k; ++j) h2sq += hh[k + j] * hh[k + j];
+    const double ww = hh[2 * k] - h2sq;
     if (!std::isfinite(ww)) return sps_fail(ctx, SPS_ERR_NONFINITE, "GMRES: non-finite Krylov vector");
-    const double hk = std::sqrt(ww);
-    for (int j = 0; j < k; ++j) Hc(j, k - 1) = h1[j] + h2[j];
+    const double hk = std::sqrt(std::max(ww, 0.0));
+    for (int j = 0; j < k; ++j) Hc(j, k - 1) = hh[j] + hh[k + j];
     Hc(k, k - 1) = hk;
     if (hk > 0.0) {
       { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
@@ -323,21 +369,21 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, double tol, int kmax,
     Hc(k, k - 1) = 0.0;
     g[k] = -sn[k - 1] * g[k - 1];
     g[k - 1] = cs[k - 1] * g[k - 1];
-    res = std::fabs(g[k]) / beta;
+    res = std::fabs(g[k]) / nb;
     if (res < tol || hk == 0.0) break;
   }
   if (k > kmax) k = kmax;
   std::vector<double> y(k);
   for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int j = i + 1; j < k; ++j) s -= Hc(i, j) * y[j];
-    y[i] = s / Hc(i, i);
+    double sacc = g[i];
+    for (int j = i + 1; j < k; ++j) sacc -= Hc(i, j) * y[j];
+    y[i] = sacc / Hc(i, i);
   }
   std::memcpy(ctx->h_pinned, y.data(), sizeof(double) * k);
-  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_h, ctx->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice,
+  SPS_CUDA(ctx, cudaMemcpyAsync(d_h1, ctx->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice,
                                 ctx->stream));
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, ctx->d_h, 0, x); }
+  k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, d_h1, warm ? 1 : 0, x); }
   SPS_LAUNCHED(ctx);
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *iters = k;
@@ -362,6 +408,8 @@ extern "C" int sps_default_params(sps_params* o) {
   o->bb_variant = 1;
   o->ir_tol = 0.0;
   o->ir_max = 10;
+  o->warm_start = 1;
+  o->bb_safeguard = 0;
   return SPS_OK;
 }
 
@@ -397,7 +445,7 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
   int rc = SPS_OK;
   if ((rc = upload(ctx, &ctx->d_unit_nrm, T.unit_nrm)) || (rc = upload(ctx, &ctx->d_unit_w, T.unit_w)) ||
       (rc = upload(ctx, &ctx->d_anal, T.anal)) || (rc = upload(ctx, &ctx->d_synthS, sS)) ||
-      (rc = upload(ctx, &ctx->d_synthK, sK)) || (rc = upload(ctx, &ctx->d_kappa, T.kappa)) ||
+      (rc = upload(ctx, &ctx->d_synthK, sK)) || (rc = upload(ctx, &ctx->d_kappa, T.kappa)) || (rc = upload(ctx, &ctx->d_potfac, T.potfac)) ||
       (rc = upload(ctx, &ctx->d_anal32, f32(T.anal))) || (rc = upload(ctx, &ctx->d_synthS32, f32(sS))) ||
       (rc = upload(ctx, &ctx->d_synthK32, f32(sK)))) {
     sps_destroy(ctx);
@@ -415,11 +463,12 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
 extern "C" int sps_destroy(sps_ctx* ctx) {
   if (!ctx) return SPS_OK;
   void* bufs[] = {ctx->d_unit_nrm, ctx->d_unit_w, ctx->d_anal, ctx->d_synthS, ctx->d_synthK,
-                  ctx->d_kappa, ctx->d_anal32, ctx->d_synthS32, ctx->d_synthK32, ctx->d_pos, ctx->d_rad,
-                  ctx->d_X, ctx->d_Nrm, ctx->d_W, ctx->d_X32, ctx->d_N32, ctx->d_W32,
-                  ctx->d_near_ptr, ctx->d_near_idx, ctx->d_coef, ctx->d_fcoef, ctx->d_mom,
+                  ctx->d_kappa, ctx->d_potfac, ctx->d_anal32, ctx->d_synthS32, ctx->d_synthK32, ctx->d_pos, ctx->d_rad,
+                  ctx->d_X, ctx->d_Nrm, ctx->d_W, ctx->d_rel32, ctx->d_N32, ctx->d_W32, ctx->d_chi, ctx->d_clo,
+                  ctx->d_near_ptr, ctx->d_near_idx, ctx->d_close_node, ctx->d_close_ptr,
+                  ctx->d_close_src, ctx->d_coef, ctx->d_fcoef, ctx->d_mom,
                   ctx->d_tmp3, ctx->d_sig32, ctx->d_part, ctx->d_Q, ctx->d_w, ctx->d_h, ctx->d_red,
-                  ctx->d_rho, ctx->d_zeta, ctx->d_b, ctx->d_u, ctx->d_r, ctx->d_dz, ctx->d_cij,
+                  ctx->d_rho, ctx->d_zeta, ctx->d_zeta_nc, ctx->d_b, ctx->d_u, ctx->d_r, ctx->d_dz, ctx->d_cij,
                   ctx->d_cphi, ctx->d_cn, ctx->d_ccount, ctx->d_cptr, ctx->d_inc_ptr, ctx->d_inc,
                   ctx->d_cub, ctx->d_keys, ctx->d_vals, ctx->d_keys2, ctx->d_vals2, ctx->d_gam,
                   ctx->d_g, ctx->d_gam_new, ctx->d_g_new, ctx->d_q, ctx->d_Mg, ctx->d_FT,
@@ -463,13 +512,14 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
   }
   if (n > ctx->capN) {
     double** d64[] = {&ctx->d_pos, &ctx->d_rad, &ctx->d_X, &ctx->d_Nrm, &ctx->d_W, &ctx->d_coef,
-                      &ctx->d_fcoef, &ctx->d_mom, &ctx->d_tmp3, &ctx->d_rho, &ctx->d_zeta, &ctx->d_b,
+                      &ctx->d_fcoef, &ctx->d_mom, &ctx->d_tmp3, &ctx->d_rho, &ctx->d_zeta,
+                      &ctx->d_zeta_nc, &ctx->d_b,
                       &ctx->d_u, &ctx->d_r, &ctx->d_dz, &ctx->d_FT, &ctx->d_Unc, &ctx->d_Uc};
     for (auto p : d64) {
       cudaFree(*p);
       *p = nullptr;
     }
-    float** d32[] = {&ctx->d_X32, &ctx->d_N32, &ctx->d_W32, &ctx->d_sig32};
+    float** d32[] = {&ctx->d_rel32, &ctx->d_N32, &ctx->d_W32, &ctx->d_sig32, &ctx->d_chi, &ctx->d_clo};
     for (auto p : d32) {
       cudaFree(*p);
       *p = nullptr;
@@ -485,7 +535,8 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
                {&ctx->d_Nrm, 3 * (size_t)NP}, {&ctx->d_W, (size_t)NP}, {&ctx->d_coef, (size_t)n * NR},
                {&ctx->d_fcoef, (size_t)n * E * sps::kFieldsK * 2}, {&ctx->d_mom, 6 * (size_t)n},
                {&ctx->d_tmp3, 3 * (size_t)NP}, {&ctx->d_rho, 3 * (size_t)NP},
-               {&ctx->d_zeta, 3 * (size_t)NP}, {&ctx->d_b, 3 * (size_t)NP}, {&ctx->d_u, 3 * (size_t)NP},
+               {&ctx->d_zeta, 3 * (size_t)NP}, {&ctx->d_zeta_nc, 3 * (size_t)NP},
+               {&ctx->d_b, 3 * (size_t)NP}, {&ctx->d_u, 3 * (size_t)NP},
                {&ctx->d_r, 3 * (size_t)NP}, {&ctx->d_dz, 3 * (size_t)NP}, {&ctx->d_FT, 6 * (size_t)n},
                {&ctx->d_Unc, 6 * (size_t)n}, {&ctx->d_Uc, 6 * (size_t)n}};
     for (auto& e : a64) {
@@ -495,8 +546,8 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
     struct {
       float** p;
       size_t n;
-    } a32[] = {{&ctx->d_X32, 3 * (size_t)NP}, {&ctx->d_N32, 3 * (size_t)NP}, {&ctx->d_W32, (size_t)NP},
-               {&ctx->d_sig32, 3 * (size_t)NP}};
+    } a32[] = {{&ctx->d_rel32, 3 * (size_t)NP}, {&ctx->d_N32, 3 * (size_t)NP}, {&ctx->d_W32, (size_t)NP},
+               {&ctx->d_sig32, 3 * (size_t)NP}, {&ctx->d_chi, 3 * (size_t)n}, {&ctx->d_clo, 3 * (size_t)n}};
     for (auto& e : a32) {
       c = 0;
       SPS_TRY(sps_grow(ctx, e.p, c, e.n));
@@ -505,12 +556,14 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
     SPS_TRY(sps_grow(ctx, &ctx->d_near_ptr, c, (size_t)n + 1));
     ctx->capN = n;
   }
+  if (n != ctx->N) ctx->zeta_nc_n = 0;
   ctx->N = n;
   ctx->NP = (int)NP;
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_rad, radii, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   SPS_TRY(sps_launch_grid(ctx));
   SPS_TRY(sps_launch_near_lists(ctx));
+  SPS_TRY(sps_launch_close_lists(ctx));
   ctx->have_geom = true;
   return SPS_OK;
 }
@@ -541,7 +594,10 @@ extern "C" int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double
 // ---------------------------------------------------------------------------
 // mobility solve on the current geometry
 // ---------------------------------------------------------------------------
-static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats* st) {
+// zeta: the density unknown of eq. rigidbodyrho for this solve; with warm it
+// holds an initial guess on entry (a previous solution for similar forces).
+static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats* st, double* zeta,
+                          bool warm) {
   const long long n = 3LL * ctx->NP;
   const bool mixed = ctx->prm.precision == SPS_MIXED;
   const bool refine = mixed && ctx->prm.ir_tol > 0;
@@ -553,7 +609,7 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
   SPS_LAUNCHED(ctx);
   int its = 0;
   double res = 0.0;
-  int rc = gmres(ctx, ctx->d_b, ctx->d_zeta, ctx->prm.gmres_tol, ctx->prm.gmres_max, mixed, &its, &res);
+  int rc = gmres(ctx, ctx->d_b, zeta, warm, ctx->prm.gmres_tol, ctx->prm.gmres_max, mixed, &its, &res);
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
   int total_its = its;
   double final_res = res;
@@ -564,7 +620,7 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
     const double nb = std::sqrt(bb);
     int sweep = 0;
     for (; sweep < ctx->prm.ir_max; ++sweep) {
-      SPS_TRY(apply_A(ctx, ctx->d_zeta, ctx->d_r, false));
+      SPS_TRY(apply_A(ctx, zeta, ctx->d_r, false));
       { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
       k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_b, -1.0, ctx->d_r, ctx->d_r); }
       SPS_LAUNCHED(ctx);
@@ -574,11 +630,12 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
       if (final_res < ctx->prm.ir_tol) break;
       int its2 = 0;
       double res2 = 0;
-      int rc2 = gmres(ctx, ctx->d_r, ctx->d_dz, ctx->prm.gmres_tol, ctx->prm.gmres_max, true, &its2, &res2);
+      int rc2 = gmres(ctx, ctx->d_r, ctx->d_dz, false, ctx->prm.gmres_tol, ctx->prm.gmres_max, true,
+                      &its2, &res2);
       if (rc2 != SPS_OK && rc2 != SPS_ERR_NOT_CONVERGED) return rc2;
       total_its += its2;
       { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-      k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_zeta, 1.0, ctx->d_dz, ctx->d_zeta); }
+      k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, zeta, 1.0, ctx->d_dz, zeta); }
       SPS_LAUNCHED(ctx);
     }
     if (st) st->ir_sweeps += sweep;
@@ -586,7 +643,7 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
   }
   // u = S[rho + zeta]
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_rho, 1.0, ctx->d_zeta, ctx->d_tmp3); }
+  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_rho, 1.0, zeta, ctx->d_tmp3); }
   SPS_LAUNCHED(ctx);
   SPS_TRY(sps_layer(ctx, SPS_OP_S, ctx->d_tmp3, ctx->d_u, mixed && !refine));
   SPS_TRY(sps_launch_moments(ctx, ctx->d_u, ctx->d_mom));
@@ -620,7 +677,7 @@ extern "C" int sps_mobility_apply(sps_ctx* ctx, int n, const double* pos, const 
   stats_begin(ctx, st, &l0);
   int rc = sps_set_geometry(ctx, n, pos, radii);
   if (rc == SPS_OK) rc = check_finite_host(ctx, FT, 6LL * n, "force/torque");
-  if (rc == SPS_OK) rc = mobility_solve(ctx, FT, UO, st);
+  if (rc == SPS_OK) rc = mobility_solve(ctx, FT, UO, st, ctx->d_zeta, false);
   if (rc == SPS_OK || rc == SPS_ERR_NOT_CONVERGED) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
@@ -680,10 +737,11 @@ static int ensure_bb(sps_ctx* ctx, int nc) {
   return SPS_OK;
 }
 
-// out = M gamma = D^T M D gamma; leaves M D gamma in d_Uc
-static int apply_M(sps_ctx* ctx, const double* gam, double* out, sps_stats* st) {
+// out = M gamma = D^T M D gamma; leaves M D gamma in d_Uc.  warm: start GMRES
+// from the density of the previous M gamma solve (same contact geometry).
+static int apply_M(sps_ctx* ctx, const double* gam, double* out, sps_stats* st, bool warm) {
   SPS_TRY(sps_launch_D(ctx, gam, ctx->d_FT));
-  int rc = mobility_solve(ctx, ctx->d_FT, ctx->d_Uc, st);
+  int rc = mobility_solve(ctx, ctx->d_FT, ctx->d_Uc, st, ctx->d_zeta, warm);
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
   if (st) st->mvops += 1;
   SPS_TRY(sps_launch_DT(ctx, ctx->d_Uc, out));
@@ -709,8 +767,10 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
   if (!(dt > 0)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "dt must be positive");
   SPS_TRY(sps_set_geometry(ctx, n, pos, radii));
   SPS_TRY(check_finite_host(ctx, FT_ext, 6LL * n, "external force/torque"));
-  // 1. U_nc
-  int rc = mobility_solve(ctx, FT_ext, ctx->d_Unc, st);
+  // 1. U_nc (warm start from the previous step's density when the size matches)
+  const bool warm_nc = ctx->prm.warm_start && ctx->zeta_nc_n == ctx->NP;
+  int rc = mobility_solve(ctx, FT_ext, ctx->d_Unc, st, ctx->d_zeta_nc, warm_nc);
+  ctx->zeta_nc_n = (rc == SPS_OK) ? ctx->NP : 0;
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
   int worst = rc;
   // 2. contacts and D
@@ -738,7 +798,7 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
     int iters = 0;
     if (!(phi < tol)) {
       // alpha_0 = g^T g / g^T M g
-      rc = apply_M(ctx, ctx->d_g, ctx->d_Mg, st);
+      rc = apply_M(ctx, ctx->d_g, ctx->d_Mg, st, false);
       if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
       if (rc) worst = rc;
       double gMg = 0.0;
@@ -749,7 +809,7 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
         { SpsPhase timer_(ctx, SPS_PH_BBPGD);
         k_bb_step<<<tb, 256, 0, ctx->stream>>>(nc, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new); }
         SPS_LAUNCHED(ctx);
-        rc = apply_M(ctx, ctx->d_gam_new, ctx->d_Mg, st);
+        rc = apply_M(ctx, ctx->d_gam_new, ctx->d_Mg, st, ctx->prm.warm_start && j >= 2);
         if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
         if (rc) worst = rc;
         { SpsPhase timer_(ctx, SPS_PH_BBPGD);
@@ -761,12 +821,16 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
         iters = j;
         phi = std::sqrt(s5[0]);
         if (phi < tol) break;
-        if (ctx->prm.bb_variant == 1) {
-          if (!(s5[2] > 0)) bb_rc = SPS_ERR_BREAKDOWN;
-          else alpha = s5[1] / s5[2];
+        const bool ok = (ctx->prm.bb_variant == 1) ? (s5[2] > 0) : (s5[2] > 0 && s5[3] > 0);
+        if (!ok) {
+          // s^T y <= 0: Algorithm 1 defines no step; stop, or keep the previous one
+          if (ctx->prm.bb_safeguard) {
+            if (st) st->bb_safeguards += 1;
+          } else {
+            bb_rc = SPS_ERR_BREAKDOWN;
+          }
         } else {
-          if (!(s5[2] > 0 && s5[3] > 0)) bb_rc = SPS_ERR_BREAKDOWN;
-          else alpha = s5[2] / s5[3];
+          alpha = (ctx->prm.bb_variant == 1) ? s5[1] / s5[2] : s5[2] / s5[3];
         }
       }
       if (bb_rc == SPS_OK && !(phi < tol)) bb_rc = SPS_ERR_NOT_CONVERGED;

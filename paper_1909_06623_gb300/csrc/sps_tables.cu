@@ -101,6 +101,21 @@ void build_tables(int p, Tables& T) {
   T.multS.assign(NR, 0.0);
   T.multK.assign(NR, 0.0);
   T.kappa.assign(NC, 0.0);
+  // near-field potentials per degree n (eq. ssgext in Lamb form):
+  //   0 a (on sW): n/(2(2n+1))       5 a (on sV): n/((2n+1)(2n+3))
+  //   1 d (on sX): 1/(2n+1)          2 alpha (on sW): (2-n)/(2(2n-1))
+  //   3 beta (on sW): (n+1)/(2n-1)   4 2 beta - P (on sW): 2(n+1)/(2n-1) - n
+  T.potfac.assign((size_t)(p + 1) * 6, 0.0);
+  for (int n = 0; n <= p; ++n) {
+    const double d = n;
+    double* f = &T.potfac[(size_t)n * 6];
+    f[0] = d / (2 * (2 * d + 1));
+    f[1] = 1.0 / (2 * d + 1);
+    f[2] = (2 - d) / (2 * (2 * d - 1));
+    f[3] = (d + 1) / (2 * d - 1);
+    f[4] = 2 * (d + 1) / (2 * d - 1) - d;
+    f[5] = d / ((2 * d + 1) * (2 * d + 3));
+  }
 
   std::vector<double> Pl;
   const int Lq = p + 1;  // Pbar up to degree p+1 for the ladder relation

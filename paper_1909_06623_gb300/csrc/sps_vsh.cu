@@ -126,48 +126,26 @@ __constant__ Field c_fieldsS[sps::kFieldsS] = {
     {POT_A, DX},  {POT_A, DY},  {POT_A, DZ},  {POT_D, DX},  {POT_D, DY},
     {POT_D, DZ},  {POT_AL, DX}, {POT_AL, DY}, {POT_AL, DZ}, {POT_BE, D1}};
 
-// potential coefficient c_pot(n, m) for signed m (zero outside 0 <= |m| <= n <= p)
+// potential coefficient c_pot(n, m) for signed m (zero outside 0 <= |m| <= n <= p).
+// fac[n*6 + pot] holds the per-degree factor of each potential (host table);
+// the potential a also takes fac[n*6 + 5] times sV.
 __device__ double2 pot_coef(const double* __restrict__ cs, const double* __restrict__ kappa,
-                            int p, int NC, int pot, int n, int m) {
+                            const double* __restrict__ fac, int p, int NC, int pot, int n, int m) {
   if (n < 0 || n > p || m > n || -m > n) return make_double2(0.0, 0.0);
   const int mm = m < 0 ? -m : m;
   const int ci = n * (n + 1) / 2 + mm;
-  const double vr = cs[(0 * NC + ci) * 2], vi = cs[(0 * NC + ci) * 2 + 1];
-  const double wr = cs[(1 * NC + ci) * 2], wi = cs[(1 * NC + ci) * 2 + 1];
-  const double xr = cs[(2 * NC + ci) * 2], xi = cs[(2 * NC + ci) * 2 + 1];
-  const double dn = n;
+  const double f = fac[n * 6 + pot];
   double re, im;
-  switch (pot) {
-    case POT_A: {
-      const double fv = dn / ((2 * dn + 1) * (2 * dn + 3)), fw = dn / (2 * (2 * dn + 1));
-      re = fv * vr + fw * wr;
-      im = fv * vi + fw * wi;
-      break;
-    }
-    case POT_D: {
-      const double f = 1.0 / (2 * dn + 1);
-      re = f * xr;
-      im = f * xi;
-      break;
-    }
-    case POT_AL: {
-      const double f = (2 - dn) / (2 * (2 * dn - 1));
-      re = f * wr;
-      im = f * wi;
-      break;
-    }
-    case POT_BE: {
-      const double f = (dn + 1) / (2 * dn - 1);
-      re = f * wr;
-      im = f * wi;
-      break;
-    }
-    default: {  // POT_Q: 2 beta - P
-      const double f = 2 * (dn + 1) / (2 * dn - 1) - dn;
-      re = f * wr;
-      im = f * wi;
-      break;
-    }
+  if (pot == POT_A) {
+    const double fv = fac[n * 6 + 5];
+    re = fv * cs[(0 * NC + ci) * 2] + f * cs[(1 * NC + ci) * 2];
+    im = fv * cs[(0 * NC + ci) * 2 + 1] + f * cs[(1 * NC + ci) * 2 + 1];
+  } else if (pot == POT_D) {
+    re = f * cs[(2 * NC + ci) * 2];
+    im = f * cs[(2 * NC + ci) * 2 + 1];
+  } else {
+    re = f * cs[(1 * NC + ci) * 2];
+    im = f * cs[(1 * NC + ci) * 2 + 1];
   }
   const double k = kappa[ci];
   re *= k;
@@ -187,10 +165,10 @@ __device__ __forceinline__ double2 mul_i(double2 a, double s) {  // s * i * a
   return make_double2(-s * a.y, s * a.x);
 }
 
-__device__ double2 field_coef(const double* cs, const double* kappa, int p, int NC, Field f, int n,
-                              int m) {
+__device__ double2 field_coef(const double* cs, const double* kappa, const double* fac, int p, int NC,
+                              Field f, int n, int m) {
   const int pot = f.pot;
-  auto c = [&](int nn, int mm) { return pot_coef(cs, kappa, p, NC, pot, nn, mm); };
+  auto c = [&](int nn, int mm) { return pot_coef(cs, kappa, fac, p, NC, pot, nn, mm); };
   switch (f.der) {
     case D1: return c(n, m);
     case DX: return cadd(c(n - 1, m - 1), c(n - 1, m + 1), 0.5, -0.5);
@@ -215,7 +193,7 @@ __device__ double2 field_coef(const double* cs, const double* kappa, int p, int 
 template <int F>
 __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
                             const double* __restrict__ coef, const double* __restrict__ kappa,
-                            double* __restrict__ fcoef) {
+                            const double* __restrict__ fac, double* __restrict__ fcoef) {
   const int s = blockIdx.x;
   const double* cs = coef + (long long)s * NR;
   const Field* fl = (F == sps::kFieldsK) ? c_fieldsK : c_fieldsS;
@@ -228,7 +206,7 @@ __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
       ++m;
     }
     const int n = m + (e - off);
-    double2 v = field_coef(cs, kappa, p, NC, fl[f], n, m);
+    double2 v = field_coef(cs, kappa, fac, p, NC, fl[f], n, m);
     const double eps = (m == 0) ? 1.0 : 2.0;
     fcoef[((long long)s * E + e) * F * 2 + 2 * f] = eps * v.x;
     fcoef[((long long)s * E + e) * F * 2 + 2 * f + 1] = eps * v.y;
@@ -238,12 +216,95 @@ __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
 // ---------------------------------------------------------------------------
 // near-field evaluation: one block per target sphere, one thread per node
 // ---------------------------------------------------------------------------
+// Contribution of source sphere j's exterior single layer at one target:
+// the velocity (F = kFieldsS; times a_j by the caller) or the traction with
+// target normal v (F = kFieldsK).  (x, y, z): target in sphere j's unit frame.
+// cf: field coefficients of sphere j, E entries x F complex (entry-major).
+template <int F, typename T, typename C>
+__device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T x, T y, T z, T vx,
+                                             T vy, T vz, T& ox, T& oy, T& oz) {
+  const T r2 = x * x + y * y + z * z, ir2 = T(1) / r2;
+  T acc[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] = T(0);
+  T dre = T(1) / sqrt(r2), dim = T(0);  // H_m^m
+  int e = 0;
+  for (int m = 0; m <= L; ++m) {
+    if (m > 0) {
+      const T fm = -(T)(2 * m - 1) * ir2;
+      const T re = fm * (x * dre - y * dim), im = fm * (x * dim + y * dre);
+      dre = re;
+      dim = im;
+    }
+    T hre = dre, him = dim, pre = T(0), pim = T(0);
+    for (int n = m; n <= L; ++n, ++e) {
+      const C* cf = cf0 + e * F * 2;
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+        acc[f] = fma((T)cf[2 * f], hre, fma(-(T)cf[2 * f + 1], him, acc[f]));
+      const T f1 = (T)(2 * n + 1) * z, f2 = (T)(n * n - m * m);
+      const T nre = -(f1 * hre + f2 * pre) * ir2, nim = -(f1 * him + f2 * pim) * ir2;
+      pre = hre;
+      pim = him;
+      hre = nre;
+      him = nim;
+    }
+  }
+  if (F == sps::kFieldsK) {
+    // Hessians: [xx, xy, xz, yy, yz, zz]
+    const T* HA = acc;
+    const T* HD = acc + 6;
+    const T* GL = acc + 12;
+    const T* HL = acc + 15;
+    const T* GB = acc + 21;
+    const T Qs = acc[24];
+    auto hv = [](const T* H, T a, T b, T c, T& o0, T& o1, T& o2) {
+      o0 = H[0] * a + H[1] * b + H[2] * c;
+      o1 = H[1] * a + H[3] * b + H[4] * c;
+      o2 = H[2] * a + H[4] * b + H[5] * c;
+    };
+    T t0, t1, t2, u0, u1, u2;
+    // Q v + 2 HA v
+    hv(HA, vx, vy, vz, t0, t1, t2);
+    T tx = Qs * vx + 2 * t0, ty = Qs * vy + 2 * t1, tz = Qs * vz + 2 * t2;
+    // x x (HD v) + HD (v x x)
+    hv(HD, vx, vy, vz, u0, u1, u2);
+    tx += y * u2 - z * u1;
+    ty += z * u0 - x * u2;
+    tz += x * u1 - y * u0;
+    const T cx = vy * z - vz * y, cy = vz * x - vx * z, cz = vx * y - vy * x;
+    hv(HD, cx, cy, cz, u0, u1, u2);
+    tx += u0;
+    ty += u1;
+    tz += u2;
+    // 2 (GL (x.v) + x (GL.v)) + 2 r^2 HL v + x (GB.v) + GB (x.v)
+    const T xv = x * vx + y * vy + z * vz;
+    const T glv = GL[0] * vx + GL[1] * vy + GL[2] * vz;
+    const T gbv = GB[0] * vx + GB[1] * vy + GB[2] * vz;
+    hv(HL, vx, vy, vz, u0, u1, u2);
+    ox = tx + 2 * (GL[0] * xv + x * glv) + 2 * r2 * u0 + x * gbv + GB[0] * xv;
+    oy = ty + 2 * (GL[1] * xv + y * glv) + 2 * r2 * u1 + y * gbv + GB[1] * xv;
+    oz = tz + 2 * (GL[2] * xv + z * glv) + 2 * r2 * u2 + z * gbv + GB[2] * xv;
+  } else {
+    const T* GA = acc;
+    const T* GD = acc + 3;
+    const T* GL = acc + 6;
+    const T Be = acc[9];
+    ox = GA[0] + (y * GD[2] - z * GD[1]) + r2 * GL[0] + x * Be;
+    oy = GA[1] + (z * GD[0] - x * GD[2]) + r2 * GL[1] + y * Be;
+    oz = GA[2] + (x * GD[1] - y * GD[0]) + r2 * GL[2] + z * Be;
+  }
+}
+
+// One block per target sphere, one thread per node; source spheres from the
+// near list staged in shared memory.  skip_r2 > 0: entries with r^2 < skip_r2
+// (in units of the source radius) are left to k_near_close (FP64).
 template <int F, typename T>
 __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict__ pos,
                             const double* __restrict__ rad, const double* __restrict__ X,
                             const double* __restrict__ Nr, const int* __restrict__ near_ptr,
                             const int* __restrict__ near_idx, const double* __restrict__ fcoef,
-                            double* __restrict__ out) {
+                            double skip_r2, double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char sraw[];
   T* sc = reinterpret_cast<T*>(sraw);
   const int i = blockIdx.x;
@@ -266,83 +327,19 @@ __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict
     for (int e = threadIdx.x; e < E * F * 2; e += blockDim.x) sc[e] = (T)src[e];
     __syncthreads();
     const double aj = rad[j], ia = 1.0 / aj;
+    if (skip_r2 > 0.0 && sps_close_r2(pos, ia, gx, gy, gz, j) < skip_r2) continue;
     const T x = (T)((gx - pos[3 * j]) * ia), y = (T)((gy - pos[3 * j + 1]) * ia),
             z = (T)((gz - pos[3 * j + 2]) * ia);
-    const T r2 = x * x + y * y + z * z, ir2 = T(1) / r2;
-    T acc[F];
-#pragma unroll
-    for (int f = 0; f < F; ++f) acc[f] = T(0);
-    T dre = T(1) / sqrt(r2), dim = T(0);  // H_m^m
-    int e = 0;
-    for (int m = 0; m <= L; ++m) {
-      if (m > 0) {
-        const T fm = -(T)(2 * m - 1) * ir2;
-        const T re = fm * (x * dre - y * dim), im = fm * (x * dim + y * dre);
-        dre = re;
-        dim = im;
-      }
-      T hre = dre, him = dim, pre = T(0), pim = T(0);
-      for (int n = m; n <= L; ++n, ++e) {
-        const T* cf = sc + e * F * 2;
-#pragma unroll
-        for (int f = 0; f < F; ++f) acc[f] = fma(cf[2 * f], hre, fma(-cf[2 * f + 1], him, acc[f]));
-        const T f1 = (T)(2 * n + 1) * z, f2 = (T)(n * n - m * m);
-        const T nre = -(f1 * hre + f2 * pre) * ir2, nim = -(f1 * him + f2 * pim) * ir2;
-        pre = hre;
-        pim = him;
-        hre = nre;
-        him = nim;
-      }
-    }
+    T tx, ty, tz;
+    near_contrib<F, T, T>(sc, L, x, y, z, vx, vy, vz, tx, ty, tz);
     if (F == sps::kFieldsK) {
-      // Hessians: [xx, xy, xz, yy, yz, zz]
-      const T* HA = acc;
-      const T* HD = acc + 6;
-      const T* GL = acc + 12;
-      const T* HL = acc + 15;
-      const T* GB = acc + 21;
-      const T Qs = acc[24];
-      auto hv = [](const T* H, T a, T b, T c, T& o0, T& o1, T& o2) {
-        o0 = H[0] * a + H[1] * b + H[2] * c;
-        o1 = H[1] * a + H[3] * b + H[4] * c;
-        o2 = H[2] * a + H[4] * b + H[5] * c;
-      };
-      T t0, t1, t2, u0, u1, u2;
-      // Q v + 2 HA v
-      hv(HA, vx, vy, vz, t0, t1, t2);
-      T tx = Qs * vx + 2 * t0, ty = Qs * vy + 2 * t1, tz = Qs * vz + 2 * t2;
-      // x x (HD v) + HD (v x x)
-      hv(HD, vx, vy, vz, u0, u1, u2);
-      tx += y * u2 - z * u1;
-      ty += z * u0 - x * u2;
-      tz += x * u1 - y * u0;
-      const T cx = vy * z - vz * y, cy = vz * x - vx * z, cz = vx * y - vy * x;
-      hv(HD, cx, cy, cz, u0, u1, u2);
-      tx += u0;
-      ty += u1;
-      tz += u2;
-      // 2 (GL (x.v) + x (GL.v)) + 2 r^2 HL v + x (GB.v) + GB (x.v)
-      const T xv = x * vx + y * vy + z * vz;
-      const T glv = GL[0] * vx + GL[1] * vy + GL[2] * vz;
-      const T gbv = GB[0] * vx + GB[1] * vy + GB[2] * vz;
-      hv(HL, vx, vy, vz, u0, u1, u2);
-      tx += 2 * (GL[0] * xv + x * glv) + 2 * r2 * u0 + x * gbv + GB[0] * xv;
-      ty += 2 * (GL[1] * xv + y * glv) + 2 * r2 * u1 + y * gbv + GB[1] * xv;
-      tz += 2 * (GL[2] * xv + z * glv) + 2 * r2 * u2 + z * gbv + GB[2] * xv;
       ox += (double)tx;
       oy += (double)ty;
       oz += (double)tz;
     } else {
-      const T* GA = acc;
-      const T* GD = acc + 3;
-      const T* GL = acc + 6;
-      const T Be = acc[9];
-      const T ux = GA[0] + (y * GD[2] - z * GD[1]) + r2 * GL[0] + x * Be;
-      const T uy = GA[1] + (z * GD[0] - x * GD[2]) + r2 * GL[1] + y * Be;
-      const T uz = GA[2] + (x * GD[1] - y * GD[0]) + r2 * GL[2] + z * Be;
-      ox += aj * (double)ux;
-      oy += aj * (double)uy;
-      oz += aj * (double)uz;
+      ox += aj * (double)tx;
+      oy += aj * (double)ty;
+      oz += aj * (double)tz;
     }
   }
   if (valid) {
@@ -352,8 +349,49 @@ __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict
   }
 }
 
+// FP64 near entries of the mixed path: one thread per close node, its close
+// source spheres in near-list order (coefficients read through the cache).
+template <int F>
+__global__ void k_near_close(int N, int P, int L, int E, int n_close, const int* __restrict__ cnode,
+                             const int* __restrict__ cptr, const int* __restrict__ csrc,
+                             const double* __restrict__ pos, const double* __restrict__ rad,
+                             const double* __restrict__ X, const double* __restrict__ Nr,
+                             const double* __restrict__ fcoef, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_close) return;
+  const long long NP = (long long)N * P;
+  const long long g = cnode[t];
+  const double gx = X[g], gy = X[NP + g], gz = X[2 * NP + g];
+  double vx = 0, vy = 0, vz = 0;
+  if (F == sps::kFieldsK) {
+    vx = Nr[g];
+    vy = Nr[NP + g];
+    vz = Nr[2 * NP + g];
+  }
+  double ox = 0, oy = 0, oz = 0;
+  for (int q = cptr[t]; q < cptr[t + 1]; ++q) {
+    const int j = csrc[q];
+    const double aj = rad[j], ia = 1.0 / aj;
+    const double x = (gx - pos[3 * j]) * ia, y = (gy - pos[3 * j + 1]) * ia, z = (gz - pos[3 * j + 2]) * ia;
+    double tx, ty, tz;
+    near_contrib<F, double, double>(fcoef + (long long)j * E * F * 2, L, x, y, z, vx, vy, vz, tx, ty, tz);
+    if (F == sps::kFieldsK) {
+      ox += tx;
+      oy += ty;
+      oz += tz;
+    } else {
+      ox += aj * tx;
+      oy += aj * ty;
+      oz += aj * tz;
+    }
+  }
+  out[g] += ox;
+  out[NP + g] += oy;
+  out[2 * NP + g] += oz;
+}
+
 template <int F, typename T>
-int launch_near_eval(sps_ctx* ctx, double* out) {
+int launch_near_eval(sps_ctx* ctx, double skip_r2, double* out) {
   const int N = ctx->N, P = ctx->T.P, L = ctx->T.L, E = ctx->T.E;
   const int threads = ((P + 31) / 32) * 32;
   const size_t sm = sizeof(T) * E * F * 2;
@@ -362,7 +400,17 @@ int launch_near_eval(sps_ctx* ctx, double* out) {
                                        (int)sm));
   k_near_eval<F, T><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
                                                       ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
-                                                      ctx->d_fcoef, out);
+                                                      ctx->d_fcoef, skip_r2, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+template <int F>
+int launch_near_close(sps_ctx* ctx, double* out) {
+  if (ctx->n_close == 0) return SPS_OK;
+  k_near_close<F><<<(ctx->n_close + 63) / 64, 64, 0, ctx->stream>>>(
+      ctx->N, ctx->T.P, ctx->T.L, ctx->T.E, ctx->n_close, ctx->d_close_node, ctx->d_close_ptr,
+      ctx->d_close_src, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm, ctx->d_fcoef, out);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -410,24 +458,37 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
     SpsPhase timer(ctx, SPS_PH_SELF);
     if (S)
       k_near_coef<sps::kFieldsS><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef,
-                                                             ctx->d_kappa, ctx->d_fcoef);
+                                                             ctx->d_kappa, ctx->d_potfac, ctx->d_fcoef);
     else
       k_near_coef<sps::kFieldsK><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef,
-                                                             ctx->d_kappa, ctx->d_fcoef);
+                                                             ctx->d_kappa, ctx->d_potfac, ctx->d_fcoef);
     SPS_LAUNCHED(ctx);
   }
   SpsPhase timer(ctx, S ? SPS_PH_NEAR_S : SPS_PH_NEAR_K);
-  if (S) return fp32 ? launch_near_eval<sps::kFieldsS, float>(ctx, out)
-                     : launch_near_eval<sps::kFieldsS, double>(ctx, out);
-  return fp32 ? launch_near_eval<sps::kFieldsK, float>(ctx, out)
-              : launch_near_eval<sps::kFieldsK, double>(ctx, out);
+  // mixed path: FP32 for near entries farther than kCloseRadius source radii,
+  // FP64 for the close ones (where the expansion's terms do not decay)
+  const double skip = fp32 ? sps::kCloseRadius * sps::kCloseRadius : 0.0;
+  if (S) {
+    if (!fp32) return launch_near_eval<sps::kFieldsS, double>(ctx, 0.0, out);
+    SPS_TRY((launch_near_eval<sps::kFieldsS, float>(ctx, skip, out)));
+    return launch_near_close<sps::kFieldsS>(ctx, out);
+  }
+  if (!fp32) return launch_near_eval<sps::kFieldsK, double>(ctx, 0.0, out);
+  SPS_TRY((launch_near_eval<sps::kFieldsK, float>(ctx, skip, out)));
+  return launch_near_close<sps::kFieldsK>(ctx, out);
 }
 
+#ifndef SPS_MIXED_VSH
+#define SPS_MIXED_VSH 1
+#endif
+#ifndef SPS_MIXED_NEAR
+#define SPS_MIXED_NEAR 1
+#endif
 int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32) {
-  SPS_TRY(sps_launch_analysis(ctx, sig, fp32));
-  SPS_TRY(sps_launch_self(ctx, op, sig, out, fp32));
+  SPS_TRY(sps_launch_analysis(ctx, sig, fp32 && SPS_MIXED_VSH));
+  SPS_TRY(sps_launch_self(ctx, op, sig, out, fp32 && SPS_MIXED_VSH));
   const int kop = (op == SPS_OP_S) ? SPS_OP_S : SPS_OP_K;
-  SPS_TRY(sps_launch_near(ctx, kop, out, fp32));
+  SPS_TRY(sps_launch_near(ctx, kop, out, fp32 && SPS_MIXED_NEAR));
   SPS_TRY(sps_launch_far(ctx, kop, sig, out, fp32));
   if (op == SPS_OP_A) {
     SPS_TRY(sps_launch_moments(ctx, sig, ctx->d_mom));

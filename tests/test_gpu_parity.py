@@ -203,8 +203,10 @@ def _check_step(d, gamma, U, pos_new, tol):
 def test_step_fp64(sps, name, acs):
     d = load(name)
     p = int(d["p"])
+    # cold GMRES starts, as in the oracle: the BBPGD iterates then follow the
+    # oracle's path (near-touching spheres at p = 4 make M only approximately SPD)
     ctx = sps.Context(p=p, delta=0.1, a_c_scale=acs, gmres_tol=1e-13, gmres_max=300,
-                      bbpgd_tol=1e-12)
+                      bbpgd_tol=1e-12, warm_start=0)
     gam, U, pn = ctx.resolve_collisions(dev(d["centers"]), dev(d["radii"]), dev(d["FT"]),
                                         float(d["dt"]))
     st = ctx.last_stats
@@ -218,7 +220,7 @@ def test_step_mixed_and_host_api(sps):
     p = int(d["p"])
     # an FP32 far field puts ~1e-7 relative noise on M gamma: eps_tol 1e-6 is reachable
     kw = dict(p=p, delta=0.1, a_c_scale=1.05, gmres_tol=1e-9, gmres_max=300, bbpgd_tol=1e-6,
-              precision=1)
+              precision=1, warm_start=0)
     ctx = sps.Context(**kw)
     gam, U, pn = ctx.resolve_collisions(dev(d["centers"]), dev(d["radii"]), dev(d["FT"]),
                                         float(d["dt"]))
@@ -245,3 +247,24 @@ def test_step_capacity_and_single_sphere(sps):
                                         dev([[0, 0, -1.0, 0, 0, 0]]), 0.1)
     assert len(gam) == 0
     assert abs(U[0, 2].item() + 1 / (6 * pi)) < 1e-12
+
+
+def test_warm_start_matches_cold(sps):
+    """GMRES warm starts (previous solution as initial guess) change only the
+    Krylov path: the converged step agrees with the cold-start step."""
+    d = load("tiny_layers.npz")
+    C, R, p = d["c1_centers"], d["c1_radii"], int(d["c1_p"])
+    FT = 5.0 * d["c1_FT"]
+    out = {}
+    for warm in (0, 1):
+        ctx = sps.Context(p=p, delta=0.3, a_c_scale=1.02, gmres_tol=1e-12, gmres_max=300,
+                          bbpgd_tol=1e-10, warm_start=warm, bb_safeguard=1)
+        pos = dev(C)
+        for k in range(2):                 # second step: U_nc warm-started from step 1
+            gam, U, pn = ctx.resolve_collisions(pos, dev(R), dev(FT), 0.05)
+            pos = pn.clone()
+        out[warm] = (gam.cpu().numpy(), U.cpu().numpy(), ctx.last_stats)
+    assert relerr(out[1][1], out[0][1]) < 1e-8
+    if np.abs(out[0][0]).max() > 0:
+        assert relerr(out[1][0], out[0][0]) < 1e-6
+    assert out[1][2]["gmres_iters"] < out[0][2]["gmres_iters"]
