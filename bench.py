@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = ("collision-resolved steps/s and layer-potential interactions/s vs FP64 GPU, "
           "% roofline")
 FLOPS_PER_PAIR = {"K": 30, "S": 29}   # algorithmic FP32 operations per pair term
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_far32<K> launch at the
+# 1,000-sphere p = 6 workload, from an ncu capture of the current kernel
+# (None whenever the kernel changes until it is captured again)
+FAR_K_TRAFFIC_BYTES = 3630336 + 32768
 SMS, LANES = 152, 128
 
 
@@ -213,6 +217,7 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
     clocks.start()
     sps._lib.load().sps_profile(ctx.h, 1)
+    torch.cuda.nvtx.range_push("timed")      # ncu --nvtx-include "timed/" captures this region
     for k in range(args.steps):
         flush.zero_()                      # L2 flush between timed steps (outside the events)
         ev[k][0].record(stream)
@@ -220,6 +225,7 @@ def run_gpu(args, w):
         ev[k][1].record(stream)
         pos.copy_(pos_out)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ph_ms = (ctypes.c_double * 10)()
     ph_n = (ctypes.c_longlong * 10)()
     sps._lib.load().sps_profile_read(ctx.h, ph_ms, ph_n)
@@ -324,7 +330,8 @@ def run_gpu(args, w):
             "interactions_per_s": interactions,
             "roofline": {"bound": "alu", "kernel": "k_far32<K> (far-field traction N-body)",
                          "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
-                         "frac": achieved / pk["fp32_tflops"], "traffic": None,
+                         "frac": achieved / pk["fp32_tflops"],
+                         "traffic": FAR_K_TRAFFIC_BYTES if w.name.startswith("cfg2") else None,
                          "flops_per_pair": FLOPS_PER_PAIR["K"], "pairs_per_launch": pairs,
                          "avg_launch_ms": avgK,
                          "peak_note": (f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz "
@@ -353,6 +360,22 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+def run_single_op(args, w):
+    """One layer-operator application on the workload's geometry (a small,
+    self-contained case for kernel captures)."""
+    import torch
+    import paper_1909_06623_gb300 as sps
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    ctx = sps.Context(**ctx_params(args.precision))
+    ctx.set_geometry(dev(w.centers), dev(w.radii))
+    torch.manual_seed(0)
+    sig = torch.randn(3, w.N * ctx.P, dtype=torch.float64, device="cuda")
+    op = {"K": sps.SPS_OP_K, "S": sps.SPS_OP_S, "A": sps.SPS_OP_A}[args.single_op]
+    out = ctx.layer_apply(op, sig)
+    torch.cuda.synchronize()
+    print(json.dumps({"single_op": args.single_op, "max_abs": out.abs().max().item()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,9 +386,14 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-matvecs-per-step", type=float, default=60.0)
+    ap.add_argument("--ref-matvecs-per-step", type=float, default=185.0)
+    ap.add_argument("--single-op", choices=["K", "S", "A"], default=None,
+                    help="apply one layer operator on the workload geometry and exit")
     args = ap.parse_args()
     w = workload(args.workload)
+    if args.single_op:
+        run_single_op(args, w)
+        return
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return

@@ -103,3 +103,15 @@ def test_collision_step_against_enumeration():
     # after the step, the linearised gaps are non-negative
     lin = out["phi"] + dt * lcp.DT_apply(ij, nrm, out["U"])
     assert lin.min() > -1e-9
+
+
+def test_bbpgd_breakdown_and_safeguard():
+    """Algorithm 1 defines no step when s^T y <= 0.  A matrix whose symmetric
+    part is indefinite produces that; the literal reading stops ("breakdown"),
+    the safeguard keeps the previous step length and carries on."""
+    M = np.array([[1.0, 0.0], [0.0, -0.3]])
+    q = np.array([-1.0, -1.0])
+    gam, g, info = lcp.bbpgd(lambda x: M @ x, q, 1e-12, jmax=50)
+    assert info["status"] == "breakdown"
+    gam, g, info = lcp.bbpgd(lambda x: M @ x, q, 1e-12, jmax=50, safeguard=True)
+    assert info["safeguards"] >= 1 and info["status"] in ("ok", "not_converged")
