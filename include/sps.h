@@ -167,6 +167,28 @@ int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* pos, const do
                                 double* UO, double* pos_out, int* n_contacts_out,
                                 sps_stats* stats);
 
+/* Transpose of a layer operator (sps_op) on the current geometry: out = Op^T v
+ * with the Euclidean inner product on the node values (3 planes of NP).  The
+ * exact transpose of the discrete operator of sps_layer_apply (same quadrature,
+ * VSH maps and near lists), evaluated in FP64.  Used by the adjoint; exposed
+ * for checks such as <w, Op v> = <Op^T w, v>.  The paper has no counterpart. */
+int sps_layer_apply_transpose(sps_ctx* ctx, int op, const double* v, double* out);
+
+/* Adjoint of sps_mobility_apply.  Given dL/dU (n x 6, device) for a loss L of
+ * the velocities U = M F, computes dL/dF (n x 6: force and torque parts) and,
+ * if dL_dpos is not NULL, dL/dc (n x 3) for the sphere centres c (radii and
+ * the near-pair lists held fixed: the gradient of the discrete map on its
+ * current piece).  The forward solve is repeated; its velocities go to UO if
+ * UO is not NULL.  Method: lambda = A^{-T} S^T E^T dL/dU (adjoint GMRES on the
+ * transpose of eq. rigidbodyrho), dL/dF = R^T (S^T E^T dL/dU - (I/2 + K)^T
+ * lambda); dL/dc from the derivatives of the far and near sums (the self, L,
+ * rho and averaging steps are translation invariant).  The paper has no
+ * adjoint; this is the exact gradient of its discretised mobility map.
+ * Errors as sps_mobility_apply; NOT_CONVERGED if either GMRES hit its cap. */
+int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                         const double* FT, const double* dL_dU, double* UO, double* dL_dFT,
+                         double* dL_dpos, sps_stats* stats);
+
 /* Contact set of sps_build_contacts for callers that cannot allocate device
  * memory when they need it: code running while a stream is being captured into
  * a CUDA graph (cudaMalloc is not a capturable operation), hosts whose own

@@ -18,7 +18,7 @@ from ._lib import (SPS_FP64, SPS_MIXED, SPS_OP_A, SPS_OP_K, SPS_OP_S, SPSError, 
                    sps_stats)
 
 __all__ = ["Context", "SPSError", "SPS_FP64", "SPS_MIXED", "SPS_OP_S", "SPS_OP_K", "SPS_OP_A",
-           "default_params", "unit_tables", "nodes_per_sphere"]
+           "default_params", "unit_tables", "nodes_per_sphere", "MobilityFunction", "mobility"]
 
 
 def nodes_per_sphere(p):
@@ -126,6 +126,26 @@ class Context:
         self._check(self.lib.sps_layer_apply(self.h, int(op), _ptr(sigma), _ptr(out)))
         return out
 
+    def layer_apply_transpose(self, op, v, out=None):
+        if out is None:
+            out = torch.empty_like(v)
+        self._check(self.lib.sps_layer_apply_transpose(self.h, int(op), _ptr(v), _ptr(out)))
+        return out
+
+    def mobility_adjoint(self, pos, radii, FT, dL_dU, want_pos=True, allow_not_converged=False):
+        """(U, dL/dFT, dL/dpos or None) for a loss whose gradient in U is dL_dU."""
+        n = radii.numel()
+        UO = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        gF = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        gx = torch.empty(n, 3, dtype=torch.float64, device="cuda") if want_pos else None
+        st = sps_stats()
+        rc = self.lib.sps_mobility_adjoint(self.h, n, _ptr(pos), _ptr(radii), _ptr(FT),
+                                           _ptr(dL_dU.contiguous()), _ptr(UO), _ptr(gF), _ptr(gx),
+                                           ctypes.byref(st))
+        self._check(rc, allow=(4,) if allow_not_converged else ())
+        self.last_stats = st.as_dict()
+        return UO, gF, gx
+
     def build_contacts(self, pos, radii):
         nc = ctypes.c_int()
         self._check(self.lib.sps_build_contacts(self.h, radii.numel(), _ptr(pos), _ptr(radii),
@@ -195,3 +215,34 @@ class Context:
         self._check(rc, allow=allow)
         self.last_stats = st.as_dict()
         return nc.value
+
+
+class MobilityFunction(torch.autograd.Function):
+    """U = M(pos) FT as a differentiable function of forces/torques and centres.
+
+    forward: sps_mobility_apply; backward: sps_mobility_adjoint (exact gradient
+    of the discrete map; radii and near lists are held fixed, so the gradient
+    in pos is that of the current piece of a piecewise-smooth map).
+    """
+
+    @staticmethod
+    def forward(fctx, pos, radii, FT, ctx):
+        U = ctx.mobility_apply(pos.detach().contiguous(), radii.detach().contiguous(),
+                               FT.detach().contiguous())
+        fctx.save_for_backward(pos, radii, FT)
+        fctx.sps = ctx
+        return U
+
+    @staticmethod
+    def backward(fctx, gU):
+        pos, radii, FT = fctx.saved_tensors
+        want_pos = fctx.needs_input_grad[0]
+        _, gF, gx = fctx.sps.mobility_adjoint(pos.detach().contiguous(), radii.detach().contiguous(),
+                                              FT.detach().contiguous(), gU.contiguous(),
+                                              want_pos=want_pos)
+        return (gx if want_pos else None), None, (gF if fctx.needs_input_grad[2] else None), None
+
+
+def mobility(pos, radii, FT, ctx):
+    """Differentiable U = M F (see MobilityFunction)."""
+    return MobilityFunction.apply(pos, radii, FT, ctx)

@@ -261,7 +261,7 @@ __global__ void k_moments(int N, int P, const double* __restrict__ pos, const do
   double m[6] = {0, 0, 0, 0, 0, 0};
   for (int k = lane; k < P; k += 32) {
     const long long g = (long long)s * P + k;
-    const double w = W[g];
+    const double w = W ? W[g] : 1.0;
     const double fx = f[g] * w, fy = f[NP + g] * w, fz = f[2 * NP + g] * w;
     const double rx = X[g] - pos[3 * s], ry = X[NP + g] - pos[3 * s + 1],
                  rz = X[2 * NP + g] - pos[3 * s + 2];
@@ -281,7 +281,7 @@ __global__ void k_moments(int N, int P, const double* __restrict__ pos, const do
 // out += L[f]: f-moments per sphere broadcast back (Sec. 4.1, operator L)
 __global__ void k_add_L(int N, int P, const double* __restrict__ pos, const double* __restrict__ rad,
                         const double* __restrict__ X, const double* __restrict__ mom,
-                        double* __restrict__ out) {
+                        const double* __restrict__ Wout, double* __restrict__ out) {
   const long long NP = (long long)N * P;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NP;
        g += (long long)gridDim.x * blockDim.x) {
@@ -292,9 +292,10 @@ __global__ void k_add_L(int N, int P, const double* __restrict__ pos, const doub
                  rz = X[2 * NP + g] - pos[3 * s + 2];
     const double* m = mom + 6 * s;
     const double tx = it * m[3], ty = it * m[4], tz = it * m[5];
-    out[g] += m[0] * ia + (ty * rz - tz * ry);
-    out[NP + g] += m[1] * ia + (tz * rx - tx * rz);
-    out[2 * NP + g] += m[2] * ia + (tx * ry - ty * rx);
+    const double wo = Wout ? Wout[g] : 1.0;
+    out[g] += wo * (m[0] * ia + (ty * rz - tz * ry));
+    out[NP + g] += wo * (m[1] * ia + (tz * rx - tx * rz));
+    out[2 * NP + g] += wo * (m[2] * ia + (tx * ry - ty * rx));
   }
 }
 
@@ -518,7 +519,24 @@ int sps_launch_moments(sps_ctx* ctx, const double* f, double* mom) {
 int sps_launch_add_L(sps_ctx* ctx, const double* mom, double* out) {
   SpsPhase timer(ctx, SPS_PH_KRYLOV);
   k_add_L<<<nblk(ctx->NP), kThreads, 0, ctx->stream>>>(ctx->N, ctx->T.P, ctx->d_pos, ctx->d_rad,
-                                                        ctx->d_X, mom, out);
+                                                        ctx->d_X, mom, nullptr, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_add_L_w(sps_ctx* ctx, const double* mom, double* out, bool weight_out) {
+  SpsPhase timer(ctx, SPS_PH_KRYLOV);
+  k_add_L<<<nblk(ctx->NP), kThreads, 0, ctx->stream>>>(ctx->N, ctx->T.P, ctx->d_pos, ctx->d_rad,
+                                                        ctx->d_X, mom, weight_out ? ctx->d_W : nullptr, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_moments_w(sps_ctx* ctx, const double* f, double* mom, bool weighted) {
+  SpsPhase timer(ctx, SPS_PH_KRYLOV);
+  k_moments<<<nblk((long long)ctx->N * 32, 128), 128, 0, ctx->stream>>>(ctx->N, ctx->T.P, ctx->d_pos,
+                                                                        ctx->d_X, weighted ? ctx->d_W : nullptr,
+                                                                        f, mom);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }

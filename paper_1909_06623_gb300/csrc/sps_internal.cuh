@@ -65,6 +65,21 @@ struct sps_ctx {
   double *d_synthS = nullptr;   // 3P x NR row-major synthesis * multS
   double *d_synthK = nullptr;   // 3P x NR row-major synthesis * multK
   double *d_kappa = nullptr, *d_potfac = nullptr;
+  // near-field coefficient map as sparse matrices (per field set K / S):
+  // fcoef_s = FM coef_s  (rows 2*E*F, cols NR) and its transpose
+  struct Sparse {
+    int rows = 0, cols = 0, nnz = 0;
+    int *rp = nullptr, *ci = nullptr;
+    double* v = nullptr;
+  } fmK, fmS, fmKt, fmSt;
+  // transposed self matrices for the adjoint
+  double *d_analT = nullptr;    // 3P x NR row-major (analysis transposed)
+  double *d_synthST = nullptr;  // NR x 3P (synthesis * multS, transposed)
+  double *d_synthKT = nullptr;  // NR x 3P
+  double *d_coefbar = nullptr;  // N x NR adjoint of the VSH coefficients
+  double *d_ebar = nullptr;     // N x E x kFieldsK x 2 adjoint of the field coefficients
+  double *d_sigtot = nullptr, *d_ubar = nullptr, *d_sbar = nullptr, *d_lam = nullptr, *d_rbar = nullptr;
+  bool adjoint_mode = false;    // GMRES applies A^T instead of A
   float *d_anal32 = nullptr, *d_synthS32 = nullptr, *d_synthK32 = nullptr;
 
   // geometry
@@ -195,6 +210,20 @@ int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out, bool f
 int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32);
 int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
 int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
+
+// generic batched product (sps_vsh.cu): mode 0 in = planes, out = rows (N x R);
+// mode 1 in = rows (N x C), out = planes; FP64
+int sps_launch_batched(sps_ctx* ctx, int mode, const double* M, int R, int C, const double* in, double* out,
+                       int scale_by_radius, const double* sig, int half);
+// adjoint helpers (sps_geometry.cu, sps_adjoint.cu)
+int sps_launch_moments_w(sps_ctx* ctx, const double* f, double* mom, bool weighted);
+int sps_launch_add_L_w(sps_ctx* ctx, const double* mom, double* out, bool weight_out);
+int sps_layer_T(sps_ctx* ctx, int op, const double* v, double* out);
+
+// near-field coefficient maps (sps_vsh.cu)
+int sps_build_field_maps(sps_ctx* ctx);
+int sps_launch_sparse_rows(sps_ctx* ctx, const sps_ctx::Sparse& m, int nsph, const double* in, int in_ld,
+                           double* out, int out_ld, int accumulate);
 
 // vector kernels (sps_solver.cu)
 int sps_dot(sps_ctx* ctx, const double* a, const double* b, long long n, double* host_out);

@@ -161,6 +161,14 @@ __global__ void k_pos_update(int n, const double* __restrict__ pos, const double
   if (i < 3 * n) out[i] = pos[i] + dt * UO[6 * (i / 3) + (i % 3)];
 }
 
+// rbar = sbar - (lam/2 + rbar): finishes rhobar = sbar - (I/2 + K)^T lambda
+__global__ void k_combine3(long long n, const double* __restrict__ sbar, const double* __restrict__ lam,
+                           double* __restrict__ rbar) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    rbar[i] = sbar[i] - (0.5 * lam[i] + rbar[i]);
+}
+
 inline int gblocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 8 * 152); }
 
 }  // namespace
@@ -270,8 +278,10 @@ static int ensure_gmres(sps_ctx* ctx, long long n, int kmax) {
   return SPS_OK;
 }
 
-// operator application for GMRES: out = (I/2 + K + L) v
+// operator application for GMRES: out = (I/2 + K + L) v, or its transpose
+// while an adjoint solve runs
 static int apply_A(sps_ctx* ctx, const double* v, double* out, bool fp32) {
+  if (ctx->adjoint_mode) return sps_layer_T(ctx, SPS_OP_A, v, out);
   return sps_layer(ctx, SPS_OP_A, v, out, fp32);
 }
 
@@ -451,6 +461,21 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
     sps_destroy(ctx);
     return rc;
   }
+  {
+    // transposed self matrices (adjoint): analysis^T (3P x NR), synthesis^T (NR x 3P)
+    std::vector<double> aT((size_t)3 * P * NR), sST((size_t)NR * 3 * P), sKT((size_t)NR * 3 * P);
+    for (int r = 0; r < NR; ++r)
+      for (int c = 0; c < 3 * P; ++c) {
+        aT[(size_t)c * NR + r] = T.anal[(size_t)r * 3 * P + c];
+        sST[(size_t)r * 3 * P + c] = sS[(size_t)c * NR + r];
+        sKT[(size_t)r * 3 * P + c] = sK[(size_t)c * NR + r];
+      }
+    if ((rc = upload(ctx, &ctx->d_analT, aT)) || (rc = upload(ctx, &ctx->d_synthST, sST)) ||
+        (rc = upload(ctx, &ctx->d_synthKT, sKT)) || (rc = sps_build_field_maps(ctx))) {
+      sps_destroy(ctx);
+      return rc;
+    }
+  }
   if (cudaMallocHost((void**)&ctx->h_pinned, sizeof(double) * 4096) != cudaSuccess) {
     cudaGetLastError();
     sps_destroy(ctx);
@@ -475,6 +500,15 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_Unc, ctx->d_Uc};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  void* more[] = {ctx->d_analT, ctx->d_synthST, ctx->d_synthKT, ctx->d_coefbar, ctx->d_ebar,
+                  ctx->d_sigtot, ctx->d_ubar, ctx->d_sbar, ctx->d_lam, ctx->d_rbar};
+  for (void* b : more)
+    if (b) cudaFree(b);
+  for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
+    cudaFree(m->rp);
+    cudaFree(m->ci);
+    cudaFree(m->v);
+  }
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
@@ -514,7 +548,9 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
     double** d64[] = {&ctx->d_pos, &ctx->d_rad, &ctx->d_X, &ctx->d_Nrm, &ctx->d_W, &ctx->d_coef,
                       &ctx->d_fcoef, &ctx->d_mom, &ctx->d_tmp3, &ctx->d_rho, &ctx->d_zeta,
                       &ctx->d_zeta_nc, &ctx->d_b,
-                      &ctx->d_u, &ctx->d_r, &ctx->d_dz, &ctx->d_FT, &ctx->d_Unc, &ctx->d_Uc};
+                      &ctx->d_u, &ctx->d_r, &ctx->d_dz, &ctx->d_FT, &ctx->d_Unc, &ctx->d_Uc,
+                      &ctx->d_coefbar, &ctx->d_ebar, &ctx->d_sigtot, &ctx->d_ubar, &ctx->d_sbar,
+                      &ctx->d_lam, &ctx->d_rbar};
     for (auto p : d64) {
       cudaFree(*p);
       *p = nullptr;
@@ -538,7 +574,10 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
                {&ctx->d_zeta, 3 * (size_t)NP}, {&ctx->d_zeta_nc, 3 * (size_t)NP},
                {&ctx->d_b, 3 * (size_t)NP}, {&ctx->d_u, 3 * (size_t)NP},
                {&ctx->d_r, 3 * (size_t)NP}, {&ctx->d_dz, 3 * (size_t)NP}, {&ctx->d_FT, 6 * (size_t)n},
-               {&ctx->d_Unc, 6 * (size_t)n}, {&ctx->d_Uc, 6 * (size_t)n}};
+               {&ctx->d_Unc, 6 * (size_t)n}, {&ctx->d_Uc, 6 * (size_t)n},
+               {&ctx->d_coefbar, (size_t)n * NR}, {&ctx->d_ebar, (size_t)n * E * sps::kFieldsK * 2},
+               {&ctx->d_sigtot, 3 * (size_t)NP}, {&ctx->d_ubar, 3 * (size_t)NP}, {&ctx->d_sbar, 3 * (size_t)NP},
+               {&ctx->d_lam, 3 * (size_t)NP}, {&ctx->d_rbar, 3 * (size_t)NP}};
     for (auto& e : a64) {
       c = 0;
       SPS_TRY(sps_grow(ctx, e.p, c, e.n));
@@ -907,4 +946,57 @@ extern "C" int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* po
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess && rc == SPS_OK) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
   return stats_end(ctx, st, l0, rc);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the mobility solve (dL/dF; dL/dx in sps_adjoint_geom.cu)
+// ---------------------------------------------------------------------------
+int sps_geom_gradient(sps_ctx* ctx, const double* ubar, const double* lam, const double* sig, double* dx);
+
+extern "C" int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                                    const double* FT, const double* dL_dU, double* UO, double* dL_dFT,
+                                    double* dL_dpos, sps_stats* st) {
+  if (!ctx || !FT || !dL_dU || !dL_dFT) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "mobility_adjoint: bad argument");
+  long long l0;
+  stats_begin(ctx, st, &l0);
+  int rc = sps_set_geometry(ctx, n, pos, radii);
+  if (rc == SPS_OK) rc = check_finite_host(ctx, FT, 6LL * n, "force/torque");
+  if (rc == SPS_OK) rc = check_finite_host(ctx, dL_dU, 6LL * n, "dL/dU");
+  if (rc != SPS_OK) return stats_end(ctx, st, l0, rc);
+  const long long n3 = 3LL * ctx->NP;
+  // forward solve; keep sigma = rho + zeta
+  double* U = UO ? UO : ctx->d_Uc;
+  int frc = mobility_solve(ctx, FT, U, st, ctx->d_zeta, false);
+  if (frc != SPS_OK && frc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, frc);
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_sigtot, ctx->d_tmp3, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+  // ubar = E^T dL/dU (weights at the nodes)
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_ubar, 0, sizeof(double) * n3, ctx->stream));
+  SPS_TRY(sps_launch_add_L_w(ctx, dL_dU, ctx->d_ubar, true));
+  // sbar = S^T ubar
+  SPS_TRY(sps_layer_T(ctx, SPS_OP_S, ctx->d_ubar, ctx->d_sbar));
+  // lambda = A^{-T} sbar
+  ctx->adjoint_mode = true;
+  int its = 0;
+  double res = 0.0;
+  int grc = gmres(ctx, ctx->d_sbar, ctx->d_lam, false, ctx->prm.gmres_tol, ctx->prm.gmres_max, false, &its, &res);
+  ctx->adjoint_mode = false;
+  if (grc != SPS_OK && grc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, grc);
+  if (st) {
+    st->gmres_iters += its;
+    st->gmres_iters_max = std::max(st->gmres_iters_max, its);
+    st->gmres_res_max = std::max(st->gmres_res_max, res);
+  }
+  // rhobar = sbar - (I/2 + K)^T lambda
+  SPS_TRY(sps_layer_T(ctx, SPS_OP_K, ctx->d_lam, ctx->d_rbar));
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_combine3<<<gblocks(n3), 256, 0, ctx->stream>>>(n3, ctx->d_sbar, ctx->d_lam, ctx->d_rbar); }
+  SPS_LAUNCHED(ctx);
+  // dL/dF = R^T rhobar: unweighted moments
+  SPS_TRY(sps_launch_moments_w(ctx, ctx->d_rbar, ctx->d_mom, false));
+  SPS_TRY(sps_launch_extract(ctx, ctx->d_mom, dL_dFT));
+  if (dL_dpos) SPS_TRY(sps_geom_gradient(ctx, ctx->d_ubar, ctx->d_lam, ctx->d_sigtot, dL_dpos));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int out_rc = (frc != SPS_OK) ? frc : grc;
+  return stats_end(ctx, st, l0, out_rc != SPS_OK ? sps_fail(ctx, out_rc, "adjoint: a solve did not converge") : SPS_OK);
 }

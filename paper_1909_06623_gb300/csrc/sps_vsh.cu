@@ -94,7 +94,9 @@ __global__ void __launch_bounds__(256) k_batched(int N, int P, int R, int C, con
       const int s = s0 + 2 * ty + u, r = r0 + 2 * tx + v;
       if (s >= N || r >= R) continue;
       if (MODE == MODE_ANALYSIS) {
-        out[(long long)s * R + r] = (double)acc[u][v];
+        double val = (double)acc[u][v];
+        if (scale_by_radius) val *= rad[s];
+        out[(long long)s * R + r] = val;
       } else {
         const int comp = r / P, k = r - comp * P;
         const long long idx = comp * NP + (long long)s * P + k;
@@ -415,7 +417,113 @@ int launch_near_close(sps_ctx* ctx, double* out) {
   return SPS_OK;
 }
 
+// out[s][r] (+)= sum over row r of a sparse map applied to in[s][:]
+__global__ void k_sparse_rows(int N, int rows, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const double* __restrict__ val, const double* __restrict__ in, int in_ld,
+                              double* __restrict__ out, int out_ld, int accumulate) {
+  const long long tot = (long long)N * rows;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(q / rows), r = (int)(q - (long long)s * rows);
+    const double* x = in + (long long)s * in_ld;
+    double acc = 0.0;
+    for (int k = rp[r]; k < rp[r + 1]; ++k) acc = fma(val[k], x[ci[k]], acc);
+    double* y = out + (long long)s * out_ld + r;
+    *y = accumulate ? *y + acc : acc;
+  }
+}
+
 }  // namespace
+
+int sps_launch_sparse_rows(sps_ctx* ctx, const sps_ctx::Sparse& m, int nsph, const double* in, int in_ld,
+                           double* out, int out_ld, int accumulate) {
+  const long long tot = (long long)nsph * m.rows;
+  k_sparse_rows<<<(int)std::min<long long>((tot + 255) / 256, 8 * 152), 256, 0, ctx->stream>>>(
+      nsph, m.rows, m.rp, m.ci, m.v, in, in_ld, out, out_ld, accumulate);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+// The coefficient builder is linear in the VSH coefficients with constant
+// weights; run it once on unit coefficient vectors to obtain that map as a
+// sparse matrix (and its transpose, for the adjoint).
+template <int F>
+static int field_map(sps_ctx* ctx, sps_ctx::Sparse& fm, sps_ctx::Sparse& fmt) {
+  const int NR = ctx->T.NR, E = ctx->T.E, NC = ctx->T.NC, L = ctx->T.L, p = ctx->T.p;
+  const int W = E * F * 2;
+  std::vector<double> eye((size_t)NR * NR, 0.0), out((size_t)NR * W);
+  for (int r = 0; r < NR; ++r) eye[(size_t)r * NR + r] = 1.0;
+  double *d_in = nullptr, *d_out = nullptr;
+  SPS_CUDA(ctx, cudaMalloc(&d_in, eye.size() * sizeof(double)));
+  SPS_CUDA(ctx, cudaMalloc(&d_out, out.size() * sizeof(double)));
+  SPS_CUDA(ctx, cudaMemcpy(d_in, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice));
+  k_near_coef<F><<<NR, 256, 0, ctx->stream>>>(NR, p, NC, NR, L, E, d_in, ctx->d_kappa, ctx->d_potfac, d_out);
+  SPS_LAUNCHED(ctx);
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpy(out.data(), d_out, out.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  cudaFree(d_in);
+  cudaFree(d_out);
+  // out[r][k] = FM[k][r]
+  std::vector<int> rp(W + 1, 0), rpt(NR + 1, 0), ci, cit;
+  std::vector<double> val, valt;
+  for (int k = 0; k < W; ++k) {
+    for (int r = 0; r < NR; ++r) {
+      const double x = out[(size_t)r * W + k];
+      if (x != 0.0) {
+        ci.push_back(r);
+        val.push_back(x);
+      }
+    }
+    rp[k + 1] = (int)ci.size();
+  }
+  for (int r = 0; r < NR; ++r) {
+    for (int k = 0; k < W; ++k) {
+      const double x = out[(size_t)r * W + k];
+      if (x != 0.0) {
+        cit.push_back(k);
+        valt.push_back(x);
+      }
+    }
+    rpt[r + 1] = (int)cit.size();
+  }
+  auto up = [&](sps_ctx::Sparse& m, int rows, int cols, const std::vector<int>& a, const std::vector<int>& b,
+                const std::vector<double>& c) -> int {
+    m.rows = rows;
+    m.cols = cols;
+    m.nnz = (int)c.size();
+    SPS_CUDA(ctx, cudaMalloc(&m.rp, sizeof(int) * a.size()));
+    SPS_CUDA(ctx, cudaMalloc(&m.ci, sizeof(int) * std::max<size_t>(1, b.size())));
+    SPS_CUDA(ctx, cudaMalloc(&m.v, sizeof(double) * std::max<size_t>(1, c.size())));
+    SPS_CUDA(ctx, cudaMemcpy(m.rp, a.data(), sizeof(int) * a.size(), cudaMemcpyHostToDevice));
+    SPS_CUDA(ctx, cudaMemcpy(m.ci, b.data(), sizeof(int) * b.size(), cudaMemcpyHostToDevice));
+    SPS_CUDA(ctx, cudaMemcpy(m.v, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice));
+    return SPS_OK;
+  };
+  SPS_TRY(up(fm, W, NR, rp, ci, val));
+  SPS_TRY(up(fmt, NR, W, rpt, cit, valt));
+  return SPS_OK;
+}
+
+int sps_build_field_maps(sps_ctx* ctx) {
+  SPS_TRY(field_map<sps::kFieldsK>(ctx, ctx->fmK, ctx->fmKt));
+  SPS_TRY(field_map<sps::kFieldsS>(ctx, ctx->fmS, ctx->fmSt));
+  return SPS_OK;
+}
+
+int sps_launch_batched(sps_ctx* ctx, int mode, const double* M, int R, int C, const double* in, double* out,
+                       int scale_by_radius, const double* sig, int half) {
+  SpsPhase timer(ctx, SPS_PH_SELF);
+  const int N = ctx->N, P = ctx->T.P;
+  dim3 grid((N + kTB - 1) / kTB, (R + kTB - 1) / kTB);
+  if (mode == 0)
+    k_batched<double, MODE_ANALYSIS><<<grid, 256, 0, ctx->stream>>>(N, P, R, C, M, in, out, ctx->d_rad,
+                                                                     scale_by_radius, nullptr, 0);
+  else
+    k_batched<double, MODE_SYNTH><<<grid, 256, 0, ctx->stream>>>(N, P, R, C, M, in, out, ctx->d_rad,
+                                                                  scale_by_radius, sig, half);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
 
 int sps_launch_analysis(sps_ctx* ctx, const double* sig, bool fp32) {
   SpsPhase timer(ctx, SPS_PH_SELF);
@@ -456,13 +564,13 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
   const bool S = (op == SPS_OP_S);
   {
     SpsPhase timer(ctx, SPS_PH_SELF);
-    if (S)
-      k_near_coef<sps::kFieldsS><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef,
-                                                             ctx->d_kappa, ctx->d_potfac, ctx->d_fcoef);
-    else
-      k_near_coef<sps::kFieldsK><<<N, 256, 0, ctx->stream>>>(N, p, NC, NR, L, E, ctx->d_coef,
-                                                             ctx->d_kappa, ctx->d_potfac, ctx->d_fcoef);
-    SPS_LAUNCHED(ctx);
+    // field coefficients of every source sphere: fcoef_s = FM coef_s (sparse)
+    const sps_ctx::Sparse& fm = S ? ctx->fmS : ctx->fmK;
+    SPS_TRY(sps_launch_sparse_rows(ctx, fm, N, ctx->d_coef, NR, ctx->d_fcoef, fm.rows, 0));
+    (void)NC;
+    (void)L;
+    (void)E;
+    (void)p;
   }
   SpsPhase timer(ctx, S ? SPS_PH_NEAR_S : SPS_PH_NEAR_K);
   // mixed path: FP32 for near entries farther than kCloseRadius source radii,

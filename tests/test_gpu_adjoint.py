@@ -1,0 +1,168 @@
+"""GPU adjoint of the mobility solve, through the C ABI.
+
+* transpose identities <w, Op v> = <Op^T w, v> for S, K and I/2+K+L (tiny
+  polydisperse cases with close pairs and the full 1,000-sphere geometry);
+* dL/dF for L = sum |U|^2 against the oracle's exact 2 M^T U (assembled
+  mobility) and against central differences of the GPU forward solve;
+* dL/dc (sphere centres) against central differences of the GPU and of the
+  oracle forward solve, on coordinates whose near pairs stay away from the
+  beta (a_i + a_j) threshold.
+Tolerance for gradients: 1e-4 relative (FP64 path), as stated for the adjoint.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint as oadj
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden")
+
+
+@pytest.fixture(scope="module")
+def sps():
+    from paper_1909_06623_gb300 import build
+    build.build()
+    import paper_1909_06623_gb300 as m
+    return m
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _transpose_gap(ctx, sps, op, NP, seed):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    v = torch.randn(3, NP, dtype=torch.float64, device="cuda", generator=g)
+    w = torch.randn(3, NP, dtype=torch.float64, device="cuda", generator=g)
+    Av = ctx.layer_apply(op, v)
+    ATw = ctx.layer_apply_transpose(op, w)
+    lhs = torch.sum(w * Av).item()
+    rhs = torch.sum(ATw * v).item()
+    scale = (torch.linalg.norm(w) * torch.linalg.norm(Av)).item()
+    return abs(lhs - rhs) / scale
+
+
+@pytest.mark.parametrize("case", ["c1", "c2", "c3"])
+def test_transpose_identities_tiny(sps, case):
+    d = np.load(os.path.join(GOLD, "tiny_layers.npz"))
+    C, R, p = d[f"{case}_centers"], d[f"{case}_radii"], int(d[f"{case}_p"])
+    ctx = sps.Context(p=p)
+    ctx.set_geometry(dev(C), dev(R))
+    NP = len(R) * (p + 1) * (2 * p + 2)
+    for op in (sps.SPS_OP_S, sps.SPS_OP_K, sps.SPS_OP_A):
+        assert _transpose_gap(ctx, sps, op, NP, 3 + op) < 1e-13, op
+
+
+def test_transpose_identities_cfg2(sps):
+    d = np.load(os.path.join(GOLD, "cfg2_sample.npz"))
+    p = int(d["p"])
+    ctx = sps.Context(p=p)
+    ctx.set_geometry(dev(d["centers"]), dev(d["radii"]))
+    NP = len(d["radii"]) * (p + 1) * (2 * p + 2)
+    for op in (sps.SPS_OP_S, sps.SPS_OP_K, sps.SPS_OP_A):
+        assert _transpose_gap(ctx, sps, op, NP, 11 + op) < 1e-12, op
+
+
+def _case3():
+    C = np.array([[0.0, 0.0, 0.0], [2.3, 0.4, 0.1], [0.6, 2.2, -0.5]])
+    R = np.array([1.0, 0.8, 0.9])
+    FT = np.array([[0.3, -0.5, 1.0, 0.1, 0.0, 0.2], [-0.2, 0.4, 0.1, 0.0, 0.3, 0.0],
+                   [0.1, 0.1, -0.6, -0.2, 0.0, 0.1]])
+    return C, R, FT
+
+
+def test_force_gradient_matches_oracle_exact(sps):
+    C, R, FT = _case3()
+    p = 4
+    ref = oadj.grad_F_exact(C, R, FT, p)
+    ctx = sps.Context(p=p, gmres_tol=1e-13, gmres_max=400)
+    U = ctx.mobility_apply(dev(C), dev(R), dev(FT))
+    _, gF, _ = ctx.mobility_adjoint(dev(C), dev(R), dev(FT), 2.0 * U, want_pos=False)
+    g = gF.cpu().numpy()
+    assert np.abs(g - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def test_force_gradient_fd_polydisperse(sps):
+    """A larger case with close pairs: dL/dF against central differences of the
+    GPU forward solve (L is quadratic in F, so differences are exact up to
+    rounding)."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.tiny(21, 12, 5, phi=0.15, n_pairs=2, gap=0.01)
+    ctx = sps.Context(p=5, gmres_tol=1e-13, gmres_max=400)
+    pos, rad, FT = dev(w.centers), dev(w.radii), dev(w.FT)
+    U = ctx.mobility_apply(pos, rad, FT)
+    _, gF, _ = ctx.mobility_adjoint(pos, rad, FT, 2.0 * U, want_pos=False)
+    h = 1e-3
+    for i, k in ((0, 0), (3, 2), (7, 4), (11, 5)):
+        vals = []
+        for s in (1, -1):
+            F2 = FT.clone()
+            F2[i, k] += s * h
+            Ui = ctx.mobility_apply(pos, rad, F2)
+            vals.append(torch.sum(Ui * Ui).item())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - gF[i, k].item()) < 1e-7 * gF.abs().max().item(), (i, k)
+
+
+def _fd_gpu(ctx, pos, rad, FT, i, k, h):
+    vals = []
+    for s in (1, -1):
+        p2 = pos.clone()
+        p2[i, k] += s * h
+        U = ctx.mobility_apply(p2, rad, FT)
+        vals.append(torch.sum(U * U).item())
+    return (vals[0] - vals[1]) / (2 * h)
+
+
+def test_centre_gradient_fd_gpu(sps):
+    """dL/dc against central differences of the GPU FP64 forward solve on a
+    polydisperse case with near pairs (no pair within 10 h of the beta
+    threshold, so the near lists are the same at c +- h)."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.tiny(21, 12, 5, phi=0.15, n_pairs=2, gap=0.01)
+    h = 1e-5
+    assert oadj.near_margin(w.centers, w.radii) > 20 * h
+    ctx = sps.Context(p=5, gmres_tol=1e-13, gmres_max=400)
+    pos, rad, FT = dev(w.centers), dev(w.radii), dev(w.FT)
+    U = ctx.mobility_apply(pos, rad, FT)
+    _, gF, gx = ctx.mobility_adjoint(pos, rad, FT, 2.0 * U)
+    scale = gx.abs().max().item()
+    for i, k in ((0, 0), (2, 1), (5, 2), (8, 0), (11, 1)):
+        fd = _fd_gpu(ctx, pos, rad, FT, i, k, h)
+        assert abs(fd - gx[i, k].item()) < 1e-4 * scale, (i, k, fd, gx[i, k].item())
+    # translation invariance: the centre gradients sum to zero
+    assert gx.sum(dim=0).abs().max().item() < 1e-9 * scale
+
+
+def test_centre_gradient_matches_oracle_fd(sps):
+    C, R, FT = _case3()
+    p = 4
+    h = 1e-5
+    assert oadj.near_margin(C, R) > 20 * h
+    coords = [("c", 0, 0), ("c", 1, 1), ("c", 2, 2)]
+    ref = oadj.grad_fd(C, R, FT, p, coords, h=h)
+    ctx = sps.Context(p=p, gmres_tol=1e-13, gmres_max=400)
+    U = ctx.mobility_apply(dev(C), dev(R), dev(FT))
+    _, _, gx = ctx.mobility_adjoint(dev(C), dev(R), dev(FT), 2.0 * U)
+    got = np.array([gx[i, k].item() for _, i, k in coords])
+    assert np.abs(got - ref).max() < 1e-4 * np.abs(gx.cpu().numpy()).max()
+
+
+def test_autograd_function(sps):
+    """torch.autograd through MobilityFunction equals the direct adjoint call."""
+    C, R, FT = _case3()
+    ctx = sps.Context(p=4, gmres_tol=1e-13, gmres_max=400)
+    pos = dev(C).requires_grad_(True)
+    F = dev(FT).requires_grad_(True)
+    U = sps.mobility(pos, dev(R), F, ctx)
+    L = (U * U).sum()
+    L.backward()
+    U2 = ctx.mobility_apply(dev(C), dev(R), dev(FT))
+    _, gF, gx = ctx.mobility_adjoint(dev(C), dev(R), dev(FT), 2.0 * U2)
+    assert torch.allclose(F.grad, gF, rtol=1e-10, atol=1e-14)
+    assert torch.allclose(pos.grad, gx, rtol=1e-10, atol=1e-14)

@@ -83,3 +83,18 @@ def test_gmres_against_dense_solve():
     assert res < 1e-13 and np.abs(x - np.linalg.solve(A, b)).max() < 1e-11
     x0, its0, _ = mobility.gmres(lambda v: A @ v, np.zeros(40), 1e-13, 40)
     assert its0 == 0 and not x0.any()
+
+
+def test_gradient_wrt_force_exact_vs_fd():
+    """dL/dF = 2 M^T U (assembled mobility) agrees with central differences of
+    the loss L = sum |U|^2; M^T differs from M by the discretisation level."""
+    from oracle import adjoint
+    c = np.array([[0.0, 0.0, 0.0], [2.4, 0.3, 0.0]])
+    a = np.array([1.0, 0.8])
+    FT = np.array([[0.3, -0.5, 1.0, 0.1, 0.0, 0.2], [-0.2, 0.4, 0.1, 0.0, 0.3, 0.0]])
+    p = 4
+    g = adjoint.grad_F_exact(c, a, FT, p)
+    coords = [("F", 0, 0), ("F", 1, 2), ("F", 0, 4)]
+    fd = adjoint.grad_fd(c, a, FT, p, coords, h=1e-4)
+    ref = np.array([g[i, k] for _, i, k in coords])
+    assert np.abs(fd - ref).max() < 1e-7 * np.abs(g).max()   # L is quadratic in F
