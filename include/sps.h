@@ -68,8 +68,11 @@ typedef struct sps_params {
                          ||r||/||b|| < ir_tol; 0 disables refinement          */
   int ir_max;         /* refinement sweep cap                                 */
   int warm_start;     /* 1: start GMRES from the previous solution where one
-                         exists (BBPGD iterates 2.., U_nc of the next step of
-                         the same suspension); 0: zero initial guess          */
+                         exists (BBPGD iterates 2.., U_nc of the next step,
+                         consecutive sps_mobility_apply / _adjoint calls on
+                         suspensions of the same size); 0: zero initial guess.
+                         Only the Krylov path changes: every solve still meets
+                         gmres_tol.                                           */
   int bb_safeguard;   /* Algorithm 1 defines no step when s^T y <= 0 (BB1) or
                          y^T y <= 0 (BB2): 0 stops with SPS_ERR_BREAKDOWN,
                          1 keeps the previous step length and continues       */

@@ -282,7 +282,10 @@ int sps_layer_T(sps_ctx* ctx, int op, const double* v, double* out) {
   // out = Analysis^T coefbar (+ v/2 for A)
   SPS_TRY(sps_launch_batched(ctx, 1, ctx->d_analT, 3 * ctx->T.P, NR, ctx->d_coefbar, out, 0,
                              op == SPS_OP_A ? v : nullptr, op == SPS_OP_A ? 1 : 0));
-  SPS_TRY(far_T(ctx, S ? SPS_OP_S : SPS_OP_K, v, out));
+  if (ctx->prm.precision == SPS_MIXED)
+    SPS_TRY(sps_launch_far_T32(ctx, S ? SPS_OP_S : SPS_OP_K, v, out));
+  else
+    SPS_TRY(far_T(ctx, S ? SPS_OP_S : SPS_OP_K, v, out));
   if (op == SPS_OP_A) {
     // L^T: unweighted moments, weighted broadcast
     SPS_TRY(sps_launch_moments_w(ctx, v, ctx->d_mom, false));

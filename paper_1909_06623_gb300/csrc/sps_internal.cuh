@@ -113,6 +113,7 @@ struct sps_ctx {
   double *d_rho = nullptr, *d_zeta = nullptr, *d_b = nullptr, *d_u = nullptr;
   double *d_zeta_nc = nullptr;   // density of the last U_nc solve (warm start)
   long long zeta_nc_n = 0;       // node count it belongs to (0: none)
+  long long zeta_n = 0;          // node count of the last sps_mobility_apply density in d_zeta
   double *d_r = nullptr, *d_dz = nullptr;
 
   // contacts
@@ -209,6 +210,7 @@ int sps_launch_analysis(sps_ctx* ctx, const double* sig, bool fp32);
 int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
 int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32);
 int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
+int sps_launch_far_T32(sps_ctx* ctx, int op, const double* v, double* out);
 int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
 
 // generic batched product (sps_vsh.cu): mode 0 in = planes, out = rows (N x R);

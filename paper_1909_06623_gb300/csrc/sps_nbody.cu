@@ -131,6 +131,8 @@ constexpr int kNPair = SPS_FAR_NPAIR;         // target pairs per thread
 // (measured on GB300: all-packed is fastest; the scalar path is kept for
 // tuning on other parts).
 constexpr int kPacked = SPS_FAR_PACKED;
+constexpr int kOpKT = 3;   // transposed traction (double-layer-type sum, source normals)
+static_assert(kPacked == kNPair, "the transposed traction uses the packed path only");
 constexpr int kTPB32 = kT32 * 2 * kNPair;     // targets per block
 constexpr int kChunkNodes = 512;              // staged source nodes (whole spheres)
 
@@ -152,7 +154,10 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
   float4* sA = sdyn;                           // (-dx, -dx, -dy, -dy)
   float4* sB = sA + cap;                       // (-dz, -dz, wx, wx)
   float4* sC = sB + cap;                       // (wy, wy, wz, wz)
-  float* sh = reinterpret_cast<float*>(sC + cap);  // spc x 6: hi xyz, lo xyz
+  // OP_KT (transposed traction): source normals (nx, nx, ny, ny), (nz, nz, -, -)
+  float4* sD = sC + cap;
+  float4* sE = sD + (OP == kOpKT ? cap : 0);
+  float* sh = reinterpret_cast<float*>(sE + (OP == kOpKT ? cap : 0));  // spc x 6: hi, lo
   // per-thread target state kept out of registers: hi, lo + offset (6 per target)
   __shared__ float sEF[6 * 2 * kNPair][kT32];
   __shared__ int sX[3 * 2 * kNPair][kT32];        // sphere, near pointer, near end
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
         for (int c = 0; c < 3; ++c) {
           sEF[6 * l + c][threadIdx.x] = chi[3 * i + c];
           sEF[6 * l + 3 + c][threadIdx.x] = clo[3 * i + c] + rel[c * NP + tt];
-          n[h][c] = (OP == SPS_OP_K) ? nrm[c * NP + tt] : 0.f;
+          n[h][c] = (OP == SPS_OP_K) ? nrm[c * NP + tt] : 0.f;   // target normal (K)
         }
         // first near neighbour not below j_begin
         int a = near_ptr[i];
@@ -210,6 +215,11 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
         sA[k] = make_float4(dx, dx, dy, dy);
         sB[k] = make_float4(dz, dz, wx, wx);
         sC[k] = make_float4(wy, wy, wz, wz);
+        if (OP == kOpKT) {
+          const float mx = nrm[g], my = nrm[NP + g], mz = nrm[2 * NP + g];
+          sD[k] = make_float4(mx, mx, my, my);
+          sE[k] = make_float4(mz, mz, 0.f, 0.f);
+        }
       }
       for (int k = threadIdx.x; k < ns * 6; k += kT32) {
         const int js = k / 6, c = k % 6;
@@ -238,6 +248,10 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
         const float4* A = sA + js * P;
         const float4* B = sB + js * P;
         const float4* C = sC + js * P;
+        const float4* D = sD + js * P;
+        const float4* Es = sE + js * P;
+        (void)D;
+        (void)Es;
 #pragma unroll 2
         for (int k = 0; k < P; ++k) {
           const float4 a4 = A[k], b4 = B[k], c4 = C[k];
@@ -260,7 +274,14 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
                 ay[q] = __ffma2_rn(wyy, inv, __ffma2_rn(cc, ry, ay[q]));
                 az[q] = __ffma2_rn(wzz, inv, __ffma2_rn(cc, rz, az[q]));
               } else {
-                const float2 rn = __ffma2_rn(rz, nz[q], __ffma2_rn(ry, ny[q], __fmul2_rn(rx, nx[q])));
+                float2 rn;
+                if (OP == kOpKT) {
+                  const float4 d4 = D[k], e4 = Es[k];
+                  rn = __ffma2_rn(rz, make_float2(e4.x, e4.y),
+                                  __ffma2_rn(ry, make_float2(d4.z, d4.w), __fmul2_rn(rx, make_float2(d4.x, d4.y))));
+                } else {
+                  rn = __ffma2_rn(rz, nz[q], __ffma2_rn(ry, ny[q], __fmul2_rn(rx, nx[q])));
+                }
                 const float2 i5 = __fmul2_rn(__fmul2_rn(i2, i2), inv);
                 const float2 cc = __fmul2_rn(__fmul2_rn(rs, rn), i5);
                 ax[q] = __ffma2_rn(cc, rx, ax[q]);
@@ -354,12 +375,13 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
 }
 
 __global__ void k_reduce_parts(long long n3, int splits, const double* __restrict__ part,
-                               double scale, double* __restrict__ out) {
+                               double scale, const double* __restrict__ Wt, double* __restrict__ out) {
+  const long long NP = n3 / 3;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n3;
        g += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int k = 0; k < splits; ++k) s += part[k * n3 + g];
-    out[g] += scale * s;
+    out[g] += scale * (Wt ? Wt[g % NP] : 1.0) * s;
   }
 }
 
@@ -368,10 +390,64 @@ __global__ void k_wsig32(long long NP, const double* __restrict__ sig, const dou
                          float* __restrict__ out) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 3 * NP;
        g += (long long)gridDim.x * blockDim.x)
-    out[g] = (float)(W[g % NP] * sig[g]);
+    out[g] = (float)((W ? W[g % NP] : 1.0) * sig[g]);
 }
 
 }  // namespace
+
+// FP32 far sum of kind kop (SPS_OP_S, SPS_OP_K or kOpKT): sources carry
+// (Wsrc ? Wsrc : 1) * sig, the result is scaled by (Wtgt ? Wtgt : 1) * scale.
+template <int KOP>
+static int far32_run(sps_ctx* ctx, const double* sig, const double* Wsrc, const double* Wtgt, double scale,
+                     double* out, int phase) {
+  const long long NP = ctx->NP;
+  const int P = ctx->T.P, N = ctx->N;
+  const long long n3 = 3 * NP;
+  {
+    SpsPhase timer(ctx, SPS_PH_FAR_AUX);
+    k_wsig32<<<(int)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, ctx->stream>>>(NP, sig, Wsrc,
+                                                                                       ctx->d_sig32);
+    SPS_LAUNCHED(ctx);
+  }
+  // persistent grid over (target block, source split) items
+  const int spc = std::max(1, kChunkNodes / P);
+  const int narr = (KOP == kOpKT) ? 5 : 3;
+  const size_t smem = (size_t)narr * spc * P * sizeof(float4) + (size_t)spc * 6 * sizeof(float);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  cudaFuncAttributes fa;
+  SPS_CUDA(ctx, cudaFuncGetAttributes(&fa, k_far32<KOP>));
+  if (smem + fa.sharedSizeBytes > 48 * 1024)   // static + dynamic above the default limit
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_far32<KOP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far32<KOP>, kT32, smem);
+  const int resident = std::max(1, per_sm) * std::max(1, sms);
+  const int n_tb = (int)((NP + kTPB32 - 1) / kTPB32);
+  // enough items for the atomic queue to balance the load (>= 8 per block)
+  int splits = (int)std::min<long long>(std::max(1, (8 * resident + n_tb - 1) / n_tb), (long long)N);
+  splits = std::min(splits, 64);
+  const int n_items = n_tb * splits;
+  const int grid = std::min(n_items, resident);
+  SPS_TRY(sps_grow(ctx, &ctx->d_part, ctx->cap_part, (size_t)splits * n3 + 1));
+  int* d_work = reinterpret_cast<int*>(ctx->d_part + (size_t)splits * n3);
+  SPS_CUDA(ctx, cudaMemsetAsync(d_work, 0, sizeof(int), ctx->stream));
+  {
+    SpsPhase timer(ctx, phase);
+    k_far32<KOP><<<grid, kT32, smem, ctx->stream>>>(N, P, spc, n_tb, n_items, splits, ctx->d_rel32, ctx->d_N32,
+                                                    ctx->d_sig32, ctx->d_chi, ctx->d_clo, ctx->d_near_ptr,
+                                                    ctx->d_near_idx, d_work, ctx->d_part);
+    SPS_LAUNCHED(ctx);
+  }
+  SpsPhase timer(ctx, SPS_PH_FAR_AUX);
+  k_reduce_parts<<<(int)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+      n3, splits, ctx->d_part, scale, Wtgt, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
 
 int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32) {
   const long long NP = ctx->NP;
@@ -389,63 +465,14 @@ int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp
     SPS_LAUNCHED(ctx);
     return SPS_OK;
   }
-  const long long n3 = 3 * NP;
-  {
-    SpsPhase timer(ctx, SPS_PH_FAR_AUX);
-    k_wsig32<<<(int)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, ctx->stream>>>(
-        NP, sig, ctx->d_W, ctx->d_sig32);
-    SPS_LAUNCHED(ctx);
-  }
-  // persistent grid over (target block, source split) items
-  const int spc = std::max(1, kChunkNodes / P);
-  const size_t smem = (size_t)3 * spc * P * sizeof(float4) + (size_t)spc * 6 * sizeof(float);
-  int per_sm[2] = {0, 0};
-  static int sms = 0;
-  const int oi = (op == SPS_OP_S) ? 0 : 1;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  if (smem > 48 * 1024) {
-    SPS_CUDA(ctx, cudaFuncSetAttribute(k_far32<SPS_OP_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SPS_CUDA(ctx, cudaFuncSetAttribute(k_far32<SPS_OP_K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
-  if (!per_sm[oi]) {
-    if (op == SPS_OP_S)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[oi], k_far32<SPS_OP_S>, kT32, smem);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[oi], k_far32<SPS_OP_K>, kT32, smem);
-    per_sm[oi] = std::max(1, per_sm[oi]);
-  }
-  const int resident = per_sm[oi] * std::max(1, sms);
-  const int n_tb = (int)((NP + kTPB32 - 1) / kTPB32);
-  // enough items for the atomic queue to balance the load (>= 8 per block)
-  int splits = (int)std::min<long long>(std::max(1, (8 * resident + n_tb - 1) / n_tb), (long long)N);
-  splits = std::min(splits, 64);
-  const int n_items = n_tb * splits;
-  const int grid = std::min(n_items, resident);
-  SPS_TRY(sps_grow(ctx, &ctx->d_part, ctx->cap_part, (size_t)splits * n3 + 1));
-  int* d_work = reinterpret_cast<int*>(ctx->d_part + (size_t)splits * n3);
-  SPS_CUDA(ctx, cudaMemsetAsync(d_work, 0, sizeof(int), ctx->stream));
-  {
-    SpsPhase timer(ctx, ph);
-    if (op == SPS_OP_S)
-      k_far32<SPS_OP_S><<<grid, kT32, smem, ctx->stream>>>(N, P, spc, n_tb, n_items, splits, ctx->d_rel32,
-                                                          ctx->d_N32, ctx->d_sig32, ctx->d_chi, ctx->d_clo,
-                                                          ctx->d_near_ptr, ctx->d_near_idx, d_work,
-                                                          ctx->d_part);
-    else
-      k_far32<SPS_OP_K><<<grid, kT32, smem, ctx->stream>>>(N, P, spc, n_tb, n_items, splits, ctx->d_rel32,
-                                                          ctx->d_N32, ctx->d_sig32, ctx->d_chi, ctx->d_clo,
-                                                          ctx->d_near_ptr, ctx->d_near_idx, d_work,
-                                                          ctx->d_part);
-    SPS_LAUNCHED(ctx);
-  }
-  SpsPhase timer(ctx, SPS_PH_FAR_AUX);
-  const double s = (op == SPS_OP_S) ? 1.0 / (8.0 * SPS_PI) : -3.0 / (4.0 * SPS_PI);
-  k_reduce_parts<<<(int)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, ctx->stream>>>(
-      n3, splits, ctx->d_part, s, out);
-  SPS_LAUNCHED(ctx);
-  return SPS_OK;
+  if (op == SPS_OP_S) return far32_run<SPS_OP_S>(ctx, sig, ctx->d_W, nullptr, 1.0 / (8.0 * SPS_PI), out, ph);
+  return far32_run<SPS_OP_K>(ctx, sig, ctx->d_W, nullptr, -3.0 / (4.0 * SPS_PI), out, ph);
+}
+
+// transposed far sums in FP32 (mixed-precision adjoint): S^T with the weights
+// at the target, K^T = +3/(4 pi) w_t sum r (r.v)(r.n_s)/|r|^5
+int sps_launch_far_T32(sps_ctx* ctx, int op, const double* v, double* out) {
+  if (op == SPS_OP_S)
+    return far32_run<SPS_OP_S>(ctx, v, nullptr, ctx->d_W, 1.0 / (8.0 * SPS_PI), out, SPS_PH_FAR_S);
+  return far32_run<kOpKT>(ctx, v, nullptr, ctx->d_W, 3.0 / (4.0 * SPS_PI), out, SPS_PH_FAR_K);
 }

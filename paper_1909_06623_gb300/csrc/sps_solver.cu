@@ -716,7 +716,10 @@ extern "C" int sps_mobility_apply(sps_ctx* ctx, int n, const double* pos, const 
   stats_begin(ctx, st, &l0);
   int rc = sps_set_geometry(ctx, n, pos, radii);
   if (rc == SPS_OK) rc = check_finite_host(ctx, FT, 6LL * n, "force/torque");
-  if (rc == SPS_OK) rc = mobility_solve(ctx, FT, UO, st, ctx->d_zeta, false);
+  // warm start from the previous solve on a suspension of the same size
+  const bool warm = ctx->prm.warm_start && ctx->zeta_n == ctx->NP;
+  if (rc == SPS_OK) rc = mobility_solve(ctx, FT, UO, st, ctx->d_zeta, warm);
+  ctx->zeta_n = (rc == SPS_OK) ? ctx->NP : 0;
   if (rc == SPS_OK || rc == SPS_ERR_NOT_CONVERGED) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
@@ -781,6 +784,7 @@ static int ensure_bb(sps_ctx* ctx, int nc) {
 static int apply_M(sps_ctx* ctx, const double* gam, double* out, sps_stats* st, bool warm) {
   SPS_TRY(sps_launch_D(ctx, gam, ctx->d_FT));
   int rc = mobility_solve(ctx, ctx->d_FT, ctx->d_Uc, st, ctx->d_zeta, warm);
+  ctx->zeta_n = 0;   // d_zeta now holds a contact-force solve
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
   if (st) st->mvops += 1;
   SPS_TRY(sps_launch_DT(ctx, ctx->d_Uc, out));
@@ -966,7 +970,9 @@ extern "C" int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, cons
   const long long n3 = 3LL * ctx->NP;
   // forward solve; keep sigma = rho + zeta
   double* U = UO ? UO : ctx->d_Uc;
-  int frc = mobility_solve(ctx, FT, U, st, ctx->d_zeta, false);
+  const bool warm = ctx->prm.warm_start && ctx->zeta_n == ctx->NP;
+  int frc = mobility_solve(ctx, FT, U, st, ctx->d_zeta, warm);
+  ctx->zeta_n = (frc == SPS_OK) ? ctx->NP : 0;
   if (frc != SPS_OK && frc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, frc);
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_sigtot, ctx->d_tmp3, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
                                 ctx->stream));

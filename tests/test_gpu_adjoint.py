@@ -166,3 +166,76 @@ def test_autograd_function(sps):
     _, gF, gx = ctx.mobility_adjoint(dev(C), dev(R), dev(FT), 2.0 * U2)
     assert torch.allclose(F.grad, gF, rtol=1e-10, atol=1e-14)
     assert torch.allclose(pos.grad, gx, rtol=1e-10, atol=1e-14)
+
+
+def test_mixed_adjoint_close_to_fp64(sps):
+    """The mixed-precision adjoint (FP32 transposed far sums, FP64 near and
+    Krylov) agrees with the FP64 adjoint to the mixed-path tolerance."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.tiny(21, 12, 5, phi=0.15, n_pairs=2, gap=0.01)
+    pos, rad, FT = dev(w.centers), dev(w.radii), dev(w.FT)
+    out = {}
+    for prec, tol in ((0, 1e-13), (1, 1e-9)):
+        ctx = sps.Context(p=5, gmres_tol=tol, gmres_max=400, precision=prec)
+        U = ctx.mobility_apply(pos, rad, FT)
+        out[prec] = ctx.mobility_adjoint(pos, rad, FT, 2.0 * U)
+        if prec == 1:
+            NP = len(w.radii) * 72
+            ctx.set_geometry(pos, rad)
+            for op in (sps.SPS_OP_S, sps.SPS_OP_K, sps.SPS_OP_A):
+                assert _transpose_gap(ctx, sps, op, NP, 5 + op) < 2e-6, op
+    for k in (1, 2):
+        a, b = out[1][k], out[0][k]
+        assert ((a - b).abs().max() / b.abs().max()).item() < 1e-4
+
+
+@pytest.mark.skipif(os.environ.get("SPS_SLOW_TESTS") != "1", reason="set SPS_SLOW_TESTS=1 (about 20 GPU minutes)")
+def test_cfg4_gradient_finite_differences(sps):
+    """1,000 unit spheres at volume fraction 0.25, p = 6, L = sum |U|^2: the
+    mixed-precision adjoint against the FP64 adjoint, and the FP64 adjoint
+    against central differences (h = 1e-6, FP64 forward solves) on 32 seeded
+    coordinates (16 forces, 16 centre components)."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.config4()
+    pos, rad, FT = dev(w.centers), dev(w.radii), dev(w.FT)
+    c64 = sps.Context(p=6, gmres_tol=1e-12, gmres_max=400)
+    U = c64.mobility_apply(pos, rad, FT)
+    _, gF, gx = c64.mobility_adjoint(pos, rad, FT, 2.0 * U)
+    cmx = sps.Context(p=6, gmres_tol=1e-8, gmres_max=400, precision=1)
+    Um = cmx.mobility_apply(pos, rad, FT)
+    _, gFm, gxm = cmx.mobility_adjoint(pos, rad, FT, 2.0 * Um)
+    for a, b in ((gFm, gF), (gxm, gx)):
+        assert ((a - b).abs().max() / b.abs().max()).item() < 1e-4
+    rng = np.random.default_rng(workloads.SEED_BASE + 40)
+    h = 1e-6
+    # centre coordinates whose near pairs stay away from the beta threshold
+    from oracle.layer import near_lists
+    errs = []
+    coords = [("F", int(i), int(k)) for i, k in zip(rng.choice(w.N, 16), rng.integers(0, 6, 16))]
+    cand = rng.permutation(w.N)
+    picked = 0
+    for i in cand:
+        d = np.linalg.norm(w.centers - w.centers[i], axis=1)
+        t = np.abs(d - 1.75 * (w.radii + w.radii[i]))
+        t[i] = np.inf
+        if t.min() > 100 * h:
+            coords.append(("c", int(i), int(rng.integers(0, 3))))
+            picked += 1
+        if picked == 16:
+            break
+    for kind, i, k in coords:
+        vals = []
+        for s in (1, -1):
+            p2, F2 = pos.clone(), FT.clone()
+            if kind == "F":
+                F2[i, k] += s * h
+            else:
+                p2[i, k] += s * h
+            Ui = c64.mobility_apply(p2, rad, F2)
+            vals.append(torch.sum(Ui * Ui).item())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        ref = (gF if kind == "F" else gx)[i, k].item()
+        scale = (gF if kind == "F" else gx).abs().max().item()
+        errs.append(abs(fd - ref) / scale)
+    print("cfg4 FD max rel err", max(errs))
+    assert max(errs) < 1e-4
