@@ -172,3 +172,67 @@ def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
                 n_active=int(np.sum(gamma > 0)))
     return {"gamma": gamma, "g": g, "q": q, "ij": ij, "phi": phi0, "normals": nrm,
             "U": U, "U_nc": U_nc, "centers_new": cnew, "info": info}
+
+
+# ----------------------------------------------------------------------------
+# Large contact sets: one sphere's row, vectorised D / D^T, identity mobility
+# ----------------------------------------------------------------------------
+def contacts_of_sphere(centers, radii, i, delta, a_c_scale=1.0):
+    """Row i of the contact set of Sec. 3.2: every j > i with Phi_ij <= delta.
+
+    The same arithmetic as build_contacts, element-wise over all j at once
+    (numpy rounds each array operation separately, so the values agree to the
+    bit).  Returns (j ascending, Phi, normals)."""
+    c = np.asarray(centers, dtype=np.float64).reshape(-1, 3)
+    a = np.asarray(radii, dtype=np.float64).reshape(-1)
+    cj = c[i + 1:]
+    dx = cj[:, 0] - c[i, 0]
+    dy = cj[:, 1] - c[i, 1]
+    dz = cj[:, 2] - c[i, 2]
+    d = np.sqrt((dx * dx + dy * dy) + dz * dz)
+    phi = (d - a[i] * a_c_scale) - a[i + 1:] * a_c_scale
+    k = np.nonzero(phi <= delta)[0]
+    nrm = np.stack([dx[k] / d[k], dy[k] / d[k], dz[k] / d[k]], axis=1)
+    return (k + i + 1).astype(np.int64), phi[k], nrm
+
+
+def D_apply_vec(N, ij, nrm, gamma):
+    """D gamma of eq. Dmatdef for large contact sets (unbuffered scatter-add)."""
+    FT = np.zeros((N, 6))
+    f = np.asarray(gamma, dtype=np.float64)[:, None] * np.asarray(nrm, dtype=np.float64)
+    for c in range(3):
+        np.add.at(FT[:, c], ij[:, 0], -f[:, c])
+        np.add.at(FT[:, c], ij[:, 1], f[:, c])
+    return FT
+
+
+def DT_apply_vec(ij, nrm, UO):
+    """D^T U of eq. Dtranspose for large contact sets."""
+    dU = UO[ij[:, 1], :3] - UO[ij[:, 0], :3]
+    return np.einsum("lc,lc->l", nrm, dU)
+
+
+def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_scale=1.0,
+                                bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False):
+    """The collision step of Sec. 3.2 with the mobility replaced by the
+    identity (U = F, Omega = T).  No fluid: M = D^T D is the constraint Gram
+    matrix, which isolates contacts, D products and Algorithm 1 at sizes where
+    no N-body sum could run.  Returns the same dict as resolve_collisions."""
+    C = np.asarray(centers, dtype=np.float64)
+    FT_ext = np.asarray(FT_ext, dtype=np.float64).reshape(-1, 6)
+    N = len(C)
+    ij, phi0, nrm = build_contacts(C, radii, delta, a_c_scale)
+    U_nc = FT_ext.copy()
+    q = phi0 / dt + DT_apply(ij, nrm, U_nc)
+    state = {"U_c": np.zeros_like(U_nc)}
+
+    def Mop(gam):
+        state["U_c"] = D_apply(N, ij, nrm, gam)
+        return DT_apply(ij, nrm, state["U_c"])
+
+    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard)
+    U_c = np.zeros_like(U_nc) if info["iters"] == 0 else state["U_c"]
+    U = U_nc + U_c
+    info.update(n_contacts=len(q), n_active=int(np.sum(gamma > 0)))
+    return {"gamma": gamma, "g": g, "q": q, "ij": ij, "phi": phi0, "normals": nrm,
+            "U": U, "U_nc": U_nc, "centers_new": C + U[:, :3] * dt, "info": info}

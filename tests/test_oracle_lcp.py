@@ -115,3 +115,95 @@ def test_bbpgd_breakdown_and_safeguard():
     assert info["status"] == "breakdown"
     gam, g, info = lcp.bbpgd(lambda x: M @ x, q, 1e-12, jmax=50, safeguard=True)
     assert info["safeguards"] >= 1 and info["status"] in ("ok", "not_converged")
+
+
+# ---------------------------------------------------------------------------
+# large contact sets: per-sphere rows, vectorised D / D^T, identity mobility
+# ---------------------------------------------------------------------------
+def test_contact_rows_bit_exact():
+    w = workloads.jittered_lattice(11, 343, jitter=0.15)
+    ij, phi, nrm = lcp.build_contacts(w.centers, w.radii, 0.1, 1.05)
+    assert len(ij) > 100
+    for i in range(w.N):
+        j, ph, nr = lcp.contacts_of_sphere(w.centers, w.radii, i, 0.1, 1.05)
+        sel = ij[:, 0] == i
+        assert np.array_equal(j, ij[sel, 1])
+        assert ph.tobytes() == phi[sel].tobytes() and nr.tobytes() == nrm[sel].tobytes()
+
+
+def test_vectorised_D_products():
+    rng = np.random.default_rng(5)
+    w = workloads.jittered_lattice(12, 216, jitter=0.2)
+    ij, phi, nrm = lcp.build_contacts(w.centers, w.radii, 0.1, 1.05)
+    gam = rng.random(len(ij))
+    U = rng.standard_normal((w.N, 6))
+    assert np.abs(lcp.D_apply_vec(w.N, ij, nrm, gam) - lcp.D_apply(w.N, ij, nrm, gam)).max() < 1e-14
+    assert np.abs(lcp.DT_apply_vec(ij, nrm, U) - lcp.DT_apply(ij, nrm, U)).max() < 1e-14
+    assert abs(np.sum(lcp.D_apply_vec(w.N, ij, nrm, gam) * U) - gam @ lcp.DT_apply_vec(ij, nrm, U)) < 1e-11
+
+
+def test_identity_step_head_on_pair():
+    # two spheres overlapping along x, no external force: M = D^T D = 2, so
+    # gamma = -Phi / (2 dt) and one step separates them to exactly Phi = 0
+    c = np.array([[0.0, 0.0, 0.0], [1.9, 0.0, 0.0]])
+    a = np.array([1.0, 1.0])
+    dt = 1e-3
+    out = lcp.resolve_collisions_identity(c, a, np.zeros((2, 6)), dt, delta=0.1, bbpgd_tol=1e-12)
+    assert out["ij"].tolist() == [[0, 1]]
+    assert abs(out["gamma"][0] - 0.1 / (2 * dt)) < 1e-9
+    cn = out["centers_new"]
+    assert abs(np.linalg.norm(cn[1] - cn[0]) - 2.0) < 1e-13
+    # approaching at speed 2f with a gap: gamma = max(0, -(Phi/dt - 2 f) / 2)
+    c2 = np.array([[0.0, 0.0, 0.0], [2.05, 0.0, 0.0]])
+    F = np.zeros((2, 6))
+    F[0, 0], F[1, 0] = 100.0, -100.0
+    out = lcp.resolve_collisions_identity(c2, a, F, dt, delta=0.1, bbpgd_tol=1e-12)
+    assert abs(out["gamma"][0] - (200.0 - 0.05 / dt) / 2) < 1e-9
+    cn = out["centers_new"]
+    assert abs(np.linalg.norm(cn[1] - cn[0]) - 2.0) < 1e-13
+    # separating pair: no force needed
+    out = lcp.resolve_collisions_identity(c2, a, -F, dt, delta=0.1, bbpgd_tol=1e-12)
+    assert out["gamma"][0] == 0.0 and out["info"]["iters"] == 0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_identity_step_matches_enumeration(seed):
+    rng = np.random.default_rng(100 + seed)
+    # a short chain of touching unit spheres along a wobbly line
+    n = 5
+    c = np.zeros((n, 3))
+    for k in range(1, n):
+        d = np.array([1.0, 0.2 * rng.standard_normal(), 0.2 * rng.standard_normal()])
+        c[k] = c[k - 1] + (1.95 + 0.1 * rng.random()) * d / np.linalg.norm(d)
+    a = np.ones(n)
+    F = rng.standard_normal((n, 6)) * 50
+    dt = 1e-3
+    out = lcp.resolve_collisions_identity(c, a, F, dt, delta=0.1, bbpgd_tol=1e-12)
+    ij, nrm, q = out["ij"], out["normals"], out["q"]
+    nc = len(q)
+    assert nc >= n - 1
+    M = np.zeros((nc, nc))
+    for k in range(nc):
+        e = np.zeros(nc)
+        e[k] = 1.0
+        M[:, k] = lcp.DT_apply(ij, nrm, lcp.D_apply(n, ij, nrm, e))
+    ref = lcp.lcp_enumerate(M, q)
+    assert np.abs(out["gamma"] - ref).max() < 1e-8 * max(1.0, np.abs(ref).max())
+    g = M @ out["gamma"] + q
+    assert out["gamma"].min() >= 0 and g.min() > -1e-9 and abs(out["gamma"] @ g) < 1e-6
+    # U = F_ext + D gamma
+    U = F + lcp.D_apply(n, ij, nrm, out["gamma"])
+    assert np.abs(out["U"] - U).max() < 1e-9
+
+
+def test_jittered_lattice_statistics():
+    w = workloads.jittered_lattice(13, 8000)
+    pairs = cKDTree(w.centers).query_pairs(2 * 1.05 + 0.1, output_type="ndarray")
+    d = np.linalg.norm(w.centers[pairs[:, 0]] - w.centers[pairs[:, 1]], axis=1)
+    phi = d - 1.05 * (w.radii[pairs[:, 0]] + w.radii[pairs[:, 1]])
+    nc = np.sum(phi <= 0.1)
+    assert 0.7 < nc / w.N < 1.3
+    assert 0.4 < np.sum(phi < 0) / nc < 0.8
+    vol = np.sum(4 / 3 * np.pi * w.radii ** 3)
+    L = np.ptp(w.centers, axis=0) + 2 * 1.0
+    assert 0.25 < vol / np.prod(L) < 0.4
