@@ -8,6 +8,12 @@ quadrature).  One "step" = one call of sps_resolve_collisions: the U_nc
 mobility solve, the contact set, BBPGD (each iteration a mobility solve) and the
 Euler update; positions advance step after step.
 
+Also (unless --no-contact-bench) one identity-mobility collision step on a
+large jittered lattice (2 x 10^7 spheres, volume fraction 0.35, a ~ U[0.5,1],
+a_c = 1.05 a, delta = 0.1): the contact search, D, D^T and Algorithm 1 with
+U = F, where no N-body sum runs; its kernels are HBM-bound and are reported
+against the measured HBM bandwidth ("contact_bbpgd_microbench").
+
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
 """
@@ -33,6 +39,10 @@ FLOPS_PER_PAIR = {"K": 30, "S": 29}   # algorithmic FP32 operations per pair ter
 # (None whenever the kernel changes until it is captured again)
 FAR_K_TRAFFIC_BYTES = None
 SMS, LANES = 152, 128
+N_PHASES = 12
+PHASES = ["far_K", "far_S", "far_aux", "near_K", "near_S", "self_vsh", "krylov", "contact",
+          "bbpgd", "geometry", "bb_D", "bb_DT"]
+CONTACT_N = 20_000_000
 
 
 def peaks():
@@ -226,8 +236,8 @@ def run_gpu(args, w):
         pos.copy_(pos_out)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    ph_ms = (ctypes.c_double * 10)()
-    ph_n = (ctypes.c_longlong * 10)()
+    ph_ms = (ctypes.c_double * N_PHASES)()
+    ph_n = (ctypes.c_longlong * N_PHASES)()
     sps._lib.load().sps_profile_read(ctx.h, ph_ms, ph_n)
     sps._lib.load().sps_profile(ctx.h, 0)
     if world > 1:
@@ -253,10 +263,8 @@ def run_gpu(args, w):
     pk = peaks()
     achieved = FLOPS_PER_PAIR["K"] * pairs / (avgK * 1e-3) / 1e12
     interactions = pairs * (farK_n + farS_n) / total_s
-    phases = ["far_K", "far_S", "far_aux", "near_K", "near_S", "self_vsh", "krylov", "contact",
-              "bbpgd", "geometry"]
     phase_report = {nm: {"ms": round(ph_ms[i], 3), "launches": int(ph_n[i])}
-                    for i, nm in enumerate(phases)}
+                    for i, nm in enumerate(PHASES)}
     launches = int(sum(s["kernel_launches"] for s in stats))
 
     # e2e: same step through the host-buffer entry point (copies inside)
@@ -315,6 +323,12 @@ def run_gpu(args, w):
                           f"({sample:.1f} s), scaled x{N}/3 to one application and "
                           f"x{mvps:.0f} applications per step (this run's GMRES counts)")}
 
+    contact = None
+    if rank == 0 and not args.no_contact_bench:
+        del flush
+        torch.cuda.empty_cache()
+        contact = run_contacts(args, args.contact_n, local)
+
     if rank == 0:
         last = stats[-1]
         line = {
@@ -354,10 +368,101 @@ def run_gpu(args, w):
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "contact_bbpgd_microbench": contact,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# contact / BBPGD microbenchmark (identity mobility, HBM-bound)
+# ---------------------------------------------------------------------------
+def contact_bytes(N, nc):
+    """Algorithmic bytes of one launch of each fused BBPGD pass: every array
+    element the pass must touch, once (FP64 values 8 B, indices 4 B).
+      per-sphere pass (projected step + D): per contact its two incidence
+        entries (8), gamma, g, n (40) and the stored projected gamma (8);
+        per sphere its incidence offset (4) and force (24);
+      per-contact pass (D^T + q + statistics): per contact i, j (8), n (24),
+        q, gamma_new, gamma, g (32) and g_new (8); per sphere its force (24)."""
+    return {"bb_D": 56 * nc + 28 * N, "bb_DT": 72 * nc + 24 * N}
+
+
+def run_contacts(args, N, gpu_index, standalone=False):
+    import torch
+    import paper_1909_06623_gb300 as sps
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.jittered_lattice(workloads.SEED_BASE + 6, N)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    tol = 1e-4 * np.sqrt(N)
+    ctx = sps.Context(stream=stream, p=2, delta=0.1, a_c_scale=1.05, mobility=sps.SPS_MOB_IDENTITY,
+                      bbpgd_tol=tol, bbpgd_max=1000, bb_safeguard=1)
+    pos, rad, FT = dev(w.centers), dev(w.radii), dev(w.FT)
+    gam = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    UO = torch.empty(N, 6, dtype=torch.float64, device="cuda")
+    pos_out = torch.empty_like(pos)
+
+    def step():
+        ctx.resolve_collisions(pos, rad, FT, w.dt, gamma=gam, UO=UO, pos_out=pos_out,
+                               gamma_cap=gam.numel(), allow=(4, 5))
+        return dict(ctx.last_stats)
+
+    for _ in range(args.warmup):
+        step()
+        pos.copy_(pos_out)
+    torch.cuda.synchronize()
+    lib = sps._lib.load()
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    lib.sps_profile(ctx.h, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        stats.append(step())
+        ev[k][1].record(stream)
+        pos.copy_(pos_out)
+    torch.cuda.synchronize()
+    ph_ms = (ctypes.c_double * N_PHASES)()
+    ph_n = (ctypes.c_longlong * N_PHASES)()
+    lib.sps_profile_read(ctx.h, ph_ms, ph_n)
+    lib.sps_profile(ctx.h, 0)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    nc = stats[-1]["n_contacts"]
+    pk = peaks()
+    by = contact_bytes(N, nc)
+    roof = []
+    for nm, kern in (("bb_D", "k_bb_ident_D"), ("bb_DT", "k_bb_ident_DT")):
+        i = PHASES.index(nm)
+        avg = ph_ms[i] / max(ph_n[i], 1)
+        ach = by[nm] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        roof.append({"kernel": kern, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "bytes_per_launch": by[nm],
+                     "avg_launch_ms": avg, "launches": int(ph_n[i]), "traffic": None,
+                     "peak_note": f"measured STREAM copy ({pk['source']})"})
+    out = {"workload": w.name, "N": N, "n_contacts": nc,
+           "n_active": stats[-1]["n_active"], "bbpgd_tol": tol,
+           "bbpgd_iters": [s["bbpgd_iters"] for s in stats],
+           "status": [s["status"] for s in stats],
+           "ms_per_step": float(np.mean(step_ms)), "step_ms": step_ms,
+           "steps_per_s": 1e3 / float(np.mean(step_ms)),
+           "contact_updates_per_s": nc * float(np.mean([s["bbpgd_iters"] for s in stats])) /
+           (float(np.mean(step_ms)) * 1e-3),
+           "phases_ms": {nm: {"ms": round(ph_ms[i], 3), "launches": int(ph_n[i])}
+                         for i, nm in enumerate(PHASES) if ph_n[i]},
+           "roofline": roof,
+           "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+           "clocks": clk,
+           "l2": "inputs larger than L2 (positions and radii alone 640 MB), no flush",
+           "data": "synthetic jittered lattice (contact statistics of the random suspensions)"}
+    ctx.close()
+    if standalone:
+        print(json.dumps({"contact_bbpgd_microbench": out}), flush=True)
+    return out
 
 
 def run_single_op(args, w):
@@ -389,7 +494,16 @@ def main():
     ap.add_argument("--ref-matvecs-per-step", type=float, default=185.0)
     ap.add_argument("--single-op", choices=["K", "S", "A"], default=None,
                     help="apply one layer operator on the workload geometry and exit")
+    ap.add_argument("--no-contact-bench", action="store_true")
+    ap.add_argument("--contact-n", type=int, default=CONTACT_N)
+    ap.add_argument("--contact-only", action="store_true",
+                    help="run only the identity-mobility contact benchmark")
     args = ap.parse_args()
+    if args.contact_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        run_contacts(args, args.contact_n, int(os.environ.get("LOCAL_RANK", "0")), standalone=True)
+        return
     w = workload(args.workload)
     if args.single_op:
         run_single_op(args, w)

@@ -46,6 +46,21 @@ typedef enum {
 
 typedef enum { SPS_FP64 = 0, SPS_MIXED = 1 } sps_precision;
 
+/* Mobility used by the solves.  SPS_MOB_BIE is the boundary-integral mobility
+ * of Sec. 4.  SPS_MOB_IDENTITY (U = F, Omega = T) is not in the paper: it
+ * drops the fluid so that the collision machinery of Sec. 3 (contact search,
+ * D, D^T, Algorithm 1) runs alone at sizes where no all-pairs layer sum can;
+ * the LCP matrix is then D^T D. */
+typedef enum { SPS_MOB_BIE = 0, SPS_MOB_IDENTITY = 1 } sps_mobility;
+
+/* Contact search.  Both give the same list to the bit (the test of Sec. 3.2
+ * is evaluated identically); the cell list is O(n) and needs finite positions. */
+typedef enum {
+  SPS_SEARCH_AUTO = 0,      /* cell list when n > 4096, else all pairs         */
+  SPS_SEARCH_ALL_PAIRS = 1, /* every pair i < j                                */
+  SPS_SEARCH_CELLS = 2      /* uniform grid of cells of side >= 2 max a_c + delta */
+} sps_contact_search;
+
 /* Layer operators of Sec. 4.1 evaluated on all surface nodes. */
 typedef enum {
   SPS_OP_S = 0, /* single layer S[sigma](x) = int G(x-y) sigma(y) dS_y         */
@@ -76,6 +91,8 @@ typedef struct sps_params {
   int bb_safeguard;   /* Algorithm 1 defines no step when s^T y <= 0 (BB1) or
                          y^T y <= 0 (BB2): 0 stops with SPS_ERR_BREAKDOWN,
                          1 keeps the previous step length and continues       */
+  int mobility;       /* sps_mobility (default SPS_MOB_BIE)                   */
+  int contact_search; /* sps_contact_search (default SPS_SEARCH_AUTO)         */
 } sps_params;
 
 typedef struct sps_stats {
@@ -230,7 +247,11 @@ typedef enum {
   SPS_PH_CONTACT = 7,  /* contact set, D, D^T                                */
   SPS_PH_BBPGD = 8,    /* BBPGD vector kernels                               */
   SPS_PH_GEOM = 9,     /* surface nodes and near lists ("Far/Near Setup")    */
-  SPS_PH_COUNT = 10
+  SPS_PH_BB_D = 10,    /* identity mobility: per-sphere pass of a BBPGD step
+                          (projected step and D)                             */
+  SPS_PH_BB_DT = 11,   /* identity mobility: per-contact pass (D^T, + q and
+                          the step's statistics)                             */
+  SPS_PH_COUNT = 12
 } sps_phase;
 
 /* enable != 0 starts recording (and clears the totals); 0 stops. */

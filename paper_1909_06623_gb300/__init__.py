@@ -14,10 +14,13 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (SPS_FP64, SPS_MIXED, SPS_OP_A, SPS_OP_K, SPS_OP_S, SPSError, sps_params,
-                   sps_stats)
+from ._lib import (SPS_FP64, SPS_MIXED, SPS_MOB_BIE, SPS_MOB_IDENTITY, SPS_OP_A, SPS_OP_K,
+                   SPS_OP_S, SPS_SEARCH_ALL_PAIRS, SPS_SEARCH_AUTO, SPS_SEARCH_CELLS, SPSError,
+                   sps_params, sps_stats)
 
 __all__ = ["Context", "SPSError", "SPS_FP64", "SPS_MIXED", "SPS_OP_S", "SPS_OP_K", "SPS_OP_A",
+           "SPS_MOB_BIE", "SPS_MOB_IDENTITY", "SPS_SEARCH_AUTO", "SPS_SEARCH_ALL_PAIRS",
+           "SPS_SEARCH_CELLS",
            "default_params", "unit_tables", "nodes_per_sphere", "MobilityFunction", "mobility"]
 
 
@@ -154,7 +157,7 @@ class Context:
         return nc.value
 
     def get_contacts(self):
-        nc = self.n_c
+        nc = getattr(self, "n_c", 0)
         ij = torch.empty(max(nc, 1), 2, dtype=torch.int32, device="cuda")
         phi = torch.empty(max(nc, 1), dtype=torch.float64, device="cuda")
         nrm = torch.empty(max(nc, 1), 3, dtype=torch.float64, device="cuda")
@@ -200,6 +203,7 @@ class Context:
                                              _ptr(pos_out), ctypes.byref(st))
         self._check(rc, allow=allow)
         self.last_stats = st.as_dict()
+        self.n_c = st.n_contacts          # the contact list stays in the context
         return gamma[: st.n_contacts], UO, pos_out
 
     def resolve_collisions_host(self, pos, radii, FT_ext, dt, gamma, UO, pos_out, allow=()):
@@ -214,6 +218,7 @@ class Context:
             ctypes.byref(st))
         self._check(rc, allow=allow)
         self.last_stats = st.as_dict()
+        self.n_c = nc.value
         return nc.value
 
 

@@ -1,0 +1,768 @@
+// Contact set (Sec. 3.2), the contact Jacobian D and its transpose
+// (eq. Dmatdef, eq. Dtranspose), the BBPGD statistics of Algorithm 1, and the
+// fused BBPGD iteration for the identity mobility.
+//
+// Contact search.  Small suspensions test every pair i < j.  Large ones use a
+// uniform grid of cells whose side is at least 2 max a_c + delta, so that every
+// contact pair lies in the same or in adjacent cells; spheres are sorted by
+// cell (stable radix sort), and each sphere scans the 3 x 3 rows of adjacent
+// cells, which are contiguous runs of the sorted order.  Candidates are
+// screened in FP32 with a margin that bounds the rounding of the FP32 copies;
+// every survivor takes the FP64 test of the all-pairs search (sps_contact_test)
+// and each row is sorted by j, so both searches give the same list to the bit.
+//
+// D and D^T: per sphere, its incident contacts in contact order (a stable sort
+// of the contact ends); per contact, n . (U_j - U_i).  All reductions use a
+// fixed partition and order, so every result is reproducible run to run.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "sps_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kStatBlocks = 4 * 152;   // fixed partition of the BBPGD reductions
+constexpr int kBoundBlocks = 2 * 152;
+
+inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+__device__ __forceinline__ bool contact_at(const double* pos, const double* rad, double acs,
+                                           double delta, int i, int j, SpsContactGeom* g) {
+  return sps_contact_test(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], rad[i], pos[3 * j],
+                          pos[3 * j + 1], pos[3 * j + 2], rad[j], acs, delta, g);
+}
+
+__device__ __forceinline__ void put_contact(int o, int i, int j, const SpsContactGeom& g, int* ij,
+                                            double* phi, double* nrm, int* keys, int* vals) {
+  ij[2 * o] = i;
+  ij[2 * o + 1] = j;
+  phi[o] = g.phi;
+  nrm[3 * o + 0] = g.nx;
+  nrm[3 * o + 1] = g.ny;
+  nrm[3 * o + 2] = g.nz;
+  keys[2 * o] = i;
+  vals[2 * o] = 2 * o;          // contact o, sphere is first (sign -1)
+  keys[2 * o + 1] = j;
+  vals[2 * o + 1] = 2 * o + 1;  // contact o, sphere is second (sign +1)
+}
+
+// ---------------------------------------------------------------------------
+// all pairs
+// ---------------------------------------------------------------------------
+__global__ void k_pairs_count(int N, const double* pos, const double* rad, double acs, double delta,
+                              int* cnt, int* cnt2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int c = 0;
+  for (int j = i + 1; j < N; ++j)
+    if (contact_at(pos, rad, acs, delta, i, j, nullptr)) {
+      ++c;
+      atomicAdd(&cnt2[j], 1);   // integer count of contacts where j is second
+    }
+  cnt[i] = c;
+}
+
+__global__ void k_pairs_fill(int N, const double* pos, const double* rad, double acs, double delta,
+                             const int* ptr, int* ij, double* phi, double* nrm, int* keys, int* vals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int o = ptr[i];
+  SpsContactGeom g;
+  for (int j = i + 1; j < N; ++j)
+    if (contact_at(pos, rad, acs, delta, i, j, &g)) put_contact(o++, i, j, g, ij, phi, nrm, keys, vals);
+}
+
+// ---------------------------------------------------------------------------
+// cell list
+// ---------------------------------------------------------------------------
+// per block: min x, y, z, max x, y, z, max a, number of bad inputs
+__global__ void k_cl_bounds(int N, const double* __restrict__ pos, const double* __restrict__ rad,
+                            double* __restrict__ part) {
+  double v[8] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], a = rad[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(a) || !(a > 0)) {
+      v[7] += 1.0;
+      continue;
+    }
+    v[0] = fmin(v[0], x);
+    v[1] = fmin(v[1], y);
+    v[2] = fmin(v[2], z);
+    v[3] = fmax(v[3], x);
+    v[4] = fmax(v[4], y);
+    v[5] = fmax(v[5], z);
+    v[6] = fmax(v[6], a);
+  }
+  __shared__ double red[kThreads / 32][8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, v[c], o);
+      v[c] = c < 3 ? fmin(v[c], w) : (c < 7 ? fmax(v[c], w) : v[c] + w);
+    }
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) red[threadIdx.x >> 5][c] = v[c];
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int c = threadIdx.x;
+    double s = red[0][c];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      s = c < 3 ? fmin(s, red[w][c]) : (c < 7 ? fmax(s, red[w][c]) : s + red[w][c]);
+    part[c * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_cl_bounds_finish(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= 8) return;
+  double s = part[c * nb];
+  for (int b = 1; b < nb; ++b) {
+    const double w = part[c * nb + b];
+    s = c < 3 ? fmin(s, w) : (c < 7 ? fmax(s, w) : s + w);
+  }
+  out[c] = s;
+}
+
+struct CellGrid {
+  double lo[3], inv_w[3];
+  int dims[3];
+  float eps;   // absolute margin of the FP32 screen
+};
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv_w, int dim) {
+  const int c = (int)((x - lo) * inv_w);
+  return min(max(c, 0), dim - 1);
+}
+
+__global__ void k_cl_keys(int N, const double* __restrict__ pos, CellGrid G, int* __restrict__ key,
+                          int* __restrict__ id) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const int cx = cell_coord(pos[3 * s], G.lo[0], G.inv_w[0], G.dims[0]);
+  const int cy = cell_coord(pos[3 * s + 1], G.lo[1], G.inv_w[1], G.dims[1]);
+  const int cz = cell_coord(pos[3 * s + 2], G.lo[2], G.inv_w[2], G.dims[2]);
+  key[s] = (cz * G.dims[1] + cy) * G.dims[0] + cx;
+  id[s] = s;
+}
+
+// start[c] = first sorted position whose cell is >= c, for c = 0..ncells
+__global__ void k_cl_start(int N, int ncells, const int* __restrict__ key, int* __restrict__ start) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  const int c0 = (k == 0) ? 0 : key[k - 1] + 1;
+  const int c1 = (k == N) ? ncells : key[k];
+  for (int c = c0; c <= c1; ++c) start[c] = k;
+}
+
+// sorted copies: FP32 (x, y, z relative to the grid origin, a), FP64 (x, y, z, a)
+__global__ void k_cl_gather(int N, const int* __restrict__ id, const double* __restrict__ pos,
+                            const double* __restrict__ rad, CellGrid G, float4* __restrict__ cf,
+                            double4_32a* __restrict__ cd) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int s = id[k];
+  const double x = pos[3 * s], y = pos[3 * s + 1], z = pos[3 * s + 2], a = rad[s];
+  cf[k] = make_float4((float)(x - G.lo[0]), (float)(y - G.lo[1]), (float)(z - G.lo[2]), (float)a);
+  cd[k] = make_double4_32a(x, y, z, a);
+}
+
+// Visits every sphere j > i in the 27 cells around sorted position k that can
+// satisfy the contact test; f(i, j) is called for each pair that passes it.
+// The FP32 screen rejects a pair only when its FP32 distance exceeds
+// (a_c,i + a_c,j + delta)(1 + 1e-5) + eps, eps bounding the rounding of the
+// FP32 coordinates, so no pair that passes the FP64 test is ever rejected.
+template <class F>
+__device__ __forceinline__ void cl_scan(int k, const int* __restrict__ key, const int* __restrict__ id,
+                                        const float4* __restrict__ cf, const double4_32a* __restrict__ cd,
+                                        const int* __restrict__ start, const CellGrid& G, float acsf,
+                                        float deltaf, double acs, double delta, F f) {
+  const int i = id[k];
+  const float4 me = cf[k];
+  const double4_32a md = cd[k];
+  const int kk = key[k];
+  const int cx = kk % G.dims[0], cy = (kk / G.dims[0]) % G.dims[1], cz = kk / (G.dims[0] * G.dims[1]);
+  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, G.dims[0] - 1);
+  for (int zz = max(cz - 1, 0); zz <= min(cz + 1, G.dims[2] - 1); ++zz)
+    for (int yy = max(cy - 1, 0); yy <= min(cy + 1, G.dims[1] - 1); ++yy) {
+      const int row = (zz * G.dims[1] + yy) * G.dims[0];
+      const int m1 = start[row + x1 + 1];
+      for (int m = start[row + x0]; m < m1; ++m) {
+        const int j = id[m];
+        if (j <= i) continue;
+        const float4 o = cf[m];
+        const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float thr = fmaf(fmaf(acsf, me.w + o.w, deltaf), 1.00001f, G.eps);
+        if (d2 > thr * thr) continue;
+        const double4_32a od = cd[m];
+        if (sps_contact_test(md.x, md.y, md.z, md.w, od.x, od.y, od.z, od.w, acs, delta, nullptr))
+          f(i, j);
+      }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cl_count(int N, const int* __restrict__ key,
+                                                      const int* __restrict__ id,
+                                                      const float4* __restrict__ cf,
+                                                      const double4_32a* __restrict__ cd,
+                                                      const int* __restrict__ start, CellGrid G,
+                                                      double acs, double delta, int* __restrict__ cnt,
+                                                      int* __restrict__ cnt2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  int c = 0;
+  cl_scan(k, key, id, cf, cd, start, G, (float)acs, (float)delta, acs, delta, [&](int, int j) {
+    ++c;
+    atomicAdd(&cnt2[j], 1);
+  });
+  cnt[id[k]] = c;
+}
+
+// writes row i: the j's found, sorted ascending in place, then the geometry of
+// each contact from the caller's arrays (the same values the test read)
+__global__ void __launch_bounds__(kThreads) k_cl_fill(int N, const int* __restrict__ key,
+                                                     const int* __restrict__ id,
+                                                     const float4* __restrict__ cf,
+                                                     const double4_32a* __restrict__ cd,
+                                                     const int* __restrict__ start, CellGrid G,
+                                                     double acs, double delta,
+                                                     const double* __restrict__ pos,
+                                                     const double* __restrict__ rad,
+                                                     const int* __restrict__ ptr, int* __restrict__ ij,
+                                                     double* __restrict__ phi, double* __restrict__ nrm,
+                                                     int* __restrict__ keys, int* __restrict__ vals) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int i = id[k];
+  const int o0 = ptr[i], oe = ptr[i + 1];
+  int o = o0;
+  // the count pass applied the same predicate, so the row fills [o0, oe)
+  // exactly; the bound only keeps every store inside the row regardless
+  cl_scan(k, key, id, cf, cd, start, G, (float)acs, (float)delta, acs, delta, [&](int, int j) {
+    if (o < oe) ij[2 * o + 1] = j;
+    ++o;
+  });
+  o = min(o, oe);
+  for (int t = o0 + 1; t < o; ++t) {   // insertion sort of the row by j
+    const int v = ij[2 * t + 1];
+    int u = t;
+    while (u > o0 && ij[2 * (u - 1) + 1] > v) {
+      ij[2 * u + 1] = ij[2 * (u - 1) + 1];
+      --u;
+    }
+    ij[2 * u + 1] = v;
+  }
+  SpsContactGeom g;
+  for (int t = o0; t < o; ++t) {
+    const int j = ij[2 * t + 1];
+    contact_at(pos, rad, acs, delta, i, j, &g);
+    put_contact(t, i, j, g, ij, phi, nrm, keys, vals);
+  }
+}
+
+__global__ void k_add_counts(int N, const int* a, const int* b, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] = a[i] + b[i];
+}
+
+// ---------------------------------------------------------------------------
+// D and D^T
+// ---------------------------------------------------------------------------
+// F_c = D gamma: per sphere, its incident contacts in contact order
+__global__ void k_D(int N, const int* __restrict__ inc_ptr, const int* __restrict__ inc,
+                    const double* __restrict__ nrm, const double* __restrict__ gam,
+                    double* __restrict__ FT) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+  for (int e = inc_ptr[s]; e < inc_ptr[s + 1]; ++e) {
+    const int v = inc[e], l = v >> 1;
+    const double g = gam[l];
+    const double a0 = __dmul_rn(g, nrm[3 * l]), a1 = __dmul_rn(g, nrm[3 * l + 1]),
+                 a2 = __dmul_rn(g, nrm[3 * l + 2]);
+    if (v & 1) {
+      f0 = __dadd_rn(f0, a0);
+      f1 = __dadd_rn(f1, a1);
+      f2 = __dadd_rn(f2, a2);
+    } else {
+      f0 = __dsub_rn(f0, a0);
+      f1 = __dsub_rn(f1, a1);
+      f2 = __dsub_rn(f2, a2);
+    }
+  }
+  FT[6 * s + 0] = f0;
+  FT[6 * s + 1] = f1;
+  FT[6 * s + 2] = f2;
+  FT[6 * s + 3] = 0.0;
+  FT[6 * s + 4] = 0.0;
+  FT[6 * s + 5] = 0.0;
+}
+
+// (D^T U)_l = n_l . (U_j - U_i)
+__global__ void k_DT(int nc, const int* __restrict__ ij, const double* __restrict__ nrm,
+                     const double* __restrict__ UO, double* __restrict__ out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nc) return;
+  const int i = ij[2 * l], j = ij[2 * l + 1];
+  double acc = 0.0;
+  for (int c = 0; c < 3; ++c) acc += nrm[3 * l + c] * (UO[6 * j + c] - UO[6 * i + c]);
+  out[l] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// BBPGD statistics: [sum min(gam_n, g_n)^2, s.s, s.y, y.y, g_n.g_n] with
+// s = gam_n - gam_o, y = g_n - g_o (Algorithm 1, eq. mmapnorm)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void stat_add(double a[5], double gn, double ggn, double go, double ggo,
+                                         bool old) {
+  const double mn = fmin(gn, ggn);
+  a[0] += mn * mn;
+  if (old) {
+    const double s = gn - go, y = ggn - ggo;
+    a[1] += s * s;
+    a[2] += s * y;
+    a[3] += y * y;
+  }
+  a[4] += ggn * ggn;
+}
+
+// block partial of the five sums into part[c * gridDim.x + blockIdx.x]
+__device__ __forceinline__ void stat_store(double a[5], double* part) {
+  __shared__ double red[kThreads / 32][5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) red[threadIdx.x >> 5][c] = a[c];
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bb_stats_part(int n, const double* __restrict__ gam_new,
+                                                           const double* __restrict__ g_new,
+                                                           const double* __restrict__ gam_old,
+                                                           const double* __restrict__ g_old,
+                                                           double* __restrict__ part) {
+  double a[5] = {0, 0, 0, 0, 0};
+  const bool old = gam_old != nullptr;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x)
+    stat_add(a, gam_new[l], g_new[l], old ? gam_old[l] : 0.0, old ? g_old[l] : 0.0, old);
+  stat_store(a, part);
+}
+
+__global__ void k_stat_finish(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= 5) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[c * nb + b];
+  out[c] = s;
+}
+
+// Identity mobility, first half of one BBPGD iteration: per sphere s, the
+// projected step gam_n = max(gam - alpha g, 0) of each incident contact (the
+// contact's first sphere stores it) and F_s = (D gam_n)_s, forces only.
+__global__ void __launch_bounds__(kThreads) k_bb_ident_D(int N, double alpha,
+                                                        const int* __restrict__ inc_ptr,
+                                                        const int* __restrict__ inc,
+                                                        const double* __restrict__ nrm,
+                                                        const double* __restrict__ gam,
+                                                        const double* __restrict__ g,
+                                                        double* __restrict__ gam_new,
+                                                        double* __restrict__ F3) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+  const int e1 = inc_ptr[s + 1];
+  for (int e = inc_ptr[s]; e < e1; ++e) {
+    const int v = inc[e], l = v >> 1;
+    const double gn = fmax(gam[l] - alpha * g[l], 0.0);
+    const double a0 = __dmul_rn(gn, nrm[3 * l]), a1 = __dmul_rn(gn, nrm[3 * l + 1]),
+                 a2 = __dmul_rn(gn, nrm[3 * l + 2]);
+    if (v & 1) {
+      f0 = __dadd_rn(f0, a0);
+      f1 = __dadd_rn(f1, a1);
+      f2 = __dadd_rn(f2, a2);
+    } else {
+      gam_new[l] = gn;
+      f0 = __dsub_rn(f0, a0);
+      f1 = __dsub_rn(f1, a1);
+      f2 = __dsub_rn(f2, a2);
+    }
+  }
+  F3[3 * s + 0] = f0;
+  F3[3 * s + 1] = f1;
+  F3[3 * s + 2] = f2;
+}
+
+// second half: g_n = D^T F + q per contact, and the five statistics
+__global__ void __launch_bounds__(kThreads) k_bb_ident_DT(int nc, const int* __restrict__ ij,
+                                                         const double* __restrict__ nrm,
+                                                         const double* __restrict__ F3,
+                                                         const double* __restrict__ q,
+                                                         const double* __restrict__ gam_new,
+                                                         const double* __restrict__ gam,
+                                                         const double* __restrict__ g,
+                                                         double* __restrict__ g_new,
+                                                         double* __restrict__ part) {
+  double a[5] = {0, 0, 0, 0, 0};
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nc; l += gridDim.x * blockDim.x) {
+    const int i = ij[2 * l], j = ij[2 * l + 1];
+    double acc = 0.0;
+    for (int c = 0; c < 3; ++c) acc += nrm[3 * l + c] * (F3[3 * j + c] - F3[3 * i + c]);
+    const double ggn = acc + q[l];
+    g_new[l] = ggn;
+    stat_add(a, gam_new[l], ggn, gam[l], g[l], true);
+  }
+  stat_store(a, part);
+}
+
+__global__ void k_identity_U(int N, const double* __restrict__ FT, const double* __restrict__ F3,
+                             double* __restrict__ UO) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 6 * N) return;
+  const int s = t / 6, c = t - 6 * s;
+  UO[t] = FT[t] + ((F3 && c < 3) ? F3[3 * s + c] : 0.0);
+}
+
+// flags: 1 non-finite position or radius, 2 non-positive radius, 4 non-finite FT
+__global__ void k_check(int N, const double* __restrict__ pos, const double* __restrict__ rad,
+                        const double* __restrict__ FT, int* __restrict__ flag) {
+  int f = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+    if (!isfinite(pos[3 * s]) || !isfinite(pos[3 * s + 1]) || !isfinite(pos[3 * s + 2]) ||
+        !isfinite(rad[s]))
+      f |= 1;
+    if (!(rad[s] > 0)) f |= 2;
+    if (FT)
+      for (int c = 0; c < 6; ++c)
+        if (!isfinite(FT[6 * s + c])) f |= 4;
+  }
+  if (f) atomicOr(flag, f);
+}
+
+__global__ void k_count_pos(int n, const double* __restrict__ v, int* __restrict__ out) {
+  int c = 0;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) c += v[l] > 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int read_int(sps_ctx* ctx, const int* d, int* h) {
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::memcpy(h, ctx->h_pinned, sizeof(int));
+  return SPS_OK;
+}
+
+int cub_scratch(sps_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->cub_bytes && ctx->d_cub) return SPS_OK;
+  size_t cap = 0;
+  char* p = static_cast<char*>(ctx->d_cub);
+  SPS_TRY(sps_grow(ctx, &p, cap, std::max<size_t>(bytes, 1 << 20)));
+  ctx->d_cub = p;
+  ctx->cub_bytes = cap;
+  return SPS_OK;
+}
+
+// cell-list counts: cnt (as first sphere), cnt2 (as second) for n spheres
+int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, CellGrid* Gout,
+                int* ncells_out) {
+  const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta;
+  size_t cp = 0;
+  if (!ctx->d_cl_part) SPS_TRY(sps_grow(ctx, &ctx->d_cl_part, cp, (size_t)8 * kBoundBlocks + 8));
+  k_cl_bounds<<<kBoundBlocks, kThreads, 0, ctx->stream>>>(n, pos, radii, ctx->d_cl_part);
+  SPS_LAUNCHED(ctx);
+  double* bounds = ctx->d_cl_part + 8 * kBoundBlocks;
+  k_cl_bounds_finish<<<1, 32, 0, ctx->stream>>>(kBoundBlocks, ctx->d_cl_part, bounds);
+  SPS_LAUNCHED(ctx);
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, bounds, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double b[8];
+  std::memcpy(b, ctx->h_pinned, sizeof(b));
+  if (b[7] > 0) return sps_fail(ctx, SPS_ERR_NONFINITE, "contacts: positions or radii not finite and positive");
+  // cell side >= 2 max a_c + delta (with a relative margin over rounding)
+  double h = (2.0 * acs * b[6] + delta) * (1.0 + 1e-9);
+  const long long cap_cells = std::min<long long>(1LL << 30, std::max<long long>(64, 2LL * n));
+  CellGrid G;
+  double ext[3], emax = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    ext[d] = b[3 + d] - b[d];
+    emax = std::max(emax, ext[d]);
+  }
+  long long dims[3];
+  for (;;) {
+    long long tot = 1;
+    for (int d = 0; d < 3; ++d) {
+      const double f = std::floor(ext[d] / h);
+      dims[d] = (f >= 1.0) ? (long long)std::min(f, 1e9) : 1;
+      tot *= dims[d];
+      if (tot > cap_cells) break;
+    }
+    if (tot <= cap_cells) break;
+    h *= 1.25;
+  }
+  for (int d = 0; d < 3; ++d) {
+    G.lo[d] = b[d];
+    G.dims[d] = (int)dims[d];
+    // cell width ext / dims >= h: pairs closer than h land in adjacent cells
+    G.inv_w[d] = dims[d] > 1 ? (double)dims[d] / ext[d] : 0.0;
+  }
+  // FP32 copies of coordinates relative to lo are within 2^-24 emax of the
+  // FP64 values: the screen's absolute margin covers both ends with room
+  G.eps = (float)(8.0 * emax * 5.9604644775390625e-8) + 1e-30f;
+  const int ncells = G.dims[0] * G.dims[1] * G.dims[2];
+  // buffers
+  if ((size_t)n > ctx->cap_cl) {
+    int** ip[] = {&ctx->d_cl_key, &ctx->d_cl_id, &ctx->d_cl_key2, &ctx->d_cl_id2};
+    for (auto p : ip) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    cudaFree(ctx->d_cl_f);
+    cudaFree(ctx->d_cl_d);
+    ctx->d_cl_f = nullptr;
+    ctx->d_cl_d = nullptr;
+    size_t c = 0;
+    for (auto p : ip) {
+      c = 0;
+      SPS_TRY(sps_grow(ctx, p, c, (size_t)n));
+    }
+    c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_cl_f, c, (size_t)n));
+    c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_cl_d, c, (size_t)n));
+    ctx->cap_cl = n;
+  }
+  if ((size_t)ncells + 1 > ctx->cap_cl_cells) {
+    cudaFree(ctx->d_cl_range);
+    ctx->d_cl_range = nullptr;
+    size_t c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_cl_range, c, (size_t)ncells + 1));
+    ctx->cap_cl_cells = c;
+  }
+  k_cl_keys<<<nblk(n), kThreads, 0, ctx->stream>>>(n, pos, G, ctx->d_cl_key, ctx->d_cl_id);
+  SPS_LAUNCHED(ctx);
+  int bits = 1;
+  while ((1LL << bits) < (long long)ncells && bits < 31) ++bits;
+  size_t tmp = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp, ctx->d_cl_key, ctx->d_cl_key2, ctx->d_cl_id,
+                                  ctx->d_cl_id2, n, 0, bits, ctx->stream);
+  SPS_TRY(cub_scratch(ctx, tmp));
+  tmp = ctx->cub_bytes;
+  SPS_CUDA(ctx, cub::DeviceRadixSort::SortPairs(ctx->d_cub, tmp, ctx->d_cl_key, ctx->d_cl_key2,
+                                                ctx->d_cl_id, ctx->d_cl_id2, n, 0, bits, ctx->stream));
+  ctx->launches += 4;
+  k_cl_start<<<nblk(n + 1), kThreads, 0, ctx->stream>>>(n, ncells, ctx->d_cl_key2, ctx->d_cl_range);
+  SPS_LAUNCHED(ctx);
+  k_cl_gather<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_id2, pos, radii, G, ctx->d_cl_f,
+                                                      ctx->d_cl_d);
+  SPS_LAUNCHED(ctx);
+  k_cl_count<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key2, ctx->d_cl_id2, ctx->d_cl_f,
+                                                     ctx->d_cl_d, ctx->d_cl_range, G, acs, delta,
+                                                     ctx->d_ccount, ctx->d_ccount2);
+  SPS_LAUNCHED(ctx);
+  *Gout = G;
+  *ncells_out = ncells;
+  return SPS_OK;
+}
+
+}  // namespace
+
+int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii) {
+  SpsPhase timer(ctx, SPS_PH_CONTACT);
+  const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta;
+  const int search = ctx->prm.contact_search;
+  const bool cells = search == SPS_SEARCH_CELLS || (search == SPS_SEARCH_AUTO && n > 4096);
+  if ((size_t)n + 1 > ctx->cap_cnt) {
+    int** ip[] = {&ctx->d_ccount, &ctx->d_ccount2, &ctx->d_inc_cnt, &ctx->d_cptr, &ctx->d_inc_ptr};
+    for (auto p : ip) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    size_t c = 0;
+    for (auto p : ip) {
+      c = 0;
+      SPS_TRY(sps_grow(ctx, p, c, (size_t)n + 1));
+    }
+    ctx->cap_cnt = (size_t)n + 1;
+  }
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_ccount, 0, sizeof(int) * (n + 1), ctx->stream));
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_ccount2, 0, sizeof(int) * (n + 1), ctx->stream));
+  CellGrid G;
+  int ncells = 0;
+  if (cells) {
+    SPS_TRY(cell_counts(ctx, n, pos, radii, &G, &ncells));
+  } else {
+    k_pairs_count<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, ctx->d_ccount,
+                                                         ctx->d_ccount2);
+    SPS_LAUNCHED(ctx);
+  }
+  k_add_counts<<<nblk(n + 1), kThreads, 0, ctx->stream>>>(n + 1, ctx->d_ccount, ctx->d_ccount2,
+                                                          ctx->d_inc_cnt);
+  SPS_LAUNCHED(ctx);
+  size_t tmp = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tmp, ctx->d_ccount, ctx->d_cptr, n + 1, ctx->stream);
+  SPS_TRY(cub_scratch(ctx, tmp));
+  tmp = ctx->cub_bytes;
+  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(ctx->d_cub, tmp, ctx->d_ccount, ctx->d_cptr, n + 1,
+                                              ctx->stream));
+  tmp = ctx->cub_bytes;
+  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(ctx->d_cub, tmp, ctx->d_inc_cnt, ctx->d_inc_ptr, n + 1,
+                                              ctx->stream));
+  ctx->launches += 2;
+  int nc = 0;
+  SPS_TRY(read_int(ctx, ctx->d_cptr + n, &nc));
+  ctx->n_c = nc;
+  if (nc > ctx->cap_c) {
+    int** ip[] = {&ctx->d_cij, &ctx->d_inc, &ctx->d_keys, &ctx->d_vals, &ctx->d_keys2};
+    for (auto p : ip) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    cudaFree(ctx->d_cphi);
+    cudaFree(ctx->d_cn);
+    ctx->d_cphi = ctx->d_cn = nullptr;
+    size_t c = 0;
+    for (auto p : ip) {
+      c = 0;
+      SPS_TRY(sps_grow(ctx, p, c, 2 * (size_t)nc));
+    }
+    c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_cphi, c, (size_t)nc));
+    c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_cn, c, 3 * (size_t)nc));
+    ctx->cap_c = nc;
+  }
+  if (nc == 0) return SPS_OK;
+  if (cells) {
+    k_cl_fill<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key2, ctx->d_cl_id2, ctx->d_cl_f,
+                                                      ctx->d_cl_d, ctx->d_cl_range, G, acs, delta, pos,
+                                                      radii, ctx->d_cptr, ctx->d_cij, ctx->d_cphi,
+                                                      ctx->d_cn, ctx->d_keys, ctx->d_vals);
+  } else {
+    k_pairs_fill<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, ctx->d_cptr,
+                                                        ctx->d_cij, ctx->d_cphi, ctx->d_cn, ctx->d_keys,
+                                                        ctx->d_vals);
+  }
+  SPS_LAUNCHED(ctx);
+  // a stable sort of (sphere, contact end) lists each sphere's incident
+  // contacts in contact order: a deterministic transpose of the list
+  int bits = 1;
+  while (bits < 31 && (1 << bits) < n) ++bits;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp, ctx->d_keys, ctx->d_keys2, ctx->d_vals, ctx->d_inc,
+                                  2 * nc, 0, bits, ctx->stream);
+  SPS_TRY(cub_scratch(ctx, tmp));
+  tmp = ctx->cub_bytes;
+  SPS_CUDA(ctx, cub::DeviceRadixSort::SortPairs(ctx->d_cub, tmp, ctx->d_keys, ctx->d_keys2, ctx->d_vals,
+                                                ctx->d_inc, 2 * nc, 0, bits, ctx->stream));
+  ctx->launches += 4;
+  return SPS_OK;
+}
+
+int sps_launch_D(sps_ctx* ctx, const double* gamma, double* FT) {
+  SpsPhase timer(ctx, SPS_PH_CONTACT);
+  const int N = ctx->c_N;
+  k_D<<<nblk(N), kThreads, 0, ctx->stream>>>(N, ctx->d_inc_ptr, ctx->d_inc, ctx->d_cn, gamma, FT);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_DT(sps_ctx* ctx, const double* UO, double* out) {
+  SpsPhase timer(ctx, SPS_PH_CONTACT);
+  if (ctx->n_c == 0) return SPS_OK;
+  k_DT<<<nblk(ctx->n_c), kThreads, 0, ctx->stream>>>(ctx->n_c, ctx->d_cij, ctx->d_cn, UO, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+// partials (5 x kStatBlocks) followed by the five results
+static int ensure_bbpart(sps_ctx* ctx) {
+  if (ctx->d_bbpart) return SPS_OK;
+  size_t c = 0;
+  return sps_grow(ctx, &ctx->d_bbpart, c, (size_t)5 * kStatBlocks + 8);
+}
+
+const double* sps_bb_out(sps_ctx* ctx) { return ctx->d_bbpart + 5 * kStatBlocks; }
+
+int sps_bb_stats_dev(sps_ctx* ctx, const double* gn, const double* ggn, const double* go,
+                     const double* ggo) {
+  SpsPhase timer(ctx, SPS_PH_BBPGD);
+  SPS_TRY(ensure_bbpart(ctx));
+  const int nb = std::max(1, std::min(kStatBlocks, nblk(ctx->n_c)));
+  k_bb_stats_part<<<nb, kThreads, 0, ctx->stream>>>(ctx->n_c, gn, ggn, go, ggo, ctx->d_bbpart);
+  SPS_LAUNCHED(ctx);
+  k_stat_finish<<<1, 32, 0, ctx->stream>>>(nb, ctx->d_bbpart, ctx->d_bbpart + 5 * kStatBlocks);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_bb_identity(sps_ctx* ctx, double alpha, const double* gam, const double* g,
+                           double* gam_new, double* g_new) {
+  SPS_TRY(ensure_bbpart(ctx));
+  const int N = ctx->c_N, nc = ctx->n_c;
+  {
+    SpsPhase timer(ctx, SPS_PH_BB_D);
+    k_bb_ident_D<<<nblk(N), kThreads, 0, ctx->stream>>>(N, alpha, ctx->d_inc_ptr, ctx->d_inc, ctx->d_cn,
+                                                         gam, g, gam_new, ctx->d_F3);
+    SPS_LAUNCHED(ctx);
+  }
+  const int nb = std::max(1, std::min(kStatBlocks, nblk(nc)));
+  {
+    SpsPhase timer(ctx, SPS_PH_BB_DT);
+    k_bb_ident_DT<<<nb, kThreads, 0, ctx->stream>>>(nc, ctx->d_cij, ctx->d_cn, ctx->d_F3, ctx->d_q,
+                                                    gam_new, gam, g, g_new, ctx->d_bbpart);
+    SPS_LAUNCHED(ctx);
+  }
+  SpsPhase timer(ctx, SPS_PH_BBPGD);
+  k_stat_finish<<<1, 32, 0, ctx->stream>>>(nb, ctx->d_bbpart, ctx->d_bbpart + 5 * kStatBlocks);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_launch_identity_U(sps_ctx* ctx, int n, const double* FT, const double* F3, double* UO) {
+  SpsPhase timer(ctx, SPS_PH_BBPGD);
+  k_identity_U<<<nblk(6LL * n), kThreads, 0, ctx->stream>>>(n, FT, F3, UO);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+int sps_check_inputs(sps_ctx* ctx, int n, const double* pos, const double* radii, const double* FT) {
+  if (!ctx->d_flag) {
+    size_t c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_flag, c, 4));
+  }
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  k_check<<<std::max(1, std::min(4 * 152, nblk(n))), kThreads, 0, ctx->stream>>>(n, pos, radii, FT,
+                                                                                  ctx->d_flag);
+  SPS_LAUNCHED(ctx);
+  int f = 0;
+  SPS_TRY(read_int(ctx, ctx->d_flag, &f));
+  if (f & 1) return sps_fail(ctx, SPS_ERR_NONFINITE, "positions or radii not finite");
+  if (f & 2) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "radii must be positive");
+  if (f & 4) return sps_fail(ctx, SPS_ERR_NONFINITE, "force/torque not finite");
+  return SPS_OK;
+}
+
+int sps_count_positive(sps_ctx* ctx, const double* v, int n, int* out) {
+  if (!ctx->d_flag) {
+    size_t c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_flag, c, 4));
+  }
+  *out = 0;
+  if (n <= 0) return SPS_OK;
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  k_count_pos<<<std::max(1, std::min(4 * 152, nblk(n))), kThreads, 0, ctx->stream>>>(n, v, ctx->d_flag);
+  SPS_LAUNCHED(ctx);
+  return read_int(ctx, ctx->d_flag, out);
+}

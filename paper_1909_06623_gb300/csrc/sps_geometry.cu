@@ -1,7 +1,7 @@
 // Geometry kernels: surface nodes (Sec. 5.4), near-pair lists (Sec. 4.2),
-// contact set and the contact Jacobian D (Sec. 3.1-3.2, eq. Dmatdef and
-// eq. Dtranspose), rho from force/torque, the local operator L and velocity
-// extraction (Sec. 4.1).
+// rho from force/torque, the local operator L and velocity extraction
+// (Sec. 4.1), and the contact builder that keeps its scratch in a static
+// device array.  The contact search and D products are in sps_contacts.cu.
 #include <cub/cub.cuh>
 
 #include <mutex>
@@ -126,109 +126,12 @@ __global__ void k_close_fill(int N, int P, const double* __restrict__ pos, const
 // contacts (Sec. 3.2): i < j, Phi = (d - R_i) - R_j <= delta; every operation
 // rounded separately so the list is reproducible to the bit.
 // ---------------------------------------------------------------------------
-struct ContactGeom {
-  double phi, nx, ny, nz;
-};
+using ContactGeom = SpsContactGeom;
 
 __device__ __forceinline__ bool contact(const double* pos, const double* rad, double acs,
                                         double delta, int i, int j, ContactGeom* g) {
-  const double dx = __dsub_rn(pos[3 * j + 0], pos[3 * i + 0]);
-  const double dy = __dsub_rn(pos[3 * j + 1], pos[3 * i + 1]);
-  const double dz = __dsub_rn(pos[3 * j + 2], pos[3 * i + 2]);
-  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-  const double d = __dsqrt_rn(d2);
-  const double Ri = __dmul_rn(rad[i], acs), Rj = __dmul_rn(rad[j], acs);
-  const double phi = __dsub_rn(__dsub_rn(d, Ri), Rj);
-  if (!(phi <= delta)) return false;
-  if (g) {
-    g->phi = phi;
-    g->nx = __ddiv_rn(dx, d);
-    g->ny = __ddiv_rn(dy, d);
-    g->nz = __ddiv_rn(dz, d);
-  }
-  return true;
-}
-
-__global__ void k_contact_count(int N, const double* pos, const double* rad, double acs,
-                                double delta, int* cnt, int* cnt2) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int c = 0;
-  for (int j = i + 1; j < N; ++j)
-    if (contact(pos, rad, acs, delta, i, j, nullptr)) {
-      ++c;
-      atomicAdd(&cnt2[j], 1);   // integer count of contacts where j is second
-    }
-  cnt[i] = c;
-}
-
-__global__ void k_contact_fill(int N, const double* pos, const double* rad, double acs,
-                               double delta, const int* ptr, int* ij, double* phi, double* nrm,
-                               int* keys, int* vals) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int o = ptr[i];
-  ContactGeom g;
-  for (int j = i + 1; j < N; ++j)
-    if (contact(pos, rad, acs, delta, i, j, &g)) {
-      ij[2 * o] = i;
-      ij[2 * o + 1] = j;
-      phi[o] = g.phi;
-      nrm[3 * o + 0] = g.nx;
-      nrm[3 * o + 1] = g.ny;
-      nrm[3 * o + 2] = g.nz;
-      keys[2 * o] = i;
-      vals[2 * o] = 2 * o;          // contact o, sphere is first (sign -1)
-      keys[2 * o + 1] = j;
-      vals[2 * o + 1] = 2 * o + 1;  // contact o, sphere is second (sign +1)
-      ++o;
-    }
-}
-
-__global__ void k_add_counts(int N, const int* a, const int* b, int* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) out[i] = a[i] + b[i];
-}
-
-// F_c = D gamma: per sphere, its incident contacts in contact order
-__global__ void k_D(int N, const int* __restrict__ inc_ptr, const int* __restrict__ inc,
-                    const double* __restrict__ nrm, const double* __restrict__ gam,
-                    double* __restrict__ FT) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= N) return;
-  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-  for (int e = inc_ptr[s]; e < inc_ptr[s + 1]; ++e) {
-    const int v = inc[e], l = v >> 1;
-    const double g = gam[l];
-    const double a0 = __dmul_rn(g, nrm[3 * l]), a1 = __dmul_rn(g, nrm[3 * l + 1]),
-                 a2 = __dmul_rn(g, nrm[3 * l + 2]);
-    if (v & 1) {
-      f0 = __dadd_rn(f0, a0);
-      f1 = __dadd_rn(f1, a1);
-      f2 = __dadd_rn(f2, a2);
-    } else {
-      f0 = __dsub_rn(f0, a0);
-      f1 = __dsub_rn(f1, a1);
-      f2 = __dsub_rn(f2, a2);
-    }
-  }
-  FT[6 * s + 0] = f0;
-  FT[6 * s + 1] = f1;
-  FT[6 * s + 2] = f2;
-  FT[6 * s + 3] = 0.0;
-  FT[6 * s + 4] = 0.0;
-  FT[6 * s + 5] = 0.0;
-}
-
-// (D^T U)_l = n_l . (U_j - U_i)
-__global__ void k_DT(int nc, const int* __restrict__ ij, const double* __restrict__ nrm,
-                     const double* __restrict__ UO, double* __restrict__ out) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= nc) return;
-  const int i = ij[2 * l], j = ij[2 * l + 1];
-  double acc = 0.0;
-  for (int c = 0; c < 3; ++c) acc += nrm[3 * l + c] * (UO[6 * j + c] - UO[6 * i + c]);
-  out[l] = acc;
+  return sps_contact_test(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], rad[i], pos[3 * j],
+                          pos[3 * j + 1], pos[3 * j + 2], rad[j], acs, delta, g);
 }
 
 // rho = F/|Gamma| + tau^{-1} T x (x - c), tau = (8 pi/3) a^4 (Sec. 4.1)
@@ -398,105 +301,6 @@ int sps_launch_close_lists(sps_ctx* ctx) {
   cudaFree(d_flag);
   cudaFree(d_sptr);
   cudaFree(d_fpos);
-  return SPS_OK;
-}
-
-int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii) {
-  SpsPhase timer(ctx, SPS_PH_CONTACT);
-  const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta;
-  // per-sphere counters (first / second) and the scan, sized for n
-  size_t c1 = 0, c2 = 0, c3 = 0;
-  int *d_cnt = nullptr, *d_cnt2 = nullptr, *d_inc_cnt = nullptr;
-  SPS_TRY(sps_grow(ctx, &d_cnt, c1, (size_t)n + 1));
-  SPS_TRY(sps_grow(ctx, &d_cnt2, c2, (size_t)n + 1));
-  SPS_TRY(sps_grow(ctx, &d_inc_cnt, c3, (size_t)n + 1));
-  size_t cp = 0, ci = 0;
-  if (ctx->d_cptr) cudaFree(ctx->d_cptr);
-  if (ctx->d_inc_ptr) cudaFree(ctx->d_inc_ptr);
-  ctx->d_cptr = nullptr;
-  ctx->d_inc_ptr = nullptr;
-  SPS_TRY(sps_grow(ctx, &ctx->d_cptr, cp, (size_t)n + 1));
-  SPS_TRY(sps_grow(ctx, &ctx->d_inc_ptr, ci, (size_t)n + 1));
-  SPS_CUDA(ctx, cudaMemsetAsync(d_cnt, 0, sizeof(int) * (n + 1), ctx->stream));
-  SPS_CUDA(ctx, cudaMemsetAsync(d_cnt2, 0, sizeof(int) * (n + 1), ctx->stream));
-  k_contact_count<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, d_cnt, d_cnt2);
-  SPS_LAUNCHED(ctx);
-  k_add_counts<<<nblk(n + 1), kThreads, 0, ctx->stream>>>(n + 1, d_cnt, d_cnt2, d_inc_cnt);
-  SPS_LAUNCHED(ctx);
-  size_t tmp1 = 0;
-  cub::DeviceScan::ExclusiveSum(nullptr, tmp1, d_cnt, ctx->d_cptr, n + 1, ctx->stream);
-  size_t need = tmp1;
-  void* d_tmp = nullptr;
-  SPS_CUDA(ctx, cudaMalloc(&d_tmp, need ? need : 1));
-  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(d_tmp, tmp1, d_cnt, ctx->d_cptr, n + 1, ctx->stream));
-  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(d_tmp, tmp1, d_inc_cnt, ctx->d_inc_ptr, n + 1,
-                                              ctx->stream));
-  ctx->launches += 2;
-  int nc = 0;
-  SPS_CUDA(ctx, cudaMemcpyAsync(&nc, ctx->d_cptr + n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  cudaFree(d_tmp);
-  ctx->n_c = nc;
-  if (nc > ctx->cap_c) {
-    cudaFree(ctx->d_cij);
-    cudaFree(ctx->d_cphi);
-    cudaFree(ctx->d_cn);
-    cudaFree(ctx->d_inc);
-    cudaFree(ctx->d_keys);
-    cudaFree(ctx->d_vals);
-    cudaFree(ctx->d_keys2);
-    ctx->d_cij = nullptr;
-    ctx->d_cphi = ctx->d_cn = nullptr;
-    ctx->d_inc = ctx->d_keys = ctx->d_vals = ctx->d_keys2 = nullptr;
-    size_t a = 0, b = 0, c = 0, d = 0, e = 0, f = 0, h = 0;
-    SPS_TRY(sps_grow(ctx, &ctx->d_cij, a, 2 * (size_t)nc));
-    SPS_TRY(sps_grow(ctx, &ctx->d_cphi, b, (size_t)nc));
-    SPS_TRY(sps_grow(ctx, &ctx->d_cn, c, 3 * (size_t)nc));
-    SPS_TRY(sps_grow(ctx, &ctx->d_inc, d, 2 * (size_t)nc));
-    SPS_TRY(sps_grow(ctx, &ctx->d_keys, e, 2 * (size_t)nc));
-    SPS_TRY(sps_grow(ctx, &ctx->d_vals, f, 2 * (size_t)nc));
-    SPS_TRY(sps_grow(ctx, &ctx->d_keys2, h, 2 * (size_t)nc));
-    ctx->cap_c = nc;
-  }
-  k_contact_fill<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, ctx->d_cptr,
-                                                         ctx->d_cij, ctx->d_cphi, ctx->d_cn,
-                                                         ctx->d_keys, ctx->d_vals);
-  SPS_LAUNCHED(ctx);
-  if (nc > 0) {
-    // stable sort of (sphere, contact side) gives each sphere's incident
-    // contacts in contact order: a deterministic transpose of the list
-    size_t tmp2 = 0;
-    int bits = 1;
-    while ((1 << bits) < n && bits < 31) ++bits;
-    cub::DeviceRadixSort::SortPairs(nullptr, tmp2, ctx->d_keys, ctx->d_keys2, ctx->d_vals,
-                                    ctx->d_inc, 2 * nc, 0, bits, ctx->stream);
-    void* d_t2 = nullptr;
-    SPS_CUDA(ctx, cudaMalloc(&d_t2, tmp2 ? tmp2 : 1));
-    SPS_CUDA(ctx, cub::DeviceRadixSort::SortPairs(d_t2, tmp2, ctx->d_keys, ctx->d_keys2, ctx->d_vals,
-                                                  ctx->d_inc, 2 * nc, 0, bits, ctx->stream));
-    ctx->launches += 4;
-    SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    cudaFree(d_t2);
-  }
-  cudaFree(d_cnt);
-  cudaFree(d_cnt2);
-  cudaFree(d_inc_cnt);
-  return SPS_OK;
-}
-
-int sps_launch_D(sps_ctx* ctx, const double* gamma, double* FT) {
-  SpsPhase timer(ctx, SPS_PH_CONTACT);
-  const int N = ctx->c_N;
-  k_D<<<nblk(N), kThreads, 0, ctx->stream>>>(N, ctx->d_inc_ptr, ctx->d_inc, ctx->d_cn, gamma, FT);
-  SPS_LAUNCHED(ctx);
-  return SPS_OK;
-}
-
-int sps_launch_DT(sps_ctx* ctx, const double* UO, double* out) {
-  SpsPhase timer(ctx, SPS_PH_CONTACT);
-  if (ctx->n_c == 0) return SPS_OK;
-  k_DT<<<nblk(ctx->n_c), kThreads, 0, ctx->stream>>>(ctx->n_c, ctx->d_cij, ctx->d_cn, UO, out);
-  SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
 

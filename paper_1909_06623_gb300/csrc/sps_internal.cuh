@@ -110,6 +110,7 @@ struct sps_ctx {
   double *d_Q = nullptr;         // (k+1) x n Krylov basis
   double *d_w = nullptr, *d_h = nullptr, *d_red = nullptr;
   double *h_pinned = nullptr;    // pinned host scratch for scalars
+  double *d_sc = nullptr;        // fixed scratch of sps_dot (partials + results), from sps_create
   double *d_rho = nullptr, *d_zeta = nullptr, *d_b = nullptr, *d_u = nullptr;
   double *d_zeta_nc = nullptr;   // density of the last U_nc solve (warm start)
   long long zeta_nc_n = 0;       // node count it belongs to (0: none)
@@ -124,12 +125,28 @@ struct sps_ctx {
   int *d_inc_ptr = nullptr, *d_inc = nullptr;  // incidence CSR by sphere (2 n_c)
   void *d_cub = nullptr; size_t cub_bytes = 0;
   int *d_keys = nullptr, *d_vals = nullptr, *d_keys2 = nullptr, *d_vals2 = nullptr;
+  int *d_ccount2 = nullptr, *d_inc_cnt = nullptr;  // N+1: contacts as second sphere, incidences
+  size_t cap_cnt = 0;
+  // cell list of the contact search: keys / sphere ids (and sorted copies),
+  // per-cell [first, end) into the sorted order, sorted FP32 / FP64 copies of
+  // (x, y, z, a); bounds partials
+  int *d_cl_key = nullptr, *d_cl_id = nullptr, *d_cl_key2 = nullptr, *d_cl_id2 = nullptr;
+  int *d_cl_range = nullptr;
+  float4 *d_cl_f = nullptr;
+  double4_32a *d_cl_d = nullptr;
+  double *d_cl_part = nullptr;
+  size_t cap_cl = 0, cap_cl_cells = 0;
+  int *d_flag = nullptr;         // one int (input checks, counts)
 
   // BBPGD vectors (n_c each)
   double *d_gam = nullptr, *d_g = nullptr, *d_gam_new = nullptr, *d_g_new = nullptr;
   double *d_q = nullptr, *d_Mg = nullptr;
   double *d_FT = nullptr, *d_Unc = nullptr, *d_Uc = nullptr;
   int cap_bb = 0;
+  double *d_bbpart = nullptr;    // BBPGD statistic partials (5 x blocks)
+  // identity mobility: contact forces (N x 3), FT / U_nc / U_c (N x 6)
+  double *d_F3 = nullptr, *d_iFT = nullptr;
+  size_t cap_ident = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -181,6 +198,30 @@ __device__ __forceinline__ double sps_close_r2(const double* pos, double ia, dou
   return x * x + y * y + z * z;
 }
 
+// Contact test of Sec. 3.2 on loaded values: Phi = (d - R_i) - R_j <= delta
+// with R = a_c_scale * a and every operation rounded separately, so that the
+// all-pairs and the cell-list searches produce the same list to the bit.
+struct SpsContactGeom {
+  double phi, nx, ny, nz;
+};
+__device__ __forceinline__ bool sps_contact_test(double xi, double yi, double zi, double ai, double xj,
+                                                 double yj, double zj, double aj, double acs,
+                                                 double delta, SpsContactGeom* g) {
+  const double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  const double d = __dsqrt_rn(d2);
+  const double Ri = __dmul_rn(ai, acs), Rj = __dmul_rn(aj, acs);
+  const double phi = __dsub_rn(__dsub_rn(d, Ri), Rj);
+  if (!(phi <= delta)) return false;
+  if (g) {
+    g->phi = phi;
+    g->nx = __ddiv_rn(dx, d);
+    g->ny = __ddiv_rn(dy, d);
+    g->nz = __ddiv_rn(dz, d);
+  }
+  return true;
+}
+
 // RAII phase timer: records an event pair around the enclosed launches
 struct SpsPhase {
   sps_ctx* c;
@@ -198,6 +239,16 @@ int sps_launch_grid(sps_ctx* ctx);
 int sps_launch_near_lists(sps_ctx* ctx);
 int sps_launch_close_lists(sps_ctx* ctx);
 int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii);
+// contacts, D products, identity-mobility BBPGD pieces (sps_contacts.cu)
+int sps_check_inputs(sps_ctx* ctx, int n, const double* pos, const double* radii, const double* FT);
+int sps_count_positive(sps_ctx* ctx, const double* v, int n, int* out);
+// the five BBPGD statistics land in sps_bb_out(ctx) (device, 5 doubles)
+int sps_bb_stats_dev(sps_ctx* ctx, const double* gn, const double* ggn, const double* go,
+                     const double* ggo);
+int sps_launch_bb_identity(sps_ctx* ctx, double alpha, const double* gam, const double* g,
+                           double* gam_new, double* g_new);
+const double* sps_bb_out(sps_ctx* ctx);
+int sps_launch_identity_U(sps_ctx* ctx, int n, const double* FT, const double* F3, double* UO);
 int sps_launch_D(sps_ctx* ctx, const double* gamma, double* FT);
 int sps_launch_DT(sps_ctx* ctx, const double* UO, double* out);
 int sps_launch_rho(sps_ctx* ctx, const double* FT, double* rho);

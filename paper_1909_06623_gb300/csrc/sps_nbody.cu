@@ -127,6 +127,11 @@ constexpr int kNPair = SPS_FAR_NPAIR;         // target pairs per thread
 #ifndef SPS_FAR_PACKED
 #define SPS_FAR_PACKED 2
 #endif
+// 1: the Kahan running sums (touched once per source sphere) live in shared
+// memory instead of registers
+#ifndef SPS_FAR_KSMEM
+#define SPS_FAR_KSMEM 0
+#endif
 // pairs q < kPacked use packed FP32x2 instructions, the others scalar FP32
 // (measured on GB300: all-packed is fastest; the scalar path is kept for
 // tuning on other parts).
@@ -161,6 +166,9 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
   // per-thread target state kept out of registers: hi, lo + offset (6 per target)
   __shared__ float sEF[6 * 2 * kNPair][kT32];
   __shared__ int sX[3 * 2 * kNPair][kT32];        // sphere, near pointer, near end
+#if SPS_FAR_KSMEM
+  __shared__ float2 sKS[6 * kNPair][kT32];        // running sums and compensations
+#endif
   __shared__ int s_item;
   for (;;) {
     __syncthreads();
@@ -174,7 +182,9 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
     // ---- targets of this thread: lanes (2q, 2q+1) of pair q
     const long long base = (long long)tb * kTPB32 + threadIdx.x;
     float2 nx[kNPair], ny[kNPair], nz[kNPair];
+#if !SPS_FAR_KSMEM
     float2 sx[kNPair], sy[kNPair], sz[kNPair], cx[kNPair], cy[kNPair], cz[kNPair];
+#endif
 #pragma unroll
     for (int q = 0; q < kNPair; ++q) {
       float n[2][3];
@@ -200,7 +210,11 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
       nx[q] = make_float2(n[0][0], n[1][0]);
       ny[q] = make_float2(n[0][1], n[1][1]);
       nz[q] = make_float2(n[0][2], n[1][2]);
+#if SPS_FAR_KSMEM
+      for (int c = 0; c < 6; ++c) sKS[6 * q + c][threadIdx.x] = make_float2(0.f, 0.f);
+#else
       sx[q] = sy[q] = sz[q] = cx[q] = cy[q] = cz[q] = make_float2(0.f, 0.f);
+#endif
     }
     // ---- source spheres, staged spc at a time
     for (int j0 = j_begin; j0 < j_end; j0 += spc) {
@@ -339,19 +353,33 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
           const float2 zx = make_float2(ex[0] ? 0.f : ax[q].x, ex[1] ? 0.f : ax[q].y);
           const float2 zy = make_float2(ex[0] ? 0.f : ay[q].x, ex[1] ? 0.f : ay[q].y);
           const float2 zz = make_float2(ex[0] ? 0.f : az[q].x, ex[1] ? 0.f : az[q].y);
+#if SPS_FAR_KSMEM
+          float2 Sx = sKS[6 * q][threadIdx.x], Sy = sKS[6 * q + 1][threadIdx.x], Sz = sKS[6 * q + 2][threadIdx.x];
+          float2 Cx = sKS[6 * q + 3][threadIdx.x], Cy = sKS[6 * q + 4][threadIdx.x], Cz = sKS[6 * q + 5][threadIdx.x];
+#else
+          float2 &Sx = sx[q], &Sy = sy[q], &Sz = sz[q], &Cx = cx[q], &Cy = cy[q], &Cz = cz[q];
+#endif
           float2 y, t;
-          y = __fadd2_rn(zx, make_float2(-cx[q].x, -cx[q].y));
-          t = __fadd2_rn(sx[q], y);
-          cx[q] = __fadd2_rn(__fadd2_rn(t, make_float2(-sx[q].x, -sx[q].y)), make_float2(-y.x, -y.y));
-          sx[q] = t;
-          y = __fadd2_rn(zy, make_float2(-cy[q].x, -cy[q].y));
-          t = __fadd2_rn(sy[q], y);
-          cy[q] = __fadd2_rn(__fadd2_rn(t, make_float2(-sy[q].x, -sy[q].y)), make_float2(-y.x, -y.y));
-          sy[q] = t;
-          y = __fadd2_rn(zz, make_float2(-cz[q].x, -cz[q].y));
-          t = __fadd2_rn(sz[q], y);
-          cz[q] = __fadd2_rn(__fadd2_rn(t, make_float2(-sz[q].x, -sz[q].y)), make_float2(-y.x, -y.y));
-          sz[q] = t;
+          y = __fadd2_rn(zx, make_float2(-Cx.x, -Cx.y));
+          t = __fadd2_rn(Sx, y);
+          Cx = __fadd2_rn(__fadd2_rn(t, make_float2(-Sx.x, -Sx.y)), make_float2(-y.x, -y.y));
+          Sx = t;
+          y = __fadd2_rn(zy, make_float2(-Cy.x, -Cy.y));
+          t = __fadd2_rn(Sy, y);
+          Cy = __fadd2_rn(__fadd2_rn(t, make_float2(-Sy.x, -Sy.y)), make_float2(-y.x, -y.y));
+          Sy = t;
+          y = __fadd2_rn(zz, make_float2(-Cz.x, -Cz.y));
+          t = __fadd2_rn(Sz, y);
+          Cz = __fadd2_rn(__fadd2_rn(t, make_float2(-Sz.x, -Sz.y)), make_float2(-y.x, -y.y));
+          Sz = t;
+#if SPS_FAR_KSMEM
+          sKS[6 * q][threadIdx.x] = Sx;
+          sKS[6 * q + 1][threadIdx.x] = Sy;
+          sKS[6 * q + 2][threadIdx.x] = Sz;
+          sKS[6 * q + 3][threadIdx.x] = Cx;
+          sKS[6 * q + 4][threadIdx.x] = Cy;
+          sKS[6 * q + 5][threadIdx.x] = Cz;
+#endif
         }
       }
     }
@@ -363,9 +391,15 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
       for (int h = 0; h < 2; ++h) {
         const long long t = base + (long long)(2 * q + h) * kT32;
         if (t < NP) {
-          const float vx = h ? sx[q].y : sx[q].x, kx = h ? cx[q].y : cx[q].x;
-          const float vy = h ? sy[q].y : sy[q].x, ky = h ? cy[q].y : cy[q].x;
-          const float vz = h ? sz[q].y : sz[q].x, kz = h ? cz[q].y : cz[q].x;
+#if SPS_FAR_KSMEM
+          const float2 Sx = sKS[6 * q][threadIdx.x], Sy = sKS[6 * q + 1][threadIdx.x], Sz = sKS[6 * q + 2][threadIdx.x];
+          const float2 Cx = sKS[6 * q + 3][threadIdx.x], Cy = sKS[6 * q + 4][threadIdx.x], Cz = sKS[6 * q + 5][threadIdx.x];
+#else
+          const float2 Sx = sx[q], Sy = sy[q], Sz = sz[q], Cx = cx[q], Cy = cy[q], Cz = cz[q];
+#endif
+          const float vx = h ? Sx.y : Sx.x, kx = h ? Cx.y : Cx.x;
+          const float vy = h ? Sy.y : Sy.x, ky = h ? Cy.y : Cy.x;
+          const float vz = h ? Sz.y : Sz.x, kz = h ? Cz.y : Cz.x;
           o[t] = (double)vx - (double)kx;
           o[NP + t] = (double)vy - (double)ky;
           o[2 * NP + t] = (double)vz - (double)kz;

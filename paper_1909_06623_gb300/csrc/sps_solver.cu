@@ -123,38 +123,6 @@ __global__ void k_q(int n, const double* __restrict__ phi, double idt, double* _
   if (l < n) q[l] = phi[l] * idt + q[l];
 }
 
-// stats for Algorithm 1: [sum min(gn, gg)^2, s.s, s.y, y.y, g.g] with
-// s = gn - go, y = ggn - ggo.  One block, fixed order.
-__global__ void __launch_bounds__(1024) k_bb_stats(int n, const double* __restrict__ gam_new,
-                                                   const double* __restrict__ g_new,
-                                                   const double* __restrict__ gam_old,
-                                                   const double* __restrict__ g_old,
-                                                   double* __restrict__ out) {
-  __shared__ double red[32][5];
-  double a[5] = {0, 0, 0, 0, 0};
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
-    const double mn = fmin(gam_new[l], g_new[l]);
-    a[0] += mn * mn;
-    if (gam_old) {
-      const double s = gam_new[l] - gam_old[l], y = g_new[l] - g_old[l];
-      a[1] += s * s;
-      a[2] += s * y;
-      a[3] += y * y;
-    }
-    a[4] += g_new[l] * g_new[l];
-  }
-  for (int c = 0; c < 5; ++c)
-    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
-  if ((threadIdx.x & 31) == 0)
-    for (int c = 0; c < 5; ++c) red[threadIdx.x >> 5][c] = a[c];
-  __syncthreads();
-  if (threadIdx.x < 5) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-}
-
 __global__ void k_pos_update(int n, const double* __restrict__ pos, const double* __restrict__ UO,
                              double dt, double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -229,13 +197,14 @@ int sps_fail(sps_ctx* ctx, int code, const std::string& msg) {
 }
 
 // out[0..k) = Q[0..k)^T w and out[k] = w . w, on the device (no sync)
+// partial: (k + 1) x kRedBlocks doubles (the GMRES workspace, or d_sc for k = 1)
 static int multidot_dev(sps_ctx* ctx, const double* Q, long long ldq, int k, const double* w,
-                        long long n, double* out) {
+                        long long n, double* out, double* partial) {
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_multidot<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(n, Q, ldq, k, w, ctx->d_red); }
+  k_multidot<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(n, Q, ldq, k, w, partial); }
   SPS_LAUNCHED(ctx);
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_finish<<<(k + 1 + 127) / 128, 128, 0, ctx->stream>>>(k + 1, kRedBlocks, ctx->d_red, out); }
+  k_finish<<<(k + 1 + 127) / 128, 128, 0, ctx->stream>>>(k + 1, kRedBlocks, partial, out); }
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -251,9 +220,10 @@ static int to_host(sps_ctx* ctx, const double* d, int cnt, double* h) {
 // a . b (host result); uses the multi-dot kernel with a one-vector "basis"
 int sps_dot(sps_ctx* ctx, const double* a, const double* b, long long n, double* out) {
   // k = 1 with Q = a gives out[0] = a.b (out[1] = b.b is ignored)
-  SPS_TRY(multidot_dev(ctx, a, 0, 1, b, n, ctx->d_h));
+  double* res = ctx->d_sc + 2 * kRedBlocks;
+  SPS_TRY(multidot_dev(ctx, a, 0, 1, b, n, res, ctx->d_sc));
   double tmp[2];
-  SPS_TRY(to_host(ctx, ctx->d_h, 2, tmp));
+  SPS_TRY(to_host(ctx, res, 2, tmp));
   *out = tmp[0];
   return SPS_OK;
 }
@@ -339,11 +309,11 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
   double* d_h2 = ctx->d_h + kmax + 8;
   for (k = 1; k <= kmax; ++k) {
     SPS_TRY(apply_A(ctx, Q + (long long)(k - 1) * n, w, fp32));
-    SPS_TRY(multidot_dev(ctx, Q, n, k, w, n, d_h1));
+    SPS_TRY(multidot_dev(ctx, Q, n, k, w, n, d_h1, ctx->d_red));
     { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
     k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, d_h1, w); }
     SPS_LAUNCHED(ctx);
-    SPS_TRY(multidot_dev(ctx, Q, n, k, w, n, d_h2));
+    SPS_TRY(multidot_dev(ctx, Q, n, k, w, n, d_h2, ctx->d_red));
     { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
     k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, d_h2, w); }
     SPS_LAUNCHED(ctx);
@@ -420,6 +390,8 @@ extern "C" int sps_default_params(sps_params* o) {
   o->ir_max = 10;
   o->warm_start = 1;
   o->bb_safeguard = 0;
+  o->mobility = SPS_MOB_BIE;
+  o->contact_search = SPS_SEARCH_AUTO;
   return SPS_OK;
 }
 
@@ -437,7 +409,9 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
       prm->gmres_max < 1 || !(prm->bbpgd_tol > 0) || prm->bbpgd_max < 1 ||
       (prm->precision != SPS_FP64 && prm->precision != SPS_MIXED) ||
       (prm->bb_variant != 1 && prm->bb_variant != 2) || !(prm->a_c_scale > 0) ||
-      !(prm->delta >= 0) || prm->ir_tol < 0 || prm->ir_max < 0)
+      !(prm->delta >= 0) || prm->ir_tol < 0 || prm->ir_max < 0 ||
+      (prm->mobility != SPS_MOB_BIE && prm->mobility != SPS_MOB_IDENTITY) ||
+      prm->contact_search < SPS_SEARCH_AUTO || prm->contact_search > SPS_SEARCH_CELLS)
     return SPS_ERR_INVALID_ARG;
   sps_ctx* ctx = new sps_ctx();
   ctx->prm = *prm;
@@ -476,6 +450,13 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
       return rc;
     }
   }
+  {
+    size_t c = 0;
+    if ((rc = sps_grow(ctx, &ctx->d_sc, c, (size_t)2 * kRedBlocks + 8))) {
+      sps_destroy(ctx);
+      return rc;
+    }
+  }
   if (cudaMallocHost((void**)&ctx->h_pinned, sizeof(double) * 4096) != cudaSuccess) {
     cudaGetLastError();
     sps_destroy(ctx);
@@ -501,7 +482,10 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   void* more[] = {ctx->d_analT, ctx->d_synthST, ctx->d_synthKT, ctx->d_coefbar, ctx->d_ebar,
-                  ctx->d_sigtot, ctx->d_ubar, ctx->d_sbar, ctx->d_lam, ctx->d_rbar};
+                  ctx->d_sigtot, ctx->d_ubar, ctx->d_sbar, ctx->d_lam, ctx->d_rbar,
+                  ctx->d_ccount2, ctx->d_inc_cnt, ctx->d_cl_key, ctx->d_cl_id, ctx->d_cl_key2,
+                  ctx->d_cl_id2, ctx->d_cl_range, ctx->d_cl_f, ctx->d_cl_d, ctx->d_cl_part,
+                  ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -711,9 +695,19 @@ static int stats_end(sps_ctx* ctx, sps_stats* st, long long l0, int rc) {
 
 extern "C" int sps_mobility_apply(sps_ctx* ctx, int n, const double* pos, const double* radii,
                                   const double* FT, double* UO, sps_stats* st) {
-  if (!ctx || !FT || !UO) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "mobility_apply: bad argument");
+  if (!ctx || !FT || !UO || n < 1 || !pos || !radii)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "mobility_apply: bad argument");
   long long l0;
   stats_begin(ctx, st, &l0);
+  if (ctx->prm.mobility == SPS_MOB_IDENTITY) {
+    int rc = sps_check_inputs(ctx, n, pos, radii, FT);
+    if (rc == SPS_OK) rc = sps_launch_identity_U(ctx, n, FT, nullptr, UO);
+    if (rc == SPS_OK) {
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return stats_end(ctx, st, l0, rc);
+  }
   int rc = sps_set_geometry(ctx, n, pos, radii);
   if (rc == SPS_OK) rc = check_finite_host(ctx, FT, 6LL * n, "force/torque");
   // warm start from the previous solve on a suspension of the same size
@@ -786,22 +780,92 @@ static int apply_M(sps_ctx* ctx, const double* gam, double* out, sps_stats* st, 
   int rc = mobility_solve(ctx, ctx->d_FT, ctx->d_Uc, st, ctx->d_zeta, warm);
   ctx->zeta_n = 0;   // d_zeta now holds a contact-force solve
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
-  if (st) st->mvops += 1;
   SPS_TRY(sps_launch_DT(ctx, ctx->d_Uc, out));
   return rc;
 }
 
-static int bb_stats(sps_ctx* ctx, const double* gn, const double* ggn, const double* go,
-                    const double* ggo, double out[5]) {
-  { SpsPhase timer_(ctx, SPS_PH_BBPGD);
-  k_bb_stats<<<1, 1024, 0, ctx->stream>>>(ctx->n_c, gn, ggn, go, ggo, ctx->d_h); }
-  SPS_LAUNCHED(ctx);
-  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_h, 5 * sizeof(double), cudaMemcpyDeviceToHost,
-                                ctx->stream));
+static int read5(sps_ctx* ctx, double out[5]) {
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, sps_bb_out(ctx), 5 * sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   std::memcpy(out, ctx->h_pinned, 5 * sizeof(double));
   for (int i = 0; i < 5; ++i)
     if (!std::isfinite(out[i])) return sps_fail(ctx, SPS_ERR_NONFINITE, "BBPGD: non-finite residual");
+  return SPS_OK;
+}
+
+static int bb_stats(sps_ctx* ctx, const double* gn, const double* ggn, const double* go,
+                    const double* ggo, double out[5]) {
+  SPS_TRY(sps_bb_stats_dev(ctx, gn, ggn, go, ggo));
+  return read5(ctx, out);
+}
+
+struct BBResult {
+  int iters = 0;
+  double phi = 0.0;
+  int bb_rc = SPS_OK;   // BREAKDOWN / NOT_CONVERGED of Algorithm 1 itself
+  int worst = SPS_OK;   // NOT_CONVERGED of an inner mobility solve
+};
+
+// Algorithm 1 from gamma_0 = 0 on the current contact list, q in d_q.
+//   mul_g():             d_Mg = M d_g   (for alpha_0 = g^T g / g^T M g)
+//   step(alpha, j, s5):  d_gam_new = max(d_gam - alpha d_g, 0),
+//                        d_g_new = M d_gam_new + q, s5 = the five statistics
+// Each returns an sps_status; NOT_CONVERGED (an inner solve) is recorded and
+// the iteration goes on.  Returns the first hard error, else SPS_OK with the
+// outcome in r; d_gam / d_g hold the last iterate.
+template <class MulG, class Step>
+static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step, BBResult& r) {
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+  double s5[5];
+  SPS_TRY(bb_stats(ctx, ctx->d_gam, ctx->d_g, nullptr, nullptr, s5));
+  r.phi = std::sqrt(s5[0]);
+  const double tol = ctx->prm.bbpgd_tol;
+  if (r.phi < tol) return SPS_OK;
+  int rc = mul_g();
+  if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+  if (rc) r.worst = rc;
+  if (st) st->mvops += 1;
+  double gMg = 0.0;
+  SPS_TRY(sps_dot(ctx, ctx->d_g, ctx->d_Mg, nc, &gMg));
+  if (!(gMg > 0)) {
+    r.bb_rc = SPS_ERR_BREAKDOWN;
+    return SPS_OK;
+  }
+  double alpha = s5[4] / gMg;
+  for (int j = 1; j <= ctx->prm.bbpgd_max; ++j) {
+    rc = step(alpha, j, s5);
+    if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+    if (rc) r.worst = rc;
+    if (st) st->mvops += 1;
+    std::swap(ctx->d_gam, ctx->d_gam_new);
+    std::swap(ctx->d_g, ctx->d_g_new);
+    r.iters = j;
+    r.phi = std::sqrt(s5[0]);
+    if (r.phi < tol) return SPS_OK;
+    const bool ok = (ctx->prm.bb_variant == 1) ? (s5[2] > 0) : (s5[2] > 0 && s5[3] > 0);
+    if (!ok) {
+      // s^T y <= 0: Algorithm 1 defines no step; stop, or keep the previous one
+      if (!ctx->prm.bb_safeguard) {
+        r.bb_rc = SPS_ERR_BREAKDOWN;
+        return SPS_OK;
+      }
+      if (st) st->bb_safeguards += 1;
+    } else {
+      alpha = (ctx->prm.bb_variant == 1) ? s5[1] / s5[2] : s5[2] / s5[3];
+    }
+  }
+  r.bb_rc = SPS_ERR_NOT_CONVERGED;
+  return SPS_OK;
+}
+
+static int finish_bb_stats(sps_ctx* ctx, int nc, const BBResult& r, sps_stats* st) {
+  if (!st) return SPS_OK;
+  st->bbpgd_iters = r.iters;
+  st->final_phi = r.phi;
+  if (nc > 0) SPS_TRY(sps_count_positive(ctx, ctx->d_gam, nc, &st->n_active));
   return SPS_OK;
 }
 
@@ -824,7 +888,7 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
   if (nc > gamma_cap) return sps_fail(ctx, SPS_ERR_CAPACITY, "gamma capacity smaller than the contact count");
   SPS_TRY(ensure_bb(ctx, nc));
   SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
-  int bb_rc = SPS_OK;
+  BBResult r;
   if (nc > 0) {
     // 3. q = Phi/dt + D^T U_nc; BBPGD (Algorithm 1) from gamma_0 = 0
     SPS_TRY(sps_launch_DT(ctx, ctx->d_Unc, ctx->d_q));
@@ -832,68 +896,26 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
     { SpsPhase timer_(ctx, SPS_PH_BBPGD);
     k_q<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_cphi, 1.0 / dt, ctx->d_q); }
     SPS_LAUNCHED(ctx);
-    SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
-    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
-    double s5[5];
-    SPS_TRY(bb_stats(ctx, ctx->d_gam, ctx->d_g, nullptr, nullptr, s5));
-    double phi = std::sqrt(s5[0]);
-    const double tol = ctx->prm.bbpgd_tol;
-    int iters = 0;
-    if (!(phi < tol)) {
-      // alpha_0 = g^T g / g^T M g
-      rc = apply_M(ctx, ctx->d_g, ctx->d_Mg, st, false);
-      if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
-      if (rc) worst = rc;
-      double gMg = 0.0;
-      SPS_TRY(sps_dot(ctx, ctx->d_g, ctx->d_Mg, nc, &gMg));
-      double alpha = (gMg > 0) ? s5[4] / gMg : 0.0;
-      if (!(gMg > 0)) bb_rc = SPS_ERR_BREAKDOWN;
-      for (int j = 1; bb_rc == SPS_OK && j <= ctx->prm.bbpgd_max; ++j) {
-        { SpsPhase timer_(ctx, SPS_PH_BBPGD);
-        k_bb_step<<<tb, 256, 0, ctx->stream>>>(nc, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new); }
-        SPS_LAUNCHED(ctx);
-        rc = apply_M(ctx, ctx->d_gam_new, ctx->d_Mg, st, ctx->prm.warm_start && j >= 2);
-        if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
-        if (rc) worst = rc;
-        { SpsPhase timer_(ctx, SPS_PH_BBPGD);
-        k_add<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_Mg, ctx->d_q, ctx->d_g_new); }
-        SPS_LAUNCHED(ctx);
-        SPS_TRY(bb_stats(ctx, ctx->d_gam_new, ctx->d_g_new, ctx->d_gam, ctx->d_g, s5));
-        std::swap(ctx->d_gam, ctx->d_gam_new);
-        std::swap(ctx->d_g, ctx->d_g_new);
-        iters = j;
-        phi = std::sqrt(s5[0]);
-        if (phi < tol) break;
-        const bool ok = (ctx->prm.bb_variant == 1) ? (s5[2] > 0) : (s5[2] > 0 && s5[3] > 0);
-        if (!ok) {
-          // s^T y <= 0: Algorithm 1 defines no step; stop, or keep the previous one
-          if (ctx->prm.bb_safeguard) {
-            if (st) st->bb_safeguards += 1;
-          } else {
-            bb_rc = SPS_ERR_BREAKDOWN;
-          }
-        } else {
-          alpha = (ctx->prm.bb_variant == 1) ? s5[1] / s5[2] : s5[2] / s5[3];
-        }
-      }
-      if (bb_rc == SPS_OK && !(phi < tol)) bb_rc = SPS_ERR_NOT_CONVERGED;
-      if (iters == 0) SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
-    }
-    if (st) {
-      st->bbpgd_iters = iters;
-      st->final_phi = phi;
-    }
+    auto mul_g = [&]() { return apply_M(ctx, ctx->d_g, ctx->d_Mg, st, false); };
+    auto step = [&](double alpha, int j, double s5[5]) -> int {
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_bb_step<<<tb, 256, 0, ctx->stream>>>(nc, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new); }
+      SPS_LAUNCHED(ctx);
+      const int rc2 = apply_M(ctx, ctx->d_gam_new, ctx->d_Mg, st, ctx->prm.warm_start && j >= 2);
+      if (rc2 != SPS_OK && rc2 != SPS_ERR_NOT_CONVERGED) return rc2;
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_add<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_Mg, ctx->d_q, ctx->d_g_new); }
+      SPS_LAUNCHED(ctx);
+      SPS_TRY(bb_stats(ctx, ctx->d_gam_new, ctx->d_g_new, ctx->d_gam, ctx->d_g, s5));
+      return rc2;
+    };
+    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r));
+    if (r.worst) worst = r.worst;
+    // U_c is the solve of the returned iterate; gamma_0 = 0 needs none
+    if (r.iters == 0) SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
     SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
-    if (st) {
-      std::vector<double> hg(nc);
-      SPS_CUDA(ctx, cudaMemcpyAsync(hg.data(), ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToHost,
-                                    ctx->stream));
-      SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      int na = 0;
-      for (double v : hg) na += v > 0;
-      st->n_active = na;
-    }
   }
+  SPS_TRY(finish_bb_stats(ctx, nc, r, st));
   // 4. U = U_nc + U_c, pos += U dt
   const long long n6 = 6LL * n;
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
@@ -905,9 +927,77 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
     SPS_LAUNCHED(ctx);
   }
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (bb_rc != SPS_OK) return sps_fail(ctx, bb_rc, bb_rc == SPS_ERR_BREAKDOWN ? "BBPGD breakdown" : "BBPGD not converged");
+  if (r.bb_rc != SPS_OK)
+    return sps_fail(ctx, r.bb_rc, r.bb_rc == SPS_ERR_BREAKDOWN ? "BBPGD breakdown" : "BBPGD not converged");
   if (worst != SPS_OK) return sps_fail(ctx, worst, "a mobility solve did not converge");
   return SPS_OK;
+}
+
+static int ensure_ident(sps_ctx* ctx, int n) {
+  if ((size_t)n <= ctx->cap_ident && ctx->d_F3) return SPS_OK;
+  cudaFree(ctx->d_F3);
+  cudaFree(ctx->d_iFT);
+  ctx->d_F3 = ctx->d_iFT = nullptr;
+  size_t c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_F3, c, 3 * (size_t)n));
+  c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_iFT, c, 6 * (size_t)n));
+  ctx->cap_ident = n;
+  return SPS_OK;
+}
+
+// The same step with the identity mobility (U = F): U_nc = F_ext, M = D^T D,
+// and each BBPGD iteration is two fused passes (per sphere: projected step
+// and D; per contact: D^T, + q and the statistics).  No surface grid exists.
+static int resolve_identity(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                            const double* FT_ext, double dt, double* gamma, int gamma_cap, double* UO,
+                            double* pos_out, sps_stats* st) {
+  if (!(dt > 0)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "dt must be positive");
+  SPS_TRY(sps_check_inputs(ctx, n, pos, radii, FT_ext));
+  SPS_TRY(ensure_ident(ctx, n));
+  SPS_TRY(sps_launch_contacts(ctx, n, pos, radii));
+  ctx->c_N = n;
+  const int nc = ctx->n_c;
+  if (st) st->n_contacts = nc;
+  if (nc > gamma_cap) return sps_fail(ctx, SPS_ERR_CAPACITY, "gamma capacity smaller than the contact count");
+  SPS_TRY(ensure_bb(ctx, nc));
+  BBResult r;
+  if (nc > 0) {
+    SPS_TRY(sps_launch_DT(ctx, FT_ext, ctx->d_q));
+    const int tb = (nc + 255) / 256;
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_q<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_cphi, 1.0 / dt, ctx->d_q); }
+    SPS_LAUNCHED(ctx);
+    auto mul_g = [&]() -> int {
+      SPS_TRY(sps_launch_D(ctx, ctx->d_g, ctx->d_iFT));
+      return sps_launch_DT(ctx, ctx->d_iFT, ctx->d_Mg);
+    };
+    auto step = [&](double alpha, int, double s5[5]) -> int {
+      SPS_TRY(sps_launch_bb_identity(ctx, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new, ctx->d_g_new));
+      return read5(ctx, s5);
+    };
+    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r));
+    SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  SPS_TRY(finish_bb_stats(ctx, nc, r, st));
+  // U = F_ext + D gamma (d_F3 holds D of the returned iterate after a step)
+  SPS_TRY(sps_launch_identity_U(ctx, n, FT_ext, r.iters > 0 ? ctx->d_F3 : nullptr, UO));
+  if (pos_out) {
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_pos_update<<<(3 * n + 255) / 256, 256, 0, ctx->stream>>>(n, pos, UO, dt, pos_out); }
+    SPS_LAUNCHED(ctx);
+  }
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (r.bb_rc != SPS_OK)
+    return sps_fail(ctx, r.bb_rc, r.bb_rc == SPS_ERR_BREAKDOWN ? "BBPGD breakdown" : "BBPGD not converged");
+  return SPS_OK;
+}
+
+static int resolve_any(sps_ctx* ctx, int n, const double* pos, const double* radii, const double* FT_ext,
+                       double dt, double* gamma, int gamma_cap, double* UO, double* pos_out, sps_stats* st) {
+  if (ctx->prm.mobility == SPS_MOB_IDENTITY)
+    return resolve_identity(ctx, n, pos, radii, FT_ext, dt, gamma, gamma_cap, UO, pos_out, st);
+  return resolve(ctx, n, pos, radii, FT_ext, dt, gamma, gamma_cap, UO, pos_out, st);
 }
 
 extern "C" int sps_resolve_collisions(sps_ctx* ctx, int n, const double* pos, const double* radii,
@@ -917,7 +1007,7 @@ extern "C" int sps_resolve_collisions(sps_ctx* ctx, int n, const double* pos, co
     return sps_fail(ctx, SPS_ERR_INVALID_ARG, "resolve_collisions: bad argument");
   long long l0;
   stats_begin(ctx, st, &l0);
-  const int rc = resolve(ctx, n, pos, radii, FT_ext, dt, gamma, gamma_cap, UO, pos_out, st);
+  const int rc = resolve_any(ctx, n, pos, radii, FT_ext, dt, gamma, gamma_cap, UO, pos_out, st);
   return stats_end(ctx, st, l0, rc);
 }
 
@@ -938,7 +1028,7 @@ extern "C" int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* po
   SPS_CUDA(ctx, cudaMemcpyAsync(dF, FT_ext, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, ctx->stream));
   long long l0;
   stats_begin(ctx, st, &l0);
-  int rc = resolve(ctx, n, dp, dr, dF, dt, dg, gamma_cap, dU, pos_out ? dpo : nullptr, st);
+  int rc = resolve_any(ctx, n, dp, dr, dF, dt, dg, gamma_cap, dU, pos_out ? dpo : nullptr, st);
   if (rc == SPS_OK || rc == SPS_ERR_NOT_CONVERGED || rc == SPS_ERR_BREAKDOWN) {
     cudaMemcpyAsync(UO, dU, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, ctx->stream);
     if (pos_out) cudaMemcpyAsync(pos_out, dpo, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
@@ -960,9 +1050,26 @@ int sps_geom_gradient(sps_ctx* ctx, const double* ubar, const double* lam, const
 extern "C" int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
                                     const double* FT, const double* dL_dU, double* UO, double* dL_dFT,
                                     double* dL_dpos, sps_stats* st) {
-  if (!ctx || !FT || !dL_dU || !dL_dFT) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "mobility_adjoint: bad argument");
+  if (!ctx || !FT || !dL_dU || !dL_dFT || n < 1 || !pos || !radii)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "mobility_adjoint: bad argument");
   long long l0;
   stats_begin(ctx, st, &l0);
+  if (ctx->prm.mobility == SPS_MOB_IDENTITY) {
+    // U = F: dL/dF = dL/dU, and U does not depend on the centres
+    int rc = sps_check_inputs(ctx, n, pos, radii, FT);
+    if (rc == SPS_OK) rc = sps_check_inputs(ctx, n, pos, radii, dL_dU);
+    if (rc == SPS_OK && UO) rc = sps_launch_identity_U(ctx, n, FT, nullptr, UO);
+    if (rc == SPS_OK) rc = sps_launch_identity_U(ctx, n, dL_dU, nullptr, dL_dFT);
+    if (rc == SPS_OK && dL_dpos) {
+      cudaError_t e = cudaMemsetAsync(dL_dpos, 0, sizeof(double) * 3 * n, ctx->stream);
+      if (e != cudaSuccess) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (rc == SPS_OK) {
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) rc = sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return stats_end(ctx, st, l0, rc);
+  }
   int rc = sps_set_geometry(ctx, n, pos, radii);
   if (rc == SPS_OK) rc = check_finite_host(ctx, FT, 6LL * n, "force/torque");
   if (rc == SPS_OK) rc = check_finite_host(ctx, dL_dU, 6LL * n, "dL/dU");
