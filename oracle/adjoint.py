@@ -13,10 +13,15 @@ forward solve:
 Finite differences must not move a pair across the near-pair threshold
 beta (a_i + a_j): callers choose coordinates and steps that keep every pair at
 least 10 h away from it (see near_margin).
+
+The collision-resolved step of Sec. 3.2 (U = U_nc + M D gamma) is
+differentiated in F_ext on its active set (collision_grad_F), assuming strict
+complementarity; step_loss gives the same L through the full oracle step for
+finite differences.
 """
 import numpy as np
 
-from . import mobility
+from . import lcp, mobility
 from .layer import Suspension
 
 
@@ -71,3 +76,47 @@ def near_margin(centers, radii, beta=1.75):
         t[i] = np.inf
         m = min(m, float(t.min()))
     return m
+
+
+# ----------------------------------------------------------------------------
+# the collision step (Sec. 3.2) differentiated on the active set
+# ----------------------------------------------------------------------------
+def D_matrix(N, ij, nrm):
+    """Dense 6N x n_c contact Jacobian of eq. Dmatdef (columns -n on i, +n on j)."""
+    D = np.zeros((6 * N, len(ij)))
+    for l, (i, j) in enumerate(ij):
+        D[6 * i:6 * i + 3, l] = -nrm[l]
+        D[6 * j:6 * j + 3, l] = nrm[l]
+    return D
+
+
+def collision_grad_F(M, D, gamma, ubar, active_tol=0.0):
+    """dL/dF_ext of U = M F + M D gamma(F) for one collision-resolved step.
+
+    On the active set A = {gamma > active_tol} (strict complementarity: the
+    inactive constraints keep g > 0 under a small change of F), the LCP gives
+    gamma_A = -(D_A^T M D_A)^{-1} (Phi_A / dt + D_A^T M F), so
+        dU/dF = M - M D_A (D_A^T M D_A)^{-1} D_A^T M,
+        dL/dF = (dU/dF)^T ubar = v - M^T D_A lam,
+        v = M^T ubar,  (D_A^T M D_A)^T lam = D_A^T v.
+    M (6N x 6N) is the assembled discrete mobility, D the contact Jacobian."""
+    A = np.asarray(gamma) > active_tol
+    v = M.T @ np.asarray(ubar, dtype=np.float64).ravel()
+    if not A.any():
+        return v.reshape(-1, 6), A
+    DA = D[:, A]
+    MAA = DA.T @ M @ DA
+    lam = np.linalg.solve(MAA.T, DA.T @ v)
+    return (v - M.T @ (DA @ lam)).reshape(-1, 6), A
+
+
+def step_loss(centers, radii, FT, dt, p, *, delta=0.1, a_c_scale=1.0, beta=1.75,
+              identity=False):
+    """L = sum |U|^2 of one collision-resolved step (oracle, tight tolerances)."""
+    if identity:
+        out = lcp.resolve_collisions_identity(centers, radii, FT, dt, delta=delta,
+                                              a_c_scale=a_c_scale, bbpgd_tol=1e-13)
+    else:
+        out = lcp.resolve_collisions(centers, radii, FT, dt, p, beta=beta, delta=delta,
+                                     a_c_scale=a_c_scale, gmres_tol=1e-13, bbpgd_tol=1e-12)
+    return float(np.sum(out["U"] ** 2)), out

@@ -126,34 +126,32 @@ def place_close_pairs(rng, C, R, n_pairs, gap_lo, gap_hi, min_gap, L=None,
 
 
 def compress(C, R, phi_from, phi_to, gap, sweeps=400):
-    """Scale the packing about its centre and push overlapping pairs apart."""
+    """Scale the packing about its centre in 40 steps and, after each, push
+    overlapping pairs apart (all pairs of a sweep at once) until every gap
+    exceeds gap."""
+    from scipy.spatial import cKDTree
     C = C.copy()
     mid = C.mean(axis=0)
     steps = 40
-    scale_total = (phi_from / phi_to) ** (1.0 / 3.0)
-    for s in range(1, steps + 1):
-        f = scale_total ** (1.0 / steps)
+    f = ((phi_from / phi_to) ** (1.0 / 3.0)) ** (1.0 / steps)
+    reach = 2.0 * R.max() + gap
+    for _ in range(steps):
         C = mid + (C - mid) * f
         for _ in range(sweeps):
-            grid = _Grid(2.0 * R.max() + gap)
-            for k in range(len(R)):
-                grid.add(k, C[k])
-            moved = False
-            for i in range(len(R)):
-                for j in grid.around(C[i]):
-                    if j <= i:
-                        continue
-                    d = C[j] - C[i]
-                    dist = np.linalg.norm(d)
-                    need = R[i] + R[j] + gap
-                    if dist < need:
-                        push = 0.5 * (need - dist) * 1.0001 + 1e-12
-                        u = d / dist
-                        C[i] -= push * u
-                        C[j] += push * u
-                        moved = True
-            if not moved:
+            pr = cKDTree(C).query_pairs(reach, output_type="ndarray")
+            if len(pr) == 0:
                 break
+            i, j = pr[:, 0], pr[:, 1]
+            d = C[j] - C[i]
+            dist = np.sqrt(np.einsum("kc,kc->k", d, d))
+            need = R[i] + R[j] + gap
+            m = dist < need
+            if not m.any():
+                break
+            push = (0.5 * (need[m] - dist[m]) * 1.0001 + 1e-12) / dist[m]
+            step = d[m] * push[:, None]
+            np.add.at(C, i[m], -step)
+            np.add.at(C, j[m], step)
         else:
             raise RuntimeError("compression did not converge")
     return C
@@ -290,3 +288,18 @@ def jittered_lattice(seed, N, phi=0.35, a_lo=0.5, a_hi=1.0, jitter=0.1):
                          0.1 * rng.standard_normal((N, 3))], axis=1)
     return Workload(f"lattice_N{N}_phi{phi:.2f}", C, R, FT, p=0, dt=1e-3, steps=1,
                     params=dict(delta=0.1, a_c_scale=1.05))
+
+
+def contact_chain(seed, n=5):
+    """n unit spheres in a wobbly chain, neighbours within U(1.96, 2.02) of
+    touching, squeezed by opposing x-forces: every neighbour pair is a contact,
+    most of them active.  F ~ 80 N(0, 1) plus a linear squeeze."""
+    rng = np.random.default_rng(seed)
+    c = np.zeros((n, 3))
+    for k in range(1, n):
+        d = np.array([1.0, 0.3 * rng.standard_normal(), 0.3 * rng.standard_normal()])
+        c[k] = c[k - 1] + (1.96 + 0.06 * rng.random()) * d / np.linalg.norm(d)
+    F = 80.0 * rng.standard_normal((n, 6))
+    F[:, 0] += np.linspace(60.0, -60.0, n)
+    return Workload(f"chain_n{n}_s{seed}", c, np.ones(n), F, p=0, dt=1e-3, steps=1,
+                    params=dict(delta=0.1))

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-from oracle import lcp, mobility, sph  # noqa: E402
+from oracle import adjoint, lcp, mobility, sph  # noqa: E402
 from oracle.layer import Suspension  # noqa: E402
 from paper_1909_06623_gb300 import workloads  # noqa: E402
 
@@ -103,7 +103,34 @@ def tiny_layers():
     print("tiny_layers")
 
 
-ALL = {"cfg1": cfg1, "active": active, "cfg2": cfg2_sample, "tiny": tiny_layers}
+
+def collision_grad():
+    """The five-sphere active step (p = 4): the assembled mobility, the step's
+    contacts and gamma, and central differences (h = 1e-5 max|F|) of
+    L = sum |U|^2 through the full oracle step in six force / torque
+    coordinates, for the active-set gradient of the step."""
+    d = np.load(os.path.join(HERE, "active_step_p4.npz"))
+    C, R, FT, dt, p = d["centers"], d["radii"], d["FT"], float(d["dt"]), int(d["p"])
+    L0, out = adjoint.step_loss(C, R, FT, dt, p, a_c_scale=1.05)
+    M = adjoint.mobility_matrix(C, R, p)
+    coords = np.array([(0, 0), (1, 1), (2, 1), (3, 2), (4, 0), (4, 4)])
+    h = 1e-5 * np.abs(FT).max()
+    fd = []
+    for i, k in coords:
+        Fp, Fm = FT.copy(), FT.copy()
+        Fp[i, k] += h
+        Fm[i, k] -= h
+        fd.append((adjoint.step_loss(C, R, Fp, dt, p, a_c_scale=1.05)[0]
+                   - adjoint.step_loss(C, R, Fm, dt, p, a_c_scale=1.05)[0]) / (2 * h))
+        print("fd", i, k, fd[-1], flush=True)
+    np.savez_compressed(os.path.join(HERE, "collision_grad_p4.npz"), centers=C, radii=R, FT=FT,
+                        dt=dt, p=p, a_c_scale=1.05, M=M, ij=out["ij"], normals=out["normals"],
+                        gamma=out["gamma"], g=out["g"], U=out["U"], loss=L0, coords=coords,
+                        h=h, fd=np.array(fd))
+
+
+ALL = {"cfg1": cfg1, "active": active, "cfg2": cfg2_sample, "tiny": tiny_layers,
+       "collision_grad": collision_grad}
 
 if __name__ == "__main__":
     for k in (sys.argv[1:] or ALL):
