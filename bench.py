@@ -37,7 +37,7 @@ FLOPS_PER_PAIR = {"K": 30, "S": 29}   # algorithmic FP32 operations per pair ter
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_far32<K> launch at the
 # 1,000-sphere p = 6 workload, from an ncu capture of the current kernel
 # (None whenever the kernel changes until it is captured again)
-FAR_K_TRAFFIC_BYTES = None
+FAR_K_TRAFFIC_BYTES = 3630080 + 71936
 SMS, LANES = 152, 128
 N_PHASES = 12
 PHASES = ["far_K", "far_S", "far_aux", "near_K", "near_S", "self_vsh", "krylov", "contact",
@@ -379,14 +379,25 @@ def run_gpu(args, w):
 # contact / BBPGD microbenchmark (identity mobility, HBM-bound)
 # ---------------------------------------------------------------------------
 def contact_bytes(N, nc):
-    """Algorithmic bytes of one launch of each fused BBPGD pass: every array
-    element the pass must touch, once (FP64 values 8 B, indices 4 B).
-      per-sphere pass (projected step + D): per contact its two incidence
-        entries (8), gamma, g, n (40) and the stored projected gamma (8);
-        per sphere its incidence offset (4) and force (24);
-      per-contact pass (D^T + q + statistics): per contact i, j (8), n (24),
-        q, gamma_new, gamma, g (32) and g_new (8); per sphere its force (24)."""
-    return {"bb_D": 56 * nc + 28 * N, "bb_DT": 72 * nc + 24 * N}
+    """Algorithmic bytes of one launch of each BBPGD pass of the identity
+    mobility: every array element the pass must touch, once (FP64 values 8 B,
+    indices 4 B).
+      per-sphere pass (F = D gamma_n): per contact its two incidence entries
+        (8), gamma_n and n (32); per sphere its incidence offset (4) and force (24);
+      per-contact pass (D^T F + q and the statistics): per contact i, j (8),
+        n (24), q, gamma_n, gamma, g (32) and g_new (8); per sphere its force (24)."""
+    return {"bb_D": 40 * nc + 28 * N, "bb_DT": 72 * nc + 24 * N}
+
+
+def contact_fp64_flops(nc, bb_variant=1):
+    """FP64 operations (an FMA counts 2) of the same launches: the per-sphere
+    pass does 3 FMA per contact end; the per-contact pass 3 subtractions and 3
+    FMA for D^T F + q, 2 subtractions and 3 FMA (4 for BB2) for the
+    statistics (the min of the min-map residual runs on the integer units)."""
+    return {"bb_D": 12 * nc, "bb_DT": (17 + 2 * (bb_variant == 2)) * nc}
+
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal), the recipe's figure
 
 
 def run_contacts(args, N, gpu_index, standalone=False):
@@ -436,14 +447,18 @@ def run_contacts(args, N, gpu_index, standalone=False):
     pk = peaks()
     by = contact_bytes(N, nc)
     roof = []
-    for nm, kern in (("bb_D", "k_bb_ident_D"), ("bb_DT", "k_bb_ident_DT")):
+    fl = contact_fp64_flops(nc)
+    for nm, kern in (("bb_D", "k_bb_gather"), ("bb_DT", "k_bb_ident_DT")):
         i = PHASES.index(nm)
         avg = ph_ms[i] / max(ph_n[i], 1)
         ach = by[nm] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        f64 = fl[nm] / (avg * 1e-3) / 1e12 if avg > 0 else 0.0
         roof.append({"kernel": kern, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
                      "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "bytes_per_launch": by[nm],
                      "avg_launch_ms": avg, "launches": int(ph_n[i]), "traffic": None,
-                     "peak_note": f"measured STREAM copy ({pk['source']})"})
+                     "peak_note": f"measured STREAM copy ({pk['source']})",
+                     "fp64": {"flops_per_launch": fl[nm], "achieved_tflops": f64,
+                              "peak_tflops": FP64_PEAK_TFLOPS, "frac": f64 / FP64_PEAK_TFLOPS}})
     out = {"workload": w.name, "N": N, "n_contacts": nc,
            "n_active": stats[-1]["n_active"], "bbpgd_tol": tol,
            "bbpgd_iters": [s["bbpgd_iters"] for s in stats],
@@ -463,6 +478,102 @@ def run_contacts(args, N, gpu_index, standalone=False):
     if standalone:
         print(json.dumps({"contact_bbpgd_microbench": out}), flush=True)
     return out
+
+
+def run_sweep(args):
+    """Sweep of the layer operator over suspension size and order (spheres
+    a ~ U[0.5, 1] at volume fraction 0.35 with close pairs): per (N, p) one
+    traction-operator application in mixed precision (far-field pair rate and
+    fraction of FP32 peak), the FP64 application where it takes under ~2 s,
+    and one full collision-resolved step in mixed precision for N <= 2000."""
+    import torch
+    import paper_1909_06623_gb300 as sps
+    from paper_1909_06623_gb300 import workloads
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    lib = sps._lib.load()
+    pk = peaks()
+    rows = []
+    for N in (500, 2000, 4000, 8000):
+        for p in (4, 6, 8):
+            try:
+                row = sweep_point(N, p, dev, stream, lib, pk)
+            except Exception as e:          # keep sweeping; the row records the failure
+                row = {"workload": f"cfg5_N{N}_p{p}", "N": N, "p": p, "error": str(e)[:300]}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"sweep": rows, "peak_fp32_tflops": pk["fp32_tflops"]}), flush=True)
+
+
+def sweep_point(N, p, dev, stream, lib, pk):
+    """One (N, p) point of run_sweep."""
+    import torch
+    import paper_1909_06623_gb300 as sps
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.config5(N, p)
+    P = (p + 1) * (2 * p + 2)
+    NP = N * P
+    row = {"workload": w.name, "N": N, "p": p, "nodes": NP}
+    for prec in ("mixed", "fp64"):
+        prm = ctx_params(prec)
+        prm["p"] = p
+        ctx = sps.Context(stream=stream, **prm)
+        ctx.set_geometry(dev(w.centers), dev(w.radii))
+        if prec == "fp64" and NP * NP > 1.2e10:
+            row["fp64_K_ms"] = None
+            ctx.close()
+            continue
+        sig = torch.randn(3, NP, dtype=torch.float64, device="cuda")
+        out = torch.empty_like(sig)
+        ctx.layer_apply(sps.SPS_OP_K, sig, out)
+        reps = 3 if prec == "mixed" else 1
+        torch.cuda.synchronize()
+        lib.sps_profile(ctx.h, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.layer_apply(sps.SPS_OP_K, sig, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ph_ms = (ctypes.c_double * N_PHASES)()
+        ph_n = (ctypes.c_longlong * N_PHASES)()
+        lib.sps_profile_read(ctx.h, ph_ms, ph_n)
+        lib.sps_profile(ctx.h, 0)
+        op_ms = e0.elapsed_time(e1) / reps
+        row[f"{prec}_K_ms"] = op_ms
+        if prec == "mixed":
+            # far pairs: all node pairs minus self and near spheres
+            near, close = ctx.geometry_counts()
+            pairs = NP * NP - P * P * (N + near)
+            farK = ph_ms[0] / max(ph_n[0], 1)
+            ach = FLOPS_PER_PAIR["K"] * pairs / (farK * 1e-3) / 1e12
+            row.update(far_pairs=pairs, near_pairs=near, close_entries=close, far_K_ms=farK,
+                       far_K_tflops=ach, far_K_frac=ach / pk["fp32_tflops"],
+                       interactions_per_s=pairs / (farK * 1e-3))
+            if N <= 2000:
+                FT = dev(w.FT)
+                pos = dev(w.centers)
+                rad = dev(w.radii)
+                g = torch.empty(16 * N, dtype=torch.float64, device="cuda")
+                U = torch.empty(N, 6, dtype=torch.float64, device="cuda")
+                po = torch.empty_like(pos)
+                ctx.resolve_collisions(pos, rad, FT, w.dt, gamma=g, UO=U, pos_out=po,
+                                       gamma_cap=g.numel(), allow=(4, 5))
+                pos.copy_(po)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                ctx.resolve_collisions(pos, rad, FT, w.dt, gamma=g, UO=U, pos_out=po,
+                                       gamma_cap=g.numel(), allow=(4, 5))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                stt = ctx.last_stats
+                row.update(step_ms=e0.elapsed_time(e1), step_gmres_iters=stt["gmres_iters"],
+                           step_bbpgd_iters=stt["bbpgd_iters"], step_contacts=stt["n_contacts"],
+                           step_status=stt["status"])
+        ctx.close()
+    if row.get("fp64_K_ms") and row.get("mixed_K_ms"):
+        row["mixed_speedup_K"] = row["fp64_K_ms"] / row["mixed_K_ms"]
+    return row
 
 
 def run_single_op(args, w):
@@ -498,7 +609,12 @@ def main():
     ap.add_argument("--contact-n", type=int, default=CONTACT_N)
     ap.add_argument("--contact-only", action="store_true",
                     help="run only the identity-mobility contact benchmark")
+    ap.add_argument("--sweep", action="store_true",
+                    help="operator / step sweep over N in {500..8000} and p in {4, 6, 8}")
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.contact_only:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

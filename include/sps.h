@@ -105,7 +105,8 @@ typedef struct sps_stats {
   int n_contacts;       /* size of the contact set A                         */
   int n_active;         /* contacts with gamma > 0 (the active set A_c)      */
   int n_near_pairs;     /* directed near pairs (i, j), i != j                */
-  int ir_sweeps;        /* refinement sweeps (SPS_MIXED with ir_tol > 0)     */
+  int ir_sweeps;        /* refinement sweeps (SPS_MIXED with ir_tol > 0);
+                           active-set iterations (sps_collision_adjoint)     */
   int bb_safeguards;    /* BBPGD steps that kept the previous step length    */
   long long kernel_launches; /* kernels launched by this call                */
   double final_phi;     /* min-map residual at exit                          */
@@ -135,6 +136,13 @@ int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const double* radii
 /* Nodes of the current geometry: X, normals (3 planes of NP) and quadrature
  * weights (NP), device outputs; any pointer may be NULL.  *np_out = NP. */
 int sps_nodes(sps_ctx* ctx, double* X, double* normals, double* weights, int* np_out);
+
+/* Sizes of the current geometry's lists (host outputs, either may be NULL):
+ * directed near pairs (i, j), i != j, |c_i - c_j| < beta (a_i + a_j)
+ * (Sec. 4.2), and close near entries (target node, near source sphere) within
+ * 1.5 source radii, which the mixed path evaluates in FP64.
+ * Errors: NO_GEOMETRY before sps_set_geometry. */
+int sps_geometry_counts(const sps_ctx* ctx, int* n_near_pairs, int* n_close_entries);
 
 /* Layer operator (sps_op) applied to sigma (3 planes of NP, device) on the
  * current geometry; out (3 planes) is overwritten.  Self part: VSH multipliers
@@ -208,6 +216,23 @@ int sps_layer_apply_transpose(sps_ctx* ctx, int op, const double* v, double* out
 int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
                          const double* FT, const double* dL_dU, double* UO, double* dL_dFT,
                          double* dL_dpos, sps_stats* stats);
+
+/* Adjoint of one collision-resolved step (sps_resolve_collisions, Sec. 3.2)
+ * in the external forces.  Runs the step (positions are not advanced; its
+ * velocities U = U_nc + M D gamma go to UO, n x 6 device, required) and, for
+ * dL/dU (n x 6 device), writes dL/dF_ext (n x 6 device).  On the active set
+ * A = {gamma > 0} of the LCP (eq. LCPdef), assuming strict complementarity,
+ *   dU/dF = M - M D_A (D_A^T M D_A)^{-1} D_A^T M,
+ * so dL/dF = v - M^T D_A lambda with v = M^T dL/dU and
+ * (D_A^T M D_A)^T lambda = D_A^T v, solved by GMRES on contact vectors
+ * (gmres_tol, gmres_max); every application of M^T is an adjoint mobility
+ * solve (identity mobility: none).  Radii, centres and the contact and near
+ * sets are held fixed.  stats->n_active = |A|, stats->ir_sweeps = iterations
+ * of the active-set solve.  The paper has no adjoint.  Errors as
+ * sps_resolve_collisions; NOT_CONVERGED if a solve hit its cap. */
+int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                          const double* FT_ext, double dt, const double* dL_dU, double* UO,
+                          double* dL_dFT, sps_stats* stats);
 
 /* Contact set of sps_build_contacts for callers that cannot allocate device
  * memory when they need it: code running while a stream is being captured into

@@ -114,6 +114,12 @@ class Context:
         self._check(self.lib.sps_set_geometry(self.h, n, _ptr(pos), _ptr(radii)))
         self.n = n
 
+    def geometry_counts(self):
+        """(directed near pairs, close near entries) of the current geometry."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.sps_geometry_counts(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def nodes(self):
         NP = self.n * self.P
         X = torch.empty(3, NP, dtype=torch.float64, device="cuda")
@@ -148,6 +154,20 @@ class Context:
         self._check(rc, allow=(4,) if allow_not_converged else ())
         self.last_stats = st.as_dict()
         return UO, gF, gx
+
+    def collision_adjoint(self, pos, radii, FT_ext, dt, dL_dU, allow=()):
+        """(U, dL/dF_ext) of one collision-resolved step (positions not advanced)."""
+        n = radii.numel()
+        UO = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        gF = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        st = sps_stats()
+        rc = self.lib.sps_collision_adjoint(self.h, n, _ptr(pos), _ptr(radii), _ptr(FT_ext), float(dt),
+                                            _ptr(dL_dU.contiguous()), _ptr(UO), _ptr(gF),
+                                            ctypes.byref(st))
+        self._check(rc, allow=allow)
+        self.last_stats = st.as_dict()
+        self.n_c = st.n_contacts
+        return UO, gF
 
     def build_contacts(self, pos, radii):
         nc = ctypes.c_int()

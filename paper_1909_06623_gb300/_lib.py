@@ -55,6 +55,7 @@ SIGNATURES = {
     "sps_last_error": (ctypes.c_char_p, [_P]),
     "sps_set_geometry": (_I, [_P, _I, _P, _P]),
     "sps_nodes": (_I, [_P, _P, _P, _P, ctypes.POINTER(_I)]),
+    "sps_geometry_counts": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sps_layer_apply": (_I, [_P, _I, _P, _P]),
     "sps_build_contacts": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I)]),
     "sps_get_contacts": (_I, [_P, _P, _P, _P]),
@@ -69,6 +70,8 @@ SIGNATURES = {
     "sps_profile": (_I, [_P, _I]),
     "sps_layer_apply_transpose": (_I, [_P, _I, _P, _P]),
     "sps_mobility_adjoint": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(sps_stats)]),
+    "sps_collision_adjoint": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P,
+                                   ctypes.POINTER(sps_stats)]),
     "sps_build_contacts_noalloc": (_I, [_I, _P, _P, _D, _D, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "sps_profile_read": (_I, [_P, _P, _P]),
 }

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 SOURCES = ["sps_tables.cu", "sps_geometry.cu", "sps_contacts.cu", "sps_nbody.cu", "sps_vsh.cu",
-           "sps_solver.cu", "sps_adjoint.cu", "sps_adjoint_geom.cu"]
+           "sps_sht_tc.cu", "sps_solver.cu", "sps_adjoint.cu", "sps_adjoint_geom.cu"]
 
 
 def nvcc():

@@ -1,6 +1,6 @@
 // Contact set (Sec. 3.2), the contact Jacobian D and its transpose
 // (eq. Dmatdef, eq. Dtranspose), the BBPGD statistics of Algorithm 1, and the
-// fused BBPGD iteration for the identity mobility.
+// BBPGD iteration for the identity mobility.
 //
 // Contact search.  Small suspensions test every pair i < j.  Large ones use a
 // uniform grid of cells whose side is at least 2 max a_c + delta, so that every
@@ -25,7 +25,7 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kStatBlocks = 4 * 152;   // fixed partition of the BBPGD reductions
+constexpr int kStatBlocks = 8 * 152;   // fixed partition of the BBPGD reductions
 constexpr int kBoundBlocks = 2 * 152;
 
 inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
@@ -34,20 +34,6 @@ __device__ __forceinline__ bool contact_at(const double* pos, const double* rad,
                                            double delta, int i, int j, SpsContactGeom* g) {
   return sps_contact_test(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], rad[i], pos[3 * j],
                           pos[3 * j + 1], pos[3 * j + 2], rad[j], acs, delta, g);
-}
-
-__device__ __forceinline__ void put_contact(int o, int i, int j, const SpsContactGeom& g, int* ij,
-                                            double* phi, double* nrm, int* keys, int* vals) {
-  ij[2 * o] = i;
-  ij[2 * o + 1] = j;
-  phi[o] = g.phi;
-  nrm[3 * o + 0] = g.nx;
-  nrm[3 * o + 1] = g.ny;
-  nrm[3 * o + 2] = g.nz;
-  keys[2 * o] = i;
-  vals[2 * o] = 2 * o;          // contact o, sphere is first (sign -1)
-  keys[2 * o + 1] = j;
-  vals[2 * o + 1] = 2 * o + 1;  // contact o, sphere is second (sign +1)
 }
 
 // ---------------------------------------------------------------------------
@@ -67,13 +53,37 @@ __global__ void k_pairs_count(int N, const double* pos, const double* rad, doubl
 }
 
 __global__ void k_pairs_fill(int N, const double* pos, const double* rad, double acs, double delta,
-                             const int* ptr, int* ij, double* phi, double* nrm, int* keys, int* vals) {
+                             const int* ptr, int* ij) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int o = ptr[i];
-  SpsContactGeom g;
   for (int j = i + 1; j < N; ++j)
-    if (contact_at(pos, rad, acs, delta, i, j, &g)) put_contact(o++, i, j, g, ij, phi, nrm, keys, vals);
+    if (contact_at(pos, rad, acs, delta, i, j, nullptr)) {
+      ij[2 * o] = i;
+      ij[2 * o + 1] = j;
+      ++o;
+    }
+}
+
+// Phi and the normal of every listed contact (one thread per contact, the
+// arithmetic of the contact test), and the contact ends for the incidence sort
+__global__ void k_contact_geom(int nc, const int* __restrict__ ij, const double* __restrict__ pos,
+                               const double* __restrict__ rad, double acs, double* __restrict__ phi,
+                               double* __restrict__ nrm, int* __restrict__ keys, int* __restrict__ vals) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nc) return;
+  const int i = ij[2 * l], j = ij[2 * l + 1];
+  SpsContactGeom g;
+  // delta = +inf: the same rounded operations, and the geometry is always written
+  contact_at(pos, rad, acs, INFINITY, i, j, &g);
+  phi[l] = g.phi;
+  nrm[3 * l + 0] = g.nx;
+  nrm[3 * l + 1] = g.ny;
+  nrm[3 * l + 2] = g.nz;
+  keys[2 * l] = i;
+  vals[2 * l] = 2 * l;          // contact l, sphere is first (sign -1)
+  keys[2 * l + 1] = j;
+  vals[2 * l + 1] = 2 * l + 1;  // contact l, sphere is second (sign +1)
 }
 
 // ---------------------------------------------------------------------------
@@ -173,9 +183,11 @@ __global__ void k_cl_gather(int N, const int* __restrict__ id, const double* __r
 
 // Visits every sphere j > i in the 27 cells around sorted position k that can
 // satisfy the contact test; f(i, j) is called for each pair that passes it.
-// The FP32 screen rejects a pair only when its FP32 distance exceeds
-// (a_c,i + a_c,j + delta)(1 + 1e-5) + eps, eps bounding the rounding of the
-// FP32 coordinates, so no pair that passes the FP64 test is ever rejected.
+// The FP32 screen decides a pair when its FP32 distance is clearly above
+// (a_c,i + a_c,j + delta)(1 + 1e-5) + eps or clearly below
+// (a_c,i + a_c,j + delta)(1 - 1e-5) - eps, eps bounding the rounding of the
+// FP32 coordinates; only pairs in that band take the FP64 test, so every
+// decision equals the FP64 test's.
 template <class F>
 __device__ __forceinline__ void cl_scan(int k, const int* __restrict__ key, const int* __restrict__ id,
                                         const float4* __restrict__ cf, const double4_32a* __restrict__ cd,
@@ -197,9 +209,15 @@ __device__ __forceinline__ void cl_scan(int k, const int* __restrict__ key, cons
         const float4 o = cf[m];
         const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float thr = fmaf(fmaf(acsf, me.w + o.w, deltaf), 1.00001f, G.eps);
-        if (d2 > thr * thr) continue;
-        const double4_32a od = cd[m];
+        const float tn = fmaf(acsf, me.w + o.w, deltaf);
+        const float hi = fmaf(tn, 1.00001f, G.eps);
+        if (d2 > hi * hi) continue;                   // certainly apart
+        const float lo = fmaf(tn, 0.99999f, -G.eps);
+        if (lo > 0.f && d2 < lo * lo) {               // certainly in contact
+          f(i, j);
+          continue;
+        }
+        const double4_32a od = cd[m];                 // near the threshold: FP64 test
         if (sps_contact_test(md.x, md.y, md.z, md.w, od.x, od.y, od.z, od.w, acs, delta, nullptr))
           f(i, j);
       }
@@ -223,19 +241,14 @@ __global__ void __launch_bounds__(kThreads) k_cl_count(int N, const int* __restr
   cnt[id[k]] = c;
 }
 
-// writes row i: the j's found, sorted ascending in place, then the geometry of
-// each contact from the caller's arrays (the same values the test read)
+// writes row i: (i, j) for the j's found, sorted ascending in place
 __global__ void __launch_bounds__(kThreads) k_cl_fill(int N, const int* __restrict__ key,
                                                      const int* __restrict__ id,
                                                      const float4* __restrict__ cf,
                                                      const double4_32a* __restrict__ cd,
                                                      const int* __restrict__ start, CellGrid G,
                                                      double acs, double delta,
-                                                     const double* __restrict__ pos,
-                                                     const double* __restrict__ rad,
-                                                     const int* __restrict__ ptr, int* __restrict__ ij,
-                                                     double* __restrict__ phi, double* __restrict__ nrm,
-                                                     int* __restrict__ keys, int* __restrict__ vals) {
+                                                     const int* __restrict__ ptr, int* __restrict__ ij) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const int i = id[k];
@@ -257,12 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_cl_fill(int N, const int* __restri
     }
     ij[2 * u + 1] = v;
   }
-  SpsContactGeom g;
-  for (int t = o0; t < o; ++t) {
-    const int j = ij[2 * t + 1];
-    contact_at(pos, rad, acs, delta, i, j, &g);
-    put_contact(t, i, j, g, ij, phi, nrm, keys, vals);
-  }
+  for (int t = o0; t < o; ++t) ij[2 * t] = i;
 }
 
 __global__ void k_add_counts(int N, const int* a, const int* b, int* out) {
@@ -360,68 +368,110 @@ __global__ void __launch_bounds__(kThreads) k_bb_stats_part(int n, const double*
   stat_store(a, part);
 }
 
+// one warp per statistic: lane-strided partial sums, then a fixed shuffle tree
 __global__ void k_stat_finish(int nb, const double* __restrict__ part, double* __restrict__ out) {
-  const int c = threadIdx.x;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (c >= 5) return;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[c * nb + b];
-  out[c] = s;
+  for (int b = lane; b < nb; b += 32) s += part[c * nb + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = s;
 }
 
-// Identity mobility, first half of one BBPGD iteration: per sphere s, the
-// projected step gam_n = max(gam - alpha g, 0) of each incident contact (the
-// contact's first sphere stores it) and F_s = (D gam_n)_s, forces only.
-__global__ void __launch_bounds__(kThreads) k_bb_ident_D(int N, double alpha,
-                                                        const int* __restrict__ inc_ptr,
-                                                        const int* __restrict__ inc,
-                                                        const double* __restrict__ nrm,
-                                                        const double* __restrict__ gam,
-                                                        const double* __restrict__ g,
-                                                        double* __restrict__ gam_new,
-                                                        double* __restrict__ F3) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+// Identity mobility, one BBPGD iteration in three passes.  On this part FP64
+// arithmetic, not memory, is the scarce resource, so each pass keeps whole
+// warps busy, every FP64 operation is needed by the result, and comparisons
+// run on the integer units:
+//   1. per contact: gam_n = max(gam - alpha g, 0)                   (1 FMA)
+//   2. per sphere:  F_s = sum of (+-gam_n) n over incident contacts (3 FMA each)
+//   3. per contact: g_n = q + n . (F_j - F_i) and the statistics    (6 + 5)
+
+// max(x, 0) on the bit pattern: a set sign bit gives +0 (a NaN stays a NaN)
+__device__ __forceinline__ double clamp_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  return __longlong_as_double(b & ~(b >> 63));
+}
+
+// min(x, y) by integer comparison of order-preserving keys (finite inputs)
+__device__ __forceinline__ double min_bits(double x, double y) {
+  const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+  const long long ka = a ^ ((a >> 63) & 0x7FFFFFFFFFFFFFFFll);
+  const long long kb = b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+  return (kb < ka) ? y : x;
+}
+
+__global__ void k_bb_proj(int nc, double alpha, const double* __restrict__ gam,
+                          const double* __restrict__ g, double* __restrict__ gam_new) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < nc) gam_new[l] = clamp_pos(fma(-alpha, g[l], gam[l]));
+}
+
+// Per block of kThreads consecutive spheres, their order by decreasing number
+// of incident contacts (ties by index): the gather below gives each warp
+// spheres of about equal work, while a block still covers the same spheres.
+__global__ void __launch_bounds__(kThreads) k_degree_order(int N, const int* __restrict__ inc_ptr,
+                                                          int* __restrict__ order) {
+  __shared__ int cnt[kThreads];
+  const int s0 = blockIdx.x * kThreads, t = threadIdx.x, s = s0 + t;
+  cnt[t] = (s < N) ? inc_ptr[s + 1] - inc_ptr[s] : -1;
+  __syncthreads();
   if (s >= N) return;
+  const int me = cnt[t];
+  int rank = 0;
+  for (int u = 0; u < kThreads; ++u) {
+    const int c = cnt[u];
+    rank += (c > me) || (c == me && u < t);
+  }
+  order[s0 + rank] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bb_gather(int N, const int* __restrict__ order,
+                                                       const int* __restrict__ inc_ptr,
+                                                       const int* __restrict__ inc,
+                                                       const double* __restrict__ nrm,
+                                                       const double* __restrict__ gam_new,
+                                                       double* __restrict__ F3) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int s = order[k];
   double f0 = 0.0, f1 = 0.0, f2 = 0.0;
   const int e1 = inc_ptr[s + 1];
   for (int e = inc_ptr[s]; e < e1; ++e) {
     const int v = inc[e], l = v >> 1;
-    const double gn = fmax(gam[l] - alpha * g[l], 0.0);
-    const double a0 = __dmul_rn(gn, nrm[3 * l]), a1 = __dmul_rn(gn, nrm[3 * l + 1]),
-                 a2 = __dmul_rn(gn, nrm[3 * l + 2]);
-    if (v & 1) {
-      f0 = __dadd_rn(f0, a0);
-      f1 = __dadd_rn(f1, a1);
-      f2 = __dadd_rn(f2, a2);
-    } else {
-      gam_new[l] = gn;
-      f0 = __dsub_rn(f0, a0);
-      f1 = __dsub_rn(f1, a1);
-      f2 = __dsub_rn(f2, a2);
-    }
+    const double gs = (v & 1) ? gam_new[l] : -gam_new[l];
+    f0 = fma(gs, nrm[3 * l], f0);
+    f1 = fma(gs, nrm[3 * l + 1], f1);
+    f2 = fma(gs, nrm[3 * l + 2], f2);
   }
   F3[3 * s + 0] = f0;
   F3[3 * s + 1] = f1;
   F3[3 * s + 2] = f2;
 }
 
-// second half: g_n = D^T F + q per contact, and the five statistics
+// statistics [sum min(gam_n, g_n)^2, s.s, s.y, y.y (BB2 only), 0]
 __global__ void __launch_bounds__(kThreads) k_bb_ident_DT(int nc, const int* __restrict__ ij,
                                                          const double* __restrict__ nrm,
                                                          const double* __restrict__ F3,
                                                          const double* __restrict__ q,
                                                          const double* __restrict__ gam_new,
                                                          const double* __restrict__ gam,
-                                                         const double* __restrict__ g,
+                                                         const double* __restrict__ g, int want_yy,
                                                          double* __restrict__ g_new,
                                                          double* __restrict__ part) {
   double a[5] = {0, 0, 0, 0, 0};
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nc; l += gridDim.x * blockDim.x) {
     const int i = ij[2 * l], j = ij[2 * l + 1];
-    double acc = 0.0;
-    for (int c = 0; c < 3; ++c) acc += nrm[3 * l + c] * (F3[3 * j + c] - F3[3 * i + c]);
-    const double ggn = acc + q[l];
-    g_new[l] = ggn;
-    stat_add(a, gam_new[l], ggn, gam[l], g[l], true);
+    double acc = q[l];
+    acc = fma(nrm[3 * l], F3[3 * j] - F3[3 * i], acc);
+    acc = fma(nrm[3 * l + 1], F3[3 * j + 1] - F3[3 * i + 1], acc);
+    acc = fma(nrm[3 * l + 2], F3[3 * j + 2] - F3[3 * i + 2], acc);
+    g_new[l] = acc;
+    const double gn = gam_new[l];
+    const double mn = min_bits(gn, acc), sv = gn - gam[l], yv = acc - g[l];
+    a[0] = fma(mn, mn, a[0]);
+    a[1] = fma(sv, sv, a[1]);
+    a[2] = fma(sv, yv, a[2]);
+    if (want_yy) a[3] = fma(yv, yv, a[3]);
   }
   stat_store(a, part);
 }
@@ -581,6 +631,7 @@ int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, Cel
 
 int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii) {
   SpsPhase timer(ctx, SPS_PH_CONTACT);
+  ctx->order_valid = false;
   const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta;
   const int search = ctx->prm.contact_search;
   const bool cells = search == SPS_SEARCH_CELLS || (search == SPS_SEARCH_AUTO && n > 4096);
@@ -647,14 +698,15 @@ int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* ra
   if (nc == 0) return SPS_OK;
   if (cells) {
     k_cl_fill<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key2, ctx->d_cl_id2, ctx->d_cl_f,
-                                                      ctx->d_cl_d, ctx->d_cl_range, G, acs, delta, pos,
-                                                      radii, ctx->d_cptr, ctx->d_cij, ctx->d_cphi,
-                                                      ctx->d_cn, ctx->d_keys, ctx->d_vals);
+                                                      ctx->d_cl_d, ctx->d_cl_range, G, acs, delta,
+                                                      ctx->d_cptr, ctx->d_cij);
   } else {
     k_pairs_fill<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, ctx->d_cptr,
-                                                        ctx->d_cij, ctx->d_cphi, ctx->d_cn, ctx->d_keys,
-                                                        ctx->d_vals);
+                                                        ctx->d_cij);
   }
+  SPS_LAUNCHED(ctx);
+  k_contact_geom<<<nblk(nc), kThreads, 0, ctx->stream>>>(nc, ctx->d_cij, pos, radii, acs, ctx->d_cphi,
+                                                          ctx->d_cn, ctx->d_keys, ctx->d_vals);
   SPS_LAUNCHED(ctx);
   // a stable sort of (sphere, contact end) lists each sphere's incident
   // contacts in contact order: a deterministic transpose of the list
@@ -702,7 +754,7 @@ int sps_bb_stats_dev(sps_ctx* ctx, const double* gn, const double* ggn, const do
   const int nb = std::max(1, std::min(kStatBlocks, nblk(ctx->n_c)));
   k_bb_stats_part<<<nb, kThreads, 0, ctx->stream>>>(ctx->n_c, gn, ggn, go, ggo, ctx->d_bbpart);
   SPS_LAUNCHED(ctx);
-  k_stat_finish<<<1, 32, 0, ctx->stream>>>(nb, ctx->d_bbpart, ctx->d_bbpart + 5 * kStatBlocks);
+  k_stat_finish<<<1, 160, 0, ctx->stream>>>(nb, ctx->d_bbpart, ctx->d_bbpart + 5 * kStatBlocks);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -712,20 +764,32 @@ int sps_launch_bb_identity(sps_ctx* ctx, double alpha, const double* gam, const 
   SPS_TRY(ensure_bbpart(ctx));
   const int N = ctx->c_N, nc = ctx->n_c;
   {
+    SpsPhase timer(ctx, SPS_PH_BBPGD);
+    k_bb_proj<<<nblk(nc), kThreads, 0, ctx->stream>>>(nc, alpha, gam, g, gam_new);
+    SPS_LAUNCHED(ctx);
+  }
+  {
     SpsPhase timer(ctx, SPS_PH_BB_D);
-    k_bb_ident_D<<<nblk(N), kThreads, 0, ctx->stream>>>(N, alpha, ctx->d_inc_ptr, ctx->d_inc, ctx->d_cn,
-                                                         gam, g, gam_new, ctx->d_F3);
+    if (!ctx->order_valid) {
+      SPS_TRY(sps_grow(ctx, &ctx->d_order, ctx->cap_order, (size_t)N));
+      k_degree_order<<<nblk(N), kThreads, 0, ctx->stream>>>(N, ctx->d_inc_ptr, ctx->d_order);
+      SPS_LAUNCHED(ctx);
+      ctx->order_valid = true;
+    }
+    k_bb_gather<<<nblk(N), kThreads, 0, ctx->stream>>>(N, ctx->d_order, ctx->d_inc_ptr, ctx->d_inc,
+                                                        ctx->d_cn, gam_new, ctx->d_F3);
     SPS_LAUNCHED(ctx);
   }
   const int nb = std::max(1, std::min(kStatBlocks, nblk(nc)));
   {
     SpsPhase timer(ctx, SPS_PH_BB_DT);
     k_bb_ident_DT<<<nb, kThreads, 0, ctx->stream>>>(nc, ctx->d_cij, ctx->d_cn, ctx->d_F3, ctx->d_q,
-                                                    gam_new, gam, g, g_new, ctx->d_bbpart);
+                                                    gam_new, gam, g, ctx->prm.bb_variant == 2, g_new,
+                                                    ctx->d_bbpart);
     SPS_LAUNCHED(ctx);
   }
   SpsPhase timer(ctx, SPS_PH_BBPGD);
-  k_stat_finish<<<1, 32, 0, ctx->stream>>>(nb, ctx->d_bbpart, ctx->d_bbpart + 5 * kStatBlocks);
+  k_stat_finish<<<1, 160, 0, ctx->stream>>>(nb, ctx->d_bbpart, ctx->d_bbpart + 5 * kStatBlocks);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }

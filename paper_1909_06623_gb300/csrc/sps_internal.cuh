@@ -81,6 +81,13 @@ struct sps_ctx {
   double *d_sigtot = nullptr, *d_ubar = nullptr, *d_sbar = nullptr, *d_lam = nullptr, *d_rbar = nullptr;
   bool adjoint_mode = false;    // GMRES applies A^T instead of A
   float *d_anal32 = nullptr, *d_synthS32 = nullptr, *d_synthK32 = nullptr;
+  // tensor-core transforms (mixed path): matrices split into three BF16 terms
+  // in the layout of k_sht_tc; analysis, synthesis x multS, synthesis x multK
+  struct TcMat {
+    uint16_t* d = nullptr;
+    int R = 0, C = 0, Kpad = 0;
+  } tcA, tcS, tcK;
+  int* d_tcflag = nullptr;       // set by a tensor-core transform that timed out
 
   // geometry
   int N = 0, NP = 0, capN = 0;
@@ -146,6 +153,11 @@ struct sps_ctx {
   double *d_bbpart = nullptr;    // BBPGD statistic partials (5 x blocks)
   // identity mobility: contact forces (N x 3), FT / U_nc / U_c (N x 6)
   double *d_F3 = nullptr, *d_iFT = nullptr;
+  double *d_adj6a = nullptr, *d_adj6b = nullptr, *d_adjc = nullptr;  // collision adjoint scratch
+  size_t cap_adj6 = 0, cap_adjc = 0;
+  int *d_order = nullptr;        // spheres by block-local incident-contact count
+  size_t cap_order = 0;
+  bool order_valid = false;
   size_t cap_ident = 0;
 };
 
@@ -258,6 +270,11 @@ int sps_launch_extract(sps_ctx* ctx, const double* mom, double* UO);
 
 // layer operators (sps_vsh.cu, sps_nbody.cu)
 int sps_launch_analysis(sps_ctx* ctx, const double* sig, bool fp32);
+// tensor-core transforms (sps_sht_tc.cu)
+int sps_sht_tc_upload(sps_ctx* ctx, sps_ctx::TcMat& out, const std::vector<double>& M, int R, int C);
+int sps_launch_sht_tc(sps_ctx* ctx, const sps_ctx::TcMat& m, int mode, const double* in, double* out,
+                      int scale_by_radius, const double* sig, int half);
+int sps_sht_tc_status(sps_ctx* ctx);
 int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);
 int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32);
 int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32);

@@ -14,6 +14,7 @@
 //    step lengths; U = U_nc + M D gamma; pos += U dt.
 //  All reductions are deterministic (fixed block partition and order).
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -285,16 +286,23 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
     SPS_LAUNCHED(ctx);
     double rr = 0.0;
     SPS_TRY(sps_dot(ctx, Q, Q, n, &rr));
-    if (!std::isfinite(rr)) return sps_fail(ctx, SPS_ERR_NONFINITE, "GMRES: non-finite initial residual");
-    beta = std::sqrt(rr);
-    if (beta / nb < tol) {
-      *relres = beta / nb;
-      return SPS_OK;
+    if (std::isfinite(rr)) {
+      beta = std::sqrt(rr);
+      if (beta / nb < tol) {
+        *relres = beta / nb;
+        return SPS_OK;
+      }
+      { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+      k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / beta, Q, 0.0, nullptr, Q); }
+      SPS_LAUNCHED(ctx);
+    } else {
+      // the guess is unusable (not finite): start from x0 = 0 instead
+      warm = false;
+      beta = nb;
+      SPS_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
     }
-    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-    k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / beta, Q, 0.0, nullptr, Q); }
-    SPS_LAUNCHED(ctx);
-  } else {
+  }
+  if (!warm) {
     { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
     k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / beta, b, 0.0, nullptr, Q); }
     SPS_LAUNCHED(ctx);
@@ -343,6 +351,10 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
     }
     const double a = Hc(k - 1, k - 1), bq = Hc(k, k - 1);
     const double den = std::hypot(a, bq);
+    if (!(den > 0.0)) {   // A q_{k-1} = 0 exactly: keep the first k-1 columns
+      --k;
+      break;
+    }
     cs[k - 1] = a / den;
     sn[k - 1] = bq / den;
     Hc(k - 1, k - 1) = den;
@@ -358,6 +370,8 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
     double sacc = g[i];
     for (int j = i + 1; j < k; ++j) sacc -= Hc(i, j) * y[j];
     y[i] = sacc / Hc(i, i);
+    if (!std::isfinite(y[i]))
+      return sps_fail(ctx, SPS_ERR_NONFINITE, "GMRES: non-finite least-squares solution");
   }
   std::memcpy(ctx->h_pinned, y.data(), sizeof(double) * k);
   SPS_CUDA(ctx, cudaMemcpyAsync(d_h1, ctx->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice,
@@ -445,7 +459,10 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
         sKT[(size_t)r * 3 * P + c] = sK[(size_t)c * NR + r];
       }
     if ((rc = upload(ctx, &ctx->d_analT, aT)) || (rc = upload(ctx, &ctx->d_synthST, sST)) ||
-        (rc = upload(ctx, &ctx->d_synthKT, sKT)) || (rc = sps_build_field_maps(ctx))) {
+        (rc = upload(ctx, &ctx->d_synthKT, sKT)) || (rc = sps_build_field_maps(ctx)) ||
+        (rc = sps_sht_tc_upload(ctx, ctx->tcA, T.anal, NR, 3 * P)) ||
+        (rc = sps_sht_tc_upload(ctx, ctx->tcS, sS, 3 * P, NR)) ||
+        (rc = sps_sht_tc_upload(ctx, ctx->tcK, sK, 3 * P, NR))) {
       sps_destroy(ctx);
       return rc;
     }
@@ -485,7 +502,9 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_sigtot, ctx->d_ubar, ctx->d_sbar, ctx->d_lam, ctx->d_rbar,
                   ctx->d_ccount2, ctx->d_inc_cnt, ctx->d_cl_key, ctx->d_cl_id, ctx->d_cl_key2,
                   ctx->d_cl_id2, ctx->d_cl_range, ctx->d_cl_f, ctx->d_cl_d, ctx->d_cl_part,
-                  ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc};
+                  ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc, ctx->tcA.d,
+                  ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
+                  ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -604,6 +623,14 @@ extern "C" int sps_nodes(sps_ctx* ctx, double* X, double* normals, double* weigh
   return SPS_OK;
 }
 
+extern "C" int sps_geometry_counts(const sps_ctx* ctx, int* n_near_pairs, int* n_close_entries) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!ctx->have_geom) return SPS_ERR_NO_GEOMETRY;
+  if (n_near_pairs) *n_near_pairs = ctx->n_near;
+  if (n_close_entries) *n_close_entries = ctx->n_close_src;
+  return SPS_OK;
+}
+
 extern "C" int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double* out) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
   if (!ctx->have_geom) return sps_fail(ctx, SPS_ERR_NO_GEOMETRY, "no geometry");
@@ -611,7 +638,7 @@ extern "C" int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double
     return sps_fail(ctx, SPS_ERR_INVALID_ARG, "layer_apply: bad argument");
   SPS_TRY(sps_layer(ctx, op, sigma, out, ctx->prm.precision == SPS_MIXED));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return SPS_OK;
+  return sps_sht_tc_status(ctx);
 }
 
 // ---------------------------------------------------------------------------
@@ -671,6 +698,7 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
   SPS_TRY(sps_layer(ctx, SPS_OP_S, ctx->d_tmp3, ctx->d_u, mixed && !refine));
   SPS_TRY(sps_launch_moments(ctx, ctx->d_u, ctx->d_mom));
   SPS_TRY(sps_launch_extract(ctx, ctx->d_mom, UO));
+  if (mixed) SPS_TRY(sps_sht_tc_status(ctx));
   if (st) {
     st->mobility_solves += 1;
     st->gmres_iters += total_its;
@@ -913,7 +941,8 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
     if (r.worst) worst = r.worst;
     // U_c is the solve of the returned iterate; gamma_0 = 0 needs none
     if (r.iters == 0) SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
-    SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (gamma)
+      SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   SPS_TRY(finish_bb_stats(ctx, nc, r, st));
   // 4. U = U_nc + U_c, pos += U dt
@@ -977,7 +1006,8 @@ static int resolve_identity(sps_ctx* ctx, int n, const double* pos, const double
       return read5(ctx, s5);
     };
     SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r));
-    SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (gamma)
+      SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   SPS_TRY(finish_bb_stats(ctx, nc, r, st));
   // U = F_ext + D gamma (d_F3 holds D of the returned iterate after a step)
@@ -1047,6 +1077,36 @@ extern "C" int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* po
 // ---------------------------------------------------------------------------
 int sps_geom_gradient(sps_ctx* ctx, const double* ubar, const double* lam, const double* sig, double* dx);
 
+// out = M^T ubar (both N x 6) on the current geometry: the force/torque part of
+// the adjoint of the mobility map.  ubar' = E^T ubar at the nodes (weights),
+// s = S^T ubar', lambda = A^{-T} s (GMRES, cold start), rhobar = s -
+// (I/2 + K)^T lambda, out = R^T rhobar.  Leaves ubar', lambda in d_ubar, d_lam.
+static int mobility_T(sps_ctx* ctx, const double* ubar, double* out, sps_stats* st) {
+  const long long n3 = 3LL * ctx->NP;
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_ubar, 0, sizeof(double) * n3, ctx->stream));
+  SPS_TRY(sps_launch_add_L_w(ctx, ubar, ctx->d_ubar, true));
+  SPS_TRY(sps_layer_T(ctx, SPS_OP_S, ctx->d_ubar, ctx->d_sbar));
+  ctx->adjoint_mode = true;
+  int its = 0;
+  double res = 0.0;
+  int grc = gmres(ctx, ctx->d_sbar, ctx->d_lam, false, ctx->prm.gmres_tol, ctx->prm.gmres_max, false, &its, &res);
+  ctx->adjoint_mode = false;
+  if (grc != SPS_OK && grc != SPS_ERR_NOT_CONVERGED) return grc;
+  if (st) {
+    st->mobility_solves += 1;
+    st->gmres_iters += its;
+    st->gmres_iters_max = std::max(st->gmres_iters_max, its);
+    st->gmres_res_max = std::max(st->gmres_res_max, res);
+  }
+  SPS_TRY(sps_layer_T(ctx, SPS_OP_K, ctx->d_lam, ctx->d_rbar));
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_combine3<<<gblocks(n3), 256, 0, ctx->stream>>>(n3, ctx->d_sbar, ctx->d_lam, ctx->d_rbar); }
+  SPS_LAUNCHED(ctx);
+  SPS_TRY(sps_launch_moments_w(ctx, ctx->d_rbar, ctx->d_mom, false));
+  SPS_TRY(sps_launch_extract(ctx, ctx->d_mom, out));
+  return grc;
+}
+
 extern "C" int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
                                     const double* FT, const double* dL_dU, double* UO, double* dL_dFT,
                                     double* dL_dpos, sps_stats* st) {
@@ -1083,33 +1143,168 @@ extern "C" int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, cons
   if (frc != SPS_OK && frc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, frc);
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_sigtot, ctx->d_tmp3, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
-  // ubar = E^T dL/dU (weights at the nodes)
-  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_ubar, 0, sizeof(double) * n3, ctx->stream));
-  SPS_TRY(sps_launch_add_L_w(ctx, dL_dU, ctx->d_ubar, true));
-  // sbar = S^T ubar
-  SPS_TRY(sps_layer_T(ctx, SPS_OP_S, ctx->d_ubar, ctx->d_sbar));
-  // lambda = A^{-T} sbar
-  ctx->adjoint_mode = true;
-  int its = 0;
-  double res = 0.0;
-  int grc = gmres(ctx, ctx->d_sbar, ctx->d_lam, false, ctx->prm.gmres_tol, ctx->prm.gmres_max, false, &its, &res);
-  ctx->adjoint_mode = false;
+  int grc = mobility_T(ctx, dL_dU, dL_dFT, st);
   if (grc != SPS_OK && grc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, grc);
-  if (st) {
-    st->gmres_iters += its;
-    st->gmres_iters_max = std::max(st->gmres_iters_max, its);
-    st->gmres_res_max = std::max(st->gmres_res_max, res);
-  }
-  // rhobar = sbar - (I/2 + K)^T lambda
-  SPS_TRY(sps_layer_T(ctx, SPS_OP_K, ctx->d_lam, ctx->d_rbar));
-  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_combine3<<<gblocks(n3), 256, 0, ctx->stream>>>(n3, ctx->d_sbar, ctx->d_lam, ctx->d_rbar); }
-  SPS_LAUNCHED(ctx);
-  // dL/dF = R^T rhobar: unweighted moments
-  SPS_TRY(sps_launch_moments_w(ctx, ctx->d_rbar, ctx->d_mom, false));
-  SPS_TRY(sps_launch_extract(ctx, ctx->d_mom, dL_dFT));
   if (dL_dpos) SPS_TRY(sps_geom_gradient(ctx, ctx->d_ubar, ctx->d_lam, ctx->d_sigtot, dL_dpos));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   const int out_rc = (frc != SPS_OK) ? frc : grc;
   return stats_end(ctx, st, l0, out_rc != SPS_OK ? sps_fail(ctx, out_rc, "adjoint: a solve did not converge") : SPS_OK);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the collision-resolved step in the external forces
+// ---------------------------------------------------------------------------
+// Applies M^T to an N x 6 force/torque array (identity: a copy).
+static int apply_MT(sps_ctx* ctx, int n, const double* in, double* out, sps_stats* st) {
+  if (ctx->prm.mobility == SPS_MOB_IDENTITY) {
+    SPS_CUDA(ctx, cudaMemcpyAsync(out, in, sizeof(double) * 6 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return SPS_OK;
+  }
+  return mobility_T(ctx, in, out, st);
+}
+
+extern "C" int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
+                                     const double* FT_ext, double dt, const double* dL_dU, double* UO,
+                                     double* dL_dFT, sps_stats* st) {
+  if (!ctx || n < 1 || !pos || !radii || !FT_ext || !dL_dU || !UO || !dL_dFT)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "collision_adjoint: bad argument");
+  long long l0;
+  stats_begin(ctx, st, &l0);
+  // forward step (positions are not advanced)
+  int rc = resolve_any(ctx, n, pos, radii, FT_ext, dt, nullptr, INT32_MAX, UO, nullptr, st);
+  if (rc != SPS_OK) return stats_end(ctx, st, l0, rc);
+  const int nc = ctx->n_c;
+  const size_t n6 = 6 * (size_t)n;
+  size_t c = 0;
+  if (ctx->cap_adj6 < n6) {
+    cudaFree(ctx->d_adj6a);
+    cudaFree(ctx->d_adj6b);
+    ctx->d_adj6a = ctx->d_adj6b = nullptr;
+    SPS_TRY(sps_grow(ctx, &ctx->d_adj6a, c, n6));
+    c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_adj6b, c, n6));
+    ctx->cap_adj6 = n6;
+  }
+  SPS_TRY(sps_grow(ctx, &ctx->d_adjc, ctx->cap_adjc, (size_t)std::max(nc, 1)));
+  // v = M^T ubar: the gradient without contacts
+  rc = apply_MT(ctx, n, dL_dU, dL_dFT, st);
+  if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, rc);
+  int worst = rc;
+  std::vector<double> gam(nc);
+  if (nc > 0) {
+    SPS_CUDA(ctx, cudaMemcpyAsync(gam.data(), ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  std::vector<char> act(nc);
+  int na = 0;
+  for (int l = 0; l < nc; ++l) na += (act[l] = gam[l] > 0.0);
+  if (na > 0) {
+    // matvec on contact vectors: y = P D^T M^T D P x + (I - P) x, P = diag(active)
+    std::vector<double> xm(nc), y(nc);
+    auto matvec = [&](const std::vector<double>& x, std::vector<double>& out) -> int {
+      for (int l = 0; l < nc; ++l) xm[l] = act[l] ? x[l] : 0.0;
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_adjc, xm.data(), sizeof(double) * nc, cudaMemcpyHostToDevice,
+                                    ctx->stream));
+      SPS_TRY(sps_launch_D(ctx, ctx->d_adjc, ctx->d_adj6a));
+      const int r2 = apply_MT(ctx, n, ctx->d_adj6a, ctx->d_adj6b, st);
+      if (r2 != SPS_OK && r2 != SPS_ERR_NOT_CONVERGED) return r2;
+      if (r2) worst = r2;
+      SPS_TRY(sps_launch_DT(ctx, ctx->d_adj6b, ctx->d_adjc));
+      SPS_CUDA(ctx, cudaMemcpyAsync(out.data(), ctx->d_adjc, sizeof(double) * nc, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+      SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      for (int l = 0; l < nc; ++l) out[l] = act[l] ? out[l] : x[l];
+      return SPS_OK;
+    };
+    // right-hand side P D^T v
+    std::vector<double> b(nc);
+    SPS_TRY(sps_launch_DT(ctx, dL_dFT, ctx->d_adjc));
+    SPS_CUDA(ctx, cudaMemcpyAsync(b.data(), ctx->d_adjc, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int l = 0; l < nc; ++l) b[l] = act[l] ? b[l] : 0.0;
+    // GMRES (modified Gram-Schmidt, x0 = 0) on the host: n_c-vectors are small
+    const int kmax = ctx->prm.gmres_max;
+    const double tol = ctx->prm.gmres_tol;
+    double nb = 0.0;
+    for (double v : b) nb += v * v;
+    nb = std::sqrt(nb);
+    std::vector<double> lam(nc, 0.0);
+    if (nb > 0.0) {
+      std::vector<std::vector<double>> V(1, b);
+      for (double& v : V[0]) v /= nb;
+      std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), g(kmax + 1, 0.0);
+      auto Hc = [&](int r, int col) -> double& { return H[(size_t)col * (kmax + 1) + r]; };
+      g[0] = nb;
+      int k = 0;
+      double res = 1.0;
+      for (k = 1; k <= kmax; ++k) {
+        std::vector<double> w(nc);
+        rc = matvec(V[k - 1], w);
+        if (rc != SPS_OK) return stats_end(ctx, st, l0, rc);
+        for (int j = 0; j < k; ++j) {
+          double h = 0.0;
+          for (int l = 0; l < nc; ++l) h += V[j][l] * w[l];
+          Hc(j, k - 1) = h;
+          for (int l = 0; l < nc; ++l) w[l] -= h * V[j][l];
+        }
+        double hn = 0.0;
+        for (double v : w) hn += v * v;
+        hn = std::sqrt(hn);
+        Hc(k, k - 1) = hn;
+        for (int j = 0; j < k - 1; ++j) {
+          const double a = Hc(j, k - 1), bq = Hc(j + 1, k - 1);
+          Hc(j, k - 1) = cs[j] * a + sn[j] * bq;
+          Hc(j + 1, k - 1) = -sn[j] * a + cs[j] * bq;
+        }
+        const double a = Hc(k - 1, k - 1), bq = Hc(k, k - 1);
+        const double den = std::hypot(a, bq);
+        if (!(den > 0.0)) {
+          --k;
+          break;
+        }
+        cs[k - 1] = a / den;
+        sn[k - 1] = bq / den;
+        Hc(k - 1, k - 1) = den;
+        Hc(k, k - 1) = 0.0;
+        g[k] = -sn[k - 1] * g[k - 1];
+        g[k - 1] = cs[k - 1] * g[k - 1];
+        res = std::fabs(g[k]) / nb;
+        if (res < tol || hn == 0.0) break;
+        for (double& v : w) v /= hn;
+        V.push_back(std::move(w));
+      }
+      if (k > kmax) k = kmax;
+      std::vector<double> yk(k);
+      for (int i = k - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int j = i + 1; j < k; ++j) acc -= Hc(i, j) * yk[j];
+        yk[i] = acc / Hc(i, i);
+        if (!std::isfinite(yk[i]))
+          return stats_end(ctx, st, l0, sps_fail(ctx, SPS_ERR_NONFINITE, "collision adjoint: singular system"));
+      }
+      for (int j = 0; j < k; ++j)
+        for (int l = 0; l < nc; ++l) lam[l] += yk[j] * V[j][l];
+      if (st) {
+        st->gmres_res_max = std::max(st->gmres_res_max, res);
+        st->ir_sweeps = k;    // outer (active-set) iterations
+      }
+      if (!(res < tol)) worst = SPS_ERR_NOT_CONVERGED;
+    }
+    // dL/dF = v - M^T D P lam
+    for (int l = 0; l < nc; ++l) xm[l] = act[l] ? lam[l] : 0.0;
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_adjc, xm.data(), sizeof(double) * nc, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    SPS_TRY(sps_launch_D(ctx, ctx->d_adjc, ctx->d_adj6a));
+    const int r3 = apply_MT(ctx, n, ctx->d_adj6a, ctx->d_adj6b, st);
+    if (r3 != SPS_OK && r3 != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, r3);
+    if (r3) worst = r3;
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_axpby<<<gblocks((long long)n6), 256, 0, ctx->stream>>>((long long)n6, 1.0, dL_dFT, -1.0, ctx->d_adj6b,
+                                                             dL_dFT); }
+    SPS_LAUNCHED(ctx);
+  }
+  if (st) st->n_active = na;
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (worst != SPS_OK) return stats_end(ctx, st, l0, sps_fail(ctx, worst, "collision adjoint: a solve did not converge"));
+  return stats_end(ctx, st, l0, SPS_OK);
 }

@@ -35,6 +35,12 @@
 // 2 Phi_beta - Phi_P); the velocity needs 10.
 #include "sps_internal.cuh"
 
+// mixed path: VSH analysis / self synthesis on the tensor cores (BF16 split
+// into three terms, FP32 accumulation) instead of FP32 CUDA-core products
+#ifndef SPS_SHT_TC
+#define SPS_SHT_TC 0
+#endif
+
 namespace {
 
 // Batched small products out(s, r) = sum_c M[r][c] in(s, c), one sphere s per
@@ -529,6 +535,9 @@ int sps_launch_analysis(sps_ctx* ctx, const double* sig, bool fp32) {
   SpsPhase timer(ctx, SPS_PH_SELF);
   const int N = ctx->N, P = ctx->T.P, NR = ctx->T.NR;
   dim3 grid((N + kTB - 1) / kTB, (NR + kTB - 1) / kTB);
+#if SPS_SHT_TC
+  if (fp32) return sps_launch_sht_tc(ctx, ctx->tcA, 0, sig, ctx->d_coef, 0, nullptr, 0);
+#endif
   if (fp32)
     k_batched<float, MODE_ANALYSIS><<<grid, 256, 0, ctx->stream>>>(N, P, NR, 3 * P, ctx->d_anal32, sig,
                                                                     ctx->d_coef, nullptr, 0, nullptr, 0);
@@ -545,6 +554,9 @@ int sps_launch_self(sps_ctx* ctx, int op, const double* sig, double* out, bool f
   const bool S = (op == SPS_OP_S);
   dim3 grid((N + kTB - 1) / kTB, (3 * P + kTB - 1) / kTB);
   const int half = (op == SPS_OP_A) ? 1 : 0;
+#if SPS_SHT_TC
+  if (fp32) return sps_launch_sht_tc(ctx, S ? ctx->tcS : ctx->tcK, 1, ctx->d_coef, out, S ? 1 : 0, sig, half);
+#endif
   if (fp32)
     k_batched<float, MODE_SYNTH><<<grid, 256, 0, ctx->stream>>>(
         N, P, 3 * P, NR, S ? ctx->d_synthS32 : ctx->d_synthK32, ctx->d_coef, out, ctx->d_rad, S ? 1 : 0,

@@ -239,3 +239,57 @@ def test_cfg4_gradient_finite_differences(sps):
         errs.append(abs(fd - ref) / scale)
     print("cfg4 FD max rel err", max(errs))
     assert max(errs) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# the collision-resolved step, differentiated in F_ext on the active set
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_collision_adjoint_identity(sps, seed):
+    """Identity mobility: GPU dL/dF against the oracle's active-set formula
+    with M = I (on the oracle's own step) and central differences of the
+    oracle step (pinned in tests/test_oracle_adjoint_lcp.py)."""
+    from oracle import adjoint as oadj
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.contact_chain(seed)
+    L0, out = oadj.step_loss(w.centers, w.radii, w.FT, w.dt, 0, identity=True)
+    N = w.N
+    D = oadj.D_matrix(N, out["ij"], out["normals"])
+    ref, A = oadj.collision_grad_F(np.eye(6 * N), D, out["gamma"], 2.0 * out["U"])
+    ctx = sps.Context(p=2, delta=0.1, mobility=sps.SPS_MOB_IDENTITY, bbpgd_tol=1e-12, gmres_tol=1e-12)
+    U, gF = ctx.collision_adjoint(dev(w.centers), dev(w.radii), dev(w.FT), w.dt,
+                                  dev(2.0 * out["U"]))
+    st = ctx.last_stats
+    assert st["n_active"] == int(A.sum())
+    assert np.abs(U.cpu().numpy() - out["U"]).max() < 1e-10 * np.abs(out["U"]).max()
+    assert np.abs(gF.cpu().numpy() - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+@pytest.fixture(scope="module")
+def collision_golden():
+    d = np.load(os.path.join(GOLD, "collision_grad_p4.npz"))
+    return d
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-4), (1, 1e-4)])
+def test_collision_adjoint_bie(sps, collision_golden, precision, tol):
+    """Five spheres at p = 4 with three active contacts: GPU dL/dF (L = sum
+    |U|^2, dL/dU = 2U of the GPU step) against the oracle's active-set formula
+    with its assembled mobility and against central differences of the full
+    oracle step, 1e-4 relative (the adjoint bar)."""
+    from oracle import adjoint as oadj
+    d = collision_golden
+    N = len(d["radii"])
+    D = oadj.D_matrix(N, d["ij"], d["normals"])
+    ref, A = oadj.collision_grad_F(d["M"], D, d["gamma"], 2.0 * d["U"])
+    ctx = sps.Context(p=int(d["p"]), delta=0.1, a_c_scale=float(d["a_c_scale"]),
+                      gmres_tol=1e-13 if precision == 0 else 1e-9, gmres_max=300,
+                      bbpgd_tol=1e-12 if precision == 0 else 1e-6, precision=precision, warm_start=0)
+    pos, rad, FT = dev(d["centers"]), dev(d["radii"]), dev(d["FT"])
+    U, _ = ctx.collision_adjoint(pos, rad, FT, float(d["dt"]), dev(2.0 * d["U"]))
+    U, gF = ctx.collision_adjoint(pos, rad, FT, float(d["dt"]), 2.0 * U)
+    assert ctx.last_stats["n_active"] == int(A.sum())
+    g = gF.cpu().numpy()
+    assert np.abs(g - ref).max() < tol * np.abs(ref).max()
+    for (i, k), fd in zip(d["coords"], d["fd"]):
+        assert abs(g[i, k] - fd) < tol * np.abs(ref).max(), (i, k)

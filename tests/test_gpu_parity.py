@@ -14,6 +14,7 @@ import torch
 
 from oracle import lcp, mobility, sph
 from oracle.layer import Suspension
+from paper_1909_06623_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -135,6 +136,36 @@ def test_layer_operators_cfg2_sampled(sps, precision, tol):
     for op, key in ((sps.SPS_OP_S, "S"), (sps.SPS_OP_K, "K"), (sps.SPS_OP_A, "A")):
         out = ctx.layer_apply(op, s).cpu().numpy().T[sl]
         assert relerr(out, d[key]) < tol, key
+
+
+@pytest.mark.parametrize("p", [3, 6, 8])
+def test_tensor_core_transforms(sps, p):
+    """The mixed path's VSH analysis and self synthesis run on the tensor
+    cores (three-term BF16 split, FP32 accumulation).  One sphere isolates the
+    self term (no far or near pairs); 200 spheres span two 128-sphere tiles
+    with a ragged tail; p = 8 takes two N tiles (270 and 486 rows).  Both are
+    compared with the oracle: the self term alone within 5e-6 (FP32-class: a
+    two-term split would leave 2^-16 = 1.5e-5), the full operator within the
+    mixed-path tolerance."""
+    rng = np.random.default_rng(40 + p)
+    P = (p + 1) * (2 * p + 2)
+    cases = [(np.zeros((1, 3)), np.array([0.8]), 5e-6)]
+    w = workloads.tiny(40 + p, 200, p, phi=0.05)
+    cases.append((w.centers, w.radii, TOLMX))
+    for C, R, tol in cases:
+        ctx = sps.Context(p=p, precision=1)
+        ctx.set_geometry(dev(C), dev(R))
+        sig = rng.standard_normal((len(R) * P, 3))
+        if len(R) > 1:
+            tg = [0, 77, 128, 199]
+            sus = Suspension(C, R, p)
+            sl = np.concatenate([np.arange(i * P, (i + 1) * P) for i in tg])
+        else:
+            tg, sus, sl = None, Suspension(C, R, p), slice(None)
+        for op, key in ((sps.SPS_OP_S, "S"), (sps.SPS_OP_K, "K")):
+            out = ctx.layer_apply(op, planes(sig)).cpu().numpy().T[sl]
+            ref = np.asarray(sus.apply(key, sig, targets=tg)).reshape(-1, 3)[sl]
+            assert relerr(out, ref) < tol, (p, len(R), key)
 
 
 # ---------------------------------------------------------------------------
