@@ -5,18 +5,20 @@
 //
 //   Out[s][n] = sum_k X_s[k] B[n][k]
 //
-// One CTA of 128 threads takes 128 spheres: the spheres are the MMA's M = 128
-// rows, the matrix rows its N (tiles of at most 256), the contraction K runs
-// in chunks of 32.  Both operands are split into three BF16 terms,
+// One CTA of 128 threads takes 128 spheres and 64 matrix rows: the spheres are
+// the MMA's M = 128 rows, the matrix rows its N = 64, the contraction K runs
+// in chunks of 32, staged into one of two shared-memory buffers while the
+// tensor core works on the other.  Both operands are split into three BF16 terms,
 // x = h + m + l (h = bf16(x), m = bf16(x - h), l = bf16(x - h - m)), and the
 // six products hh, hm, mh, hl, lh, mm of a chunk accumulate in FP32 in tensor
 // memory (the dropped products are 2^-24 relative), hh in one accumulator and
-// the five smaller ones in another; the accumulators and the chunk sums are
-// then added in FP64.  The tensor core's FP32 accumulation rounds less carefully
+// the five smaller ones in another; the chunk results are summed per thread
+// with Kahan compensation.  The tensor core's FP32 accumulation rounds less carefully
 // than an FMA chain: one accumulator over the whole contraction lost about a
 // decimal digit against the FP32 CUDA-core product; with 32-term chunks and
 // the large and small products apart the transforms are as accurate as the
-// FP32 product, and the mixed mobility solve more accurate (measured).
+// FP32 product, and the mixed mobility solve more accurate (measured; 64-term
+// chunks were 5% faster and gave back most of that gain).
 //
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // 8 x 16-byte core matrices, adjacent along K 128 bytes apart (leading byte
@@ -37,16 +39,22 @@
 namespace {
 
 constexpr int kM = 128;                    // spheres per CTA (MMA M)
-constexpr int kKC = 32;                    // K chunk (one FP32 accumulation in tensor memory)
-constexpr int kNT = 256;                   // widest N tile
+#ifndef SPS_TC_KC
+#define SPS_TC_KC 32
+#endif
+constexpr int kKC = SPS_TC_KC;             // K chunk (one FP32 accumulation in tensor memory)
+constexpr int kNT = 64;                    // N tile: one CTA per (128 spheres, 64 matrix rows)
 constexpr int kSBO = (kKC / 8) * 128;      // bytes between 8-row groups
 constexpr int kABytes = kM * kKC * 2;      // one split of the A chunk
-constexpr int kBBytes = kNT * kKC * 2;     // one split of the B chunk (widest tile)
-constexpr int kSmem = 3 * kABytes + 3 * kBBytes;
+constexpr int kBBytes = kNT * kKC * 2;     // one split of the B chunk
+constexpr int kStage = 3 * kABytes + 3 * kBBytes;   // one buffer: A and B, three splits each
+constexpr int kAccBytes = 2 * kNT * kM * 4;   // per-thread Kahan sums (sum, compensation)
+constexpr int kSmem = 2 * kStage + kAccBytes;   // double-buffered operands + sums
 constexpr unsigned kSpin = 1u << 22;       // try_wait rounds before giving up
-// the hh products accumulate in columns [0, 256), the five smaller products in
-// [256, 512): the large terms never share an FP32 accumulator with the small ones
-constexpr int kTmemCols = 2 * kNT;
+// tensor memory: two accumulator sets (chunks alternate), each with the hh
+// products in one 64-column block and the five smaller products in the next,
+// so the large terms never share an FP32 accumulator with the small ones
+constexpr int kTmemCols = 4 * kNT;
 
 enum { MODE_ANALYSIS = 0, MODE_SYNTH = 1 };
 
@@ -114,23 +122,69 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16&
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
+// stage K chunk kc: A (rows = the CTA's spheres, split on the fly) and the
+// pre-split B chunk of this N tile, into one smem buffer
 template <int MODE>
-__global__ void __launch_bounds__(128, 1) k_sht_tc(int Ns, int P, int Nout, int K, int Kpad,
-                                                  const uint16_t* __restrict__ Bt,
-                                                  const double* __restrict__ in,
-                                                  double* __restrict__ out,
-                                                  const double* __restrict__ rad, int scale_by_radius,
-                                                  const double* __restrict__ sig, int half,
-                                                  int* __restrict__ flag) {
+__device__ __forceinline__ void stage_chunk(unsigned char* buf, int kc, int s0, int Ns, int P, int K,
+                                            long long NP, const double* __restrict__ in,
+                                            const uint16_t* __restrict__ Bchunk, int nrows) {
+  unsigned char* sA = buf;
+  unsigned char* sB = buf + 3 * kABytes;
+  for (int it = threadIdx.x; it < kM * (kKC / 8); it += 128) {
+    const int r = it / (kKC / 8), k8 = (it % (kKC / 8)) * 8;
+    const int s = s0 + r;
+    __align__(16) __nv_bfloat16 vh[8], vm[8], vl[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = kc * kKC + k8 + u;
+      float x = 0.f;
+      if (s < Ns && k < K) {
+        if (MODE == MODE_ANALYSIS) {
+          const int comp = k / P, kk = k - comp * P;
+          x = (float)in[comp * NP + (long long)s * P + kk];
+        } else {
+          x = (float)in[(long long)s * K + k];
+        }
+      }
+      split3(x, vh[u], vm[u], vl[u]);
+    }
+    const int off = tc_off(r, k8);
+    *reinterpret_cast<uint4*>(sA + off) = *reinterpret_cast<const uint4*>(vh);
+    *reinterpret_cast<uint4*>(sA + kABytes + off) = *reinterpret_cast<const uint4*>(vm);
+    *reinterpret_cast<uint4*>(sA + 2 * kABytes + off) = *reinterpret_cast<const uint4*>(vl);
+  }
+  const int bytes = nrows * kKC * 2;
+  const uint4* src = reinterpret_cast<const uint4*>(Bchunk);
+  for (int v = threadIdx.x; v < 3 * bytes / 16; v += 128) {
+    const int sp = v / (bytes / 16), w = v % (bytes / 16);
+    *reinterpret_cast<uint4*>(sB + sp * kBBytes + 16 * w) = src[v];
+  }
+  // generic-proxy smem writes -> visible to the tensor core (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// grid (sphere blocks of 128, N tiles of 64); 128 threads, thread t owns
+// sphere s0 + t (tensor-memory lane t) and the tile's columns
+template <int MODE>
+__global__ void __launch_bounds__(128) k_sht_tc(int Ns, int P, int Nout, int K, int Kpad,
+                                               const uint16_t* __restrict__ Bt,
+                                               const double* __restrict__ in,
+                                               double* __restrict__ out,
+                                               const double* __restrict__ rad, int scale_by_radius,
+                                               const double* __restrict__ sig, int half,
+                                               int* __restrict__ flag) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_slot;
-  unsigned char* sA = smem;                  // 3 splits x kABytes
-  unsigned char* sB = smem + 3 * kABytes;    // 3 splits x kBBytes
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int s0 = blockIdx.x * kM;
+  const int t = blockIdx.y;
+  const int nrows = tile_rows(Nout, t), n0 = t * kNT;
+  const int nkc = Kpad / kKC;
   const long long NP = (long long)Ns * P;
-  const uint32_t bar_a = smem_u32(&bar);
+  // tiles before t are full (kNT rows); chunk kc of tile t at tile base + kc * 3 * nrows * kKC
+  const uint16_t* Btile = Bt + (size_t)t * 3 * kNT * Kpad;
+  const uint32_t bar0 = smem_u32(&bar[0]), bar1 = smem_u32(&bar[1]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -138,127 +192,104 @@ __global__ void __launch_bounds__(128, 1) k_sht_tc(int Ns, int P, int Nout, int 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  stage_chunk<MODE>(smem, 0, s0, Ns, P, K, NP, in, Btile, nrows);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  uint32_t parity = 0;
-  bool ok = true;
-
-  const int ntiles = (Nout + kNT - 1) / kNT;
-  const int nkc = Kpad / kKC;
-  size_t tbase = 0;                           // element offset of tile t in Bt
-  for (int t = 0; t < ntiles && ok; ++t) {
-    const int nrows = tile_rows(Nout, t);
-    const int n0 = t * kNT;
-    const uint32_t id = idesc(nrows);
-    for (int kc = 0; kc < nkc && ok; ++kc) {
-      // ---- stage A: rows = spheres, 8 consecutive k per item (one core-matrix row)
-      for (int it = tid; it < kM * (kKC / 8); it += 128) {
-        const int r = it / (kKC / 8), k8 = (it % (kKC / 8)) * 8;
-        const int s = s0 + r;
-        __align__(16) __nv_bfloat16 vh[8], vm[8], vl[8];
+  const uint32_t id = idesc(nrows);
+  // (A split, B split) of the six products kept; product 0 (hh) in its own accumulator
+  auto issue = [&](int kc) {
+    const int b = kc & 1;
+    const uint32_t a0 = smem_u32(smem + b * kStage), b0 = a0 + 3 * kABytes;
+    const uint32_t acc = tmem + (uint32_t)(b * 2 * kNT);
+    const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int k = kc * kKC + k8 + u;
-          float x = 0.f;
-          if (s < Ns && k < K) {
-            if (MODE == MODE_ANALYSIS) {
-              const int comp = k / P, kk = k - comp * P;
-              x = (float)in[comp * NP + (long long)s * P + kk];
-            } else {
-              x = (float)in[(long long)s * K + k];
-            }
-          }
-          split3(x, vh[u], vm[u], vl[u]);
-        }
-        const int off = tc_off(r, k8);
-        *reinterpret_cast<uint4*>(sA + off) = *reinterpret_cast<const uint4*>(vh);
-        *reinterpret_cast<uint4*>(sA + kABytes + off) = *reinterpret_cast<const uint4*>(vm);
-        *reinterpret_cast<uint4*>(sA + 2 * kABytes + off) = *reinterpret_cast<const uint4*>(vl);
+    for (int ks = 0; ks < kKC / 16; ++ks)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const uint64_t da = sdesc(a0 + pa[q] * kABytes + ks * 256);
+        const uint64_t db = sdesc(b0 + pb[q] * kBBytes + ks * 256);
+        if (q == 0)
+          mma_bf16(acc, da, db, id, ks > 0 ? 1 : 0);
+        else
+          mma_bf16(acc + kNT, da, db, id, (ks > 0 || q > 1) ? 1 : 0);
       }
-      // ---- stage B: the pre-split chunk (3 x nrows x 64 BF16, already laid out)
-      {
-        const int bytes = nrows * kKC * 2;
-        const uint4* src = reinterpret_cast<const uint4*>(Bt + tbase + (size_t)kc * 3 * nrows * kKC);
-        for (int v = tid; v < 3 * bytes / 16; v += 128) {
-          const int sp = v / (bytes / 16), w = v % (bytes / 16);
-          *reinterpret_cast<uint4*>(sB + sp * kBBytes + 16 * w) = src[v];
-        }
-      }
-      // generic-proxy smem writes -> visible to the tensor core (async proxy)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b ? bar1 : bar0)
+                 : "memory");
+  };
+  if (tid == 0) issue(0);
+
+  // compensated FP32 sums of the chunk results, one per column of the tile,
+  // in shared memory ([column][thread]: consecutive threads, consecutive words)
+  float* sum = reinterpret_cast<float*>(smem + 2 * kStage);
+  float* cmp = sum + kNT * kM;
+  for (int c = 0; c < kNT; ++c) sum[c * kM + tid] = cmp[c * kM + tid] = 0.f;
+  uint32_t par[2] = {0u, 0u};
+  bool ok = true;
+  for (int kc = 0; kc < nkc; ++kc) {
+    if (kc + 1 < nkc) {
+      // buffer (kc+1)&1 was read by chunk kc-1, whose completion was awaited
+      stage_chunk<MODE>(smem + ((kc + 1) & 1) * kStage, kc + 1, s0, Ns, P, K, NP, in,
+                        Btile + (size_t)(kc + 1) * 3 * nrows * kKC, nrows);
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) {
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        // (A split, B split) of the six products kept
-        const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+      if (tid == 0) issue(kc + 1);
+    }
+    const int b = kc & 1;
+    ok = __syncthreads_and(bar_wait(b ? bar1 : bar0, par[b])) != 0;   // CTA-uniform outcome
+    par[b] ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) break;
+    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 2 * kNT);
+    for (int c0 = 0; c0 < nrows; c0 += 16) {
+      uint32_t v[16], w[16];
+      tmem_ld16(ta + c0, v);
+      tmem_ld16(ta + kNT + c0, w);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int ks = 0; ks < kKC / 16; ++ks)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const uint64_t da = sdesc(a0 + pa[q] * kABytes + ks * 256);
-            const uint64_t db = sdesc(b0 + pb[q] * kBBytes + ks * 256);
-            if (q == 0)
-              mma_bf16(tmem, da, db, id, ks > 0 ? 1 : 0);
-            else
-              mma_bf16(tmem + kNT, da, db, id, (ks > 0 || q > 1) ? 1 : 0);
-          }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
-                     : "memory");
+      for (int u = 0; u < 16; ++u) {
+        // Kahan: sum += (hh part + small part)
+        const int e = (c0 + u) * kM + tid;
+        const float x = __uint_as_float(v[u]) + __uint_as_float(w[u]);
+        const float sv = sum[e];
+        const float y = x - cmp[e];
+        const float z = sv + y;
+        cmp[e] = (z - sv) - y;
+        sum[e] = z;
       }
-      ok = __syncthreads_and(bar_wait(bar_a, parity)) != 0;   // CTA-uniform outcome
-      parity ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (!ok) break;
-      // ---- the chunk's partial sums (warp w reads tensor-memory lanes 32w..),
-      // added in FP64 to the previous chunks'; scaling on the last chunk
-      const int r = warp * 32 + lane;
-      const int s = s0 + r;
-      const bool first = (kc == 0), last = (kc == nkc - 1);
-      for (int c0 = 0; c0 < nrows; c0 += 16) {
-        uint32_t v[16], w[16];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-        tmem_ld16(ta, v);
-        tmem_ld16(ta + kNT, w);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (s < Ns) {
-          const double sc = scale_by_radius ? rad[s] : 1.0;
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int n = n0 + c0 + u;
-            if (n >= Nout) continue;
-            long long idx;
-            if (MODE == MODE_ANALYSIS) {
-              idx = (long long)s * Nout + n;
-            } else {
-              const int comp = n / P, kk = n - comp * P;
-              idx = comp * NP + (long long)s * P + kk;
-            }
-            double acc = (double)__uint_as_float(v[u]) + (double)__uint_as_float(w[u]);
-            if (!first) acc += out[idx];
-            if (last) {
-              acc *= sc;
-              if (MODE == MODE_SYNTH && half) acc += 0.5 * sig[idx];
-            }
-            out[idx] = acc;
-          }
+    }
+    // the next issue into this accumulator set comes after a barrier preceded
+    // by tcgen05.fence::before_thread_sync, so these reads complete first
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  if (ok) {
+    const int s = s0 + tid;
+    if (s < Ns) {
+      const double sc = scale_by_radius ? rad[s] : 1.0;
+      for (int c = 0; c < kNT; ++c) {
+        const int n = n0 + c;
+        if (c >= nrows || n >= Nout) continue;
+        double val = ((double)sum[c * kM + tid] - (double)cmp[c * kM + tid]) * sc;
+        if (MODE == MODE_ANALYSIS) {
+          out[(long long)s * Nout + n] = val;
+        } else {
+          const int comp = n / P, kk = n - comp * P;
+          const long long idx = comp * NP + (long long)s * P + kk;
+          if (half) val += 0.5 * sig[idx];
+          out[idx] = val;
         }
       }
     }
-    tbase += (size_t)3 * nrows * Kpad;
-    // staging for the next chunk or tile is preceded by a barrier with
-    // tcgen05.fence::before_thread_sync, so these tensor-memory reads complete
-    // before the next MMAs overwrite the accumulator
-  }
-  if (!ok) {
+  } else {
     if (tid == 0) atomicOr(flag, 1);
-    bar_wait(bar_a, parity);   // one more bounded wait for the MMAs in flight
+    bar_wait(bar0, par[0]);   // one more bounded wait for MMAs in flight
+    bar_wait(bar1, par[1]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -337,7 +368,7 @@ int sps_launch_sht_tc(sps_ctx* ctx, const sps_ctx::TcMat& m, int mode, const dou
     SPS_CUDA(ctx, cudaFuncSetAttribute(k_sht_tc<MODE_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     attr = true;
   }
-  const int grid = (N + kM - 1) / kM;
+  const dim3 grid((N + kM - 1) / kM, (m.R + kNT - 1) / kNT);
   if (mode == 0)
     k_sht_tc<MODE_ANALYSIS><<<grid, 128, kSmem, ctx->stream>>>(N, P, m.R, m.C, m.Kpad, m.d, in, out, ctx->d_rad,
                                                                scale_by_radius, sig, half, ctx->d_tcflag);

@@ -863,6 +863,9 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
     return SPS_OK;
   }
   double alpha = s5[4] / gMg;
+  // divergence: an indefinite discrete M (nearly touching spheres at low
+  // order) makes the projected steps grow without bound
+  const double phi_limit = 1e6 * std::max(r.phi, tol);
   for (int j = 1; j <= ctx->prm.bbpgd_max; ++j) {
     rc = step(alpha, j, s5);
     if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
@@ -873,6 +876,10 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
     r.iters = j;
     r.phi = std::sqrt(s5[0]);
     if (r.phi < tol) return SPS_OK;
+    if (!(r.phi < phi_limit)) {
+      r.bb_rc = SPS_ERR_BREAKDOWN;
+      return SPS_OK;
+    }
     const bool ok = (ctx->prm.bb_variant == 1) ? (s5[2] > 0) : (s5[2] > 0 && s5[3] > 0);
     if (!ok) {
       // s^T y <= 0: Algorithm 1 defines no step; stop, or keep the previous one

@@ -38,7 +38,7 @@
 // mixed path: VSH analysis / self synthesis on the tensor cores (BF16 split
 // into three terms, FP32 accumulation) instead of FP32 CUDA-core products
 #ifndef SPS_SHT_TC
-#define SPS_SHT_TC 0
+#define SPS_SHT_TC 1
 #endif
 
 namespace {

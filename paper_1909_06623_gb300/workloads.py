@@ -245,9 +245,10 @@ def config4(N=1000, seed=SEED_BASE + 4):
 
 
 def config5(N, p, seed=None):
-    """Sweep point: N spheres a ~ U[0.5,1] at volume fraction 0.35, order p."""
+    """Sweep point: N spheres a ~ U[0.5,1] at volume fraction 0.35, order p
+    (no pre-placed close pairs: all gaps above 0.02)."""
     seed = SEED_BASE + 5 + 17 * N + p if seed is None else seed
-    C, R, rng = random_suspension(seed, N, 0.35)
+    C, R, rng = random_suspension(seed, N, 0.35, pair_frac=0.0)
     FT = np.concatenate([rng.standard_normal((N, 3)),
                          0.1 * rng.standard_normal((N, 3))], axis=1)
     return Workload(f"cfg5_N{N}_p{p}_phi0.35", C, R, FT, p=p, dt=1e-3, steps=1,
