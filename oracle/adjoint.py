@@ -120,3 +120,40 @@ def step_loss(centers, radii, FT, dt, p, *, delta=0.1, a_c_scale=1.0, beta=1.75,
         out = lcp.resolve_collisions(centers, radii, FT, dt, p, beta=beta, delta=delta,
                                      a_c_scale=a_c_scale, gmres_tol=1e-13, bbpgd_tol=1e-12)
     return float(np.sum(out["U"] ** 2)), out
+
+
+def collision_grad_c_contacts(M, D, gamma, ubar, U, centers, ij, nrm, dt, active_tol=0.0):
+    """The part of dL/dc (sphere centres) of one collision step that comes
+    through the contact geometry: Phi_l = |c_j - c_i| - R_i - R_j and
+    n_l = (c_j - c_i)/|c_j - c_i| in D, on the active set (strict
+    complementarity, contact and near sets fixed).  With
+    mu = (D_A^T M D_A)^{-T} D_A^T M^T ubar and w = dL/dF = M^T (ubar - D_A mu),
+    differentiating gamma_A = -(D_A^T M D_A)^{-1} (Phi_A/dt + D_A^T M F) and
+    U = M (F + D_A gamma_A) gives, per active contact l,
+        v_l = (I - n n^T) t_l / |c_j - c_i| - (mu_l / dt) n_l,
+        t_l = gamma_l (w_j - w_i) - mu_l (U_j - U_i)   (force parts),
+    added to dL/dc_j and subtracted from dL/dc_i.  The remaining part is
+    (ubar - D_A mu)^T (dM/dc) (F + D_A gamma_A); it vanishes for the identity
+    mobility.  Returns (dL/dc contact part (N x 3), mu (n_c, zero off A))."""
+    A = np.asarray(gamma) > active_tol
+    N = len(centers)
+    ub = np.asarray(ubar, dtype=np.float64).ravel()
+    mu = np.zeros(len(gamma))
+    g = np.zeros((N, 3))
+    if not A.any():
+        return g, mu
+    DA = D[:, A]
+    MAA = DA.T @ M @ DA
+    mu[A] = np.linalg.solve(MAA.T, DA.T @ (M.T @ ub))
+    w = (M.T @ (ub - D @ mu)).reshape(N, 6)
+    Uf = np.asarray(U).reshape(N, 6)
+    C = np.asarray(centers, dtype=np.float64)
+    for l in np.nonzero(A)[0]:
+        i, j = ij[l]
+        n = np.asarray(nrm[l])
+        d = np.linalg.norm(C[j] - C[i])
+        t = gamma[l] * (w[j, :3] - w[i, :3]) - mu[l] * (Uf[j, :3] - Uf[i, :3])
+        v = (t - n * (n @ t)) / d - (mu[l] / dt) * n
+        g[j] += v
+        g[i] -= v
+    return g, mu

@@ -129,8 +129,29 @@ def collision_grad():
                         h=h, fd=np.array(fd))
 
 
+def collision_grad_c():
+    """The same step: central differences (h = 1e-6) of L = sum |U|^2 through
+    the full oracle step in six centre coordinates (every pair stays at least
+    10 h from the near-pair and contact thresholds)."""
+    d = np.load(os.path.join(HERE, "active_step_p4.npz"))
+    C, R, FT, dt, p = d["centers"], d["radii"], d["FT"], float(d["dt"]), int(d["p"])
+    h = 1e-6
+    assert adjoint.near_margin(C, R) > 10 * h
+    coords = np.array([(0, 0), (1, 1), (2, 2), (3, 0), (4, 1), (4, 2)])
+    fd = []
+    for i, k in coords:
+        Cp, Cm = C.copy(), C.copy()
+        Cp[i, k] += h
+        Cm[i, k] -= h
+        fd.append((adjoint.step_loss(Cp, R, FT, dt, p, a_c_scale=1.05)[0]
+                   - adjoint.step_loss(Cm, R, FT, dt, p, a_c_scale=1.05)[0]) / (2 * h))
+        print("fd", i, k, fd[-1], flush=True)
+    np.savez_compressed(os.path.join(HERE, "collision_grad_c_p4.npz"), coords=coords, h=h,
+                        fd=np.array(fd))
+
+
 ALL = {"cfg1": cfg1, "active": active, "cfg2": cfg2_sample, "tiny": tiny_layers,
-       "collision_grad": collision_grad}
+       "collision_grad": collision_grad, "collision_grad_c": collision_grad_c}
 
 if __name__ == "__main__":
     for k in (sys.argv[1:] or ALL):

@@ -92,3 +92,30 @@ def test_bie_collision_gradient_fd(bie_case):
     grad, _ = adjoint.collision_grad_F(bie_case["M"], bie_case["D"], d["gamma"], 2.0 * d["U"])
     for (i, k), fd in zip(d["coords"], d["fd"]):
         assert abs(grad[i, k] - fd) < 1e-6 * np.abs(grad).max(), (i, k, grad[i, k], fd)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_identity_collision_gradient_centres_fd(seed):
+    """Identity mobility: dL/dc of the step comes only from the contact
+    geometry (Phi and the normals in D); central differences of the full
+    oracle step in every centre coordinate."""
+    c, a, F = chain(seed)
+    dt = 1e-3
+    L0, out = adjoint.step_loss(c, a, F, dt, 0, identity=True)
+    assert strict(out)
+    N = len(a)
+    D = adjoint.D_matrix(N, out["ij"], out["normals"])
+    grad, _ = adjoint.collision_grad_c_contacts(np.eye(6 * N), D, out["gamma"], 2.0 * out["U"], out["U"],
+                                                c, out["ij"], out["normals"], dt)
+    h = 1e-7
+    fd = np.zeros((N, 3))
+    for i in range(N):
+        for k in range(3):
+            cp, cm = c.copy(), c.copy()
+            cp[i, k] += h
+            cm[i, k] -= h
+            fd[i, k] = (adjoint.step_loss(cp, a, F, dt, 0, identity=True)[0]
+                        - adjoint.step_loss(cm, a, F, dt, 0, identity=True)[0]) / (2 * h)
+    assert np.abs(grad - fd).max() < 1e-5 * np.abs(fd).max()
+    # translation invariance: the gradient sums to zero over the spheres
+    assert np.abs(grad.sum(axis=0)).max() < 1e-9 * np.abs(grad).max()
