@@ -117,6 +117,10 @@ def workload(name):
     from paper_1909_06623_gb300 import workloads
     if name == "cfg2":
         return workloads.config2()
+    if name == "cfg3":
+        return workloads.config3()
+    if name == "cfg4":
+        return workloads.config4()
     if name.startswith("cfg5"):
         _, N, p = name.split("_")
         return workloads.config5(int(N), int(p))

@@ -226,13 +226,16 @@ int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, const double* r
  * so dL/dF = v - M^T D_A lambda with v = M^T dL/dU and
  * (D_A^T M D_A)^T lambda = D_A^T v, solved by GMRES on contact vectors
  * (gmres_tol, gmres_max); every application of M^T is an adjoint mobility
- * solve (identity mobility: none).  Radii, centres and the contact and near
- * sets are held fixed.  stats->n_active = |A|, stats->ir_sweeps = iterations
+ * solve (identity mobility: none).  If dL_dpos (n x 3 device) is not NULL it
+ * receives dL/dc for the centres, with the radii and the contact, active and
+ * near sets held fixed: (dL/dU - D_A mu)^T (dM/dc) (F + D gamma) plus the
+ * terms of Phi and the normals in D, mu the active-set solution above (one
+ * more forward and adjoint mobility solve).  stats->n_active = |A|, stats->ir_sweeps = iterations
  * of the active-set solve.  The paper has no adjoint.  Errors as
  * sps_resolve_collisions; NOT_CONVERGED if a solve hit its cap. */
 int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
                           const double* FT_ext, double dt, const double* dL_dU, double* UO,
-                          double* dL_dFT, sps_stats* stats);
+                          double* dL_dFT, double* dL_dpos, sps_stats* stats);
 
 /* Contact set of sps_build_contacts for callers that cannot allocate device
  * memory when they need it: code running while a stream is being captured into

@@ -21,7 +21,8 @@ from ._lib import (SPS_FP64, SPS_MIXED, SPS_MOB_BIE, SPS_MOB_IDENTITY, SPS_OP_A,
 __all__ = ["Context", "SPSError", "SPS_FP64", "SPS_MIXED", "SPS_OP_S", "SPS_OP_K", "SPS_OP_A",
            "SPS_MOB_BIE", "SPS_MOB_IDENTITY", "SPS_SEARCH_AUTO", "SPS_SEARCH_ALL_PAIRS",
            "SPS_SEARCH_CELLS",
-           "default_params", "unit_tables", "nodes_per_sphere", "MobilityFunction", "mobility"]
+           "default_params", "unit_tables", "nodes_per_sphere", "MobilityFunction", "mobility",
+           "CollisionStepFunction", "collision_step"]
 
 
 def nodes_per_sphere(p):
@@ -155,19 +156,21 @@ class Context:
         self.last_stats = st.as_dict()
         return UO, gF, gx
 
-    def collision_adjoint(self, pos, radii, FT_ext, dt, dL_dU, allow=()):
-        """(U, dL/dF_ext) of one collision-resolved step (positions not advanced)."""
+    def collision_adjoint(self, pos, radii, FT_ext, dt, dL_dU, want_pos=False, allow=()):
+        """(U, dL/dF_ext, dL/dpos or None) of one collision-resolved step
+        (positions are not advanced)."""
         n = radii.numel()
         UO = torch.empty(n, 6, dtype=torch.float64, device="cuda")
         gF = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        gx = torch.empty(n, 3, dtype=torch.float64, device="cuda") if want_pos else None
         st = sps_stats()
         rc = self.lib.sps_collision_adjoint(self.h, n, _ptr(pos), _ptr(radii), _ptr(FT_ext), float(dt),
-                                            _ptr(dL_dU.contiguous()), _ptr(UO), _ptr(gF),
+                                            _ptr(dL_dU.contiguous()), _ptr(UO), _ptr(gF), _ptr(gx),
                                             ctypes.byref(st))
         self._check(rc, allow=allow)
         self.last_stats = st.as_dict()
         self.n_c = st.n_contacts
-        return UO, gF
+        return UO, gF, gx
 
     def build_contacts(self, pos, radii):
         nc = ctypes.c_int()
@@ -271,3 +274,35 @@ class MobilityFunction(torch.autograd.Function):
 def mobility(pos, radii, FT, ctx):
     """Differentiable U = M F (see MobilityFunction)."""
     return MobilityFunction.apply(pos, radii, FT, ctx)
+
+
+class CollisionStepFunction(torch.autograd.Function):
+    """U of one collision-resolved step (Sec. 3.2) as a differentiable function
+    of the external forces/torques and the centres.
+
+    forward: sps_collision_adjoint's forward step; backward: its adjoint on the
+    active set of the LCP (contact, active and near sets held fixed)."""
+
+    @staticmethod
+    def forward(fctx, pos, radii, FT, dt, ctx):
+        U, _, _ = ctx.collision_adjoint(pos.detach().contiguous(), radii.detach().contiguous(),
+                                        FT.detach().contiguous(), dt,
+                                        torch.zeros_like(FT, dtype=torch.float64).contiguous())
+        fctx.save_for_backward(pos, radii, FT)
+        fctx.sps = ctx
+        fctx.dt = dt
+        return U
+
+    @staticmethod
+    def backward(fctx, gU):
+        pos, radii, FT = fctx.saved_tensors
+        want_pos = fctx.needs_input_grad[0]
+        _, gF, gx = fctx.sps.collision_adjoint(pos.detach().contiguous(), radii.detach().contiguous(),
+                                               FT.detach().contiguous(), fctx.dt, gU.contiguous(),
+                                               want_pos=want_pos)
+        return (gx if want_pos else None), None, (gF if fctx.needs_input_grad[2] else None), None, None
+
+
+def collision_step(pos, radii, FT, dt, ctx):
+    """Differentiable U of one collision-resolved step (see CollisionStepFunction)."""
+    return CollisionStepFunction.apply(pos, radii, FT, dt, ctx)

@@ -70,7 +70,7 @@ SIGNATURES = {
     "sps_profile": (_I, [_P, _I]),
     "sps_layer_apply_transpose": (_I, [_P, _I, _P, _P]),
     "sps_mobility_adjoint": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(sps_stats)]),
-    "sps_collision_adjoint": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P,
+    "sps_collision_adjoint": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P, _P,
                                    ctypes.POINTER(sps_stats)]),
     "sps_build_contacts_noalloc": (_I, [_I, _P, _P, _D, _D, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "sps_profile_read": (_I, [_P, _P, _P]),

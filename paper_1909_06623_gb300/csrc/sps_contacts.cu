@@ -476,6 +476,48 @@ __global__ void __launch_bounds__(kThreads) k_bb_ident_DT(int nc, const int* __r
   stat_store(a, part);
 }
 
+// dL/dc through the contact geometry of a collision step (Phi and the normals
+// in D), per sphere over its incident active contacts l (first sphere -, second +):
+//   v_l = (I - n n^T) t_l / |c_j - c_i| - (mu_l / dt) n_l,
+//   t_l = gamma_l (w_j - w_i) - mu_l (U_j - U_i),  w = dL/dF, force parts
+__global__ void k_contact_grad(int N, const int* __restrict__ inc_ptr, const int* __restrict__ inc,
+                               const int* __restrict__ ij, const double* __restrict__ nrm,
+                               const double* __restrict__ pos, const double* __restrict__ gam,
+                               const double* __restrict__ mu, const double* __restrict__ w,
+                               const double* __restrict__ U, double idt, double* __restrict__ dx) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  for (int e = inc_ptr[s]; e < inc_ptr[s + 1]; ++e) {
+    const int v = inc[e], l = v >> 1;
+    if (!(gam[l] > 0.0)) continue;
+    const int i = ij[2 * l], j = ij[2 * l + 1];
+    const double nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
+    const double dx0 = pos[3 * j] - pos[3 * i], dy0 = pos[3 * j + 1] - pos[3 * i + 1],
+                 dz0 = pos[3 * j + 2] - pos[3 * i + 2];
+    const double d = sqrt(dx0 * dx0 + dy0 * dy0 + dz0 * dz0);
+    const double tx = gam[l] * (w[6 * j] - w[6 * i]) - mu[l] * (U[6 * j] - U[6 * i]);
+    const double ty = gam[l] * (w[6 * j + 1] - w[6 * i + 1]) - mu[l] * (U[6 * j + 1] - U[6 * i + 1]);
+    const double tz = gam[l] * (w[6 * j + 2] - w[6 * i + 2]) - mu[l] * (U[6 * j + 2] - U[6 * i + 2]);
+    const double nt = nx * tx + ny * ty + nz * tz;
+    const double c = mu[l] * idt;
+    const double vx = (tx - nx * nt) / d - c * nx, vy = (ty - ny * nt) / d - c * ny,
+                 vz = (tz - nz * nt) / d - c * nz;
+    if (v & 1) {
+      g0 += vx;
+      g1 += vy;
+      g2 += vz;
+    } else {
+      g0 -= vx;
+      g1 -= vy;
+      g2 -= vz;
+    }
+  }
+  dx[3 * s] += g0;
+  dx[3 * s + 1] += g1;
+  dx[3 * s + 2] += g2;
+}
+
 __global__ void k_identity_U(int N, const double* __restrict__ FT, const double* __restrict__ F3,
                              double* __restrict__ UO) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -829,4 +871,15 @@ int sps_count_positive(sps_ctx* ctx, const double* v, int n, int* out) {
   k_count_pos<<<std::max(1, std::min(4 * 152, nblk(n))), kThreads, 0, ctx->stream>>>(n, v, ctx->d_flag);
   SPS_LAUNCHED(ctx);
   return read_int(ctx, ctx->d_flag, out);
+}
+
+int sps_launch_contact_grad(sps_ctx* ctx, const double* pos, const double* mu, const double* w,
+                            const double* U, double dt, double* dx) {
+  SpsPhase timer(ctx, SPS_PH_CONTACT);
+  const int N = ctx->c_N;
+  if (ctx->n_c == 0) return SPS_OK;
+  k_contact_grad<<<nblk(N), kThreads, 0, ctx->stream>>>(N, ctx->d_inc_ptr, ctx->d_inc, ctx->d_cij, ctx->d_cn,
+                                                         pos, ctx->d_gam, mu, w, U, 1.0 / dt, dx);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
 }

@@ -151,6 +151,8 @@ struct sps_ctx {
   double *d_FT = nullptr, *d_Unc = nullptr, *d_Uc = nullptr;
   int cap_bb = 0;
   double *d_bbpart = nullptr;    // BBPGD statistic partials (5 x blocks)
+  double *d_gam_best = nullptr, *d_aux_best = nullptr;  // smallest-residual BBPGD iterate
+  size_t cap_gam_best = 0, cap_aux_best = 0;
   // identity mobility: contact forces (N x 3), FT / U_nc / U_c (N x 6)
   double *d_F3 = nullptr, *d_iFT = nullptr;
   double *d_adj6a = nullptr, *d_adj6b = nullptr, *d_adjc = nullptr;  // collision adjoint scratch
@@ -261,6 +263,8 @@ int sps_launch_bb_identity(sps_ctx* ctx, double alpha, const double* gam, const 
                            double* gam_new, double* g_new);
 const double* sps_bb_out(sps_ctx* ctx);
 int sps_launch_identity_U(sps_ctx* ctx, int n, const double* FT, const double* F3, double* UO);
+int sps_launch_contact_grad(sps_ctx* ctx, const double* pos, const double* mu, const double* w,
+                            const double* U, double dt, double* dx);
 int sps_launch_D(sps_ctx* ctx, const double* gamma, double* FT);
 int sps_launch_DT(sps_ctx* ctx, const double* UO, double* out);
 int sps_launch_rho(sps_ctx* ctx, const double* FT, double* rho);

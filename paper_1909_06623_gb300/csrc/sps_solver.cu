@@ -504,7 +504,7 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_cl_id2, ctx->d_cl_range, ctx->d_cl_f, ctx->d_cl_d, ctx->d_cl_part,
                   ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc, ctx->tcA.d,
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
-                  ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc};
+                  ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -830,6 +830,7 @@ static int bb_stats(sps_ctx* ctx, const double* gn, const double* ggn, const dou
 
 struct BBResult {
   int iters = 0;
+  int best_iter = 0;    // iterate returned (differs from iters after a failure)
   double phi = 0.0;
   int bb_rc = SPS_OK;   // BREAKDOWN / NOT_CONVERGED of Algorithm 1 itself
   int worst = SPS_OK;   // NOT_CONVERGED of an inner mobility solve
@@ -843,7 +844,8 @@ struct BBResult {
 // the iteration goes on.  Returns the first hard error, else SPS_OK with the
 // outcome in r; d_gam / d_g hold the last iterate.
 template <class MulG, class Step>
-static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step, BBResult& r) {
+static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step, BBResult& r,
+                     double* aux = nullptr, size_t aux_len = 0) {
   SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
@@ -866,7 +868,33 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
   // divergence: an indefinite discrete M (nearly touching spheres at low
   // order) makes the projected steps grow without bound
   const double phi_limit = 1e6 * std::max(r.phi, tol);
-  for (int j = 1; j <= ctx->prm.bbpgd_max; ++j) {
+  // with aux (the vector holding M D gamma of the current iterate), the
+  // iterate of smallest residual is kept and returned if the loop fails
+  double best_phi = r.phi;
+  int best_j = 0;
+  if (aux) {
+    SPS_TRY(sps_grow(ctx, &ctx->d_gam_best, ctx->cap_gam_best, (size_t)std::max(nc, 1)));
+    SPS_TRY(sps_grow(ctx, &ctx->d_aux_best, ctx->cap_aux_best, std::max<size_t>(aux_len, 1)));
+  }
+  auto fail = [&](int code, int j) -> int {
+    r.bb_rc = code;
+    if (aux && best_j != j) {
+      if (best_j == 0) {
+        SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
+        SPS_CUDA(ctx, cudaMemsetAsync(aux, 0, sizeof(double) * aux_len, ctx->stream));
+      } else {
+        SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_gam, ctx->d_gam_best, sizeof(double) * nc,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+        SPS_CUDA(ctx, cudaMemcpyAsync(aux, ctx->d_aux_best, sizeof(double) * aux_len,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      r.phi = best_phi;
+      r.best_iter = best_j;
+    }
+    return SPS_OK;
+  };
+  int j = 1;
+  for (; j <= ctx->prm.bbpgd_max; ++j) {
     rc = step(alpha, j, s5);
     if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
     if (rc) r.worst = rc;
@@ -874,26 +902,28 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
     std::swap(ctx->d_gam, ctx->d_gam_new);
     std::swap(ctx->d_g, ctx->d_g_new);
     r.iters = j;
+    r.best_iter = j;
     r.phi = std::sqrt(s5[0]);
     if (r.phi < tol) return SPS_OK;
-    if (!(r.phi < phi_limit)) {
-      r.bb_rc = SPS_ERR_BREAKDOWN;
-      return SPS_OK;
+    if (aux && r.phi < best_phi) {
+      best_phi = r.phi;
+      best_j = j;
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_gam_best, ctx->d_gam, sizeof(double) * nc,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_aux_best, aux, sizeof(double) * aux_len,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
     }
+    if (!(r.phi < phi_limit)) return fail(SPS_ERR_BREAKDOWN, j);
     const bool ok = (ctx->prm.bb_variant == 1) ? (s5[2] > 0) : (s5[2] > 0 && s5[3] > 0);
     if (!ok) {
       // s^T y <= 0: Algorithm 1 defines no step; stop, or keep the previous one
-      if (!ctx->prm.bb_safeguard) {
-        r.bb_rc = SPS_ERR_BREAKDOWN;
-        return SPS_OK;
-      }
+      if (!ctx->prm.bb_safeguard) return fail(SPS_ERR_BREAKDOWN, j);
       if (st) st->bb_safeguards += 1;
     } else {
       alpha = (ctx->prm.bb_variant == 1) ? s5[1] / s5[2] : s5[2] / s5[3];
     }
   }
-  r.bb_rc = SPS_ERR_NOT_CONVERGED;
-  return SPS_OK;
+  return fail(SPS_ERR_NOT_CONVERGED, j - 1);
 }
 
 static int finish_bb_stats(sps_ctx* ctx, int nc, const BBResult& r, sps_stats* st) {
@@ -944,7 +974,7 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
       SPS_TRY(bb_stats(ctx, ctx->d_gam_new, ctx->d_g_new, ctx->d_gam, ctx->d_g, s5));
       return rc2;
     };
-    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r));
+    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, ctx->d_Uc, 6 * (size_t)n));
     if (r.worst) worst = r.worst;
     // U_c is the solve of the returned iterate; gamma_0 = 0 needs none
     if (r.iters == 0) SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
@@ -1172,7 +1202,7 @@ static int apply_MT(sps_ctx* ctx, int n, const double* in, double* out, sps_stat
 
 extern "C" int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, const double* radii,
                                      const double* FT_ext, double dt, const double* dL_dU, double* UO,
-                                     double* dL_dFT, sps_stats* st) {
+                                     double* dL_dFT, double* dL_dpos, sps_stats* st) {
   if (!ctx || n < 1 || !pos || !radii || !FT_ext || !dL_dU || !UO || !dL_dFT)
     return sps_fail(ctx, SPS_ERR_INVALID_ARG, "collision_adjoint: bad argument");
   long long l0;
@@ -1309,6 +1339,42 @@ extern "C" int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, con
     k_axpby<<<gblocks((long long)n6), 256, 0, ctx->stream>>>((long long)n6, 1.0, dL_dFT, -1.0, ctx->d_adj6b,
                                                              dL_dFT); }
     SPS_LAUNCHED(ctx);
+  }
+  if (dL_dpos) {
+    // dL/dc = (ubar - D_A mu)^T (dM/dc) F_tot + the contact-geometry terms,
+    // mu = the active-set solution above (masked, in d_adjc), F_tot = F + D gamma
+    const long long m6 = (long long)n6;
+    if (na > 0) {
+      SPS_TRY(sps_launch_D(ctx, ctx->d_adjc, ctx->d_adj6a));
+      { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+      k_axpby<<<gblocks(m6), 256, 0, ctx->stream>>>(m6, 1.0, dL_dU, -1.0, ctx->d_adj6a, ctx->d_adj6b); }
+      SPS_LAUNCHED(ctx);
+      SPS_TRY(sps_launch_D(ctx, ctx->d_gam, ctx->d_adj6a));
+      { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+      k_axpby<<<gblocks(m6), 256, 0, ctx->stream>>>(m6, 1.0, FT_ext, 1.0, ctx->d_adj6a, ctx->d_adj6a); }
+      SPS_LAUNCHED(ctx);
+    } else {
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_adj6b, dL_dU, sizeof(double) * n6, cudaMemcpyDeviceToDevice, ctx->stream));
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_adj6a, FT_ext, sizeof(double) * n6, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (ctx->prm.mobility == SPS_MOB_IDENTITY) {
+      SPS_CUDA(ctx, cudaMemsetAsync(dL_dpos, 0, sizeof(double) * 3 * n, ctx->stream));
+    } else {
+      // forward solve with F_tot (keeps sigma), adjoint with a, then the
+      // derivative of the far and near sums
+      const long long n3 = 3LL * ctx->NP;
+      int frc = mobility_solve(ctx, ctx->d_adj6a, ctx->d_Uc, st, ctx->d_zeta, false);
+      ctx->zeta_n = 0;
+      if (frc != SPS_OK && frc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, frc);
+      if (frc) worst = frc;
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_sigtot, ctx->d_tmp3, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+      int grc = mobility_T(ctx, ctx->d_adj6b, ctx->d_FT, st);
+      if (grc != SPS_OK && grc != SPS_ERR_NOT_CONVERGED) return stats_end(ctx, st, l0, grc);
+      if (grc) worst = grc;
+      SPS_TRY(sps_geom_gradient(ctx, ctx->d_ubar, ctx->d_lam, ctx->d_sigtot, dL_dpos));
+    }
+    if (na > 0) SPS_TRY(sps_launch_contact_grad(ctx, pos, ctx->d_adjc, dL_dFT, UO, dt, dL_dpos));
   }
   if (st) st->n_active = na;
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

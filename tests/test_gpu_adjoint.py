@@ -257,12 +257,17 @@ def test_collision_adjoint_identity(sps, seed):
     D = oadj.D_matrix(N, out["ij"], out["normals"])
     ref, A = oadj.collision_grad_F(np.eye(6 * N), D, out["gamma"], 2.0 * out["U"])
     ctx = sps.Context(p=2, delta=0.1, mobility=sps.SPS_MOB_IDENTITY, bbpgd_tol=1e-12, gmres_tol=1e-12)
-    U, gF = ctx.collision_adjoint(dev(w.centers), dev(w.radii), dev(w.FT), w.dt,
-                                  dev(2.0 * out["U"]))
+    U, gF, gx = ctx.collision_adjoint(dev(w.centers), dev(w.radii), dev(w.FT), w.dt,
+                                      dev(2.0 * out["U"]), want_pos=True)
     st = ctx.last_stats
     assert st["n_active"] == int(A.sum())
     assert np.abs(U.cpu().numpy() - out["U"]).max() < 1e-10 * np.abs(out["U"]).max()
     assert np.abs(gF.cpu().numpy() - ref).max() < 1e-9 * np.abs(ref).max()
+    # centres: the identity mobility does not depend on them, so only the
+    # contact geometry contributes (pinned against central differences)
+    refx, _ = oadj.collision_grad_c_contacts(np.eye(6 * N), D, out["gamma"], 2.0 * out["U"], out["U"],
+                                             w.centers, out["ij"], out["normals"], w.dt)
+    assert np.abs(gx.cpu().numpy() - refx).max() < 1e-9 * np.abs(refx).max()
 
 
 @pytest.fixture(scope="module")
@@ -286,10 +291,32 @@ def test_collision_adjoint_bie(sps, collision_golden, precision, tol):
                       gmres_tol=1e-13 if precision == 0 else 1e-9, gmres_max=300,
                       bbpgd_tol=1e-12 if precision == 0 else 1e-6, precision=precision, warm_start=0)
     pos, rad, FT = dev(d["centers"]), dev(d["radii"]), dev(d["FT"])
-    U, _ = ctx.collision_adjoint(pos, rad, FT, float(d["dt"]), dev(2.0 * d["U"]))
-    U, gF = ctx.collision_adjoint(pos, rad, FT, float(d["dt"]), 2.0 * U)
+    U, _, _ = ctx.collision_adjoint(pos, rad, FT, float(d["dt"]), dev(2.0 * d["U"]))
+    U, gF, gx = ctx.collision_adjoint(pos, rad, FT, float(d["dt"]), 2.0 * U, want_pos=True)
     assert ctx.last_stats["n_active"] == int(A.sum())
     g = gF.cpu().numpy()
     assert np.abs(g - ref).max() < tol * np.abs(ref).max()
     for (i, k), fd in zip(d["coords"], d["fd"]):
         assert abs(g[i, k] - fd) < tol * np.abs(ref).max(), (i, k)
+    # centres: central differences of the full oracle step
+    dc = np.load(os.path.join(GOLD, "collision_grad_c_p4.npz"))
+    gxx = gx.cpu().numpy()
+    scale = np.abs(dc["fd"]).max()
+    for (i, k), fd in zip(dc["coords"], dc["fd"]):
+        assert abs(gxx[i, k] - fd) < tol * scale, (i, k, gxx[i, k], fd)
+    assert np.abs(gxx.sum(axis=0)).max() < 1e-6 * np.abs(gxx).max()   # translation invariance
+
+
+def test_collision_step_autograd(sps):
+    """torch.autograd through the collision step matches the adjoint calls."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.contact_chain(2)
+    ctx = sps.Context(p=2, delta=0.1, mobility=sps.SPS_MOB_IDENTITY, bbpgd_tol=1e-12, gmres_tol=1e-12)
+    pos = dev(w.centers).requires_grad_(True)
+    FT = dev(w.FT).requires_grad_(True)
+    U = sps.collision_step(pos, dev(w.radii), FT, w.dt, ctx)
+    (U * U).sum().backward()
+    U2, gF, gx = ctx.collision_adjoint(dev(w.centers), dev(w.radii), dev(w.FT), w.dt, 2.0 * U.detach(),
+                                       want_pos=True)
+    assert torch.allclose(FT.grad, gF, rtol=1e-12, atol=0)
+    assert torch.allclose(pos.grad, gx, rtol=1e-12, atol=0)
