@@ -438,7 +438,9 @@ __global__ void __launch_bounds__(kThreads) k_bb_gather(int N, const int* __rest
   const int e1 = inc_ptr[s + 1];
   for (int e = inc_ptr[s]; e < e1; ++e) {
     const int v = inc[e], l = v >> 1;
-    const double gs = (v & 1) ? gam_new[l] : -gam_new[l];
+    // -gamma for the contact's first sphere: a sign-bit flip on the integer units
+    const double gs = __longlong_as_double(__double_as_longlong(gam_new[l]) ^
+                                           ((long long)(~v & 1) << 63));
     f0 = fma(gs, nrm[3 * l], f0);
     f1 = fma(gs, nrm[3 * l + 1], f1);
     f2 = fma(gs, nrm[3 * l + 2], f2);

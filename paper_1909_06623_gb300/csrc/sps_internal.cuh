@@ -123,6 +123,12 @@ struct sps_ctx {
   long long zeta_nc_n = 0;       // node count it belongs to (0: none)
   long long zeta_n = 0;          // node count of the last sps_mobility_apply density in d_zeta
   double *d_r = nullptr, *d_dz = nullptr;
+  // solve history of one collision step (initial guesses): orthonormal
+  // right-hand sides and matching solution combinations
+  double *d_Pb = nullptr, *d_Px = nullptr;
+  long long proj_n = 0;
+  int proj_m = 0;
+  bool proj_on = false;
 
   // contacts
   int n_c = 0, cap_c = 0, c_N = 0;   // contacts, capacity, spheres they refer to

@@ -504,7 +504,8 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_cl_id2, ctx->d_cl_range, ctx->d_cl_f, ctx->d_cl_d, ctx->d_cl_part,
                   ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc, ctx->tcA.d,
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
-                  ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best};
+                  ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
+                  ctx->d_Pb, ctx->d_Px};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -644,6 +645,92 @@ extern "C" int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double
 // ---------------------------------------------------------------------------
 // mobility solve on the current geometry
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Initial guesses from earlier solves with the same operator (one geometry,
+// inside one collision step): an orthonormal basis Pb of earlier right-hand
+// sides and the matching combinations Px of their solutions (A Px_k ~ Pb_k).
+// For a new b the guess x0 = Px (Pb^T b) leaves the residual b - Pb Pb^T b,
+// the smallest over combinations of the earlier solutions.  Every solve still
+// runs GMRES to gmres_tol; only its starting point changes.
+// ---------------------------------------------------------------------------
+constexpr int kProjMax = 16;
+
+static int proj_ensure(sps_ctx* ctx, long long n) {
+  if (ctx->proj_n == n && ctx->d_Pb) return SPS_OK;
+  cudaFree(ctx->d_Pb);
+  cudaFree(ctx->d_Px);
+  ctx->d_Pb = ctx->d_Px = nullptr;
+  size_t c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_Pb, c, (size_t)kProjMax * n));
+  c = 0;
+  SPS_TRY(sps_grow(ctx, &ctx->d_Px, c, (size_t)kProjMax * n));
+  ctx->proj_n = n;
+  ctx->proj_m = 0;
+  return SPS_OK;
+}
+
+static int proj_guess(sps_ctx* ctx, const double* b, double* x, bool* used) {
+  *used = false;
+  const int m = ctx->proj_m;
+  const long long n = 3LL * ctx->NP;
+  if (!ctx->proj_on || m == 0 || ctx->proj_n != n) return SPS_OK;
+  SPS_TRY(ensure_gmres(ctx, n, ctx->prm.gmres_max));
+  SPS_TRY(multidot_dev(ctx, ctx->d_Pb, n, m, b, n, ctx->d_h, ctx->d_red));
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, ctx->d_Px, n, m, ctx->d_h, 0, x); }
+  SPS_LAUNCHED(ctx);
+  *used = true;
+  return SPS_OK;
+}
+
+static int proj_add(sps_ctx* ctx, const double* b, const double* x) {
+  if (!ctx->proj_on) return SPS_OK;
+  const long long n = 3LL * ctx->NP;
+  SPS_TRY(proj_ensure(ctx, n));
+  SPS_TRY(ensure_gmres(ctx, n, ctx->prm.gmres_max));
+  int m = ctx->proj_m;
+  if (m == kProjMax) m = ctx->proj_m = 0;   // full: start a new basis
+  double* pb = ctx->d_Pb + (size_t)m * n;
+  double* px = ctx->d_Px + (size_t)m * n;
+  double bb = 0.0;
+  SPS_TRY(sps_dot(ctx, b, b, n, &bb));
+  if (!(bb > 0.0) || !std::isfinite(bb)) return SPS_OK;
+  SPS_CUDA(ctx, cudaMemcpyAsync(pb, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpyAsync(px, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int pass = 0; pass < 2 && m > 0; ++pass) {   // classical Gram-Schmidt, twice
+    SPS_TRY(multidot_dev(ctx, ctx->d_Pb, n, m, pb, n, ctx->d_h, ctx->d_red));
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, ctx->d_Pb, n, m, ctx->d_h, pb);
+    k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, ctx->d_Px, n, m, ctx->d_h, px); }
+    ctx->launches += 2;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  double nn = 0.0;
+  SPS_TRY(sps_dot(ctx, pb, pb, n, &nn));
+  if (!(nn > 1e-20 * bb) || !std::isfinite(nn)) return SPS_OK;   // b already in the span
+  const double inv = 1.0 / std::sqrt(nn);
+  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, inv, pb, 0.0, nullptr, pb);
+  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, inv, px, 0.0, nullptr, px); }
+  ctx->launches += 2;
+  ctx->proj_m = m + 1;
+  return SPS_OK;
+}
+
+// the projection space lives for one collision step
+struct ProjScope {
+  sps_ctx* c;
+  explicit ProjScope(sps_ctx* ctx) : c(ctx) {
+    c->proj_on = ctx->prm.warm_start != 0;
+    c->proj_m = 0;
+  }
+  ~ProjScope() {
+    c->proj_on = false;
+    c->proj_m = 0;
+  }
+};
+
 // zeta: the density unknown of eq. rigidbodyrho for this solve; with warm it
 // holds an initial guess on entry (a previous solution for similar forces).
 static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats* st, double* zeta,
@@ -659,7 +746,10 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
   SPS_LAUNCHED(ctx);
   int its = 0;
   double res = 0.0;
-  int rc = gmres(ctx, ctx->d_b, zeta, warm, ctx->prm.gmres_tol, ctx->prm.gmres_max, mixed, &its, &res);
+  bool projected = false;
+  SPS_TRY(proj_guess(ctx, ctx->d_b, zeta, &projected));
+  int rc = gmres(ctx, ctx->d_b, zeta, warm || projected, ctx->prm.gmres_tol, ctx->prm.gmres_max, mixed,
+                 &its, &res);
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
   int total_its = its;
   double final_res = res;
@@ -691,6 +781,7 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
     if (st) st->ir_sweeps += sweep;
     rc = (final_res < ctx->prm.ir_tol) ? SPS_OK : SPS_ERR_NOT_CONVERGED;
   }
+  if (rc == SPS_OK) SPS_TRY(proj_add(ctx, ctx->d_b, zeta));
   // u = S[rho + zeta]
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
   k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_rho, 1.0, zeta, ctx->d_tmp3); }
@@ -939,6 +1030,7 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
   if (!(dt > 0)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "dt must be positive");
   SPS_TRY(sps_set_geometry(ctx, n, pos, radii));
   SPS_TRY(check_finite_host(ctx, FT_ext, 6LL * n, "external force/torque"));
+  ProjScope proj_scope(ctx);
   // 1. U_nc (warm start from the previous step's density when the size matches)
   const bool warm_nc = ctx->prm.warm_start && ctx->zeta_nc_n == ctx->NP;
   int rc = mobility_solve(ctx, FT_ext, ctx->d_Unc, st, ctx->d_zeta_nc, warm_nc);

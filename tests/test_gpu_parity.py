@@ -299,3 +299,26 @@ def test_warm_start_matches_cold(sps):
     if np.abs(out[0][0]).max() > 0:
         assert relerr(out[1][0], out[0][0]) < 1e-6
     assert out[1][2]["gmres_iters"] < out[0][2]["gmres_iters"]
+
+
+def test_bbpgd_cap_returns_consistent_best_iterate(sps):
+    """With the BBPGD cap hit (NOT_CONVERGED) the step returns the iterate of
+    smallest min-map residual together with its own M D gamma: U - U_nc equals
+    the mobility of D gamma, and the reported residual is that of gamma."""
+    d = load("active_step_p4.npz")
+    p = int(d["p"])
+    ctx = sps.Context(p=p, delta=0.1, a_c_scale=1.05, gmres_tol=1e-12, gmres_max=300, bbpgd_tol=1e-12,
+                      bbpgd_max=3, warm_start=0)
+    C, R, FT = dev(d["centers"]), dev(d["radii"]), dev(d["FT"])
+    gam, U, _ = ctx.resolve_collisions(C, R, FT, float(d["dt"]), allow=(4,))
+    st = dict(ctx.last_stats)
+    assert st["status"] == 4 and st["bbpgd_iters"] == 3
+    n = len(d["radii"])
+    Fc = ctx.contact_force(gam.contiguous(), n)
+    Uc = ctx.mobility_apply(C, R, Fc)
+    Unc = ctx.mobility_apply(C, R, FT)
+    assert relerr((U - Unc).cpu().numpy(), Uc.cpu().numpy()) < 1e-9
+    q = d["phi"] / float(d["dt"]) + ctx.contact_rate(Unc).cpu().numpy()
+    g = ctx.contact_rate(Uc).cpu().numpy() + q
+    phi = np.linalg.norm(np.minimum(gam.cpu().numpy(), g))
+    assert abs(phi - st["final_phi"]) < 1e-8 * max(phi, 1.0)
