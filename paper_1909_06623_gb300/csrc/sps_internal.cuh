@@ -127,7 +127,7 @@ struct sps_ctx {
   // right-hand sides and matching solution combinations
   double *d_Pb = nullptr, *d_Px = nullptr;
   long long proj_n = 0;
-  int proj_m = 0;
+  int proj_m = 0, proj_old = 0;   // columns in use, oldest column once full
   bool proj_on = false;
 
   // contacts
