@@ -129,6 +129,11 @@ constexpr int kNPair = SPS_FAR_NPAIR;         // target pairs per thread
 #endif
 // 1: the Kahan running sums (touched once per source sphere) live in shared
 // memory instead of registers
+// source nodes per unrolled inner-loop iteration
+#ifndef SPS_FAR_UNROLL
+#define SPS_FAR_UNROLL 4
+#endif
+constexpr int kUnroll = SPS_FAR_UNROLL;
 #ifndef SPS_FAR_KSMEM
 #define SPS_FAR_KSMEM 0
 #endif
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(kT32, SPS_FAR_MINB) k_far32(
         const float4* Es = sE + js * P;
         (void)D;
         (void)Es;
-#pragma unroll 2
+#pragma unroll kUnroll
         for (int k = 0; k < P; ++k) {
           const float4 a4 = A[k], b4 = B[k], c4 = C[k];
           const float2 sxx = make_float2(a4.x, a4.y), syy = make_float2(a4.z, a4.w);
