@@ -37,7 +37,7 @@ FLOPS_PER_PAIR = {"K": 30, "S": 29}   # algorithmic FP32 operations per pair ter
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_far32<K> launch at the
 # 1,000-sphere p = 6 workload, from an ncu capture of the current kernel
 # (None whenever the kernel changes until it is captured again)
-FAR_K_TRAFFIC_BYTES = 3629312 + 54784
+FAR_K_TRAFFIC_BYTES = 3630848 + 76800
 SMS, LANES = 152, 128
 N_PHASES = 12
 PHASES = ["far_K", "far_S", "far_aux", "near_K", "near_S", "self_vsh", "krylov", "contact",
