@@ -111,6 +111,8 @@ typedef struct sps_stats {
   long long kernel_launches; /* kernels launched by this call                */
   double final_phi;     /* min-map residual at exit                          */
   double gmres_res_max; /* largest final relative residual over the solves   */
+  int layer_applies;    /* layer-operator applications (S, K or I/2 + K + L,
+                           forward or transposed) made by this call          */
 } sps_stats;
 
 typedef struct sps_ctx sps_ctx;

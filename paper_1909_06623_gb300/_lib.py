@@ -38,7 +38,7 @@ class sps_stats(ctypes.Structure):
                 ("n_near_pairs", ctypes.c_int), ("ir_sweeps", ctypes.c_int),
                 ("bb_safeguards", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong), ("final_phi", ctypes.c_double),
-                ("gmres_res_max", ctypes.c_double)]
+                ("gmres_res_max", ctypes.c_double), ("layer_applies", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

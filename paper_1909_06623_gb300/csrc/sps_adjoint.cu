@@ -264,6 +264,7 @@ static int near_reverse(sps_ctx* ctx, const double* ybar) {
 
 // out = Op^T v for op S, K or A (= I/2 + K + L), all FP64
 int sps_layer_T(sps_ctx* ctx, int op, const double* v, double* out) {
+  ctx->layer_applies += 1;
   const int N = ctx->N, NR = ctx->T.NR;
   const bool S = (op == SPS_OP_S);
   // self: coefbar = Synth^T v (times a_s for S)

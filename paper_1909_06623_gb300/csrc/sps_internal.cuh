@@ -25,7 +25,10 @@ constexpr int kFieldsS = 10;   // fields summed per target for the velocity
 constexpr int kMaxP = 16;
 // near entries closer than this many source radii from the source centre are
 // evaluated in FP64 in the mixed path (the VSH terms decay slowly there)
-constexpr double kCloseRadius = 1.5;
+#ifndef SPS_CLOSE_RADIUS
+#define SPS_CLOSE_RADIUS 1.5
+#endif
+constexpr double kCloseRadius = SPS_CLOSE_RADIUS;
 
 struct Tables {
   int p = 0, P = 0, NC = 0, NR = 0, L = 0, E = 0;
@@ -80,6 +83,8 @@ struct sps_ctx {
   double *d_ebar = nullptr;     // N x E x kFieldsK x 2 adjoint of the field coefficients
   double *d_sigtot = nullptr, *d_ubar = nullptr, *d_sbar = nullptr, *d_lam = nullptr, *d_rbar = nullptr;
   bool adjoint_mode = false;    // GMRES applies A^T instead of A
+  long long layer_applies = 0;  // layer-operator applications since creation
+  long long stats_layer0 = 0;   // ... at the start of the current API call
   float *d_anal32 = nullptr, *d_synthS32 = nullptr, *d_synthK32 = nullptr;
   // tensor-core transforms (mixed path): matrices split into three BF16 terms
   // in the layout of k_sht_tc; analysis, synthesis x multS, synthesis x multK
@@ -106,6 +111,7 @@ struct sps_ctx {
   // operator scratch
   double *d_coef = nullptr;      // N x NR
   double *d_fcoef = nullptr;     // N x E x kFieldsK x 2
+  float *d_fcoef32 = nullptr;    // the same rounded to FP32 (mixed near field)
   double *d_mom = nullptr;       // N x 6 (per-sphere moments)
   double *d_tmp3 = nullptr;      // 3NP scratch
   float *d_sig32 = nullptr;      // 3NP FP32 w*sigma for the mixed far field
@@ -302,8 +308,9 @@ int sps_layer_T(sps_ctx* ctx, int op, const double* v, double* out);
 
 // near-field coefficient maps (sps_vsh.cu)
 int sps_build_field_maps(sps_ctx* ctx);
+// out32 (optional): a copy of the result rounded to FP32 (not with accumulate)
 int sps_launch_sparse_rows(sps_ctx* ctx, const sps_ctx::Sparse& m, int nsph, const double* in, int in_ld,
-                           double* out, int out_ld, int accumulate);
+                           double* out, int out_ld, int accumulate, float* out32 = nullptr);
 
 // vector kernels (sps_solver.cu)
 int sps_dot(sps_ctx* ctx, const double* a, const double* b, long long n, double* host_out);

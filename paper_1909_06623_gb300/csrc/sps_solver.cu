@@ -256,13 +256,17 @@ static int apply_A(sps_ctx* ctx, const double* v, double* out, bool fp32) {
   return sps_layer(ctx, SPS_OP_A, v, out, fp32);
 }
 
-// GMRES on A x = b.  warm: x holds an initial guess (else x0 = 0).  Stops when
-// ||b - A x|| / ||b|| < tol.  Classical Gram-Schmidt applied twice; each
-// Arnoldi step reads its dot products and norm back with one synchronisation:
-// the norm after the second pass is sqrt(||w||^2 - ||h2||^2) (w is then
-// orthogonal to the basis).  Returns SPS_OK or NOT_CONVERGED.
+// GMRES on A x = b.  warm: x holds an initial guess (else x0 = 0); r0: its
+// residual b - A x0 when the caller knows it (else one application of A).
+// Stops when ||b - A x|| / ||b|| < tol.  Classical Gram-Schmidt applied twice;
+// each Arnoldi step reads its dot products and norm back with one
+// synchronisation: the norm after the second pass is sqrt(||w||^2 - ||h2||^2)
+// (w is then orthogonal to the basis).  Ax (optional) receives A x from the
+// Arnoldi relation, A x = b - r0 + V_{k+1} Hbar y, without applying A.
+// Returns SPS_OK or NOT_CONVERGED.
 static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol, int kmax,
-                 bool fp32, int* iters, double* relres) {
+                 bool fp32, int* iters, double* relres, const double* r0 = nullptr,
+                 double* Ax = nullptr) {
   const long long n = 3LL * ctx->NP;
   SPS_TRY(ensure_gmres(ctx, n, kmax));
   double bb = 0.0;
@@ -273,6 +277,7 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
   *relres = 0.0;
   if (nb == 0.0) {
     SPS_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+    if (Ax) SPS_CUDA(ctx, cudaMemsetAsync(Ax, 0, sizeof(double) * n, ctx->stream));
     return SPS_OK;
   }
   double* Q = ctx->d_Q;
@@ -280,16 +285,25 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
   // r0 = b - A x0 (in Q_0 before normalisation)
   double beta = nb;
   if (warm) {
-    SPS_TRY(apply_A(ctx, x, w, fp32));
-    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-    k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, b, -1.0, w, Q); }
-    SPS_LAUNCHED(ctx);
+    if (r0) {
+      SPS_CUDA(ctx, cudaMemcpyAsync(Q, r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+      SPS_TRY(apply_A(ctx, x, w, fp32));
+      { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+      k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, b, -1.0, w, Q); }
+      SPS_LAUNCHED(ctx);
+    }
     double rr = 0.0;
     SPS_TRY(sps_dot(ctx, Q, Q, n, &rr));
     if (std::isfinite(rr)) {
       beta = std::sqrt(rr);
       if (beta / nb < tol) {
         *relres = beta / nb;
+        if (Ax) {
+          SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+          k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, b, -1.0, Q, Ax);
+          SPS_LAUNCHED(ctx);
+        }
         return SPS_OK;
       }
       { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
@@ -308,6 +322,7 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
     SPS_LAUNCHED(ctx);
   }
   std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), g(kmax + 1, 0.0);
+  std::vector<double> Hbar(Ax ? (size_t)(kmax + 1) * kmax : 0);   // before the rotations
   std::vector<double> hh(2 * kmax + 4);
   g[0] = beta;
   int k = 0;
@@ -339,6 +354,8 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
     const double hk = std::sqrt(std::max(ww, 0.0));
     for (int j = 0; j < k; ++j) Hc(j, k - 1) = hh[j] + hh[k + j];
     Hc(k, k - 1) = hk;
+    if (Ax)
+      std::copy(&Hc(0, k - 1), &Hc(0, k - 1) + k + 1, Hbar.begin() + (size_t)(k - 1) * (kmax + 1));
     if (hk > 0.0) {
       { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
       k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0 / hk, w, 0.0, nullptr, Q + (long long)k * n); }
@@ -379,6 +396,22 @@ static int gmres(sps_ctx* ctx, const double* b, double* x, bool warm, double tol
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
   k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, k, d_h1, warm ? 1 : 0, x); }
   SPS_LAUNCHED(ctx);
+  if (Ax) {
+    // A x = A x0 + A V y = (b - beta v_0) + V_{k+1} Hbar y; a zero last norm
+    // leaves v_k unwritten and its coefficient zero
+    std::vector<double> z(k + 1, 0.0);
+    z[0] = -beta;
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i <= j + 1; ++i) z[i] += Hbar[(size_t)j * (kmax + 1) + i] * y[j];
+    const int cols = (k > 0 && Hbar[(size_t)(k - 1) * (kmax + 1) + k] > 0.0) ? k + 1 : k;
+    std::memcpy(ctx->h_pinned + k, z.data(), sizeof(double) * cols);
+    SPS_CUDA(ctx, cudaMemcpyAsync(d_h2, ctx->h_pinned + k, sizeof(double) * cols, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    SPS_CUDA(ctx, cudaMemcpyAsync(Ax, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
+    k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, Q, n, cols, d_h2, 1, Ax); }
+    SPS_LAUNCHED(ctx);
+  }
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *iters = k;
   *relres = res;
@@ -505,7 +538,7 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc, ctx->tcA.d,
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
                   ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
-                  ctx->d_Pb, ctx->d_Px};
+                  ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -559,7 +592,8 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
       cudaFree(*p);
       *p = nullptr;
     }
-    float** d32[] = {&ctx->d_rel32, &ctx->d_N32, &ctx->d_W32, &ctx->d_sig32, &ctx->d_chi, &ctx->d_clo};
+    float** d32[] = {&ctx->d_rel32, &ctx->d_N32, &ctx->d_W32, &ctx->d_sig32, &ctx->d_chi, &ctx->d_clo,
+                     &ctx->d_fcoef32};
     for (auto p : d32) {
       cudaFree(*p);
       *p = nullptr;
@@ -590,7 +624,8 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
       float** p;
       size_t n;
     } a32[] = {{&ctx->d_rel32, 3 * (size_t)NP}, {&ctx->d_N32, 3 * (size_t)NP}, {&ctx->d_W32, (size_t)NP},
-               {&ctx->d_sig32, 3 * (size_t)NP}, {&ctx->d_chi, 3 * (size_t)n}, {&ctx->d_clo, 3 * (size_t)n}};
+               {&ctx->d_sig32, 3 * (size_t)NP}, {&ctx->d_chi, 3 * (size_t)n}, {&ctx->d_clo, 3 * (size_t)n},
+               {&ctx->d_fcoef32, (size_t)n * E * sps::kFieldsK * 2}};
     for (auto& e : a32) {
       c = 0;
       SPS_TRY(sps_grow(ctx, e.p, c, e.n));
@@ -647,11 +682,13 @@ extern "C" int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Initial guesses from earlier solves with the same operator (one geometry,
-// inside one collision step): an orthonormal basis Pb of earlier right-hand
-// sides and the matching combinations Px of their solutions (A Px_k ~ Pb_k).
-// For a new b the guess x0 = Px (Pb^T b) leaves the residual b - Pb Pb^T b,
-// the smallest over combinations of the earlier solutions.  Every solve still
-// runs GMRES to gmres_tol; only its starting point changes.
+// inside one collision step): an orthonormal basis Pb of the products A x of
+// earlier solutions and the matching combinations Px of those solutions
+// (A Px_k = Pb_k to rounding; GMRES returns A x from its Arnoldi relation).
+// For a new b the guess x0 = Px (Pb^T b) has the residual b - Pb Pb^T b, the
+// smallest over combinations of the earlier solutions, known without an
+// application of A.  Every solve still runs GMRES to gmres_tol; only its
+// starting point changes.
 // ---------------------------------------------------------------------------
 constexpr int kProjMax = 16;
 
@@ -669,20 +706,26 @@ static int proj_ensure(sps_ctx* ctx, long long n) {
   return SPS_OK;
 }
 
-static int proj_guess(sps_ctx* ctx, const double* b, double* x, bool* used) {
+// x = Px Pb^T b and r = b - Pb Pb^T b (= b - A x)
+static int proj_guess(sps_ctx* ctx, const double* b, double* x, double* r, bool* used) {
   *used = false;
   const int m = ctx->proj_m;
   const long long n = 3LL * ctx->NP;
   if (!ctx->proj_on || m == 0 || ctx->proj_n != n) return SPS_OK;
   SPS_TRY(ensure_gmres(ctx, n, ctx->prm.gmres_max));
   SPS_TRY(multidot_dev(ctx, ctx->d_Pb, n, m, b, n, ctx->d_h, ctx->d_red));
+  SPS_CUDA(ctx, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, ctx->d_Px, n, m, ctx->d_h, 0, x); }
-  SPS_LAUNCHED(ctx);
+  k_combine<<<gblocks(n), 256, 0, ctx->stream>>>(n, ctx->d_Px, n, m, ctx->d_h, 0, x);
+  k_sub_proj<<<gblocks(n), 256, 0, ctx->stream>>>(n, ctx->d_Pb, n, m, ctx->d_h, r); }
+  ctx->launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return sps_fail(ctx, SPS_ERR_CUDA, cudaGetErrorString(e));
   *used = true;
   return SPS_OK;
 }
 
+// adds the pair (b, x) with b = A x
 static int proj_add(sps_ctx* ctx, const double* b, const double* x) {
   if (!ctx->proj_on) return SPS_OK;
   const long long n = 3LL * ctx->NP;
@@ -732,7 +775,9 @@ static int proj_add(sps_ctx* ctx, const double* b, const double* x) {
   }
   double nn = 0.0;
   SPS_TRY(sps_dot(ctx, pb, pb, n, &nn));
-  if (!(nn > 1e-20 * bb) || !std::isfinite(nn)) return SPS_OK;   // b already in the span
+  // b (nearly) in the span already: normalising what is left would amplify
+  // the rounding of A Px = Pb
+  if (!(nn > 1e-12 * bb) || !std::isfinite(nn)) return SPS_OK;
   const double inv = 1.0 / std::sqrt(nn);
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
   k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, inv, pb, 0.0, nullptr, pb);
@@ -764,23 +809,40 @@ struct ProjScope {
 
 // zeta: the density unknown of eq. rigidbodyrho for this solve; with warm it
 // holds an initial guess on entry (a previous solution for similar forces).
+// SPS_MU_FORM: zeta holds mu = rho + zeta instead, the solution of
+// (I/2 + K + L)[mu] = L[rho]; since (I/2 + K + L)[rho] - (I/2 + K)[rho] =
+// L[rho] this is the same discrete solve, with a right-hand side that needs
+// only the sphere moments of rho instead of a traction application.
+#ifndef SPS_MU_FORM
+#define SPS_MU_FORM 1
+#endif
 static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats* st, double* zeta,
                           bool warm) {
   const long long n = 3LL * ctx->NP;
   const bool mixed = ctx->prm.precision == SPS_MIXED;
   const bool refine = mixed && ctx->prm.ir_tol > 0;
   SPS_TRY(sps_launch_rho(ctx, FT, ctx->d_rho));
+#if SPS_MU_FORM
+  // b = L[rho]: the unknown is mu = rho + zeta, (I/2 + K + L)[mu] = L[rho]
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_b, 0, sizeof(double) * n, ctx->stream));
+  SPS_TRY(sps_launch_moments(ctx, ctx->d_rho, ctx->d_mom));
+  SPS_TRY(sps_launch_add_L(ctx, ctx->d_mom, ctx->d_b));
+#else
   // b = -(I/2 + K)[rho]
   SPS_TRY(sps_layer(ctx, SPS_OP_K, ctx->d_rho, ctx->d_tmp3, mixed && !refine));
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
   k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, -0.5, ctx->d_rho, -1.0, ctx->d_tmp3, ctx->d_b); }
   SPS_LAUNCHED(ctx);
+#endif
   int its = 0;
   double res = 0.0;
   bool projected = false;
-  SPS_TRY(proj_guess(ctx, ctx->d_b, zeta, &projected));
+  // with refinement the stored pairs would not match the refined solutions:
+  // the projection then stays off
+  if (!refine) SPS_TRY(proj_guess(ctx, ctx->d_b, zeta, ctx->d_r, &projected));
+  // A zeta lands in d_u (free until the velocity is formed)
   int rc = gmres(ctx, ctx->d_b, zeta, warm || projected, ctx->prm.gmres_tol, ctx->prm.gmres_max, mixed,
-                 &its, &res);
+                 &its, &res, projected ? ctx->d_r : nullptr, (refine || !ctx->proj_on) ? nullptr : ctx->d_u);
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
   int total_its = its;
   double final_res = res;
@@ -812,11 +874,15 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
     if (st) st->ir_sweeps += sweep;
     rc = (final_res < ctx->prm.ir_tol) ? SPS_OK : SPS_ERR_NOT_CONVERGED;
   }
-  if (rc == SPS_OK) SPS_TRY(proj_add(ctx, ctx->d_b, zeta));
+  if (!refine && rc == SPS_OK) SPS_TRY(proj_add(ctx, ctx->d_u, zeta));
   // u = S[rho + zeta]
+#if SPS_MU_FORM
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_tmp3, zeta, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+#else
   { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
   k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_rho, 1.0, zeta, ctx->d_tmp3); }
   SPS_LAUNCHED(ctx);
+#endif
   SPS_TRY(sps_layer(ctx, SPS_OP_S, ctx->d_tmp3, ctx->d_u, mixed && !refine));
   SPS_TRY(sps_launch_moments(ctx, ctx->d_u, ctx->d_mom));
   SPS_TRY(sps_launch_extract(ctx, ctx->d_mom, UO));
@@ -833,11 +899,13 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
 static void stats_begin(sps_ctx* ctx, sps_stats* st, long long* l0) {
   if (st) std::memset(st, 0, sizeof(*st));
   *l0 = ctx->launches;
+  ctx->stats_layer0 = ctx->layer_applies;
 }
 static int stats_end(sps_ctx* ctx, sps_stats* st, long long l0, int rc) {
   if (st) {
     st->status = rc;
     st->kernel_launches = ctx->launches - l0;
+    st->layer_applies = (int)(ctx->layer_applies - ctx->stats_layer0);
     st->n_near_pairs = ctx->n_near;
   }
   return rc;

@@ -248,8 +248,18 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
     for (int n = m; n <= L; ++n, ++e) {
       const C* cf = cf0 + e * F * 2;
 #pragma unroll
-      for (int f = 0; f < F; ++f)
-        acc[f] = fma((T)cf[2 * f], hre, fma(-(T)cf[2 * f + 1], him, acc[f]));
+      for (int f = 0; f < F; ++f) {
+        T cre, cim;
+        if constexpr (sizeof(C) == 4) {   // FP32 coefficients: one 8-byte load per field
+          const float2 v = reinterpret_cast<const float2*>(cf)[f];
+          cre = v.x;
+          cim = v.y;
+        } else {
+          cre = (T)cf[2 * f];
+          cim = (T)cf[2 * f + 1];
+        }
+        acc[f] = fma(cre, hre, fma(-cim, him, acc[f]));
+      }
       const T f1 = (T)(2 * n + 1) * z, f2 = (T)(n * n - m * m);
       const T nre = -(f1 * hre + f2 * pre) * ir2, nim = -(f1 * him + f2 * pim) * ir2;
       pre = hre;
@@ -258,7 +268,7 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
       him = nim;
     }
   }
-  if (F == sps::kFieldsK) {
+  if constexpr (F == sps::kFieldsK) {
     // Hessians: [xx, xy, xz, yy, yz, zz]
     const T* HA = acc;
     const T* HD = acc + 6;
@@ -357,6 +367,85 @@ __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict
   }
 }
 
+// Mixed-precision near field: k_near_eval with FP32 field coefficients
+// (staged as float2), the target's position in the source frame formed in
+// FP32 from per-source values computed once per block, and compensated FP32
+// sums per target.  Entries closer than kCloseRadius source radii belong to
+// k_near_close: the FP32 distance decides where it is clear by a wide
+// margin, the close list's own FP64 test inside the margin, so the two
+// kernels split the entries exactly as the list does.
+template <int F>
+__global__ void k_near_eval32(int N, int P, int L, int E, const double* __restrict__ pos,
+                              const double* __restrict__ rad, const double* __restrict__ X,
+                              const double* __restrict__ Nr, const int* __restrict__ near_ptr,
+                              const int* __restrict__ near_idx, const float* __restrict__ fcoef,
+                              double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  float2* sc2 = reinterpret_cast<float2*>(sraw);
+  __shared__ float s_geo[5];   // (c_i - c_j) / a_j, 1 / a_j, a_j
+  __shared__ double s_iad;     // 1 / a_j in FP64
+  const int i = blockIdx.x;
+  const long long NP = (long long)N * P;
+  const int k = threadIdx.x;
+  const bool valid = k < P;
+  const long long g = (long long)i * P + (valid ? k : 0);
+  const double ci0 = pos[3 * i], ci1 = pos[3 * i + 1], ci2 = pos[3 * i + 2];
+  const float lx = (float)(X[g] - ci0), ly = (float)(X[NP + g] - ci1), lz = (float)(X[2 * NP + g] - ci2);
+  float vx = 0.f, vy = 0.f, vz = 0.f;
+  if (F == sps::kFieldsK) {
+    vx = (float)Nr[g];
+    vy = (float)Nr[NP + g];
+    vz = (float)Nr[2 * NP + g];
+  }
+  const double lim = sps::kCloseRadius * sps::kCloseRadius;
+  const float lo = (float)(lim * (1.0 - 1e-4)), hi = (float)(lim * (1.0 + 1e-4));
+  float ox = 0.f, oy = 0.f, oz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;   // sums, compensations
+  auto kadd = [](float& sum, float& c, float v) {
+    const float y = v - c, t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+  };
+  for (int q = near_ptr[i]; q < near_ptr[i + 1]; ++q) {
+    const int j = near_idx[q];
+    __syncthreads();
+    const float2* src = reinterpret_cast<const float2*>(fcoef + (long long)j * E * F * 2);
+    for (int e = threadIdx.x; e < E * F; e += blockDim.x) sc2[e] = src[e];
+    if (threadIdx.x == 0) {
+      const double aj = rad[j], ia = 1.0 / aj;
+      s_geo[0] = (float)((ci0 - pos[3 * j]) * ia);
+      s_geo[1] = (float)((ci1 - pos[3 * j + 1]) * ia);
+      s_geo[2] = (float)((ci2 - pos[3 * j + 2]) * ia);
+      s_geo[3] = (float)ia;
+      s_geo[4] = (float)aj;
+      s_iad = ia;
+    }
+    __syncthreads();
+    const float ia = s_geo[3];
+    const float x = fmaf(lx, ia, s_geo[0]), y = fmaf(ly, ia, s_geo[1]), z = fmaf(lz, ia, s_geo[2]);
+    const float r2 = x * x + y * y + z * z;
+    if (r2 < hi) {
+      if (r2 < lo) continue;
+      if (sps_close_r2(pos, s_iad, X[g], X[NP + g], X[2 * NP + g], j) < lim) continue;
+    }
+    float tx, ty, tz;
+    near_contrib<F, float, float>(reinterpret_cast<const float*>(sc2), L, x, y, z, vx, vy, vz, tx, ty, tz);
+    if (F == sps::kFieldsS) {
+      const float aj = s_geo[4];
+      tx *= aj;
+      ty *= aj;
+      tz *= aj;
+    }
+    kadd(ox, ex, tx);
+    kadd(oy, ey, ty);
+    kadd(oz, ez, tz);
+  }
+  if (valid) {
+    out[g] += (double)ox - (double)ex;
+    out[NP + g] += (double)oy - (double)ey;
+    out[2 * NP + g] += (double)oz - (double)ez;
+  }
+}
+
 // FP64 near entries of the mixed path: one thread per close node, its close
 // source spheres in near-list order (coefficients read through the cache).
 template <int F>
@@ -414,6 +503,21 @@ int launch_near_eval(sps_ctx* ctx, double skip_r2, double* out) {
 }
 
 template <int F>
+int launch_near_eval32(sps_ctx* ctx, double* out) {
+  const int N = ctx->N, P = ctx->T.P, L = ctx->T.L, E = ctx->T.E;
+  const int threads = ((P + 31) / 32) * 32;
+  const size_t sm = sizeof(float) * E * F * 2;
+  if (sm > 48 * 1024)
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_eval32<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm));
+  k_near_eval32<F><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
+                                                     ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
+                                                     ctx->d_fcoef32, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+template <int F>
 int launch_near_close(sps_ctx* ctx, double* out) {
   if (ctx->n_close == 0) return SPS_OK;
   k_near_close<F><<<(ctx->n_close + 63) / 64, 64, 0, ctx->stream>>>(
@@ -424,9 +528,11 @@ int launch_near_close(sps_ctx* ctx, double* out) {
 }
 
 // out[s][r] (+)= sum over row r of a sparse map applied to in[s][:]
+// (out32: the result rounded to FP32, same layout)
 __global__ void k_sparse_rows(int N, int rows, const int* __restrict__ rp, const int* __restrict__ ci,
                               const double* __restrict__ val, const double* __restrict__ in, int in_ld,
-                              double* __restrict__ out, int out_ld, int accumulate) {
+                              double* __restrict__ out, int out_ld, int accumulate,
+                              float* __restrict__ out32) {
   const long long tot = (long long)N * rows;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
        q += (long long)gridDim.x * blockDim.x) {
@@ -436,16 +542,17 @@ __global__ void k_sparse_rows(int N, int rows, const int* __restrict__ rp, const
     for (int k = rp[r]; k < rp[r + 1]; ++k) acc = fma(val[k], x[ci[k]], acc);
     double* y = out + (long long)s * out_ld + r;
     *y = accumulate ? *y + acc : acc;
+    if (out32) out32[(long long)s * out_ld + r] = (float)acc;
   }
 }
 
 }  // namespace
 
 int sps_launch_sparse_rows(sps_ctx* ctx, const sps_ctx::Sparse& m, int nsph, const double* in, int in_ld,
-                           double* out, int out_ld, int accumulate) {
+                           double* out, int out_ld, int accumulate, float* out32) {
   const long long tot = (long long)nsph * m.rows;
   k_sparse_rows<<<(int)std::min<long long>((tot + 255) / 256, 8 * 152), 256, 0, ctx->stream>>>(
-      nsph, m.rows, m.rp, m.ci, m.v, in, in_ld, out, out_ld, accumulate);
+      nsph, m.rows, m.rp, m.ci, m.v, in, in_ld, out, out_ld, accumulate, accumulate ? nullptr : out32);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -578,7 +685,8 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
     SpsPhase timer(ctx, SPS_PH_SELF);
     // field coefficients of every source sphere: fcoef_s = FM coef_s (sparse)
     const sps_ctx::Sparse& fm = S ? ctx->fmS : ctx->fmK;
-    SPS_TRY(sps_launch_sparse_rows(ctx, fm, N, ctx->d_coef, NR, ctx->d_fcoef, fm.rows, 0));
+    SPS_TRY(sps_launch_sparse_rows(ctx, fm, N, ctx->d_coef, NR, ctx->d_fcoef, fm.rows, 0,
+                                   fp32 ? ctx->d_fcoef32 : nullptr));
     (void)NC;
     (void)L;
     (void)E;
@@ -587,14 +695,13 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
   SpsPhase timer(ctx, S ? SPS_PH_NEAR_S : SPS_PH_NEAR_K);
   // mixed path: FP32 for near entries farther than kCloseRadius source radii,
   // FP64 for the close ones (where the expansion's terms do not decay)
-  const double skip = fp32 ? sps::kCloseRadius * sps::kCloseRadius : 0.0;
   if (S) {
     if (!fp32) return launch_near_eval<sps::kFieldsS, double>(ctx, 0.0, out);
-    SPS_TRY((launch_near_eval<sps::kFieldsS, float>(ctx, skip, out)));
+    SPS_TRY(launch_near_eval32<sps::kFieldsS>(ctx, out));
     return launch_near_close<sps::kFieldsS>(ctx, out);
   }
   if (!fp32) return launch_near_eval<sps::kFieldsK, double>(ctx, 0.0, out);
-  SPS_TRY((launch_near_eval<sps::kFieldsK, float>(ctx, skip, out)));
+  SPS_TRY(launch_near_eval32<sps::kFieldsK>(ctx, out));
   return launch_near_close<sps::kFieldsK>(ctx, out);
 }
 
@@ -605,6 +712,7 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
 #define SPS_MIXED_NEAR 1
 #endif
 int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32) {
+  ctx->layer_applies += 1;
   SPS_TRY(sps_launch_analysis(ctx, sig, fp32 && SPS_MIXED_VSH));
   SPS_TRY(sps_launch_self(ctx, op, sig, out, fp32 && SPS_MIXED_VSH));
   const int kop = (op == SPS_OP_S) ? SPS_OP_S : SPS_OP_K;
