@@ -124,6 +124,8 @@ def workload(name):
     if name.startswith("cfg5"):
         _, N, p = name.split("_")
         return workloads.config5(int(N), int(p))
+    if name == "sed":
+        return workloads.sedimenting_cluster()
     raise ValueError(name)
 
 
@@ -202,7 +204,12 @@ def run_gpu(args, w):
         dist.init_process_group("nccl")
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    ctx = sps.Context(stream=stream, **ctx_params(args.precision))
+    prm = ctx_params(args.precision)
+    if w.name.startswith("sed"):
+        # the sedimenting cluster of Sec. 6.3 with the paper's own settings:
+        # threshold 30% of the sum of the radii, eps_tol = 1e-4
+        prm.update({k: w.params[k] for k in ("delta", "delta_rel", "bbpgd_tol")})
+    ctx = sps.Context(stream=stream, **prm)
     pos = dev(w.centers)
     rad = dev(w.radii)
     FT = dev(w.FT)
@@ -340,6 +347,7 @@ def run_gpu(args, w):
             "data": "synthetic",
             "config": {"workload": w.name, "N": N, "p": w.p, "nodes": NP, "precision": args.precision,
                        "gmres_tol": ctx.prm.gmres_tol, "bbpgd_tol": ctx.prm.bbpgd_tol,
+                       "delta": ctx.prm.delta, "delta_rel": ctx.prm.delta_rel,
                        "a_c_scale": ctx.prm.a_c_scale, "bbpgd_max": ctx.prm.bbpgd_max,
                        "dt": w.dt, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},

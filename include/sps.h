@@ -93,6 +93,11 @@ typedef struct sps_params {
                          1 keeps the previous step length and continues       */
   int mobility;       /* sps_mobility (default SPS_MOB_BIE)                   */
   int contact_search; /* sps_contact_search (default SPS_SEARCH_AUTO)         */
+  double delta_rel;   /* relative part of the contact threshold: a pair is in
+                         the set when Phi <= delta + delta_rel (a_i + a_j)
+                         (a: sphere radii, not collision radii).  Sec. 3.2
+                         sets delta to 30% of the sum of the radii: delta = 0,
+                         delta_rel = 0.3.  Default 0.                        */
 } sps_params;
 
 typedef struct sps_stats {
@@ -188,6 +193,17 @@ int sps_mobility_apply(sps_ctx* ctx, int n, const double* pos, const double* rad
 int sps_resolve_collisions(sps_ctx* ctx, int n, const double* pos, const double* radii,
                            const double* FT_ext, double dt, double* gamma, int gamma_cap,
                            double* UO, double* pos_out, sps_stats* stats);
+
+/* `steps` collision-resolved steps of sps_resolve_collisions in a row, the
+ * positions advanced in place: pos (n x 3, device) is read and overwritten
+ * with the positions after each step; FT_ext (n x 6) acts at every step; UO
+ * (n x 6) receives the velocities of the last step.  stats_per_step: HOST
+ * array of `steps` sps_stats or NULL.  Stops at the first step whose status
+ * is not SPS_OK and returns it; *steps_done (host, may be NULL) counts the
+ * completed steps.  The multi-step workloads of Sec. 6 (for instance the
+ * sedimenting cluster of Sec. 6.3) are this loop. */
+int sps_simulate(sps_ctx* ctx, int n, double* pos, const double* radii, const double* FT_ext,
+                 double dt, int steps, double* UO, sps_stats* stats_per_step, int* steps_done);
 
 /* Same step with HOST arrays: copies the inputs to the device, runs the step
  * and copies gamma, UO and pos_out back (stream ordered, synchronised before

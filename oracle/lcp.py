@@ -6,8 +6,10 @@ Paper: Yan et al., arXiv 1909.06623.
   * Sec. 3.2: the constraint set A(C, delta) = {pairs with Phi <= delta}.
     Phi_ij = |c_i - c_j| - R_i - R_j for spheres, with R the collision radius
     a_c (Sec. 6.1 sets a_c slightly above a).  Readings: delta is an absolute
-    distance (the workloads quote "contact cutoff 0.1"; the paper's own choice,
-    30% of R_i + R_j, is a caller option); pairs i < j sorted by (i, j);
+    distance (the workloads quote "contact cutoff 0.1").  The paper's own
+    choice, 30% of the sum of the radii, is the option delta_rel: the pair's
+    threshold is delta + delta_rel (a_i + a_j), a the sphere radii (not the
+    collision radii), evaluated in that order; pairs i < j sorted by (i, j);
     d^2 = (dx dx + dy dy) + dz dz evaluated without fused multiply-add, so the
     list is reproducible to the bit.
   * eq. Dmatdef / Dtranspose: column D_l carries -n_l on sphere i's force and
@@ -33,10 +35,11 @@ from . import mobility
 from .layer import Suspension
 
 
-def build_contacts(centers, radii, delta, a_c_scale=1.0):
+def build_contacts(centers, radii, delta, a_c_scale=1.0, delta_rel=0.0):
     """Contact list (Sec. 3.2): ij (n_c x 2, i < j), Phi (n_c), normals (n_c x 3)."""
     c = np.asarray(centers, dtype=np.float64).reshape(-1, 3)
-    R = np.asarray(radii, dtype=np.float64).reshape(-1) * a_c_scale
+    a = np.asarray(radii, dtype=np.float64).reshape(-1)
+    R = a * a_c_scale
     ij, ph, nr = [], [], []
     N = len(R)
     for i in range(N):
@@ -48,7 +51,7 @@ def build_contacts(centers, radii, delta, a_c_scale=1.0):
             d2 = (dx * dx + dy * dy) + dz * dz
             d = np.sqrt(d2)
             phi = (d - R[i]) - R[j]
-            if phi <= delta:
+            if phi <= delta + delta_rel * (a[i] + a[j]):
                 ij.append((i, j))
                 ph.append(phi)
                 nr.append((dx / d, dy / d, dz / d))
@@ -140,7 +143,8 @@ def lcp_enumerate(Mmat, q):
 
 def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
                        a_c_scale=1.0, gmres_tol=1e-12, gmres_max=200,
-                       bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False):
+                       bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
+                       delta_rel=0.0):
     """One collision-resolved Euler step (Sec. 3.2, four-step procedure).
 
     1. U_nc = M F_ext; 2. contacts and D; 3. BBPGD for gamma with
@@ -149,7 +153,7 @@ def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
     """
     sus = Suspension(centers, radii, p, beta)
     U_nc, inf0 = mobility.mobility_apply(sus, FT_ext, gmres_tol, gmres_max, return_info=True)
-    ij, phi0, nrm = build_contacts(centers, radii, delta, a_c_scale)
+    ij, phi0, nrm = build_contacts(centers, radii, delta, a_c_scale, delta_rel)
     q = phi0 / dt + DT_apply(ij, nrm, U_nc)
     state = {"U_c": np.zeros_like(U_nc), "solves": 1, "gmres": inf0["gmres_iters"]}
 
@@ -177,7 +181,7 @@ def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
 # ----------------------------------------------------------------------------
 # Large contact sets: one sphere's row, vectorised D / D^T, identity mobility
 # ----------------------------------------------------------------------------
-def contacts_of_sphere(centers, radii, i, delta, a_c_scale=1.0):
+def contacts_of_sphere(centers, radii, i, delta, a_c_scale=1.0, delta_rel=0.0):
     """Row i of the contact set of Sec. 3.2: every j > i with Phi_ij <= delta.
 
     The same arithmetic as build_contacts, element-wise over all j at once
@@ -191,7 +195,7 @@ def contacts_of_sphere(centers, radii, i, delta, a_c_scale=1.0):
     dz = cj[:, 2] - c[i, 2]
     d = np.sqrt((dx * dx + dy * dy) + dz * dz)
     phi = (d - a[i] * a_c_scale) - a[i + 1:] * a_c_scale
-    k = np.nonzero(phi <= delta)[0]
+    k = np.nonzero(phi <= delta + delta_rel * (a[i] + a[i + 1:]))[0]
     nrm = np.stack([dx[k] / d[k], dy[k] / d[k], dz[k] / d[k]], axis=1)
     return (k + i + 1).astype(np.int64), phi[k], nrm
 
@@ -213,7 +217,8 @@ def DT_apply_vec(ij, nrm, UO):
 
 
 def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_scale=1.0,
-                                bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False):
+                                bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
+                                delta_rel=0.0):
     """The collision step of Sec. 3.2 with the mobility replaced by the
     identity (U = F, Omega = T).  No fluid: M = D^T D is the constraint Gram
     matrix, which isolates contacts, D products and Algorithm 1 at sizes where
@@ -221,7 +226,7 @@ def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_sc
     C = np.asarray(centers, dtype=np.float64)
     FT_ext = np.asarray(FT_ext, dtype=np.float64).reshape(-1, 6)
     N = len(C)
-    ij, phi0, nrm = build_contacts(C, radii, delta, a_c_scale)
+    ij, phi0, nrm = build_contacts(C, radii, delta, a_c_scale, delta_rel)
     U_nc = FT_ext.copy()
     q = phi0 / dt + DT_apply(ij, nrm, U_nc)
     state = {"U_c": np.zeros_like(U_nc)}

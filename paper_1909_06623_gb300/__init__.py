@@ -229,6 +229,24 @@ class Context:
         self.n_c = st.n_contacts          # the contact list stays in the context
         return gamma[: st.n_contacts], UO, pos_out
 
+    def simulate(self, pos, radii, FT_ext, dt, steps, UO=None, allow=()):
+        """`steps` collision-resolved steps (sps_simulate); pos (n x 3, CUDA,
+        float64) is advanced in place.  Returns (pos, UO of the last step,
+        list of per-step stats dicts)."""
+        n = radii.numel()
+        if UO is None:
+            UO = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        stats = (sps_stats * max(steps, 1))()
+        done = ctypes.c_int()
+        rc = self.lib.sps_simulate(self.h, n, _ptr(pos), _ptr(radii), _ptr(FT_ext), float(dt),
+                                   int(steps), _ptr(UO), stats, ctypes.byref(done))
+        self._check(rc, allow=allow)
+        out = [stats[k].as_dict() for k in range(done.value)]
+        if out:
+            self.last_stats = out[-1]
+            self.n_c = out[-1]["n_contacts"]
+        return pos, UO, out
+
     def resolve_collisions_host(self, pos, radii, FT_ext, dt, gamma, UO, pos_out, allow=()):
         """Same step on host (CPU, ideally pinned) tensors; copies happen inside."""
         n = radii.numel()

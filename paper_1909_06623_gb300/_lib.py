@@ -27,7 +27,8 @@ class sps_params(ctypes.Structure):
                 ("bbpgd_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bb_variant", ctypes.c_int), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("bb_safeguard", ctypes.c_int),
-                ("mobility", ctypes.c_int), ("contact_search", ctypes.c_int)]
+                ("mobility", ctypes.c_int), ("contact_search", ctypes.c_int),
+                ("delta_rel", ctypes.c_double)]
 
 
 class sps_stats(ctypes.Structure):
@@ -74,6 +75,8 @@ SIGNATURES = {
                                    ctypes.POINTER(sps_stats)]),
     "sps_build_contacts_noalloc": (_I, [_I, _P, _P, _D, _D, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "sps_profile_read": (_I, [_P, _P, _P]),
+    "sps_simulate": (_I, [_P, _I, _P, _P, _P, _D, _I, _P, ctypes.POINTER(sps_stats),
+                          ctypes.POINTER(_I)]),
 }
 
 _lib = None

@@ -31,21 +31,21 @@ constexpr int kBoundBlocks = 2 * 152;
 inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
 __device__ __forceinline__ bool contact_at(const double* pos, const double* rad, double acs,
-                                           double delta, int i, int j, SpsContactGeom* g) {
+                                           double delta, double drel, int i, int j, SpsContactGeom* g) {
   return sps_contact_test(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], rad[i], pos[3 * j],
-                          pos[3 * j + 1], pos[3 * j + 2], rad[j], acs, delta, g);
+                          pos[3 * j + 1], pos[3 * j + 2], rad[j], acs, delta, drel, g);
 }
 
 // ---------------------------------------------------------------------------
 // all pairs
 // ---------------------------------------------------------------------------
 __global__ void k_pairs_count(int N, const double* pos, const double* rad, double acs, double delta,
-                              int* cnt, int* cnt2) {
+                              double drel, int* cnt, int* cnt2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int c = 0;
   for (int j = i + 1; j < N; ++j)
-    if (contact_at(pos, rad, acs, delta, i, j, nullptr)) {
+    if (contact_at(pos, rad, acs, delta, drel, i, j, nullptr)) {
       ++c;
       atomicAdd(&cnt2[j], 1);   // integer count of contacts where j is second
     }
@@ -53,12 +53,12 @@ __global__ void k_pairs_count(int N, const double* pos, const double* rad, doubl
 }
 
 __global__ void k_pairs_fill(int N, const double* pos, const double* rad, double acs, double delta,
-                             const int* ptr, int* ij) {
+                             double drel, const int* ptr, int* ij) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int o = ptr[i];
   for (int j = i + 1; j < N; ++j)
-    if (contact_at(pos, rad, acs, delta, i, j, nullptr)) {
+    if (contact_at(pos, rad, acs, delta, drel, i, j, nullptr)) {
       ij[2 * o] = i;
       ij[2 * o + 1] = j;
       ++o;
@@ -75,7 +75,7 @@ __global__ void k_contact_geom(int nc, const int* __restrict__ ij, const double*
   const int i = ij[2 * l], j = ij[2 * l + 1];
   SpsContactGeom g;
   // delta = +inf: the same rounded operations, and the geometry is always written
-  contact_at(pos, rad, acs, INFINITY, i, j, &g);
+  contact_at(pos, rad, acs, INFINITY, 0.0, i, j, &g);
   phi[l] = g.phi;
   nrm[3 * l + 0] = g.nx;
   nrm[3 * l + 1] = g.ny;
@@ -184,15 +184,16 @@ __global__ void k_cl_gather(int N, const int* __restrict__ id, const double* __r
 // Visits every sphere j > i in the 27 cells around sorted position k that can
 // satisfy the contact test; f(i, j) is called for each pair that passes it.
 // The FP32 screen decides a pair when its FP32 distance is clearly above
-// (a_c,i + a_c,j + delta)(1 + 1e-5) + eps or clearly below
-// (a_c,i + a_c,j + delta)(1 - 1e-5) - eps, eps bounding the rounding of the
+// (a_c,i + a_c,j + delta_l)(1 + 1e-5) + eps or clearly below
+// (a_c,i + a_c,j + delta_l)(1 - 1e-5) - eps, eps bounding the rounding of the
 // FP32 coordinates; only pairs in that band take the FP64 test, so every
 // decision equals the FP64 test's.
 template <class F>
 __device__ __forceinline__ void cl_scan(int k, const int* __restrict__ key, const int* __restrict__ id,
                                         const float4* __restrict__ cf, const double4_32a* __restrict__ cd,
                                         const int* __restrict__ start, const CellGrid& G, float acsf,
-                                        float deltaf, double acs, double delta, F f) {
+                                        float deltaf, float drelf, double acs, double delta,
+                                        double drel, F f) {
   const int i = id[k];
   const float4 me = cf[k];
   const double4_32a md = cd[k];
@@ -209,7 +210,7 @@ __device__ __forceinline__ void cl_scan(int k, const int* __restrict__ key, cons
         const float4 o = cf[m];
         const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float tn = fmaf(acsf, me.w + o.w, deltaf);
+        const float tn = fmaf(acsf + drelf, me.w + o.w, deltaf);
         const float hi = fmaf(tn, 1.00001f, G.eps);
         if (d2 > hi * hi) continue;                   // certainly apart
         const float lo = fmaf(tn, 0.99999f, -G.eps);
@@ -218,7 +219,7 @@ __device__ __forceinline__ void cl_scan(int k, const int* __restrict__ key, cons
           continue;
         }
         const double4_32a od = cd[m];                 // near the threshold: FP64 test
-        if (sps_contact_test(md.x, md.y, md.z, md.w, od.x, od.y, od.z, od.w, acs, delta, nullptr))
+        if (sps_contact_test(md.x, md.y, md.z, md.w, od.x, od.y, od.z, od.w, acs, delta, drel, nullptr))
           f(i, j);
       }
     }
@@ -229,12 +230,13 @@ __global__ void __launch_bounds__(kThreads) k_cl_count(int N, const int* __restr
                                                       const float4* __restrict__ cf,
                                                       const double4_32a* __restrict__ cd,
                                                       const int* __restrict__ start, CellGrid G,
-                                                      double acs, double delta, int* __restrict__ cnt,
-                                                      int* __restrict__ cnt2) {
+                                                      double acs, double delta, double drel,
+                                                      int* __restrict__ cnt, int* __restrict__ cnt2) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   int c = 0;
-  cl_scan(k, key, id, cf, cd, start, G, (float)acs, (float)delta, acs, delta, [&](int, int j) {
+  cl_scan(k, key, id, cf, cd, start, G, (float)acs, (float)delta, (float)drel, acs, delta, drel,
+          [&](int, int j) {
     ++c;
     atomicAdd(&cnt2[j], 1);
   });
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_cl_fill(int N, const int* __restri
                                                      const float4* __restrict__ cf,
                                                      const double4_32a* __restrict__ cd,
                                                      const int* __restrict__ start, CellGrid G,
-                                                     double acs, double delta,
+                                                     double acs, double delta, double drel,
                                                      const int* __restrict__ ptr, int* __restrict__ ij) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -256,7 +258,8 @@ __global__ void __launch_bounds__(kThreads) k_cl_fill(int N, const int* __restri
   int o = o0;
   // the count pass applied the same predicate, so the row fills [o0, oe)
   // exactly; the bound only keeps every store inside the row regardless
-  cl_scan(k, key, id, cf, cd, start, G, (float)acs, (float)delta, acs, delta, [&](int, int j) {
+  cl_scan(k, key, id, cf, cd, start, G, (float)acs, (float)delta, (float)drel, acs, delta, drel,
+          [&](int, int j) {
     if (o < oe) ij[2 * o + 1] = j;
     ++o;
   });
@@ -571,7 +574,7 @@ int cub_scratch(sps_ctx* ctx, size_t bytes) {
 // cell-list counts: cnt (as first sphere), cnt2 (as second) for n spheres
 int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, CellGrid* Gout,
                 int* ncells_out) {
-  const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta;
+  const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta, drel = ctx->prm.delta_rel;
   size_t cp = 0;
   if (!ctx->d_cl_part) SPS_TRY(sps_grow(ctx, &ctx->d_cl_part, cp, (size_t)8 * kBoundBlocks + 8));
   k_cl_bounds<<<kBoundBlocks, kThreads, 0, ctx->stream>>>(n, pos, radii, ctx->d_cl_part);
@@ -585,8 +588,8 @@ int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, Cel
   double b[8];
   std::memcpy(b, ctx->h_pinned, sizeof(b));
   if (b[7] > 0) return sps_fail(ctx, SPS_ERR_NONFINITE, "contacts: positions or radii not finite and positive");
-  // cell side >= 2 max a_c + delta (with a relative margin over rounding)
-  double h = (2.0 * acs * b[6] + delta) * (1.0 + 1e-9);
+  // cell side >= 2 max a_c + max delta_l (with a relative margin over rounding)
+  double h = (2.0 * (acs + drel) * b[6] + delta) * (1.0 + 1e-9);
   const long long cap_cells = std::min<long long>(1LL << 30, std::max<long long>(64, 2LL * n));
   CellGrid G;
   double ext[3], emax = 0.0;
@@ -663,7 +666,7 @@ int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, Cel
                                                       ctx->d_cl_d);
   SPS_LAUNCHED(ctx);
   k_cl_count<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key2, ctx->d_cl_id2, ctx->d_cl_f,
-                                                     ctx->d_cl_d, ctx->d_cl_range, G, acs, delta,
+                                                     ctx->d_cl_d, ctx->d_cl_range, G, acs, delta, drel,
                                                      ctx->d_ccount, ctx->d_ccount2);
   SPS_LAUNCHED(ctx);
   *Gout = G;
@@ -676,7 +679,7 @@ int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, Cel
 int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii) {
   SpsPhase timer(ctx, SPS_PH_CONTACT);
   ctx->order_valid = false;
-  const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta;
+  const double acs = ctx->prm.a_c_scale, delta = ctx->prm.delta, drel = ctx->prm.delta_rel;
   const int search = ctx->prm.contact_search;
   const bool cells = search == SPS_SEARCH_CELLS || (search == SPS_SEARCH_AUTO && n > 4096);
   if ((size_t)n + 1 > ctx->cap_cnt) {
@@ -699,7 +702,7 @@ int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* ra
   if (cells) {
     SPS_TRY(cell_counts(ctx, n, pos, radii, &G, &ncells));
   } else {
-    k_pairs_count<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, ctx->d_ccount,
+    k_pairs_count<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, drel, ctx->d_ccount,
                                                          ctx->d_ccount2);
     SPS_LAUNCHED(ctx);
   }
@@ -742,10 +745,10 @@ int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* ra
   if (nc == 0) return SPS_OK;
   if (cells) {
     k_cl_fill<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key2, ctx->d_cl_id2, ctx->d_cl_f,
-                                                      ctx->d_cl_d, ctx->d_cl_range, G, acs, delta,
+                                                      ctx->d_cl_d, ctx->d_cl_range, G, acs, delta, drel,
                                                       ctx->d_cptr, ctx->d_cij);
   } else {
-    k_pairs_fill<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, ctx->d_cptr,
+    k_pairs_fill<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, drel, ctx->d_cptr,
                                                         ctx->d_cij);
   }
   SPS_LAUNCHED(ctx);

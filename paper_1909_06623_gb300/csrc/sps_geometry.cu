@@ -131,7 +131,7 @@ using ContactGeom = SpsContactGeom;
 __device__ __forceinline__ bool contact(const double* pos, const double* rad, double acs,
                                         double delta, int i, int j, ContactGeom* g) {
   return sps_contact_test(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], rad[i], pos[3 * j],
-                          pos[3 * j + 1], pos[3 * j + 2], rad[j], acs, delta, g);
+                          pos[3 * j + 1], pos[3 * j + 2], rad[j], acs, delta, 0.0, g);
 }
 
 // rho = F/|Gamma| + tau^{-1} T x (x - c), tau = (8 pi/3) a^4 (Sec. 4.1)

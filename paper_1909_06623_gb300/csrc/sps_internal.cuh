@@ -224,21 +224,24 @@ __device__ __forceinline__ double sps_close_r2(const double* pos, double ia, dou
   return x * x + y * y + z * z;
 }
 
-// Contact test of Sec. 3.2 on loaded values: Phi = (d - R_i) - R_j <= delta
-// with R = a_c_scale * a and every operation rounded separately, so that the
-// all-pairs and the cell-list searches produce the same list to the bit.
+// Contact test of Sec. 3.2 on loaded values: Phi = (d - R_i) - R_j <= delta_l
+// with R = a_c_scale * a, delta_l = delta + drel (a_i + a_j) (drel = 0.3 is the
+// paper's 30% of the sum of the radii) and every operation rounded
+// separately, so that the all-pairs and the cell-list searches produce the
+// same list to the bit.
 struct SpsContactGeom {
   double phi, nx, ny, nz;
 };
 __device__ __forceinline__ bool sps_contact_test(double xi, double yi, double zi, double ai, double xj,
                                                  double yj, double zj, double aj, double acs,
-                                                 double delta, SpsContactGeom* g) {
+                                                 double delta, double drel, SpsContactGeom* g) {
   const double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
   const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   const double d = __dsqrt_rn(d2);
   const double Ri = __dmul_rn(ai, acs), Rj = __dmul_rn(aj, acs);
   const double phi = __dsub_rn(__dsub_rn(d, Ri), Rj);
-  if (!(phi <= delta)) return false;
+  const double dl = __dadd_rn(delta, __dmul_rn(drel, __dadd_rn(ai, aj)));
+  if (!(phi <= dl)) return false;
   if (g) {
     g->phi = phi;
     g->nx = __ddiv_rn(dx, d);

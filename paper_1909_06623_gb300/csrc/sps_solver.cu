@@ -1,9 +1,11 @@
 // Context, mobility solve and collision resolution (C ABI of include/sps.h).
 //
-//  * Mobility (Sec. 4.1): rho from F, T; b = -(I/2 + K)[rho]; GMRES on
-//    (I/2 + K + L)[zeta] = b (eq. rigidbodyrho); u = S[rho + zeta] (eq. velS);
-//    U, Omega as averages of u over each sphere.
-//    GMRES: unrestarted, zero initial guess, classical Gram-Schmidt applied
+//  * Mobility (Sec. 4.1): rho from F, T; GMRES on (I/2 + K + L)[mu] = L[rho]
+//    for mu = rho + zeta (eq. rigidbodyrho rearranged: the same discrete
+//    solution, no traction application on its right-hand side);
+//    u = S[rho + zeta] = S[mu] (eq. velS); U, Omega as averages of u over
+//    each sphere.
+//    GMRES: unrestarted, zero or warm initial guess, classical Gram-Schmidt applied
 //    twice, Givens rotations on the host, FP64 everywhere; stop when
 //    ||r|| / ||b|| < gmres_tol.  Mixed precision: the far-field sums run in
 //    FP32 (compensated), the Krylov basis, orthogonalisation and residual in
@@ -439,6 +441,7 @@ extern "C" int sps_default_params(sps_params* o) {
   o->bb_safeguard = 0;
   o->mobility = SPS_MOB_BIE;
   o->contact_search = SPS_SEARCH_AUTO;
+  o->delta_rel = 0.0;
   return SPS_OK;
 }
 
@@ -456,7 +459,7 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
       prm->gmres_max < 1 || !(prm->bbpgd_tol > 0) || prm->bbpgd_max < 1 ||
       (prm->precision != SPS_FP64 && prm->precision != SPS_MIXED) ||
       (prm->bb_variant != 1 && prm->bb_variant != 2) || !(prm->a_c_scale > 0) ||
-      !(prm->delta >= 0) || prm->ir_tol < 0 || prm->ir_max < 0 ||
+      !(prm->delta >= 0) || !(prm->delta_rel >= 0) || !std::isfinite(prm->delta_rel) || prm->ir_tol < 0 || prm->ir_max < 0 ||
       (prm->mobility != SPS_MOB_BIE && prm->mobility != SPS_MOB_IDENTITY) ||
       prm->contact_search < SPS_SEARCH_AUTO || prm->contact_search > SPS_SEARCH_CELLS)
     return SPS_ERR_INVALID_ARG;
@@ -807,33 +810,22 @@ struct ProjScope {
   ~ProjScope() { c->proj_on = false; }
 };
 
-// zeta: the density unknown of eq. rigidbodyrho for this solve; with warm it
-// holds an initial guess on entry (a previous solution for similar forces).
-// SPS_MU_FORM: zeta holds mu = rho + zeta instead, the solution of
-// (I/2 + K + L)[mu] = L[rho]; since (I/2 + K + L)[rho] - (I/2 + K)[rho] =
-// L[rho] this is the same discrete solve, with a right-hand side that needs
-// only the sphere moments of rho instead of a traction application.
-#ifndef SPS_MU_FORM
-#define SPS_MU_FORM 1
-#endif
+// zeta: receives mu = rho + zeta, where zeta is the density unknown of eq.
+// rigidbodyrho; with warm it holds an initial guess on entry (a previous
+// solution for similar forces).  mu solves (I/2 + K + L)[mu] = L[rho]: since
+// (I/2 + K + L)[rho] - (I/2 + K)[rho] = L[rho] this is eq. rigidbodyrho's
+// discrete solve, with a right-hand side that needs only the sphere moments
+// of rho instead of a traction application.  The density of eq. velS is mu.
 static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats* st, double* zeta,
                           bool warm) {
   const long long n = 3LL * ctx->NP;
   const bool mixed = ctx->prm.precision == SPS_MIXED;
   const bool refine = mixed && ctx->prm.ir_tol > 0;
   SPS_TRY(sps_launch_rho(ctx, FT, ctx->d_rho));
-#if SPS_MU_FORM
   // b = L[rho]: the unknown is mu = rho + zeta, (I/2 + K + L)[mu] = L[rho]
   SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_b, 0, sizeof(double) * n, ctx->stream));
   SPS_TRY(sps_launch_moments(ctx, ctx->d_rho, ctx->d_mom));
   SPS_TRY(sps_launch_add_L(ctx, ctx->d_mom, ctx->d_b));
-#else
-  // b = -(I/2 + K)[rho]
-  SPS_TRY(sps_layer(ctx, SPS_OP_K, ctx->d_rho, ctx->d_tmp3, mixed && !refine));
-  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, -0.5, ctx->d_rho, -1.0, ctx->d_tmp3, ctx->d_b); }
-  SPS_LAUNCHED(ctx);
-#endif
   int its = 0;
   double res = 0.0;
   bool projected = false;
@@ -875,14 +867,8 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
     rc = (final_res < ctx->prm.ir_tol) ? SPS_OK : SPS_ERR_NOT_CONVERGED;
   }
   if (!refine && rc == SPS_OK) SPS_TRY(proj_add(ctx, ctx->d_u, zeta));
-  // u = S[rho + zeta]
-#if SPS_MU_FORM
+  // u = S[rho + zeta] = S[mu]
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_tmp3, zeta, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-#else
-  { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
-  k_axpby<<<gblocks(n), 256, 0, ctx->stream>>>(n, 1.0, ctx->d_rho, 1.0, zeta, ctx->d_tmp3); }
-  SPS_LAUNCHED(ctx);
-#endif
   SPS_TRY(sps_layer(ctx, SPS_OP_S, ctx->d_tmp3, ctx->d_u, mixed && !refine));
   SPS_TRY(sps_launch_moments(ctx, ctx->d_u, ctx->d_mom));
   SPS_TRY(sps_launch_extract(ctx, ctx->d_mom, UO));
@@ -1267,6 +1253,26 @@ extern "C" int sps_resolve_collisions(sps_ctx* ctx, int n, const double* pos, co
   stats_begin(ctx, st, &l0);
   const int rc = resolve_any(ctx, n, pos, radii, FT_ext, dt, gamma, gamma_cap, UO, pos_out, st);
   return stats_end(ctx, st, l0, rc);
+}
+
+extern "C" int sps_simulate(sps_ctx* ctx, int n, double* pos, const double* radii, const double* FT_ext,
+                            double dt, int steps, double* UO, sps_stats* stats_per_step, int* steps_done) {
+  if (!ctx || n < 1 || !pos || !radii || !FT_ext || !UO || steps < 0)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "simulate: bad argument");
+  if (steps_done) *steps_done = 0;
+  for (int k = 0; k < steps; ++k) {
+    sps_stats tmp;
+    sps_stats* st = stats_per_step ? stats_per_step + k : &tmp;
+    long long l0;
+    stats_begin(ctx, st, &l0);
+    // positions advance in place: the step reads pos into the context before
+    // its last kernel overwrites it element by element
+    const int rc = stats_end(ctx, st, l0, resolve_any(ctx, n, pos, radii, FT_ext, dt, nullptr, INT32_MAX,
+                                                      UO, pos, st));
+    if (rc != SPS_OK) return rc;
+    if (steps_done) *steps_done = k + 1;
+  }
+  return SPS_OK;
 }
 
 extern "C" int sps_resolve_collisions_host(sps_ctx* ctx, int n, const double* pos, const double* radii,

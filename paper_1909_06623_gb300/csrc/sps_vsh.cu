@@ -228,6 +228,8 @@ __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
 // the velocity (F = kFieldsS; times a_j by the caller) or the traction with
 // target normal v (F = kFieldsK).  (x, y, z): target in sphere j's unit frame.
 // cf: field coefficients of sphere j, E entries x F complex (entry-major).
+// FP32 coefficients (C = float) are read with the entry stride padded to an
+// even number of fields (zero pad), 16-byte aligned.
 template <int F, typename T, typename C>
 __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T x, T y, T z, T vx,
                                              T vy, T vz, T& ox, T& oy, T& oz) {
@@ -246,19 +248,21 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
     }
     T hre = dre, him = dim, pre = T(0), pim = T(0);
     for (int n = m; n <= L; ++n, ++e) {
-      const C* cf = cf0 + e * F * 2;
+      if constexpr (sizeof(C) == 4) {
+        // FP32 coefficients, entries padded to an even field count: one
+        // 16-byte shared-memory load per two fields
+        constexpr int FP = (F + 1) & ~1;
+        const float4* cf4 = reinterpret_cast<const float4*>(cf0) + e * (FP / 2);
 #pragma unroll
-      for (int f = 0; f < F; ++f) {
-        T cre, cim;
-        if constexpr (sizeof(C) == 4) {   // FP32 coefficients: one 8-byte load per field
-          const float2 v = reinterpret_cast<const float2*>(cf)[f];
-          cre = v.x;
-          cim = v.y;
-        } else {
-          cre = (T)cf[2 * f];
-          cim = (T)cf[2 * f + 1];
+        for (int f2 = 0; f2 < FP / 2; ++f2) {
+          const float4 v = cf4[f2];
+          acc[2 * f2] = fma(v.x, hre, fma(-v.y, him, acc[2 * f2]));
+          if (2 * f2 + 1 < F) acc[2 * f2 + 1] = fma(v.z, hre, fma(-v.w, him, acc[2 * f2 + 1]));
         }
-        acc[f] = fma(cre, hre, fma(-cim, him, acc[f]));
+      } else {
+        const C* cf = cf0 + e * F * 2;
+#pragma unroll
+        for (int f = 0; f < F; ++f) acc[f] = fma((T)cf[2 * f], hre, fma(-(T)cf[2 * f + 1], him, acc[f]));
       }
       const T f1 = (T)(2 * n + 1) * z, f2 = (T)(n * n - m * m);
       const T nre = -(f1 * hre + f2 * pre) * ir2, nim = -(f1 * him + f2 * pim) * ir2;
@@ -380,6 +384,7 @@ __global__ void k_near_eval32(int N, int P, int L, int E, const double* __restri
                               const double* __restrict__ Nr, const int* __restrict__ near_ptr,
                               const int* __restrict__ near_idx, const float* __restrict__ fcoef,
                               double* __restrict__ out) {
+  constexpr int FP = (F + 1) & ~1;   // padded field count of a staged entry
   extern __shared__ __align__(16) unsigned char sraw[];
   float2* sc2 = reinterpret_cast<float2*>(sraw);
   __shared__ float s_geo[5];   // (c_i - c_j) / a_j, 1 / a_j, a_j
@@ -409,7 +414,10 @@ __global__ void k_near_eval32(int N, int P, int L, int E, const double* __restri
     const int j = near_idx[q];
     __syncthreads();
     const float2* src = reinterpret_cast<const float2*>(fcoef + (long long)j * E * F * 2);
-    for (int e = threadIdx.x; e < E * F; e += blockDim.x) sc2[e] = src[e];
+    for (int q2 = threadIdx.x; q2 < E * FP; q2 += blockDim.x) {
+      const int e = q2 / FP, f = q2 - e * FP;
+      sc2[q2] = (f < F) ? src[e * F + f] : make_float2(0.f, 0.f);
+    }
     if (threadIdx.x == 0) {
       const double aj = rad[j], ia = 1.0 / aj;
       s_geo[0] = (float)((ci0 - pos[3 * j]) * ia);
@@ -506,7 +514,7 @@ template <int F>
 int launch_near_eval32(sps_ctx* ctx, double* out) {
   const int N = ctx->N, P = ctx->T.P, L = ctx->T.L, E = ctx->T.E;
   const int threads = ((P + 31) / 32) * 32;
-  const size_t sm = sizeof(float) * E * F * 2;
+  const size_t sm = sizeof(float) * E * ((F + 1) & ~1) * 2;
   if (sm > 48 * 1024)
     SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_eval32<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm));

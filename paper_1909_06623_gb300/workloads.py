@@ -304,3 +304,34 @@ def contact_chain(seed, n=5):
     F[:, 0] += np.linspace(60.0, -60.0, n)
     return Workload(f"chain_n{n}_s{seed}", c, np.ones(n), F, p=0, dt=1e-3, steps=1,
                     params=dict(delta=0.1))
+
+
+def sedimenting_cluster(seed=SEED_BASE + 6, N=1000, phi=0.20, a=1.0, a_c_scale=1.05, p=6,
+                        steps=20):
+    """The sedimentation test of Sec. 6.3: N monodisperse spheres of radius a in
+    a dense spherical cluster of volume fraction phi in unbounded fluid, every
+    sphere pulled by the same force F = (0, 0, -1) (no torque), collision radius
+    a_c = 1.05 a, dt = 0.05 eta a^2 / F, p = 6, BBPGD tolerance 1e-4, contact
+    threshold 30% of the sum of the radii (Sec. 3.2).  The cluster radius is
+    a (N / phi)^(1/3); centres by random sequential addition inside it with
+    every gap above 2 (a_c - a) + 0.02 a, so the start is collision-free."""
+    rng = np.random.default_rng(seed)
+    R = np.full(N, float(a))
+    Rb = a * (N / phi) ** (1.0 / 3.0)
+    gap = 2.0 * (a_c_scale - 1.0) * a + 0.02 * a
+    C = np.full((N, 3), np.nan)
+    grid = _Grid(2.0 * a + gap)
+    for k in range(N):
+        for _ in range(200000):
+            v = rng.standard_normal(3)
+            c = v / np.linalg.norm(v) * (Rb - a) * rng.random() ** (1.0 / 3.0)
+            if _fits(k, c, a, C, R, grid, gap):
+                C[k] = c
+                grid.add(k, c)
+                break
+        else:
+            raise RuntimeError("random sequential addition jammed")
+    FT = np.zeros((N, 6))
+    FT[:, 2] = -1.0
+    return Workload(f"sed_cluster_N{N}_phi{phi:.2f}", C, R, FT, p=p, dt=0.05 * a * a, steps=steps,
+                    params=dict(delta=0.0, delta_rel=0.3, a_c_scale=a_c_scale, bbpgd_tol=1e-4))

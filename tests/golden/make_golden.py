@@ -150,8 +150,34 @@ def collision_grad_c():
                         fd=np.array(fd))
 
 
+def sed_steps():
+    """Two collision-resolved steps of a 10-sphere sedimenting cluster (Sec.
+    6.3 geometry, p = 4, threshold 30% of the sum of the radii, a_c = 1.05 a)
+    with strong random forces added to gravity and dt = 0.5, so that both
+    steps have active contacts; the oracle's step applied twice."""
+    w = workloads.sedimenting_cluster(N=10, phi=0.25, p=4)
+    rng = np.random.default_rng(workloads.SEED_BASE + 60)
+    FT = w.FT.copy()
+    FT[:, :3] += 20.0 * rng.standard_normal((w.N, 3))
+    dt, kw = 0.5, dict(delta=0.0, delta_rel=0.3, a_c_scale=1.05, gmres_tol=1e-13,
+                       bbpgd_tol=1e-12, bbpgd_max=20000)
+    C = w.centers.copy()
+    traj, Us, active = [C], [], []
+    for _ in range(2):
+        out = lcp.resolve_collisions(C, w.radii, FT, dt, 4, **kw)
+        print("sed_steps", out["info"])
+        C = out["centers_new"]
+        traj.append(C)
+        Us.append(out["U"])
+        active.append(out["info"]["n_active"])
+    np.savez_compressed(os.path.join(HERE, "sed_steps_p4.npz"), centers=w.centers, radii=w.radii,
+                        FT=FT, dt=dt, p=4, traj=np.array(traj), U=np.array(Us),
+                        n_active=np.array(active))
+
+
 ALL = {"cfg1": cfg1, "active": active, "cfg2": cfg2_sample, "tiny": tiny_layers,
-       "collision_grad": collision_grad, "collision_grad_c": collision_grad_c}
+       "collision_grad": collision_grad, "collision_grad_c": collision_grad_c,
+       "sed_steps": sed_steps}
 
 if __name__ == "__main__":
     for k in (sys.argv[1:] or ALL):
