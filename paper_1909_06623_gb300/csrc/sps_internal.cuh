@@ -112,6 +112,7 @@ struct sps_ctx {
   double *d_coef = nullptr;      // N x NR
   double *d_fcoef = nullptr;     // N x E x kFieldsK x 2
   float *d_fcoef32 = nullptr;    // the same rounded to FP32 (mixed near field)
+  float2 *d_fcoefdw = nullptr;   // the same as FP32 hi + lo pairs (close entries)
   double *d_mom = nullptr;       // N x 6 (per-sphere moments)
   double *d_tmp3 = nullptr;      // 3NP scratch
   float *d_sig32 = nullptr;      // 3NP FP32 w*sigma for the mixed far field
@@ -311,9 +312,11 @@ int sps_layer_T(sps_ctx* ctx, int op, const double* v, double* out);
 
 // near-field coefficient maps (sps_vsh.cu)
 int sps_build_field_maps(sps_ctx* ctx);
-// out32 (optional): a copy of the result rounded to FP32 (not with accumulate)
+// out32 / outdw (optional): copies of the result rounded to FP32 / split
+// into FP32 hi + lo pairs (not with accumulate)
 int sps_launch_sparse_rows(sps_ctx* ctx, const sps_ctx::Sparse& m, int nsph, const double* in, int in_ld,
-                           double* out, int out_ld, int accumulate, float* out32 = nullptr);
+                           double* out, int out_ld, int accumulate, float* out32 = nullptr,
+                           float2* outdw = nullptr);
 
 // vector kernels (sps_solver.cu)
 int sps_dot(sps_ctx* ctx, const double* a, const double* b, long long n, double* host_out);

@@ -541,7 +541,7 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc, ctx->tcA.d,
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
                   ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
-                  ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32};
+                  ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -597,6 +597,8 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
     }
     float** d32[] = {&ctx->d_rel32, &ctx->d_N32, &ctx->d_W32, &ctx->d_sig32, &ctx->d_chi, &ctx->d_clo,
                      &ctx->d_fcoef32};
+    cudaFree(ctx->d_fcoefdw);
+    ctx->d_fcoefdw = nullptr;
     for (auto p : d32) {
       cudaFree(*p);
       *p = nullptr;
@@ -633,6 +635,8 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
       c = 0;
       SPS_TRY(sps_grow(ctx, e.p, c, e.n));
     }
+    c = 0;
+    SPS_TRY(sps_grow(ctx, &ctx->d_fcoefdw, c, (size_t)n * E * sps::kFieldsK * 2));
     c = 0;
     SPS_TRY(sps_grow(ctx, &ctx->d_near_ptr, c, (size_t)n + 1));
     ctx->capN = n;

@@ -33,6 +33,8 @@
 // grad u, whose grad Phi_d term cancels, leaving 25 fields (6+6 Hessian
 // components of Phi_a, Phi_d; grad and Hessian of Phi_alpha; grad Phi_beta;
 // 2 Phi_beta - Phi_P); the velocity needs 10.
+#include <type_traits>
+
 #include "sps_internal.cuh"
 
 // mixed path: VSH analysis / self synthesis on the tensor cores (BF16 split
@@ -222,6 +224,82 @@ __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
 }
 
 // ---------------------------------------------------------------------------
+// Double-float numbers for the close near entries: value h + l with |l| at
+// most half an ulp of h once normalised.  Built from the error-free
+// transforms TwoSum (Knuth), FastTwoSum (Dekker) and TwoProd by FMA; products
+// drop l*l and sums add the low parts without compensation, so an operation's
+// absolute error is about u^2 (u = 2^-24) times its operands, against 2^-53
+// in FP64 -- ample for the close entries, at FP32-pipe throughput (GB300's
+// FP64 pipe is ~1/64 of it).
+// ---------------------------------------------------------------------------
+// Every operation below is an explicitly rounded intrinsic (__fadd_rn,
+// __fmul_rn, fmaf), so the compiler cannot contract a product into a later
+// sum and break the error-free transforms.
+struct dw {
+  float h, l;
+  dw() = default;
+  __device__ __forceinline__ dw(float a, float b) : h(a), l(b) {}
+  __device__ __forceinline__ dw(int a) : h((float)a), l(0.f) {}   // exact for |a| < 2^24
+};
+__device__ __forceinline__ dw two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return dw(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return dw(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dw operator+(dw a, dw b) {
+  const dw s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dw operator-(dw a) { return dw(-a.h, -a.l); }
+__device__ __forceinline__ dw operator-(dw a, dw b) { return a + (-b); }
+__device__ __forceinline__ dw& operator+=(dw& a, dw b) { return a = a + b; }
+__device__ __forceinline__ dw operator*(dw a, dw b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dw operator*(int a, dw b) { return dw(a) * b; }
+// 1 / a: one Newton step from the FP32 reciprocal, its residual by FMAs
+__device__ __forceinline__ dw recip(dw a) {
+  const float y = __frcp_rn(a.h);
+  const float r = fmaf(-a.l, y, fmaf(-a.h, y, 1.0f));
+  return fast_two_sum(y, __fmul_rn(y, r));
+}
+__device__ __forceinline__ dw operator/(dw a, dw b) { return a * recip(b); }
+// acc += a b without renormalising acc (the low part collects the errors)
+__device__ __forceinline__ void dw_mac(dw& acc, dw a, dw b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+  const dw s = two_sum(acc.h, p);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
+}
+__device__ __forceinline__ dw dw_of(double d) {
+  const float h = __double2float_rn(d);
+  return dw(h, __double2float_rn(d - (double)h));
+}
+__device__ __forceinline__ double dw_val(dw a) { return (double)a.h + (double)a.l; }
+
+// 1 / sqrt(a) for the near-field expansion's arithmetic types
+template <typename T>
+__device__ __forceinline__ T inv_sqrt(T a) {
+  return T(1) / sqrt(a);
+}
+template <>
+__device__ __forceinline__ dw inv_sqrt<dw>(dw a) {
+  // FP32 estimate refined once in FP32, then one Newton step with the
+  // residual 1 - a y^2 formed by FMAs (y^2 = t + te exactly)
+  float y = rsqrtf(a.h);
+  y = __fmul_rn(y, fmaf(__fmul_rn(-0.5f, a.h), __fmul_rn(y, y), 1.5f));
+  const float t = __fmul_rn(y, y), te = fmaf(y, y, -t);
+  const float r = fmaf(-a.l, t, fmaf(-a.h, te, fmaf(-a.h, t, 1.0f)));
+  return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), r));
+}
+
+// ---------------------------------------------------------------------------
 // near-field evaluation: one block per target sphere, one thread per node
 // ---------------------------------------------------------------------------
 // Contribution of source sphere j's exterior single layer at one target:
@@ -229,7 +307,8 @@ __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
 // target normal v (F = kFieldsK).  (x, y, z): target in sphere j's unit frame.
 // cf: field coefficients of sphere j, E entries x F complex (entry-major).
 // FP32 coefficients (C = float) are read with the entry stride padded to an
-// even number of fields (zero pad), 16-byte aligned.
+// even number of fields (zero pad), 16-byte aligned; double-float ones
+// (T = dw, C = float4) as one (re hi, re lo, im hi, im lo) per field.
 template <int F, typename T, typename C>
 __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T x, T y, T z, T vx,
                                              T vy, T vz, T& ox, T& oy, T& oz) {
@@ -237,7 +316,7 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
   T acc[F];
 #pragma unroll
   for (int f = 0; f < F; ++f) acc[f] = T(0);
-  T dre = T(1) / sqrt(r2), dim = T(0);  // H_m^m
+  T dre = inv_sqrt(r2), dim = T(0);  // H_m^m
   int e = 0;
   for (int m = 0; m <= L; ++m) {
     if (m > 0) {
@@ -248,7 +327,15 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
     }
     T hre = dre, him = dim, pre = T(0), pim = T(0);
     for (int n = m; n <= L; ++n, ++e) {
-      if constexpr (sizeof(C) == 4) {
+      if constexpr (std::is_same<T, dw>::value) {
+        const float4* cf4 = reinterpret_cast<const float4*>(cf0) + e * F;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          const float4 v = cf4[f];
+          dw_mac(acc[f], dw(v.x, v.y), hre);
+          dw_mac(acc[f], dw(-v.z, -v.w), him);
+        }
+      } else if constexpr (sizeof(C) == 4) {
         // FP32 coefficients, entries padded to an even field count: one
         // 16-byte shared-memory load per two fields
         constexpr int FP = (F + 1) & ~1;
@@ -271,6 +358,10 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
       hre = nre;
       him = nim;
     }
+  }
+  if constexpr (std::is_same<T, dw>::value) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = two_sum(acc[f].h, acc[f].l);
   }
   if constexpr (F == sps::kFieldsK) {
     // Hessians: [xx, xy, xz, yy, yz, zz]
@@ -525,8 +616,57 @@ int launch_near_eval32(sps_ctx* ctx, double* out) {
   return SPS_OK;
 }
 
+// The same entries in double-float arithmetic (coefficients as hi + lo FP32
+// pairs): FP64 only to place the target in the source frame and to add up.
+template <int F>
+__global__ void k_near_close_dw(int N, int P, int L, int E, int n_close, const int* __restrict__ cnode,
+                                const int* __restrict__ cptr, const int* __restrict__ csrc,
+                                const double* __restrict__ pos, const double* __restrict__ rad,
+                                const double* __restrict__ X, const double* __restrict__ Nr,
+                                const float4* __restrict__ fcoef, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_close) return;
+  const long long NP = (long long)N * P;
+  const long long g = cnode[t];
+  const double gx = X[g], gy = X[NP + g], gz = X[2 * NP + g];
+  dw vx(0), vy(0), vz(0);
+  if (F == sps::kFieldsK) {
+    vx = dw_of(Nr[g]);
+    vy = dw_of(Nr[NP + g]);
+    vz = dw_of(Nr[2 * NP + g]);
+  }
+  double ox = 0, oy = 0, oz = 0;
+  for (int q = cptr[t]; q < cptr[t + 1]; ++q) {
+    const int j = csrc[q];
+    const double aj = rad[j], ia = 1.0 / aj;
+    const dw x = dw_of((gx - pos[3 * j]) * ia), y = dw_of((gy - pos[3 * j + 1]) * ia),
+             z = dw_of((gz - pos[3 * j + 2]) * ia);
+    dw tx, ty, tz;
+    near_contrib<F, dw, float4>(fcoef + (long long)j * E * F, L, x, y, z, vx, vy, vz, tx, ty, tz);
+    const double s = (F == sps::kFieldsK) ? 1.0 : aj;
+    ox += s * dw_val(tx);
+    oy += s * dw_val(ty);
+    oz += s * dw_val(tz);
+  }
+  out[g] += ox;
+  out[NP + g] += oy;
+  out[2 * NP + g] += oz;
+}
+
+#ifndef SPS_CLOSE_DW
+#define SPS_CLOSE_DW 1
+#endif
 template <int F>
 int launch_near_close(sps_ctx* ctx, double* out) {
+  if (SPS_CLOSE_DW) {
+    if (ctx->n_close == 0) return SPS_OK;
+    k_near_close_dw<F><<<(ctx->n_close + 63) / 64, 64, 0, ctx->stream>>>(
+        ctx->N, ctx->T.P, ctx->T.L, ctx->T.E, ctx->n_close, ctx->d_close_node, ctx->d_close_ptr,
+        ctx->d_close_src, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm,
+        reinterpret_cast<const float4*>(ctx->d_fcoefdw), out);
+    SPS_LAUNCHED(ctx);
+    return SPS_OK;
+  }
   if (ctx->n_close == 0) return SPS_OK;
   k_near_close<F><<<(ctx->n_close + 63) / 64, 64, 0, ctx->stream>>>(
       ctx->N, ctx->T.P, ctx->T.L, ctx->T.E, ctx->n_close, ctx->d_close_node, ctx->d_close_ptr,
@@ -536,11 +676,12 @@ int launch_near_close(sps_ctx* ctx, double* out) {
 }
 
 // out[s][r] (+)= sum over row r of a sparse map applied to in[s][:]
-// (out32: the result rounded to FP32, same layout)
+// (out32: the result rounded to FP32; outdw: split into FP32 hi + lo; same
+// layout)
 __global__ void k_sparse_rows(int N, int rows, const int* __restrict__ rp, const int* __restrict__ ci,
                               const double* __restrict__ val, const double* __restrict__ in, int in_ld,
                               double* __restrict__ out, int out_ld, int accumulate,
-                              float* __restrict__ out32) {
+                              float* __restrict__ out32, float2* __restrict__ outdw) {
   const long long tot = (long long)N * rows;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
        q += (long long)gridDim.x * blockDim.x) {
@@ -551,16 +692,21 @@ __global__ void k_sparse_rows(int N, int rows, const int* __restrict__ rp, const
     double* y = out + (long long)s * out_ld + r;
     *y = accumulate ? *y + acc : acc;
     if (out32) out32[(long long)s * out_ld + r] = (float)acc;
+    if (outdw) {
+      const float h = __double2float_rn(acc);
+      outdw[(long long)s * out_ld + r] = make_float2(h, __double2float_rn(acc - (double)h));
+    }
   }
 }
 
 }  // namespace
 
 int sps_launch_sparse_rows(sps_ctx* ctx, const sps_ctx::Sparse& m, int nsph, const double* in, int in_ld,
-                           double* out, int out_ld, int accumulate, float* out32) {
+                           double* out, int out_ld, int accumulate, float* out32, float2* outdw) {
   const long long tot = (long long)nsph * m.rows;
   k_sparse_rows<<<(int)std::min<long long>((tot + 255) / 256, 8 * 152), 256, 0, ctx->stream>>>(
-      nsph, m.rows, m.rp, m.ci, m.v, in, in_ld, out, out_ld, accumulate, accumulate ? nullptr : out32);
+      nsph, m.rows, m.rp, m.ci, m.v, in, in_ld, out, out_ld, accumulate, accumulate ? nullptr : out32,
+      accumulate ? nullptr : outdw);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -694,7 +840,8 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
     // field coefficients of every source sphere: fcoef_s = FM coef_s (sparse)
     const sps_ctx::Sparse& fm = S ? ctx->fmS : ctx->fmK;
     SPS_TRY(sps_launch_sparse_rows(ctx, fm, N, ctx->d_coef, NR, ctx->d_fcoef, fm.rows, 0,
-                                   fp32 ? ctx->d_fcoef32 : nullptr));
+                                   fp32 ? ctx->d_fcoef32 : nullptr,
+                                   (fp32 && SPS_CLOSE_DW) ? ctx->d_fcoefdw : nullptr));
     (void)NC;
     (void)L;
     (void)E;
