@@ -306,8 +306,8 @@ __device__ __forceinline__ dw inv_sqrt<dw>(dw a) {
 // the velocity (F = kFieldsS; times a_j by the caller) or the traction with
 // target normal v (F = kFieldsK).  (x, y, z): target in sphere j's unit frame.
 // cf: field coefficients of sphere j, E entries x F complex (entry-major).
-// FP32 coefficients (C = float) are read with the entry stride padded to an
-// even number of fields (zero pad), 16-byte aligned; double-float ones
+// FP32 coefficients (C = float) are read as field pairs (re, re', -im, -im'),
+// the entry stride padded to an even number of fields; double-float ones
 // (T = dw, C = float4) as one (re hi, re lo, im hi, im lo) per field.
 template <int F, typename T, typename C>
 __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T x, T y, T z, T vx,
@@ -316,6 +316,10 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
   T acc[F];
 #pragma unroll
   for (int f = 0; f < F; ++f) acc[f] = T(0);
+  constexpr int FH = (F + 1) / 2;   // field pairs (FP32 path)
+  float2 acc2[FH];
+#pragma unroll
+  for (int f = 0; f < FH; ++f) acc2[f] = make_float2(0.f, 0.f);
   T dre = inv_sqrt(r2), dim = T(0);  // H_m^m
   int e = 0;
   for (int m = 0; m <= L; ++m) {
@@ -336,15 +340,15 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
           dw_mac(acc[f], dw(-v.z, -v.w), him);
         }
       } else if constexpr (sizeof(C) == 4) {
-        // FP32 coefficients, entries padded to an even field count: one
-        // 16-byte shared-memory load per two fields
-        constexpr int FP = (F + 1) & ~1;
-        const float4* cf4 = reinterpret_cast<const float4*>(cf0) + e * (FP / 2);
+        // FP32 coefficients staged per field pair as (re_f, re_f+1, -im_f,
+        // -im_f+1) (zero pad for odd F): one 16-byte shared-memory load and
+        // two packed FP32x2 FMAs per two fields
+        const float4* cf4 = reinterpret_cast<const float4*>(cf0) + e * FH;
+        const float2 hr2 = make_float2(hre, hre), hi2 = make_float2(him, him);
 #pragma unroll
-        for (int f2 = 0; f2 < FP / 2; ++f2) {
+        for (int f2 = 0; f2 < FH; ++f2) {
           const float4 v = cf4[f2];
-          acc[2 * f2] = fma(v.x, hre, fma(-v.y, him, acc[2 * f2]));
-          if (2 * f2 + 1 < F) acc[2 * f2 + 1] = fma(v.z, hre, fma(-v.w, him, acc[2 * f2 + 1]));
+          acc2[f2] = __ffma2_rn(make_float2(v.x, v.y), hr2, __ffma2_rn(make_float2(v.z, v.w), hi2, acc2[f2]));
         }
       } else {
         const C* cf = cf0 + e * F * 2;
@@ -362,6 +366,9 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
   if constexpr (std::is_same<T, dw>::value) {
 #pragma unroll
     for (int f = 0; f < F; ++f) acc[f] = two_sum(acc[f].h, acc[f].l);
+  } else if constexpr (sizeof(C) == 4) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = (f & 1) ? acc2[f / 2].y : acc2[f / 2].x;
   }
   if constexpr (F == sps::kFieldsK) {
     // Hessians: [xx, xy, xz, yy, yz, zz]
@@ -505,9 +512,16 @@ __global__ void k_near_eval32(int N, int P, int L, int E, const double* __restri
     const int j = near_idx[q];
     __syncthreads();
     const float2* src = reinterpret_cast<const float2*>(fcoef + (long long)j * E * F * 2);
-    for (int q2 = threadIdx.x; q2 < E * FP; q2 += blockDim.x) {
-      const int e = q2 / FP, f = q2 - e * FP;
-      sc2[q2] = (f < F) ? src[e * F + f] : make_float2(0.f, 0.f);
+    // field pairs of entry e: (re_2k, re_2k+1, -im_2k, -im_2k+1), one warp per entry
+    {
+      float4* sc4 = reinterpret_cast<float4*>(sc2);
+      const int lane = threadIdx.x & 31;
+      for (int e = threadIdx.x >> 5; e < E; e += blockDim.x >> 5)
+        if (lane < FP / 2) {
+          const float2 a = src[e * F + 2 * lane];
+          const float2 b = (2 * lane + 1 < F) ? src[e * F + 2 * lane + 1] : make_float2(0.f, 0.f);
+          sc4[e * (FP / 2) + lane] = make_float4(a.x, b.x, -a.y, -b.y);
+        }
     }
     if (threadIdx.x == 0) {
       const double aj = rad[j], ia = 1.0 / aj;
