@@ -191,6 +191,21 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def replica_throughput(total_s, steps, world, device):
+    """Whole-job steps/s of `world` independent replicas that each timed
+    `steps` steps in total_s seconds: the job lasts as long as its slowest
+    replica (max over ranks), so value = world * steps / that time.  Returns
+    (value, max time).  Collective: one all-reduce of a scalar (NCCL on the
+    GPU run, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return world * steps / total_s, total_s
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -254,12 +269,7 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    value, total_s = replica_throughput(sum(step_ms) / 1e3, args.steps, world, "cuda")
 
     # dominant kernel: far-field traction N-body (phase 0)
     N, P = w.N, (w.p + 1) * (2 * w.p + 2)
