@@ -129,13 +129,15 @@ def workload(name):
     raise ValueError(name)
 
 
-def ctx_params(precision):
+def ctx_params(precision, bb_warm=1):
     """Solver settings of the benchmark step.  Collision radius a_c = 1.05 a and
     eps_tol = 1e-5 are the paper's choices at p = 6 (Sec. 3.3.2, 6.1); the
-    GMRES tolerance and the BBPGD cap are this benchmark's."""
+    GMRES tolerance and the BBPGD cap are this benchmark's.  bb_warm = 1 starts
+    Algorithm 1 from the previous step's gamma (the paper's runs: gamma_0 = 0,
+    --bb-warm 0)."""
     return dict(p=6, delta=0.1, beta=1.75, a_c_scale=1.05,
                 gmres_tol=1e-6 if precision == "mixed" else 1e-8, gmres_max=150,
-                bbpgd_tol=1e-5, bbpgd_max=100, bb_safeguard=1, warm_start=1,
+                bbpgd_tol=1e-5, bbpgd_max=100, bb_safeguard=1, warm_start=1, bb_warm=bb_warm,
                 precision=1 if precision == "mixed" else 0)
 
 
@@ -219,7 +221,7 @@ def run_gpu(args, w):
         dist.init_process_group("nccl")
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    prm = ctx_params(args.precision)
+    prm = ctx_params(args.precision, args.bb_warm)
     if w.name.startswith("sed"):
         # the sedimenting cluster of Sec. 6.3 with the paper's own settings:
         # threshold 30% of the sum of the radii, eps_tol = 1e-4
@@ -358,6 +360,7 @@ def run_gpu(args, w):
             "config": {"workload": w.name, "N": N, "p": w.p, "nodes": NP, "precision": args.precision,
                        "gmres_tol": ctx.prm.gmres_tol, "bbpgd_tol": ctx.prm.bbpgd_tol,
                        "delta": ctx.prm.delta, "delta_rel": ctx.prm.delta_rel,
+                       "bbpgd_gamma0": "previous step" if ctx.prm.bb_warm else "zero",
                        "a_c_scale": ctx.prm.a_c_scale, "bbpgd_max": ctx.prm.bbpgd_max,
                        "dt": w.dt, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -627,6 +630,8 @@ def main():
     ap.add_argument("--single-op", choices=["K", "S", "A"], default=None,
                     help="apply one layer operator on the workload geometry and exit")
     ap.add_argument("--no-contact-bench", action="store_true")
+    ap.add_argument("--bb-warm", type=int, default=1, choices=[0, 1],
+                    help="1: Algorithm 1 starts from the previous step's gamma; 0: gamma_0 = 0")
     ap.add_argument("--contact-n", type=int, default=CONTACT_N)
     ap.add_argument("--contact-only", action="store_true",
                     help="run only the identity-mobility contact benchmark")

@@ -98,6 +98,14 @@ typedef struct sps_params {
                          (a: sphere radii, not collision radii).  Sec. 3.2
                          sets delta to 30% of the sum of the radii: delta = 0,
                          delta_rel = 0.3.  Default 0.                        */
+  int bb_warm;        /* Algorithm 1 takes an initial guess gamma_0; the
+                         paper's runs use 0.  1: sps_resolve_collisions on
+                         the same number of spheres as the previous call
+                         starts from the previous step's gamma on the pairs
+                         both contact sets share (0 elsewhere); a nonzero
+                         gamma_0 costs one more mobility solve (g_0 = M
+                         gamma_0 + q).  Every step still meets bbpgd_tol.
+                         Default 0.                                          */
 } sps_params;
 
 typedef struct sps_stats {

@@ -78,13 +78,20 @@ def minmap(gamma, g):
     return float(np.linalg.norm(np.minimum(gamma, g)))
 
 
-def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False):
-    """Algorithm 1.  Mop(gamma) -> M gamma.  Returns gamma, g, info."""
+def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False, gamma0=None):
+    """Algorithm 1.  Mop(gamma) -> M gamma.  gamma0: the algorithm's initial
+    guess (default 0, the paper's choice, whose product M gamma_0 = 0 needs no
+    evaluation).  Returns gamma, g, info."""
     q = np.asarray(q, dtype=np.float64)
     mv = 0
-    gamma = np.zeros_like(q)
-    g = q.copy()                                   # M gamma_0 = 0 for gamma_0 = 0
-    info = {"iters": 0, "mvops": 0, "status": "ok", "phi": minmap(gamma, g), "safeguards": 0}
+    if gamma0 is None or not np.any(gamma0):
+        gamma = np.zeros_like(q)
+        g = q.copy()                               # M gamma_0 = 0 for gamma_0 = 0
+    else:
+        gamma = np.asarray(gamma0, dtype=np.float64).copy()
+        g = Mop(gamma) + q
+        mv += 1
+    info = {"iters": 0, "mvops": mv, "status": "ok", "phi": minmap(gamma, g), "safeguards": 0}
     if info["phi"] < tol:
         return gamma, g, info
     Mg = Mop(g)

@@ -136,6 +136,12 @@ struct sps_ctx {
   long long proj_n = 0;
   int proj_m = 0, proj_old = 0;   // columns in use, oldest column once full
   bool proj_on = false;
+  // the previous collision step's contact pairs and gamma (initial guess of
+  // Algorithm 1 with bb_warm)
+  int *d_prev_ij = nullptr;
+  double *d_prev_gam = nullptr;
+  size_t cap_prev_ij = 0, cap_prev_gam = 0;
+  int prev_nc = 0, prev_N = 0;
 
   // contacts
   int n_c = 0, cap_c = 0, c_N = 0;   // contacts, capacity, spheres they refer to

@@ -120,6 +120,24 @@ __global__ void k_add(int n, const double* __restrict__ a, const double* __restr
   if (l < n) g[l] = a[l] + q[l];
 }
 
+// gamma_0 for a new contact list from the previous step's solution: the
+// value of the same pair (i, j) if it was a contact then, else 0 (both lists
+// sorted by (i, j); binary search)
+__global__ void k_map_gamma(int nc, const int* __restrict__ ij, int nprev, const int* __restrict__ pij,
+                            const double* __restrict__ pgam, double* __restrict__ gam) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nc) return;
+  const int i = ij[2 * l], j = ij[2 * l + 1];
+  int lo = 0, hi = nprev;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int pi = pij[2 * mid], pj = pij[2 * mid + 1];
+    if (pi < i || (pi == i && pj < j)) lo = mid + 1;
+    else hi = mid;
+  }
+  gam[l] = (lo < nprev && pij[2 * lo] == i && pij[2 * lo + 1] == j) ? pgam[lo] : 0.0;
+}
+
 // q = phi/dt + D^T U_nc (D^T U_nc already in q)
 __global__ void k_q(int n, const double* __restrict__ phi, double idt, double* __restrict__ q) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -442,6 +460,7 @@ extern "C" int sps_default_params(sps_params* o) {
   o->mobility = SPS_MOB_BIE;
   o->contact_search = SPS_SEARCH_AUTO;
   o->delta_rel = 0.0;
+  o->bb_warm = 0;
   return SPS_OK;
 }
 
@@ -461,7 +480,8 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
       (prm->bb_variant != 1 && prm->bb_variant != 2) || !(prm->a_c_scale > 0) ||
       !(prm->delta >= 0) || !(prm->delta_rel >= 0) || !std::isfinite(prm->delta_rel) || prm->ir_tol < 0 || prm->ir_max < 0 ||
       (prm->mobility != SPS_MOB_BIE && prm->mobility != SPS_MOB_IDENTITY) ||
-      prm->contact_search < SPS_SEARCH_AUTO || prm->contact_search > SPS_SEARCH_CELLS)
+      prm->contact_search < SPS_SEARCH_AUTO || prm->contact_search > SPS_SEARCH_CELLS ||
+      (prm->bb_warm != 0 && prm->bb_warm != 1))
     return SPS_ERR_INVALID_ARG;
   sps_ctx* ctx = new sps_ctx();
   ctx->prm = *prm;
@@ -541,7 +561,7 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc, ctx->tcA.d,
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
                   ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
-                  ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw};
+                  ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw, ctx->d_prev_ij, ctx->d_prev_gam};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -1023,18 +1043,40 @@ struct BBResult {
 // Each returns an sps_status; NOT_CONVERGED (an inner solve) is recorded and
 // the iteration goes on.  Returns the first hard error, else SPS_OK with the
 // outcome in r; d_gam / d_g hold the last iterate.
-template <class MulG, class Step>
+template <class MulG, class Step, class MulGam>
 static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step, BBResult& r,
-                     double* aux = nullptr, size_t aux_len = 0) {
-  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
-  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice,
-                                ctx->stream));
+                     double* aux, size_t aux_len, bool warm0, MulGam mul_gam) {
+  int rc = SPS_OK;
+  if (warm0) {
+    // gamma_0 (in d_gam) from the caller: g_0 = M gamma_0 + q
+    rc = mul_gam();
+    if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+    if (rc) r.worst = rc;
+    if (st) st->mvops += 1;
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_add<<<(nc + 255) / 256, 256, 0, ctx->stream>>>(nc, ctx->d_Mg, ctx->d_q, ctx->d_g); }
+    SPS_LAUNCHED(ctx);
+  } else {
+    SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+  }
   double s5[5];
   SPS_TRY(bb_stats(ctx, ctx->d_gam, ctx->d_g, nullptr, nullptr, s5));
   r.phi = std::sqrt(s5[0]);
   const double tol = ctx->prm.bbpgd_tol;
   if (r.phi < tol) return SPS_OK;
-  int rc = mul_g();
+  if (aux) {
+    SPS_TRY(sps_grow(ctx, &ctx->d_gam_best, ctx->cap_gam_best, (size_t)std::max(nc, 1)));
+    SPS_TRY(sps_grow(ctx, &ctx->d_aux_best, ctx->cap_aux_best, std::max<size_t>(aux_len, 1)));
+    if (warm0) {   // the start is the first candidate for the best iterate
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_gam_best, ctx->d_gam, sizeof(double) * nc,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_aux_best, aux, sizeof(double) * aux_len,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+  }
+  rc = mul_g();
   if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
   if (rc) r.worst = rc;
   if (st) st->mvops += 1;
@@ -1052,14 +1094,10 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
   // iterate of smallest residual is kept and returned if the loop fails
   double best_phi = r.phi;
   int best_j = 0;
-  if (aux) {
-    SPS_TRY(sps_grow(ctx, &ctx->d_gam_best, ctx->cap_gam_best, (size_t)std::max(nc, 1)));
-    SPS_TRY(sps_grow(ctx, &ctx->d_aux_best, ctx->cap_aux_best, std::max<size_t>(aux_len, 1)));
-  }
   auto fail = [&](int code, int j) -> int {
     r.bb_rc = code;
     if (aux && best_j != j) {
-      if (best_j == 0) {
+      if (best_j == 0 && !warm0) {
         SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
         SPS_CUDA(ctx, cudaMemsetAsync(aux, 0, sizeof(double) * aux_len, ctx->stream));
       } else {
@@ -1136,7 +1174,8 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
   SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
   BBResult r;
   if (nc > 0) {
-    // 3. q = Phi/dt + D^T U_nc; BBPGD (Algorithm 1) from gamma_0 = 0
+    // 3. q = Phi/dt + D^T U_nc; BBPGD (Algorithm 1) from gamma_0 = 0 or, with
+    //    bb_warm, from the previous step's gamma
     SPS_TRY(sps_launch_DT(ctx, ctx->d_Unc, ctx->d_q));
     const int tb = (nc + 255) / 256;
     { SpsPhase timer_(ctx, SPS_PH_BBPGD);
@@ -1155,13 +1194,38 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
       SPS_TRY(bb_stats(ctx, ctx->d_gam_new, ctx->d_g_new, ctx->d_gam, ctx->d_g, s5));
       return rc2;
     };
-    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, ctx->d_Uc, 6 * (size_t)n));
+    // gamma_0: the previous step's gamma on the shared pairs (bb_warm), else 0
+    bool warm0 = false;
+    if (ctx->prm.bb_warm && ctx->prev_nc > 0 && ctx->prev_N == n) {
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_map_gamma<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_cij, ctx->prev_nc, ctx->d_prev_ij,
+                                               ctx->d_prev_gam, ctx->d_gam); }
+      SPS_LAUNCHED(ctx);
+      int npos = 0;
+      SPS_TRY(sps_count_positive(ctx, ctx->d_gam, nc, &npos));
+      warm0 = npos > 0;
+    }
+    auto mul_gam = [&]() { return apply_M(ctx, ctx->d_gam, ctx->d_Mg, st, false); };
+    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, ctx->d_Uc, 6 * (size_t)n, warm0, mul_gam));
     if (r.worst) worst = r.worst;
     // U_c is the solve of the returned iterate; gamma_0 = 0 needs none
-    if (r.iters == 0) SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
+    if (r.iters == 0 && !warm0)
+      SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_Uc, 0, sizeof(double) * 6 * n, ctx->stream));
     if (gamma)
       SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
   }
+  // this step's pairs and gamma: the next step's initial guess
+  ctx->prev_nc = 0;
+  if (ctx->prm.bb_warm && nc > 0) {
+    SPS_TRY(sps_grow(ctx, &ctx->d_prev_ij, ctx->cap_prev_ij, 2 * (size_t)nc));
+    SPS_TRY(sps_grow(ctx, &ctx->d_prev_gam, ctx->cap_prev_gam, (size_t)nc));
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_prev_ij, ctx->d_cij, sizeof(int) * 2 * nc, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_prev_gam, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    ctx->prev_nc = nc;
+  }
+  ctx->prev_N = n;
   SPS_TRY(finish_bb_stats(ctx, nc, r, st));
   // 4. U = U_nc + U_c, pos += U dt
   const long long n6 = 6LL * n;
@@ -1223,7 +1287,7 @@ static int resolve_identity(sps_ctx* ctx, int n, const double* pos, const double
       SPS_TRY(sps_launch_bb_identity(ctx, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new, ctx->d_g_new));
       return read5(ctx, s5);
     };
-    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r));
+    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, nullptr, 0, false, []() { return SPS_OK; }));
     if (gamma)
       SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
   }

@@ -73,6 +73,30 @@ def test_bbpgd_matches_enumeration(seed):
         assert np.linalg.norm(gam - exact) <= bound + 1e-15
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_bbpgd_initial_guess_reaches_enumerated_solution(seed):
+    """Algorithm 1 takes gamma_0 as input: from the exact solution it stops
+    after the single evaluation of g_0 (no GD step), from a perturbed one it
+    converges to the same LCP solution (unique for SPD M, Sec. 3.3.2)."""
+    rng = np.random.default_rng(100 + seed)
+    n = 2 + seed % 5
+    B = rng.standard_normal((n, n))
+    M = B @ B.T + 0.5 * np.eye(n)
+    q = rng.standard_normal(n)
+    exact = lcp.lcp_enumerate(M, q)
+    if not np.any(exact):
+        q[0] = -abs(q[0]) - 1.0
+        exact = lcp.lcp_enumerate(M, q)
+    gam, g, info = lcp.bbpgd(lambda x: M @ x, q, 1e-9, gamma0=exact)
+    assert info["iters"] == 0 and info["mvops"] == 1 and np.array_equal(gam, exact)
+    g0 = np.maximum(exact + 0.3 * rng.standard_normal(n), 0.0)
+    if not np.any(g0):
+        g0[0] = 1.0
+    gam, g, info = lcp.bbpgd(lambda x: M @ x, q, 1e-12, gamma0=g0, safeguard=True)
+    assert info["status"] == "ok" and info["mvops"] == info["iters"] + 2
+    assert np.abs(gam - exact).max() < 1e-10
+
+
 def test_scalar_lcp_one_step_and_trivial_cases():
     gam, g, info = lcp.bbpgd(lambda x: 2.0 * x, np.array([-3.0]), 1e-12)
     assert info["iters"] == 1 and info["mvops"] == 2 and abs(gam[0] - 1.5) < 1e-15

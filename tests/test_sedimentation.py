@@ -157,3 +157,58 @@ def test_gpu_simulate_mixed_vs_fp64(sps):
     disp = np.abs(out[0][0] - w.centers).max()
     assert np.abs(out[1][0] - out[0][0]).max() <= 1e-5 * disp
     assert np.abs(out[1][1] - out[0][1]).max() <= 1e-5 * np.abs(out[0][1]).max()
+
+
+@pytest.mark.gpu
+def test_gpu_bb_warm_start_matches_oracle_steps(sps):
+    """Algorithm 1 started from the previous step's gamma (bb_warm = 1): the
+    second step's LCP solution still matches the oracle's step (which starts
+    from gamma_0 = 0) to the FP64 tolerance."""
+    d = np.load(GOLDEN / "sed_steps_p4.npz")
+    ctx = sps.Context(p=int(d["p"]), delta=0.0, delta_rel=0.3, a_c_scale=1.05, gmres_tol=1e-13,
+                      gmres_max=300, bbpgd_tol=1e-12, bbpgd_max=20000, bb_warm=1)
+    pos = dev(d["centers"])
+    pos, UO, stats = ctx.simulate(pos, dev(d["radii"]), dev(d["FT"]), float(d["dt"]), 2)
+    assert all(s["status"] == 0 for s in stats)
+    # step 2 started from a nonzero gamma_0: g_0 = M gamma_0 + q costs one
+    # evaluation of M gamma (and the step length one more if it iterates)
+    s2 = stats[1]
+    assert (s2["bbpgd_iters"] == 0 and s2["mvops"] == 1) or s2["mvops"] == s2["bbpgd_iters"] + 2
+    traj = d["traj"]
+    disp = np.abs(traj[-1] - traj[0]).max()
+    assert np.abs(pos.cpu().numpy() - traj[-1]).max() <= 1e-10 * disp
+    assert np.abs(UO.cpu().numpy() - d["U"][-1]).max() <= 1e-10 * np.abs(d["U"][-1]).max()
+
+
+@pytest.mark.gpu
+def test_gpu_bb_warm_start_config2_mixed(sps):
+    """Config 2 (1,000 spheres, p = 6, mixed): after the benchmark's three
+    warm-up steps (which resolve the initial overlaps at the collision
+    radius), three steps from gamma_0 = 0 and three from the previous step's
+    gamma reach the same velocities within the mixed-path tolerance, the
+    warm-started steps with fewer BBPGD iterations."""
+    w = workloads.config2()
+    # the benchmark's solver settings (eps_tol = 1e-5: the mixed operator's
+    # rounding keeps the min-map residual from settling much below that)
+    kw = dict(p=6, delta=0.1, a_c_scale=1.05, gmres_tol=1e-6, gmres_max=150, bbpgd_tol=1e-5,
+              bbpgd_max=100, bb_safeguard=1, precision=1)
+    ctx = sps.Context(bb_warm=0, **kw)
+    pos, rad, FT = dev(w.centers), dev(w.radii), dev(w.FT)
+    pos_out = torch.empty_like(pos)
+    for _ in range(3):
+        ctx.resolve_collisions(pos, rad, FT, w.dt, pos_out=pos_out, allow=(4, 5))
+        pos.copy_(pos_out)
+    start = pos.clone()
+    out = {}
+    for warm in (0, 1):
+        c = sps.Context(bb_warm=warm, **kw)
+        p, UO, stats = c.simulate(start.clone(), rad, FT, w.dt, 3)
+        assert all(s["status"] == 0 for s in stats)
+        out[warm] = (p.cpu().numpy(), UO.cpu().numpy(), stats)
+    U0, U1 = out[0][1], out[1][1]
+    assert np.abs(U1 - U0).max() <= 1e-5 * np.abs(U0).max()
+    disp = np.abs(out[0][0] - start.cpu().numpy()).max()
+    assert np.abs(out[1][0] - out[0][0]).max() <= 1e-5 * disp
+    it0 = sum(s["bbpgd_iters"] for s in out[0][2][1:])
+    it1 = sum(s["bbpgd_iters"] for s in out[1][2][1:])
+    assert it1 < it0
