@@ -539,7 +539,9 @@ def sweep_point(N, p, dev, stream, lib, pk):
     NP = N * P
     row = {"workload": w.name, "N": N, "p": p, "nodes": NP}
     for prec in ("mixed", "fp64"):
-        prm = ctx_params(prec)
+        # one step after one warm-up step: gamma_0 = 0 (the warm-up step's
+        # gamma resolves the initial overlaps and is no guess for the next)
+        prm = ctx_params(prec, bb_warm=0)
         prm["p"] = p
         ctx = sps.Context(stream=stream, **prm)
         ctx.set_geometry(dev(w.centers), dev(w.radii))

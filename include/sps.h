@@ -104,8 +104,9 @@ typedef struct sps_params {
                          starts from the previous step's gamma on the pairs
                          both contact sets share (0 elsewhere); a nonzero
                          gamma_0 costs one more mobility solve (g_0 = M
-                         gamma_0 + q).  Every step still meets bbpgd_tol.
-                         Default 0.                                          */
+                         gamma_0 + q) and is dropped for gamma_0 = 0 when its
+                         min-map residual is not below that of gamma_0 = 0.
+                         Every step still meets bbpgd_tol.  Default 0.       */
 } sps_params;
 
 typedef struct sps_stats {

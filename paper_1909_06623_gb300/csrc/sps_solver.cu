@@ -1063,6 +1063,21 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
   }
   double s5[5];
   SPS_TRY(bb_stats(ctx, ctx->d_gam, ctx->d_g, nullptr, nullptr, s5));
+  if (warm0) {
+    // keep the initial guess only if its min-map residual beats gamma_0 = 0's
+    // (a guess from a step that resolved large overlaps can be far worse)
+    double z5[5];
+    SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam_new, 0, sizeof(double) * nc, ctx->stream));
+    SPS_TRY(bb_stats(ctx, ctx->d_gam_new, ctx->d_q, nullptr, nullptr, z5));
+    if (!(s5[0] < z5[0])) {
+      warm0 = false;
+      SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
+      SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+      if (aux) SPS_CUDA(ctx, cudaMemsetAsync(aux, 0, sizeof(double) * aux_len, ctx->stream));
+      std::memcpy(s5, z5, sizeof(s5));
+    }
+  }
   r.phi = std::sqrt(s5[0]);
   const double tol = ctx->prm.bbpgd_tol;
   if (r.phi < tol) return SPS_OK;
