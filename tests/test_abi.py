@@ -37,6 +37,8 @@ def test_default_params(lib):
     prm = _lib.sps_params()
     assert lib.sps_default_params(ctypes.byref(prm)) == 0
     assert prm.p == 6 and prm.beta == 1.75 and prm.bb_variant == 1
+    # the fields appended last: the Python mirror of the struct ends where the C one does
+    assert prm.delta_rel == 0.0 and prm.bb_warm == 0 and prm.contact_search == 0
 
 
 def test_create_rejects_bad_params(lib):
@@ -46,6 +48,11 @@ def test_create_rejects_bad_params(lib):
     h = ctypes.c_void_p()
     assert lib.sps_create(ctypes.byref(prm), None, ctypes.byref(h)) == 1
     assert lib.sps_unit_tables(0, None, None, None, None) == 1
+    for field, bad in (("delta_rel", -0.1), ("delta_rel", float("inf")), ("bb_warm", 2),
+                       ("delta", -1.0), ("mobility", 5)):
+        lib.sps_default_params(ctypes.byref(prm))
+        setattr(prm, field, bad)
+        assert lib.sps_create(ctypes.byref(prm), None, ctypes.byref(h)) == 1, field
 
 
 @pytest.mark.parametrize("p", [2, 4, 6, 8])
