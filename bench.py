@@ -628,7 +628,11 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-matvecs-per-step", type=float, default=185.0)
+    ap.add_argument("--ref-matvecs-per-step", type=float, default=185.0,
+                    help="layer-operator applications per config-2 step for the oracle's "
+                         "algorithm (the paper's formulation: zeta with its traction "
+                         "right-hand side, gamma_0 = 0, GMRES from the previous solve's "
+                         "density; measured on the GPU path in that form)")
     ap.add_argument("--single-op", choices=["K", "S", "A"], default=None,
                     help="apply one layer operator on the workload geometry and exit")
     ap.add_argument("--no-contact-bench", action="store_true")
