@@ -106,7 +106,9 @@ typedef struct sps_params {
                          gamma_0 costs one more mobility solve (g_0 = M
                          gamma_0 + q) and is dropped for gamma_0 = 0 when its
                          min-map residual is not below that of gamma_0 = 0.
-                         Every step still meets bbpgd_tol.  Default 0.       */
+                         Every step still meets bbpgd_tol.  Boundary-integral
+                         mobility only (the identity mobility always starts
+                         from 0).  Default 0.                                */
 } sps_params;
 
 typedef struct sps_stats {
@@ -208,8 +210,9 @@ int sps_resolve_collisions(sps_ctx* ctx, int n, const double* pos, const double*
  * with the positions after each step; FT_ext (n x 6) acts at every step; UO
  * (n x 6) receives the velocities of the last step.  stats_per_step: HOST
  * array of `steps` sps_stats or NULL.  Stops at the first step whose status
- * is not SPS_OK and returns it; *steps_done (host, may be NULL) counts the
- * completed steps.  The multi-step workloads of Sec. 6 (for instance the
+ * is not SPS_OK and returns it (pos then holds that step's update, as
+ * sps_resolve_collisions' pos_out would); *steps_done (host, may be NULL)
+ * counts the steps completed with SPS_OK.  The multi-step workloads of Sec. 6 (for instance the
  * sedimenting cluster of Sec. 6.3) are this loop. */
 int sps_simulate(sps_ctx* ctx, int n, double* pos, const double* radii, const double* FT_ext,
                  double dt, int steps, double* UO, sps_stats* stats_per_step, int* steps_done);
