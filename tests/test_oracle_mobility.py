@@ -8,7 +8,9 @@
   discretisation level, improving spectrally with p;
 * exact equivariance under the rotation by 2 pi/(2p+2) about z, which maps the
   grid onto itself;
-* the GMRES routine against a dense solve."""
+* the GMRES routine against a dense solve;
+* eq. rigidbodyrho rearranged for mu = rho + zeta (the form the CUDA path
+  solves) gives the same density and velocities."""
 from math import pi
 
 import numpy as np
@@ -98,3 +100,26 @@ def test_gradient_wrt_force_exact_vs_fd():
     fd = adjoint.grad_fd(c, a, FT, p, coords, h=1e-4)
     ref = np.array([g[i, k] for _, i, k in coords])
     assert np.abs(fd - ref).max() < 1e-7 * np.abs(g).max()   # L is quadratic in F
+
+
+def test_rearranged_unknown_gives_the_same_solve():
+    """eq. rigidbodyrho solved for mu = rho + zeta: (I/2 + K + L)[mu] = L[rho],
+    since (I/2 + K + L)[rho] - (I/2 + K)[rho] = L[rho].  The CUDA path solves
+    this form (its right-hand side needs no traction application); with the
+    oracle's operators both forms give the same density and velocities."""
+    rng = np.random.default_rng(11)
+    C = np.array([[0.0, 0.0, 0.0], [2.3, 0.4, -0.2], [0.3, 2.6, 0.5]])
+    R = np.array([1.0, 0.8, 0.9])
+    sus = Suspension(C, R, 3)
+    FT = rng.standard_normal((3, 6))
+    rho = mobility.rho_from_FT(sus, FT)
+    A = lambda z: mobility.apply_A(sus, z.reshape(-1, 3)).reshape(-1)
+    b_zeta = -(0.5 * rho + sus.apply("K", rho)).reshape(-1)
+    b_mu = mobility.apply_L(sus, rho).reshape(-1)
+    zeta, _, _ = mobility.gmres(A, b_zeta, 1e-14, 300)
+    mu, _, _ = mobility.gmres(A, b_mu, 1e-14, 300)
+    assert np.abs(mu - (rho.reshape(-1) + zeta)).max() < 1e-11 * np.abs(mu).max()
+    U_zeta = mobility.extract_velocity(sus, sus.apply("S", rho + zeta.reshape(-1, 3)))
+    U_mu = mobility.extract_velocity(sus, sus.apply("S", mu.reshape(-1, 3)))
+    assert np.abs(U_mu - U_zeta).max() < 1e-11 * np.abs(U_zeta).max()
+    assert np.abs(U_zeta - mobility.mobility_apply(sus, FT, tol=1e-14)).max() < 1e-11 * np.abs(U_zeta).max()
