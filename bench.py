@@ -253,6 +253,7 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
     clocks.start()
     sps._lib.load().sps_profile(ctx.h, 1)
+    pos_t0 = pos.clone()                     # the e2e leg replays from here
     torch.cuda.nvtx.range_push("timed")      # ncu --nvtx-include "timed/" captures this region
     for k in range(args.steps):
         flush.zero_()                      # L2 flush between timed steps (outside the events)
@@ -297,7 +298,9 @@ def run_gpu(args, w):
         hg = torch.empty(16 * N, dtype=torch.float64).pin_memory()
         hU = torch.empty(N, 6, dtype=torch.float64).pin_memory()
         hp = torch.empty(N, 3, dtype=torch.float64).pin_memory()
-        hpos.copy_(pos.cpu())
+        # replay the timed region's trajectory: one untimed host step from its
+        # first positions, then the timed host steps (its steps 2, 3, ...)
+        hpos.copy_(pos_t0.cpu())
         ctx.resolve_collisions_host(hpos, hrad, hFT, w.dt, hg, hU, hp, allow=allow)
         hpos.copy_(hp)
         # re-run timing cleanly (per-call wall time, flush outside)
@@ -313,7 +316,8 @@ def run_gpu(args, w):
         e2e = {"value": args.e2e_steps / e2e_total, "unit": "steps/s",
                "h2d_bytes_per_step": int(8 * (3 * N + N + 6 * N)),
                "d2h_bytes_per_step": int(8 * (6 * N + 3 * N + nc)),
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps,
+               "replays": "steps 2.. of the timed region (positions restored, one untimed host step)"}
 
     # FP64 vs mixed: one traction-operator application each, same geometry
     mv = {}
