@@ -260,18 +260,40 @@ def self_terms(sig_sphere, p, radius):
 # full layer operators on a suspension
 # ----------------------------------------------------------------------------
 class Suspension:
-    """Geometry of N spheres of order p: nodes, normals, weights, near lists."""
+    """Geometry of N spheres of order p: nodes, normals, weights, near lists.
 
-    def __init__(self, centers, radii, p, beta=1.75):
+    rotations (optional, N x 3 x 3 orthogonal): the orientation Q_i of each
+    sphere's grid (Sec. 5.4 orients every sphere's grid at random).  Node k of
+    sphere i sits at c_i + a_i Q_i n_k; the sphere's VSH expansions live in its
+    own frame, so densities are rotated into it (components Q_i^T s) before
+    the analysis and fields evaluated from it are rotated back (Q_i u).
+    Without rotations every Q_i is the identity."""
+
+    def __init__(self, centers, radii, p, beta=1.75, rotations=None):
         self.c = np.asarray(centers, dtype=np.float64).reshape(-1, 3)
         self.a = np.asarray(radii, dtype=np.float64).reshape(-1)
         self.p = p
         self.N = len(self.a)
         self.P = sph.nodes_per_sphere(p)
         self.beta = beta
+        self.Q = None if rotations is None else np.asarray(rotations, dtype=np.float64).reshape(-1, 3, 3)
         self.X, self.Nrm, self.W = sph.sphere_nodes(self.c, self.a, p)
+        if self.Q is not None:
+            # rotate each sphere's unit grid: n_k -> Q_i n_k (rows: n_k^T Q_i^T)
+            nrm = self.Nrm.reshape(self.N, self.P, 3)
+            nrm = np.einsum("ikj,imj->ikm", nrm, self.Q)
+            self.Nrm = nrm.reshape(-1, 3)
+            self.X = (self.c[:, None, :] + self.a[:, None, None] * nrm).reshape(-1, 3)
         self.sph_of = np.repeat(np.arange(self.N), self.P)
         self.near = near_lists(self.c, self.a, beta)
+
+    def to_local(self, j, v):
+        """Vectors (rows) from the lab frame into sphere j's grid frame."""
+        return v if self.Q is None else v @ self.Q[j]
+
+    def to_lab(self, j, v):
+        """Vectors (rows) from sphere j's grid frame into the lab frame."""
+        return v if self.Q is None else v @ self.Q[j].T
 
     def nodes(self, i):
         return slice(i * self.P, (i + 1) * self.P)
@@ -288,19 +310,20 @@ class Suspension:
 
         def coef_of(j):
             if j not in coefs:
-                coefs[j] = sph.analysis(sig[self.nodes(j)] , self.p)
+                coefs[j] = sph.analysis(self.to_local(j, sig[self.nodes(j)]), self.p)
             return coefs[j]
 
         for i in tg:
             sl = self.nodes(i)
-            # self
-            ss, ks = self_terms(sig[sl], self.p, self.a[i])
-            acc = (ss if op == "S" else ks).copy()
-            # near
+            # self (in sphere i's grid frame)
+            ss, ks = self_terms(self.to_local(i, sig[sl]), self.p, self.a[i])
+            acc = self.to_lab(i, ss if op == "S" else ks).copy()
+            # near: targets and normals in sphere j's frame, fields back
             for j in self.near[i]:
-                u, t = vsh_field(coef_of(j), self.p, self.c[j], self.a[j],
-                                 self.X[sl], None if op == "S" else self.Nrm[sl])
-                acc += u if op == "S" else t
+                xt = self.c[j] + self.to_local(j, self.X[sl] - self.c[j])
+                nt = None if op == "S" else self.to_local(j, self.Nrm[sl])
+                u, t = vsh_field(coef_of(j), self.p, self.c[j], self.a[j], xt, nt)
+                acc += self.to_lab(j, u if op == "S" else t)
             out[sl] = acc
         # far
         tmask = np.zeros(self.N, dtype=bool)

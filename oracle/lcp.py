@@ -151,14 +151,14 @@ def lcp_enumerate(Mmat, q):
 def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
                        a_c_scale=1.0, gmres_tol=1e-12, gmres_max=200,
                        bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
-                       delta_rel=0.0):
+                       delta_rel=0.0, rotations=None):
     """One collision-resolved Euler step (Sec. 3.2, four-step procedure).
 
     1. U_nc = M F_ext; 2. contacts and D; 3. BBPGD for gamma with
     M gamma = D^T M D gamma; 4. U = U_nc + M D gamma, c += U dt.
     Returns dict with gamma, ij, phi, normals, U (N x 6), centers_new, info.
     """
-    sus = Suspension(centers, radii, p, beta)
+    sus = Suspension(centers, radii, p, beta, rotations)
     U_nc, inf0 = mobility.mobility_apply(sus, FT_ext, gmres_tol, gmres_max, return_info=True)
     ij, phi0, nrm = build_contacts(centers, radii, delta, a_c_scale, delta_rel)
     q = phi0 / dt + DT_apply(ij, nrm, U_nc)

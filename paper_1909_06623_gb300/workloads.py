@@ -335,3 +335,17 @@ def sedimenting_cluster(seed=SEED_BASE + 6, N=1000, phi=0.20, a=1.0, a_c_scale=1
     FT[:, 2] = -1.0
     return Workload(f"sed_cluster_N{N}_phi{phi:.2f}", C, R, FT, p=p, dt=0.05 * a * a, steps=steps,
                     params=dict(delta=0.0, delta_rel=0.3, a_c_scale=a_c_scale, bbpgd_tol=1e-4))
+
+
+def random_rotations(seed, N):
+    """N rotation matrices drawn uniformly from SO(3) (unit quaternions from
+    normalised 4-d Gaussian vectors): the random orientation of each sphere's
+    grid (Sec. 5.4).  N x 3 x 3 float64."""
+    rng = np.random.default_rng(seed)
+    q = rng.standard_normal((N, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)

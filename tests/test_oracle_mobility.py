@@ -10,7 +10,11 @@
   grid onto itself;
 * the GMRES routine against a dense solve;
 * eq. rigidbodyrho rearranged for mu = rho + zeta (the form the CUDA path
-  solves) gives the same density and velocities."""
+  solves) gives the same density and velocities;
+* randomly oriented sphere grids (Sec. 5.4): identity orientations change
+  nothing, one sphere keeps its exact drag, a global rotation of centres,
+  grids and forces rotates the velocities exactly, and the velocities differ
+  from the unrotated grids' only at the discretisation level."""
 from math import pi
 
 import numpy as np
@@ -18,6 +22,7 @@ import pytest
 
 from oracle import mobility
 from oracle.layer import Suspension
+from paper_1909_06623_gb300 import workloads
 
 
 @pytest.mark.parametrize("a", [1.0, 0.55])
@@ -123,3 +128,34 @@ def test_rearranged_unknown_gives_the_same_solve():
     U_mu = mobility.extract_velocity(sus, sus.apply("S", mu.reshape(-1, 3)))
     assert np.abs(U_mu - U_zeta).max() < 1e-11 * np.abs(U_zeta).max()
     assert np.abs(U_zeta - mobility.mobility_apply(sus, FT, tol=1e-14)).max() < 1e-11 * np.abs(U_zeta).max()
+
+
+def _rot6(U, R):
+    return np.concatenate([U[:, :3] @ R.T, U[:, 3:] @ R.T], axis=1)
+
+
+def test_random_grid_orientations():
+    p = 4
+    c = np.array([[0.0, 0.0, 0.0], [2.4, 0.5, -0.3], [0.2, 2.5, 0.6]])
+    a = np.array([1.0, 0.8, 0.9])
+    FT = np.array([[0.2, -0.5, 1.0, 0.1, 0.0, 0.3], [-0.4, 0.1, 0.2, 0.0, 0.2, 0.0],
+                   [0.3, 0.3, -0.6, 0.1, -0.2, 0.4]])
+    Q = workloads.random_rotations(5, 3)
+    assert np.abs(np.einsum("nij,nkj->nik", Q, Q) - np.eye(3)).max() < 1e-14
+    assert np.allclose(np.linalg.det(Q), 1.0)
+    U0 = mobility.mobility_apply(Suspension(c, a, p), FT, 1e-13)
+    # identity orientations: the same arithmetic
+    Ui = mobility.mobility_apply(Suspension(c, a, p, rotations=np.tile(np.eye(3), (3, 1, 1))), FT, 1e-13)
+    assert np.abs(Ui - U0).max() < 1e-14
+    # one sphere: exact drag in any orientation
+    U1 = mobility.mobility_apply(Suspension(c[:1], a[:1], p, rotations=Q[:1]), FT[:1], 1e-14)
+    assert np.abs(U1[0, :3] - FT[0, :3] / (6 * pi)).max() < 1e-14
+    assert np.abs(U1[0, 3:] - FT[0, 3:] / (8 * pi)).max() < 1e-14
+    # global rotation of centres, grids and forces
+    UQ = mobility.mobility_apply(Suspension(c, a, p, rotations=Q), FT, 1e-13)
+    R = workloads.random_rotations(6, 1)[0]
+    UR = mobility.mobility_apply(Suspension(c @ R.T, a, p, rotations=np.einsum("ij,njk->nik", R, Q)),
+                                 _rot6(FT, R), 1e-13)
+    assert np.abs(UR - _rot6(UQ, R)).max() < 1e-11 * np.abs(UQ).max()
+    # orientation changes the result only through the discretisation
+    assert 1e-9 < np.abs(UQ - U0).max() < 1e-3 * np.abs(U0).max()
