@@ -162,6 +162,16 @@ int sps_nodes(sps_ctx* ctx, double* X, double* normals, double* weights, int* np
  * Errors: NO_GEOMETRY before sps_set_geometry. */
 int sps_geometry_counts(const sps_ctx* ctx, int* n_near_pairs, int* n_close_entries);
 
+/* The near-pair lists of the current geometry (Sec. 4.2: sphere j is near
+ * sphere i when j != i and |c_i - c_j| < beta (a_i + a_j), with
+ * d^2 = (dx dx + dy dy) + dz dz and the product beta (a_j + a_i) each rounded
+ * once), as CSR by target sphere: near_ptr (N + 1 int32, device output),
+ * near_idx (the n_near_pairs of sps_geometry_counts, int32, device output),
+ * the sources of sphere i in near_idx[near_ptr[i] .. near_ptr[i+1]), ascending.
+ * These pairs take the VSH near evaluation; every other pair takes the far
+ * quadrature.  Either pointer may be NULL.  Errors: NO_GEOMETRY. */
+int sps_near_lists(sps_ctx* ctx, int* near_ptr, int* near_idx);
+
 /* Layer operator (sps_op) applied to sigma (3 planes of NP, device) on the
  * current geometry; out (3 planes) is overwritten.  Self part: VSH multipliers
  * (Sec. 4.2); near pairs: VSH expansion of the source sphere (Sec. 4.2); all
@@ -268,26 +278,37 @@ int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, const double* 
                           double* dL_dFT, double* dL_dpos, sps_stats* stats);
 
 /* Contact set of sps_build_contacts for callers that cannot allocate device
- * memory when they need it: code running while a stream is being captured into
- * a CUDA graph (cudaMalloc is not a capturable operation), hosts whose own
- * memory pool owns the device, or stepping loops that must never allocate.
- * No counterpart in the paper: it is the same contact set (Sec. 3.2), computed
- * without a context and without any cudaMalloc / cudaFree.
+ * memory when they need it: code embedded in a host whose own memory pool has
+ * reserved the device (a framework's caching allocator, an MPS client with a
+ * hard memory limit), where a cudaMalloc outside that pool fails or fragments
+ * it, and time-stepping loops that must not pay for, or risk failing on, an
+ * allocation in the middle of a step.  The paper has no counterpart: it is an
+ * allocation-free variant of sps_build_contacts, computed without a context
+ * and without any cudaMalloc / cudaFree.
+ *
+ * Threshold: the absolute delta only, i.e. the list of sps_build_contacts with
+ * delta_rel = 0 (the relative part delta_rel (a_i + a_j) is not supported).
+ * Search: all pairs, one thread per sphere i testing every j > i, so the cost
+ * is n (n - 1) / 2 pair tests (3.4e10 at the size limit) and the work per
+ * thread falls from n - 1 to 0 across the grid; the context builder's cell
+ * list is the one for large n.
  *
  * Scratch: a fixed device array inside the library (one counter per sphere,
  * about 1 MB) that every GPU loading the library keeps until the process
  * exits.  n <= 262,144 spheres (larger n returns SPS_ERR_CAPACITY).  The first
- * call on a device looks up that array's device address; make that first call
- * before any stream capture.  All calls share the array: calls that overlap on
- * the GPU (different streams or threads at the same time) race and must not be
- * issued.  Every counter a call reads is written by the same call first.
+ * call on a device looks up that array's device address (once per device,
+ * with that device current).  All calls share the array and it keeps the
+ * last call's contents: calls that overlap on the GPU (different streams or
+ * threads at the same time) race and must not be issued.  Every counter a
+ * call reads is written by the same call first.
  *
  * pos (n x 3), radii (n): device inputs.  ij (max_contacts x 2 int32), phi
  * (max_contacts), normals (max_contacts x 3): device outputs, written in the
  * order of sps_build_contacts (bit-identical values).  *n_contacts_out (host)
  * receives n_c; if n_c > max_contacts the call returns SPS_ERR_CAPACITY and
  * writes no output array.  stream: cudaStream_t (NULL = legacy default).  The
- * call synchronises the stream before returning. */
+ * call reads the count back to the host and synchronises the stream before
+ * returning. */
 int sps_build_contacts_noalloc(int n, const double* pos, const double* radii, double a_c_scale,
                                double delta, int max_contacts, int* ij, double* phi,
                                double* normals, int* n_contacts_out, void* stream);

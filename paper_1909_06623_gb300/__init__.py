@@ -121,6 +121,14 @@ class Context:
         self._check(self.lib.sps_geometry_counts(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
+    def near_lists(self):
+        """(near_ptr (N+1), near_idx) of the current geometry, int32 device tensors."""
+        nn, _ = self.geometry_counts()
+        ptr = torch.empty(self.n + 1, dtype=torch.int32, device="cuda")
+        idx = torch.empty(max(nn, 1), dtype=torch.int32, device="cuda")
+        self._check(self.lib.sps_near_lists(self.h, _ptr(ptr, torch.int32), _ptr(idx, torch.int32)))
+        return ptr, idx[:nn]
+
     def nodes(self):
         NP = self.n * self.P
         X = torch.empty(3, NP, dtype=torch.float64, device="cuda")

@@ -694,6 +694,19 @@ extern "C" int sps_geometry_counts(const sps_ctx* ctx, int* n_near_pairs, int* n
   return SPS_OK;
 }
 
+extern "C" int sps_near_lists(sps_ctx* ctx, int* near_ptr, int* near_idx) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!ctx->have_geom) return sps_fail(ctx, SPS_ERR_NO_GEOMETRY, "no geometry");
+  if (near_ptr)
+    SPS_CUDA(ctx, cudaMemcpyAsync(near_ptr, ctx->d_near_ptr, sizeof(int) * (ctx->N + 1),
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  if (near_idx && ctx->n_near > 0)
+    SPS_CUDA(ctx, cudaMemcpyAsync(near_idx, ctx->d_near_idx, sizeof(int) * ctx->n_near,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
 extern "C" int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double* out) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
   if (!ctx->have_geom) return sps_fail(ctx, SPS_ERR_NO_GEOMETRY, "no geometry");

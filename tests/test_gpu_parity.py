@@ -64,6 +64,29 @@ def test_nodes_match_oracle(sps):
     assert np.abs(W.cpu().numpy() - Wo).max() < 1e-14
 
 
+@pytest.mark.parametrize("name", ["cfg2_sample.npz", "tiny_layers.npz"])
+def test_near_lists_match_oracle(sps, name):
+    """Near pairs (Sec. 4.2), exact: per-sphere counts against the oracle's
+    stored counts (config 2) and the whole CSR against the oracle's lists."""
+    from oracle.layer import near_lists
+    d = load(name)
+    if name == "tiny_layers.npz":
+        C, R, p = d["c1_centers"], d["c1_radii"], int(d["c1_p"])
+    else:
+        C, R, p = d["centers"], d["radii"], int(d["p"])
+    ctx = sps.Context(p=p, beta=1.75)
+    ctx.set_geometry(dev(C), dev(R))
+    ptr, idx = ctx.near_lists()
+    ptr, idx = ptr.cpu().numpy(), idx.cpu().numpy()
+    ref = near_lists(C, R, 1.75)
+    counts = np.diff(ptr)
+    assert np.array_equal(counts, [len(x) for x in ref])
+    if "near_count" in d.files:
+        assert np.array_equal(counts, d["near_count"])
+    assert np.array_equal(idx, np.concatenate(ref).astype(np.int32))
+    assert ctx.geometry_counts()[0] == len(idx)
+
+
 @pytest.mark.parametrize("name,acs", [("cfg2_sample.npz", 1.0), ("cfg1_step.npz", 1.0),
                                       ("active_step_p4.npz", 1.05)])
 def test_contacts_bit_exact(sps, name, acs):

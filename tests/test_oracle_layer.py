@@ -186,3 +186,57 @@ def test_kernel_formulas():
             for l in range(3):
                 S[i, k, l] = -pk[k] * (i == l) + dG[l, i, k] + dG[i, l, k]
     assert np.allclose(S, T, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# near-pair lists (Sec. 4.2): j is near i when |c_i - c_j| < beta (R_i + R_j)
+# ---------------------------------------------------------------------------
+def test_near_lists_threshold_hand_example():
+    """Spheres placed on the threshold beta (R_i + R_j), beta = 1.75, each
+    against sphere 0 (a = 1 at the origin) along its own axis, far from the
+    others.  Along an axis the centre distance is exactly the coordinate
+    (sqrt(fl(x * x)) = |x| in binary floating point).
+      1: a = 0.5 at exactly 1.75 * 1.5 = 2.625          -> not near (strict <)
+      2: a = 0.5 at 2.625 (1 - 1e-12)                    -> near
+      3: a = 1   at 3.5 (1 + 1e-12)                      -> not near
+      4: a = 0.6 at 1.5 * 1.75 * 1.6: inside beta times the sum of the
+         diameters, outside beta times the sum of the radii -> not near
+      5: a = 0.6 at 2.8 (1 - 1e-12) on -y                -> near"""
+    beta = 1.75
+    C = np.array([[0.0, 0.0, 0.0],
+                  [2.625, 0.0, 0.0],
+                  [0.0, 2.625 * (1 - 1e-12), 0.0],
+                  [0.0, 0.0, 3.5 * (1 + 1e-12)],
+                  [-1.5 * 1.75 * 1.6, 0.0, 0.0],
+                  [0.0, -2.8 * (1 - 1e-12), 0.0]])
+    R = np.array([1.0, 0.5, 0.5, 1.0, 0.6, 0.6])
+    near = layer.near_lists(C, R, beta)
+    assert [list(x) for x in near] == [[2, 5], [], [0], [], [], [0]]
+
+
+def test_near_lists_match_kdtree_brute_force():
+    """Random polydisperse suspension: the lists equal those from a k-d tree
+    pair query (candidates within beta * 2 max a) filtered with an independent
+    distance routine (math.dist), both directions, no self pairs, ascending."""
+    import math
+
+    from scipy.spatial import cKDTree
+
+    from paper_1909_06623_gb300 import workloads
+    C, R, _ = workloads.random_suspension(1234, 400, 0.30, pair_frac=0.05)
+    beta = 1.75
+    near = layer.near_lists(C, R, beta)
+    ref = [set() for _ in range(len(R))]
+    margins = []
+    for i, j in cKDTree(C).query_pairs(beta * 2 * R.max()):
+        d = math.dist(C[i], C[j])
+        lim = beta * (R[i] + R[j])
+        margins.append(abs(d - lim) / lim)
+        if d < lim:
+            ref[i].add(j)
+            ref[j].add(i)
+    assert min(margins) > 1e-9      # no pair sits on the threshold
+    for i in range(len(R)):
+        assert list(near[i]) == sorted(ref[i])
+    total = sum(len(x) for x in near)
+    assert 5 * len(R) < total < 30 * len(R)   # about 15 per sphere at this packing
