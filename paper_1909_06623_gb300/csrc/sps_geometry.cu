@@ -356,15 +356,16 @@ int sps_launch_extract(sps_ctx* ctx, const double* mom, double* UO) {
 // Contact set without allocation.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// contact list: code running while a CUDA stream is being captured into a
-// graph (a plain cudaMalloc is not a capturable operation), code embedded in a
-// host that owns the whole device through its own memory pool (a framework
-// allocator, an MPS client with a hard memory limit), or a time-stepping loop
-// that must not pay for, or risk failing on, an allocation in the middle of a
-// step.  This variant of the contact builder keeps its only scratch (one
-// counter per sphere plus the scan's block totals) in a fixed device array
-// that lives as long as the library is loaded.  The caller passes positions,
-// radii and output buffers.
+// contact list: code embedded in a host whose own memory pool has reserved the
+// device (a framework's caching allocator, an MPS client with a hard memory
+// limit), where a cudaMalloc outside that pool fails or fragments it, or a
+// time-stepping loop that must not pay for, or risk failing on, an allocation
+// in the middle of a step.  This variant of the contact builder keeps its only
+// scratch (one counter per sphere plus the scan's block totals) in a fixed
+// device array that lives as long as the library is loaded.  The caller passes
+// positions, radii and output buffers.  It searches all pairs (one thread per
+// sphere i over j > i), O(n^2) pair tests, with the absolute threshold delta
+// only (no relative part).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -468,7 +469,9 @@ extern "C" int sps_build_contacts_noalloc(int n, const double* pos, const double
   int* totals = cnt + kStaticMaxSpheres + 1;
   cudaStream_t st = (cudaStream_t)stream;
   k_static_count<<<(n + 127) / 128, 128, 0, st>>>(n, pos, radii, a_c_scale, delta, cnt);
+  if (cudaGetLastError() != cudaSuccess) return SPS_ERR_CUDA;
   k_static_scan<<<1, kScanThreads, 0, st>>>(n + 1, cnt, totals);
+  if (cudaGetLastError() != cudaSuccess) return SPS_ERR_CUDA;
   int nc = 0;
   if (cudaMemcpyAsync(&nc, cnt + n, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {

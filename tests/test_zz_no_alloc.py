@@ -1,13 +1,14 @@
 """The allocation-free contact builder (sps_build_contacts_noalloc).
 
 Some callers cannot allocate device memory when they need the contact list:
-code running while a stream is captured into a CUDA graph (cudaMalloc is not
-capturable), hosts whose own memory pool owns the whole device, and stepping
-loops that must never allocate mid-step.  For them the library keeps the
-builder's scratch in a fixed device array.  This test calls that entry point
-through the C ABI and checks it against the ordinary entry point
-(sps_build_contacts + sps_get_contacts), bit for bit, on two calls in a row
-with different inputs (the shared array must not carry state between calls).
+code inside a host whose own memory pool has reserved the device (a framework's
+caching allocator, an MPS client with a hard memory limit), where a cudaMalloc
+outside that pool fails, and stepping loops that must never allocate mid-step.
+For them the library keeps the builder's scratch in a fixed device array.
+This test calls that entry point through the C ABI and checks it against the
+ordinary entry point (sps_build_contacts + sps_get_contacts, delta_rel = 0),
+bit for bit, on two calls in a row with different inputs (the shared array
+must not carry state between calls).
 The file name sorts last so that a run stopping at the first failure has run
 every other test before this one.
 """
