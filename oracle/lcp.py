@@ -24,6 +24,13 @@ Paper: Yan et al., arXiv 1909.06623.
     symmetric only to discretisation accuracy, so s^T M s can turn
     non-positive for nearly touching spheres at low order p); j_max caps the
     loop.
+  * Failure rule (keep_best=True; Algorithm 1 says nothing about a loop that
+    ends without meeting eps_tol): a residual at or above GROWTH_LIMIT times
+    max(phi_0, eps_tol) stops with "breakdown" (an indefinite discrete M makes
+    the projected steps grow without bound), and whenever the loop stops
+    without meeting eps_tol (breakdown, growth or j_max) the iterate of
+    smallest residual among gamma_0, gamma_1, ... is returned (the earliest
+    on ties).  Off by default.
   * eq. time-step: C^{k+1} = C^k + (U_nc + M D gamma) dt, positions only
     (spheres are isotropic; the grid keeps its lab-frame orientation).
 """
@@ -78,10 +85,15 @@ def minmap(gamma, g):
     return float(np.linalg.norm(np.minimum(gamma, g)))
 
 
-def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False, gamma0=None):
+GROWTH_LIMIT = 1e6
+
+
+def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False, gamma0=None, keep_best=False):
     """Algorithm 1.  Mop(gamma) -> M gamma.  gamma0: the algorithm's initial
     guess (default 0, the paper's choice, whose product M gamma_0 = 0 needs no
-    evaluation).  Returns gamma, g, info."""
+    evaluation).  keep_best: the failure rule of the module docstring.
+    Returns gamma, g, info; info["history"] lists the residual of every
+    iterate (gamma_0 first) and info["best"] the index of the one returned."""
     q = np.asarray(q, dtype=np.float64)
     mv = 0
     if gamma0 is None or not np.any(gamma0):
@@ -91,8 +103,10 @@ def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False, gamma0=None):
         gamma = np.asarray(gamma0, dtype=np.float64).copy()
         g = Mop(gamma) + q
         mv += 1
-    info = {"iters": 0, "mvops": mv, "status": "ok", "phi": minmap(gamma, g), "safeguards": 0}
-    if info["phi"] < tol:
+    phi0 = minmap(gamma, g)
+    info = {"iters": 0, "mvops": mv, "status": "ok", "phi": phi0, "safeguards": 0,
+            "history": [phi0], "best": 0}
+    if phi0 < tol:
         return gamma, g, info
     Mg = Mop(g)
     mv += 1
@@ -101,6 +115,16 @@ def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False, gamma0=None):
         info.update(status="breakdown", mvops=mv)
         return gamma, g, info
     alpha = (g @ g) / gMg
+    best = (phi0, 0, gamma, g)
+    limit = GROWTH_LIMIT * max(phi0, tol)
+
+    def stop(status):
+        info["status"] = status
+        if keep_best and best[1] != info["iters"]:
+            info.update(phi=best[0], best=best[1])
+            return best[2], best[3], info
+        return gamma, g, info
+
     for j in range(1, jmax + 1):
         gamma_new = np.maximum(gamma - alpha * g, 0.0)
         g_new = Mop(gamma_new) + q
@@ -109,21 +133,24 @@ def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False, gamma0=None):
         s = gamma_new - gamma
         y = g_new - g
         gamma, g = gamma_new, g_new
-        info.update(iters=j, mvops=mv, phi=phi)
+        info.update(iters=j, mvops=mv, phi=phi, best=j)
+        info["history"].append(phi)
         if phi < tol:
             return gamma, g, info
+        if phi < best[0]:
+            best = (phi, j, gamma, g)
+        if keep_best and not phi < limit:
+            return stop("breakdown")
         sy = s @ y
         yy = y @ y
         ok = sy > 0 if variant == 1 else (sy > 0 and yy > 0)
         if not ok:
             if not safeguard:
-                info["status"] = "breakdown"
-                return gamma, g, info
+                return stop("breakdown")
             info["safeguards"] += 1          # keep the previous step length
             continue
         alpha = (s @ s) / sy if variant == 1 else sy / yy
-    info["status"] = "not_converged"
-    return gamma, g, info
+    return stop("not_converged")
 
 
 def lcp_enumerate(Mmat, q):
@@ -151,12 +178,14 @@ def lcp_enumerate(Mmat, q):
 def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
                        a_c_scale=1.0, gmres_tol=1e-12, gmres_max=200,
                        bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
-                       delta_rel=0.0, rotations=None):
+                       delta_rel=0.0, rotations=None, keep_best=False):
     """One collision-resolved Euler step (Sec. 3.2, four-step procedure).
 
     1. U_nc = M F_ext; 2. contacts and D; 3. BBPGD for gamma with
     M gamma = D^T M D gamma; 4. U = U_nc + M D gamma, c += U dt.
-    Returns dict with gamma, ij, phi, normals, U (N x 6), centers_new, info.
+    keep_best: the failure rule of bbpgd; U then uses M D gamma of the
+    iterate returned.  Returns dict with gamma, ij, phi, normals, U (N x 6),
+    centers_new, info.
     """
     sus = Suspension(centers, radii, p, beta, rotations)
     U_nc, inf0 = mobility.mobility_apply(sus, FT_ext, gmres_tol, gmres_max, return_info=True)
@@ -168,15 +197,19 @@ def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
         UO, inf = mobility.mobility_apply(sus, D_apply(sus.N, ij, nrm, gam),
                                           gmres_tol, gmres_max, return_info=True)
         state["U_c"] = UO
+        state["U_c_of"].append(UO)
         state["solves"] += 1
         state["gmres"] += inf["gmres_iters"]
         return DT_apply(ij, nrm, UO)
 
-    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard)
-    if info["iters"] == 0:
+    state["U_c_of"] = []
+    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard, keep_best=keep_best)
+    if info["iters"] == 0 or info["best"] == 0:
         U_c = np.zeros_like(U_nc)       # gamma = gamma_0 = 0
     else:
-        U_c = state["U_c"]              # solve of the last iterate, the returned gamma
+        # the solve of the returned iterate: Mop's calls are M g_0, then one
+        # per iterate gamma_1, gamma_2, ...
+        U_c = state["U_c_of"][info["best"]]
     U = U_nc + U_c
     cnew = np.asarray(centers, dtype=np.float64) + U[:, :3] * dt
     info.update(solves=state["solves"], gmres_iters=state["gmres"], n_contacts=len(q),

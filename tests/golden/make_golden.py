@@ -56,6 +56,26 @@ def active():
           bbpgd_tol=1e-12)
 
 
+def capped():
+    """The five-sphere active step with Algorithm 1 capped at j_max = 2 and 7
+    under the failure rule (keep_best): at both caps the last iterate is not
+    the one of smallest residual (residuals 2.47, 0.968, 1.002, ...; iterate
+    6 at 3.6e-3, iterate 7 at 6.8e-3)."""
+    d = np.load(os.path.join(HERE, "active_step_p4.npz"))
+    out = {}
+    for jmax in (2, 7):
+        r = lcp.resolve_collisions(d["centers"], d["radii"], d["FT"], float(d["dt"]), int(d["p"]),
+                                   delta=0.1, a_c_scale=1.05, gmres_tol=1e-13, bbpgd_tol=1e-12,
+                                   bbpgd_max=jmax, keep_best=True)
+        out[f"gamma_{jmax}"] = r["gamma"]
+        out[f"U_{jmax}"] = r["U"]
+        out[f"best_{jmax}"] = r["info"]["best"]
+        out[f"phi_{jmax}"] = r["info"]["phi"]
+        out[f"history_{jmax}"] = np.array(r["info"]["history"])
+        print("capped", jmax, r["info"]["status"], r["info"]["best"], r["info"]["history"])
+    np.savez_compressed(os.path.join(HERE, "capped_step_p4.npz"), **out)
+
+
 def cfg2_sample():
     """Config 2 geometry (1,000 spheres, p = 6): contacts, near lists and the
     layer operators S, K, I/2+K+L of a seeded random density on a sample of
@@ -175,7 +195,7 @@ def sed_steps():
                         n_active=np.array(active))
 
 
-ALL = {"cfg1": cfg1, "active": active, "cfg2": cfg2_sample, "tiny": tiny_layers,
+ALL = {"cfg1": cfg1, "active": active, "capped": capped, "cfg2": cfg2_sample, "tiny": tiny_layers,
        "collision_grad": collision_grad, "collision_grad_c": collision_grad_c,
        "sed_steps": sed_steps}
 

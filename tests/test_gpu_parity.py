@@ -269,6 +269,27 @@ def test_step_fp64(sps, name, acs):
     _check_step(d, gam.cpu().numpy(), U.cpu().numpy(), pn.cpu().numpy(), TOL64)
 
 
+@pytest.mark.parametrize("jmax", [2, 7])
+def test_capped_step_returns_oracle_best_iterate(sps, jmax):
+    """Algorithm 1 capped at j_max = 2 and 7 on the five-sphere active step:
+    the library ends with NOT_CONVERGED and returns the iterate of smallest
+    min-map residual with its own M D gamma, which is not the last iterate
+    at either cap; the oracle's failure rule (keep_best) gives the same
+    gamma and U (FP64 path, 1e-10)."""
+    d = load("active_step_p4.npz")
+    c = load("capped_step_p4.npz")
+    assert int(c[f"best_{jmax}"]) < jmax
+    ctx = sps.Context(p=int(d["p"]), delta=0.1, a_c_scale=1.05, gmres_tol=1e-13, gmres_max=300,
+                      bbpgd_tol=1e-12, bbpgd_max=jmax, warm_start=0)
+    gam, U, _ = ctx.resolve_collisions(dev(d["centers"]), dev(d["radii"]), dev(d["FT"]),
+                                       float(d["dt"]), allow=(4,))
+    st = ctx.last_stats
+    assert st["status"] == 4 and st["bbpgd_iters"] == jmax
+    assert abs(st["final_phi"] - float(c[f"phi_{jmax}"])) <= 1e-10 * float(c[f"phi_{jmax}"])
+    assert relerr(gam.cpu().numpy(), c[f"gamma_{jmax}"]) < TOL64
+    assert relerr(U.cpu().numpy(), c[f"U_{jmax}"]) < TOL64
+
+
 def test_step_mixed_and_host_api(sps):
     d = load("active_step_p4.npz")
     p = int(d["p"])

@@ -231,3 +231,60 @@ def test_jittered_lattice_statistics():
     vol = np.sum(4 / 3 * np.pi * w.radii ** 3)
     L = np.ptp(w.centers, axis=0) + 2 * 1.0
     assert 0.25 < vol / np.prod(L) < 0.4
+
+
+# ---------------------------------------------------------------------------
+# failure rule (keep_best): smallest-residual iterate, growth guard
+# ---------------------------------------------------------------------------
+def _spd_lcp(seed, n=24):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    M = A @ A.T / n + 0.05 * np.eye(n)
+    return M, rng.standard_normal(n)
+
+
+def test_bbpgd_keep_best_returns_smallest_residual():
+    """Capped where BB's residual is not monotone: the returned residual is
+    the minimum over the recorded iterates (gamma_0 included), the returned
+    pair (gamma, g) has that residual, and it is the iterate an uncapped run
+    reaches at that index (bit for bit); without the rule the last iterate is
+    returned."""
+    found = 0
+    for seed in range(20):
+        M, q = _spd_lcp(seed)
+        mop = lambda g: M @ g
+        _, _, full = lcp.bbpgd(mop, q, 1e-12, jmax=500)
+        h = full["history"]
+        bad = [j for j in range(1, len(h)) if h[j] > min(h[:j])]
+        if not bad:
+            continue
+        j = bad[0]
+        gam, g, info = lcp.bbpgd(mop, q, 1e-12, jmax=j, keep_best=True)
+        assert info["status"] == "not_converged" and info["iters"] == j
+        assert info["phi"] == min(info["history"]) < info["history"][-1]
+        assert np.array_equal(g, M @ gam + q)
+        assert lcp.minmap(gam, g) == info["phi"]
+        gb, _, ib = lcp.bbpgd(mop, q, 1e-12, jmax=info["best"])
+        assert ib["iters"] == info["best"] and np.array_equal(gb, gam)
+        gl, _, il = lcp.bbpgd(mop, q, 1e-12, jmax=j)
+        assert il["phi"] == h[j] and not np.array_equal(gl, gam)
+        found += 1
+    assert found >= 3
+
+
+def test_bbpgd_growth_guard():
+    """An indefinite M (a negative diagonal entry) makes the projected steps
+    grow without bound; with the safeguard the loop would run to j_max and
+    overflow, the growth guard stops it with breakdown once the residual
+    reaches 1e6 times the initial one and returns the best iterate."""
+    M = np.array([[2.0, 0.0], [0.0, -0.5]])
+    q = np.array([-1.0, -1.0])
+    with np.errstate(over="ignore", invalid="ignore"):
+        _, _, free = lcp.bbpgd(lambda g: M @ g, q, 1e-10, jmax=200, safeguard=True)
+    assert free["status"] == "not_converged" and not free["phi"] < 1e12
+    gam, g, info = lcp.bbpgd(lambda g: M @ g, q, 1e-10, jmax=200, safeguard=True,
+                             keep_best=True)
+    h = info["history"]
+    assert info["status"] == "breakdown" and info["iters"] < 200
+    assert h[-1] >= lcp.GROWTH_LIMIT * h[0] and all(x < lcp.GROWTH_LIMIT * h[0] for x in h[:-1])
+    assert info["phi"] == min(h) and lcp.minmap(gam, g) == info["phi"]
