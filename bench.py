@@ -144,19 +144,52 @@ def ctx_params(precision, bb_warm=1):
 # ---------------------------------------------------------------------------
 # oracle (CPU) leg: a bounded sample of one layer-operator application
 # ---------------------------------------------------------------------------
-def oracle_sample(w, n_targets=3, seed=0):
-    """Times the FP64 oracle's traction operator K on n_targets target spheres
-    (self + near + all-pairs far field for those spheres) and scales it to one
-    full application (x N / n_targets)."""
+# layer-operator applications per config-2 step of the oracle's own algorithm
+# (eq. rigidbodyrho in zeta with its traction right-hand side, gamma_0 = 0,
+# GMRES from the previous solve's density), counted on the GPU path run in
+# that form; both CPU legs scale a one-application sample by it
+ORACLE_APPLIES_PER_STEP = 185.0
+
+
+def _oracle_worker(job):
+    """One process of the oracle sample: the traction operator K on its share
+    of the target spheres (seconds spent in the operator)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    centers, radii, p, seed, targets = job
     from oracle.layer import Suspension
-    sus = Suspension(w.centers, w.radii, w.p)
-    rng = np.random.default_rng(seed)
-    sig = rng.standard_normal((sus.N * sus.P, 3))
-    tg = list(rng.choice(sus.N, n_targets, replace=False))
+    sus = Suspension(centers, radii, p)
+    sig = np.random.default_rng(seed).standard_normal((sus.N * sus.P, 3))
     t0 = time.perf_counter()
-    sus.apply("K", sig, targets=tg)
-    dt = time.perf_counter() - t0
-    return dt * sus.N / n_targets, dt
+    sus.apply("K", sig, targets=list(targets))
+    return time.perf_counter() - t0
+
+
+def oracle_sample(w, n_targets=3, seed=0, cores=1):
+    """Times the FP64 oracle's traction operator K (self + near + all-pairs
+    far field) on n_targets target spheres per core and scales it to one full
+    application.  cores > 1 runs one spawned process per core, each on its own
+    targets, and takes the wall time of the parallel section.  Returns
+    (seconds per full application, wall seconds of the sample, targets)."""
+    rng = np.random.default_rng(seed)
+    tg = rng.choice(w.N, min(w.N, n_targets * cores), replace=False)
+    if cores == 1:
+        dt = _oracle_worker((w.centers, w.radii, w.p, seed, tg))
+        return dt * w.N / len(tg), dt, len(tg)
+    import multiprocessing as mp
+    jobs = [(w.centers, w.radii, w.p, seed, part) for part in np.array_split(tg, cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_worker, jobs[:cores])       # start-up: imports, geometry
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, jobs)
+        dt = time.perf_counter() - t0
+    return dt * w.N / len(tg), dt, len(tg)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def matvecs_per_step_estimate(stats_list):
@@ -170,9 +203,10 @@ def matvecs_per_step_estimate(stats_list):
 # ---------------------------------------------------------------------------
 def run_reference(args, w):
     steps, warm = args.steps, args.warmup
+    cores = host_cores()
     times = []
     for k in range(warm + steps):
-        full, sample = oracle_sample(w, seed=k)
+        full, sample, ntg = oracle_sample(w, seed=k, cores=cores)
         if k >= warm:
             times.append(full)
     mv = args.ref_matvecs_per_step
@@ -183,11 +217,12 @@ def run_reference(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "N": w.N, "p": w.p,
                                             "l2": "cpu"},
-            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": (f"FP64 numpy oracle: traction operator K on 3 of {w.N} "
-                                        f"target spheres per step (all-pairs far field + VSH "
-                                        f"near/self), scaled x{w.N}/3 to one application and "
-                                        f"x{mv:.0f} applications per step")},
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": (f"FP64 numpy oracle on {cores} host cores (one process "
+                                        f"each): traction operator K on {ntg} of {w.N} target "
+                                        f"spheres per step (all-pairs far field + VSH near/self), "
+                                        f"scaled x{w.N}/{ntg} to one application and x{mv:.0f} "
+                                        f"applications per step (the oracle's algorithm)")},
             "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -256,6 +291,8 @@ def run_gpu(args, w):
     pos_t0 = pos.clone()                     # the e2e leg replays from here
     torch.cuda.nvtx.range_push("timed")      # ncu --nvtx-include "timed/" captures this region
     for k in range(args.steps):
+        if k == args.steps - 1:
+            pos_last = pos.clone()         # the FP64 check reruns this step
         flush.zero_()                      # L2 flush between timed steps (outside the events)
         ev[k][0].record(stream)
         stats.append(dict(step(pos)))
@@ -263,6 +300,8 @@ def run_gpu(args, w):
         pos.copy_(pos_out)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    nc_last = stats[-1]["n_contacts"]
+    gam_last, U_last = gam[:nc_last].clone(), UO.clone()
     ph_ms = (ctypes.c_double * N_PHASES)()
     ph_n = (ctypes.c_longlong * N_PHASES)()
     sps._lib.load().sps_profile_read(ctx.h, ph_ms, ph_n)
@@ -319,6 +358,64 @@ def run_gpu(args, w):
                "steps": args.e2e_steps,
                "replays": "steps 2.. of the timed region (positions restored, one untimed host step)"}
 
+    # the last timed step again on the FP64 path (GMRES 1e-10, gamma_0 = 0),
+    # from the same positions: a measured FP64 step and the error of the
+    # mixed step against it (relative 2-norms, the paper's eps_2)
+    fp64_step = None
+    if not args.no_fp64_step and w.name.startswith("cfg2"):
+        prm64 = ctx_params("fp64", bb_warm=0)
+        prm64["gmres_tol"] = 1e-10
+        c64 = sps.Context(stream=stream, **prm64)
+        g64 = torch.empty_like(gam)
+        U64 = torch.empty_like(UO)
+        p64 = torch.empty_like(pos)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c64.resolve_collisions(pos_last, rad, FT, w.dt, gamma=g64, UO=U64, pos_out=p64,
+                               gamma_cap=g64.numel(), allow=allow)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s64 = dict(c64.last_stats)
+        ms64 = e0.elapsed_time(e1)
+        c64.close()
+        rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        same = s64["n_contacts"] == nc_last
+        fp64_step = {
+            "steps_per_s": 1e3 / ms64, "ms": ms64, "gmres_tol": 1e-10, "bbpgd_gamma0": "zero",
+            "status": s64["status"], "bbpgd_iters": s64["bbpgd_iters"],
+            "gmres_iters": s64["gmres_iters"], "layer_applies": s64["layer_applies"],
+            "mixed_speedup": (1e3 / step_ms[-1]) / (1e3 / ms64),
+            "err_vs_fp64": {"U": rel(U_last, U64), "gamma": rel(gam_last, g64[:nc_last]) if same and nc_last else None,
+                            "norm": "relative 2-norm over all spheres / contacts",
+                            "step": f"timed step {args.steps} from the same positions"}}
+
+    # the paper's initial guess gamma_0 = 0 on the same trajectory: a few
+    # steps from the timed region's first positions with a fresh context
+    gamma0_leg = None
+    if args.gamma0_steps > 0 and args.bb_warm:
+        cz = sps.Context(stream=stream, **dict(prm, bb_warm=0))
+        pz = pos_t0.clone()
+        tz = []
+        for k in range(args.gamma0_steps + 1):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cz.resolve_collisions(pz, rad, FT, w.dt, gamma=gam, UO=UO, pos_out=pos_out,
+                                  gamma_cap=gam.numel(), allow=allow)
+            e1.record(stream)
+            pz.copy_(pos_out)
+            torch.cuda.synchronize()
+            if k > 0:                     # the first step only warms the context
+                tz.append((e0.elapsed_time(e1), dict(cz.last_stats)))
+        cz.close()
+        gamma0_leg = {"steps_per_s": 1e3 * len(tz) / sum(t for t, _ in tz),
+                      "steps": len(tz), "bbpgd_iters": [st["bbpgd_iters"] for _, st in tz],
+                      "gmres_iters": [st["gmres_iters"] for _, st in tz],
+                      "note": "Algorithm 1 from gamma_0 = 0 (the paper's runs), steps 2.. of "
+                              "the timed region replayed with a fresh context"}
+
     # FP64 vs mixed: one traction-operator application each, same geometry
     mv = {}
     for prec in ("fp64", "mixed"):
@@ -341,12 +438,17 @@ def run_gpu(args, w):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        full, sample = oracle_sample(w)
-        cpu_step = full * mvps
-        cpu = {"value": 1.0 / cpu_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": (f"FP64 numpy oracle: traction operator K on 3 of {N} target spheres "
-                          f"({sample:.1f} s), scaled x{N}/3 to one application and "
-                          f"x{mvps:.0f} applications per step (this run's GMRES counts)")}
+        cores = host_cores()
+        mvo = args.ref_matvecs_per_step
+        full, sample, ntg = oracle_sample(w, cores=cores)
+        full1, sample1, ntg1 = oracle_sample(w, cores=1)
+        cpu = {"value": 1.0 / (full * mvo), "unit": "steps/s", "cores": cores, "kind": "oracle",
+               "sample": (f"FP64 numpy oracle on {cores} host cores (one process each): traction "
+                          f"operator K on {ntg} of {N} target spheres ({sample:.1f} s wall), "
+                          f"scaled x{N}/{ntg} to one application and x{mvo:.0f} applications "
+                          f"per step (the oracle's algorithm)"),
+               "one_core": {"value": 1.0 / (full1 * mvo), "cores": 1,
+                            "sample": f"K on {ntg1} target spheres ({sample1:.1f} s)"}}
 
     contact = None
     if rank == 0 and not args.no_contact_bench:
@@ -378,9 +480,11 @@ def run_gpu(args, w):
                          "peak_note": (f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz "
                                        f"(sm_max_mhz {pk['source']})")},
             "fp64_gpu": {"traction_matvec_ms": mv["fp64"], "mixed_traction_matvec_ms": mv["mixed"],
-                         "mixed_speedup": mv["fp64"] / mv["mixed"],
-                         "fp64_steps_per_s_est": 1.0 / (mvps * mv["fp64"] / 1e3),
-                         "matvecs_per_step": mvps},
+                         "mixed_speedup_matvec": mv["fp64"] / mv["mixed"],
+                         "matvecs_per_step": mvps,
+                         "step": fp64_step},
+            "err_vs_fp64": fp64_step["err_vs_fp64"] if fp64_step else None,
+            "gamma0_zero": gamma0_leg,
             "solver": {"gmres_iters_per_step": float(np.mean([s["gmres_iters"] for s in stats])),
                        "layer_applies_per_step": float(np.mean([s["layer_applies"] for s in stats])),
                        "mobility_solves_per_step": float(np.mean([s["mobility_solves"] for s in stats])),
@@ -415,6 +519,16 @@ def contact_bytes(N, nc):
       per-contact pass (D^T F + q and the statistics): per contact i, j (8),
         n (24), q, gamma_n, gamma, g (32) and g_new (8); per sphere its force (24)."""
     return {"bb_D": 40 * nc + 28 * N, "bb_DT": 72 * nc + 24 * N}
+
+
+def contact_bytes_per_end(N, nc):
+    """The same launches counted per contact END, the survey's D gamma formula
+    (gamma 8, n 24 and an index 4 read for each of the two ends of a contact,
+    48 B written per sphere), and D^T U as 2 x 24 + 24 + 8 read and 8 written
+    per contact with U read per end (the 8 written is g_new); the per-contact
+    statistics add q, gamma_n, gamma and g (32).  Counts gamma and n twice
+    per contact, so it reads higher than contact_bytes."""
+    return {"bb_D": 72 * nc + 48 * N, "bb_DT": (2 * 24 + 24 + 8 + 8 + 32) * nc}
 
 
 def contact_fp64_flops(nc, bb_variant=1):
@@ -474,6 +588,7 @@ def run_contacts(args, N, gpu_index, standalone=False):
     nc = stats[-1]["n_contacts"]
     pk = peaks()
     by = contact_bytes(N, nc)
+    by_end = contact_bytes_per_end(N, nc)
     roof = []
     fl = contact_fp64_flops(nc)
     for nm, kern in (("bb_D", "k_bb_gather"), ("bb_DT", "k_bb_ident_DT")):
@@ -485,6 +600,10 @@ def run_contacts(args, N, gpu_index, standalone=False):
                      "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "bytes_per_launch": by[nm],
                      "avg_launch_ms": avg, "launches": int(ph_n[i]), "traffic": None,
                      "peak_note": f"measured STREAM copy ({pk['source']})",
+                     "per_end_count": {"bytes_per_launch": by_end[nm],
+                                       "achieved": by_end[nm] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0,
+                                       "frac": (by_end[nm] / (avg * 1e-3) / 1e9 / pk["hbm_gbs"]
+                                                if avg > 0 else 0.0)},
                      "fp64": {"flops_per_launch": fl[nm], "achieved_tflops": f64,
                               "peak_tflops": FP64_PEAK_TFLOPS, "frac": f64 / FP64_PEAK_TFLOPS}})
     out = {"workload": w.name, "N": N, "n_contacts": nc,
@@ -632,7 +751,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-matvecs-per-step", type=float, default=185.0,
+    ap.add_argument("--ref-matvecs-per-step", type=float, default=ORACLE_APPLIES_PER_STEP,
                     help="layer-operator applications per config-2 step for the oracle's "
                          "algorithm (the paper's formulation: zeta with its traction "
                          "right-hand side, gamma_0 = 0, GMRES from the previous solve's "
@@ -640,6 +759,10 @@ def main():
     ap.add_argument("--single-op", choices=["K", "S", "A"], default=None,
                     help="apply one layer operator on the workload geometry and exit")
     ap.add_argument("--no-contact-bench", action="store_true")
+    ap.add_argument("--no-fp64-step", action="store_true",
+                    help="skip the FP64 rerun of the last timed step (error and FP64 rate)")
+    ap.add_argument("--gamma0-steps", type=int, default=3,
+                    help="steps of the gamma_0 = 0 comparison leg (0: skip)")
     ap.add_argument("--bb-warm", type=int, default=1, choices=[0, 1],
                     help="1: Algorithm 1 starts from the previous step's gamma; 0: gamma_0 = 0")
     ap.add_argument("--contact-n", type=int, default=CONTACT_N)

@@ -162,13 +162,24 @@ def box_side(radii, phi):
 
 
 def random_suspension(seed, N, phi, a_lo=0.5, a_hi=1.0, pair_frac=0.05,
-                      gap_lo=1e-4, gap_hi=1e-2, min_gap=2e-2):
-    """Polydisperse random suspension at volume fraction phi plus close pairs."""
+                      gap_lo=1e-4, gap_hi=1e-2, min_gap=2e-2, collision_scale=None):
+    """Polydisperse random suspension at volume fraction phi plus close pairs.
+
+    collision_scale (dense packings, phi > 0.33): place and compress with the
+    collision radii a_c = collision_scale * a and min_gap measured between
+    collision spheres, so that no pair overlaps at the collision radius (the
+    state the collision solver keeps: Phi >= 0); phi stays the volume
+    fraction of the true spheres."""
     rng = np.random.default_rng(seed)
     R = a_lo + (a_hi - a_lo) * rng.random(N) if a_hi > a_lo else np.full(N, a_lo)
     L = box_side(R, phi)
     if phi <= 0.33:
         C = rsa(rng, R, L, min_gap)
+    elif collision_scale is not None:
+        Rc = collision_scale * R
+        phic = phi * collision_scale ** 3
+        L0 = box_side(Rc, 0.30)
+        C = compress(rsa(rng, Rc, L0, min_gap), Rc, 0.30, phic, min_gap)
     else:
         L0 = box_side(R, 0.30)
         C = compress(rsa(rng, R, L0, min_gap), R, 0.30, phi, min_gap)
