@@ -237,10 +237,13 @@ def config2(N=1000, seed=SEED_BASE + 2):
                     params=dict(delta=0.1, gmres_tol=1e-8, bbpgd_tol=1e-6))
 
 
-def config3(N=4000, seed=SEED_BASE + 3):
+def config3(N=4000, seed=SEED_BASE + 3, a_c_scale=1.05):
     """4,000 spheres a ~ U[0.5,1] at volume fraction 0.40, p = 6, gravity
-    F = (0,0,-(a/0.75)^3), 10 steps of dt = 5e-4."""
-    C, R, _ = random_suspension(seed, N, 0.40, pair_frac=0.0)
+    F = (0,0,-(a/0.75)^3), 10 steps of dt = 5e-4.  Packed at the collision
+    radius a_c = 1.05 a with no gap (a dense sediment: many pairs touching at
+    a_c, none overlapping)."""
+    C, R, _ = random_suspension(seed, N, 0.40, pair_frac=0.0, min_gap=0.0,
+                                collision_scale=a_c_scale)
     FT = np.zeros((N, 6))
     FT[:, 2] = -(R / 0.75) ** 3
     return Workload(f"cfg3_N{N}_p6_phi0.40", C, R, FT, p=6, dt=5e-4, steps=10,
@@ -255,11 +258,13 @@ def config4(N=1000, seed=SEED_BASE + 4):
                     params=dict(delta=0.1))
 
 
-def config5(N, p, seed=None):
-    """Sweep point: N spheres a ~ U[0.5,1] at volume fraction 0.35, order p
-    (no pre-placed close pairs: all gaps above 0.02)."""
+def config5(N, p, seed=None, a_c_scale=1.05):
+    """Sweep point: N spheres a ~ U[0.5,1] at volume fraction 0.35, order p,
+    packed at the collision radius a_c = 1.05 a with no gap (no pre-placed
+    close pairs; no pair overlaps at a_c)."""
     seed = SEED_BASE + 5 + 17 * N + p if seed is None else seed
-    C, R, rng = random_suspension(seed, N, 0.35, pair_frac=0.0)
+    C, R, rng = random_suspension(seed, N, 0.35, pair_frac=0.0, min_gap=0.0,
+                                  collision_scale=a_c_scale)
     FT = np.concatenate([rng.standard_normal((N, 3)),
                          0.1 * rng.standard_normal((N, 3))], axis=1)
     return Workload(f"cfg5_N{N}_p{p}_phi0.35", C, R, FT, p=p, dt=1e-3, steps=1,

@@ -288,3 +288,16 @@ def test_bbpgd_growth_guard():
     assert info["status"] == "breakdown" and info["iters"] < 200
     assert h[-1] >= lcp.GROWTH_LIMIT * h[0] and all(x < lcp.GROWTH_LIMIT * h[0] for x in h[:-1])
     assert info["phi"] == min(h) and lcp.minmap(gam, g) == info["phi"]
+
+
+def test_dense_packings_touch_at_the_collision_radius():
+    """Dense workloads (volume fraction above random sequential addition) are
+    compressed at the collision radius a_c = 1.05 a: no pair overlaps there
+    (Phi >= 0, the state the collision solver maintains) and many pairs
+    touch, as in a sediment; the contact set at delta = 0.1 has about two
+    pairs per sphere."""
+    w = workloads.config5(500, 4)
+    ij, phi, _ = lcp.build_contacts(w.centers, w.radii, 0.1, a_c_scale=1.05)
+    assert phi.min() >= 0.0
+    assert np.sum(phi < 1e-6) > 0.2 * len(w.radii)
+    assert 1.0 < len(phi) / len(w.radii) < 4.0
