@@ -44,7 +44,13 @@ typedef enum {
   SPS_ERR_NONFINITE = 8      /* NaN or Inf met in an input or a residual     */
 } sps_status;
 
-typedef enum { SPS_FP64 = 0, SPS_MIXED = 1 } sps_precision;
+/* Arithmetic of the layer operators.  SPS_FP64: FP64 throughout.  SPS_MIXED:
+ * FP32 far-field pair sums with compensated totals, BF16-split tensor-core
+ * VSH transforms, FP32 / double-float near field, FP64 Krylov and BBPGD.
+ * SPS_FP64_DW: the FP64 path with the far-field pair terms in double-float
+ * arithmetic on the FP32 pipe (about 2^-46 relative per operation, FP64
+ * accumulation per source sphere), agreeing with SPS_FP64 to about 1e-13. */
+typedef enum { SPS_FP64 = 0, SPS_MIXED = 1, SPS_FP64_DW = 2 } sps_precision;
 
 /* Mobility used by the solves.  SPS_MOB_BIE is the boundary-integral mobility
  * of Sec. 4.  SPS_MOB_IDENTITY (U = F, Omega = T) is not in the paper: it
@@ -79,8 +85,10 @@ typedef struct sps_params {
   int bbpgd_max;      /* j_max of Algorithm 1                                 */
   int precision;      /* sps_precision                                        */
   int bb_variant;     /* 1: alpha^BB1, 2: alpha^BB2 (Algorithm 1)            */
-  double ir_tol;      /* SPS_MIXED: refine against an FP64 residual until
-                         ||r||/||b|| < ir_tol; 0 disables refinement          */
+  double ir_tol;      /* SPS_MIXED: refine against an FP64-accurate residual
+                         until ||r||/||b|| < ir_tol (the velocity of a
+                         refined solve is then evaluated FP64-accurate too);
+                         0 disables refinement                                */
   int ir_max;         /* refinement sweep cap                                 */
   int warm_start;     /* 1: start GMRES from the previous solution where one
                          exists (BBPGD iterates 2.., U_nc of the next step,
@@ -109,6 +117,10 @@ typedef struct sps_params {
                          Every step still meets bbpgd_tol.  Boundary-integral
                          mobility only (the identity mobility always starts
                          from 0).  Default 0.                                */
+  int ir_dw;          /* the FP64-accurate applications of the refinement
+                         (ir_tol > 0): 1 evaluates their far field as
+                         SPS_FP64_DW does (double-float on the FP32 pipe), 0
+                         in native FP64.  Default 1.                         */
 } sps_params;
 
 typedef struct sps_stats {

@@ -14,11 +14,11 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (SPS_FP64, SPS_MIXED, SPS_MOB_BIE, SPS_MOB_IDENTITY, SPS_OP_A, SPS_OP_K,
+from ._lib import (SPS_FP64, SPS_FP64_DW, SPS_MIXED, SPS_MOB_BIE, SPS_MOB_IDENTITY, SPS_OP_A, SPS_OP_K,
                    SPS_OP_S, SPS_SEARCH_ALL_PAIRS, SPS_SEARCH_AUTO, SPS_SEARCH_CELLS, SPSError,
                    sps_params, sps_stats)
 
-__all__ = ["Context", "SPSError", "SPS_FP64", "SPS_MIXED", "SPS_OP_S", "SPS_OP_K", "SPS_OP_A",
+__all__ = ["Context", "SPSError", "SPS_FP64", "SPS_MIXED", "SPS_FP64_DW", "SPS_OP_S", "SPS_OP_K", "SPS_OP_A",
            "SPS_MOB_BIE", "SPS_MOB_IDENTITY", "SPS_SEARCH_AUTO", "SPS_SEARCH_ALL_PAIRS",
            "SPS_SEARCH_CELLS",
            "default_params", "unit_tables", "nodes_per_sphere", "MobilityFunction", "mobility",

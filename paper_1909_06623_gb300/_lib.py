@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libsps.so")
 SPS_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED",
           5: "BREAKDOWN", 6: "CAPACITY", 7: "NO_GEOMETRY", 8: "NONFINITE"}
-SPS_FP64, SPS_MIXED = 0, 1
+SPS_FP64, SPS_MIXED, SPS_FP64_DW = 0, 1, 2
 SPS_OP_S, SPS_OP_K, SPS_OP_A = 0, 1, 2
 SPS_MOB_BIE, SPS_MOB_IDENTITY = 0, 1
 SPS_SEARCH_AUTO, SPS_SEARCH_ALL_PAIRS, SPS_SEARCH_CELLS = 0, 1, 2
@@ -28,7 +28,7 @@ class sps_params(ctypes.Structure):
                 ("bb_variant", ctypes.c_int), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("bb_safeguard", ctypes.c_int),
                 ("mobility", ctypes.c_int), ("contact_search", ctypes.c_int),
-                ("delta_rel", ctypes.c_double), ("bb_warm", ctypes.c_int)]
+                ("delta_rel", ctypes.c_double), ("bb_warm", ctypes.c_int), ("ir_dw", ctypes.c_int)]
 
 
 class sps_stats(ctypes.Structure):

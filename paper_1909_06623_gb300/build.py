@@ -36,8 +36,9 @@ def _compile(src, verbose):
 
 def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
-    srcs = [os.path.join(SRC, s) for s in SOURCES] + [os.path.join(SRC, "sps_internal.cuh"),
-                                                      os.path.join(HERE, "..", "include", "sps.h")]
+    srcs = ([os.path.join(SRC, s) for s in SOURCES] +
+            [os.path.join(SRC, h) for h in sorted(os.listdir(SRC)) if h.endswith(".cuh")] +
+            [os.path.join(HERE, "..", "include", "sps.h")])
     if (not force and os.path.exists(OUT)
             and os.path.getmtime(OUT) > max(os.path.getmtime(s) for s in srcs)):
         return OUT

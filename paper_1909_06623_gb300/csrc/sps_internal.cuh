@@ -118,6 +118,8 @@ struct sps_ctx {
   float *d_sig32 = nullptr;      // 3NP FP32 w*sigma for the mixed far field
   double *d_part = nullptr;      // far-field partial sums (splits x 3NP)
   size_t cap_part = 0;
+  float4 *d_dwsrc = nullptr;     // double-float far field: 3 x NP staged source values
+  size_t cap_dwsrc = 0;
 
   // GMRES
   int gm_cap_n = 0, gm_cap_k = 0;
@@ -181,6 +183,12 @@ struct sps_ctx {
   bool order_valid = false;
   size_t cap_ident = 0;
 };
+
+// far field of an FP64-class application (fp32 = false) in double-float
+// arithmetic: the SPS_FP64_DW path, or the mixed path's refinement with ir_dw
+inline bool sps_far_dw(const sps_ctx* c) {
+  return c->prm.precision == SPS_FP64_DW || (c->prm.precision == SPS_MIXED && c->prm.ir_dw);
+}
 
 // ---------------------------------------------------------------------------
 // error helpers

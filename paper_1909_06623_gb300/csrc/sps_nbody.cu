@@ -12,6 +12,7 @@
 // excluded spheres, FP32 sums per tile combined with Kahan compensation across
 // tiles, and a source split (gridDim.y) whose partial sums are added in FP64 in
 // a fixed order.
+#include "sps_dw.cuh"
 #include "sps_internal.cuh"
 
 namespace {
@@ -460,7 +461,204 @@ __global__ void k_wsig32(long long NP, const double* __restrict__ sig, const dou
     out[g] = (float)((W ? W[g % NP] : 1.0) * sig[g]);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float kernel: FP64-accurate far field on the FP32 pipe
+//
+// The same sums as k_far64 with every pair term in double-float arithmetic
+// (sps_dw.cuh: about 2^-46 relative per operation) and FP64 accumulation of
+// the per-sphere partial sums, so that the result agrees with the FP64
+// kernel to about 1e-13 of its size while the arithmetic runs on the FP32
+// pipe, which GB300 executes about 64 times faster than FP64.  It evaluates
+// the FP64-class operator applications of the mixed path's iterative
+// refinement (residual and final velocity) and of the SPS_FP64_DW path.
+//
+// For target t on sphere i and source s on sphere j:
+//   r = E_ij(t) - l_s,  E_ij(t) = (c_i - c_j) + l_t,  l = node - own centre,
+// with E formed in FP64 once per (target, source sphere) and split into a
+// double-float, and l_s, w_s sigma_s staged in shared memory as double-floats
+// (prepared per application by k_dw_src).  1/|r| comes from the SFU estimate
+// and one double-float Newton step.  Partial sums over a source sphere are
+// folded into FP64 unless j is i or a near neighbour of i; work items (target
+// block, source split) come from an atomic queue and write FP64 partials that
+// k_reduce_parts adds in a fixed order.
+// ---------------------------------------------------------------------------
+using namespace sps_dw;
+constexpr int kTdw = 128;          // threads per block, one target each
+constexpr int kChunkDw = 512;      // staged source nodes (whole spheres)
+
+// per node: (-l_x, -l_y) hi/lo, (-l_z, (w sigma)_x) hi/lo, (w sigma)_y, _z hi/lo
+__global__ void k_dw_src(int N, int P, const double* __restrict__ pos, const double* __restrict__ X,
+                         const double* __restrict__ W, const double* __restrict__ sig,
+                         float4* __restrict__ A, float4* __restrict__ B, float4* __restrict__ C) {
+  const long long NP = (long long)N * P;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NP;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(g / P);
+    const dw lx = dw_of(pos[3 * s] - X[g]), ly = dw_of(pos[3 * s + 1] - X[NP + g]),
+             lz = dw_of(pos[3 * s + 2] - X[2 * NP + g]);
+    const double w = W[g];
+    const dw fx = dw_of(w * sig[g]), fy = dw_of(w * sig[NP + g]), fz = dw_of(w * sig[2 * NP + g]);
+    A[g] = make_float4(lx.h, lx.l, ly.h, ly.l);
+    B[g] = make_float4(lz.h, lz.l, fx.h, fx.l);
+    C[g] = make_float4(fy.h, fy.l, fz.h, fz.l);
+  }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kTdw) k_far_dw(int N, int P, int spc, int n_tb, int n_items, int n_splits,
+                                                 const double* __restrict__ pos, const double* __restrict__ X,
+                                                 const double* __restrict__ Nr, const float4* __restrict__ gA,
+                                                 const float4* __restrict__ gB, const float4* __restrict__ gC,
+                                                 const int* __restrict__ near_ptr,
+                                                 const int* __restrict__ near_idx, int* __restrict__ work,
+                                                 double* __restrict__ part) {
+  extern __shared__ __align__(16) float4 sdw[];
+  const long long NP = (long long)N * P;
+  const int cap = spc * P;
+  float4* sA = sdw;
+  float4* sB = sA + cap;
+  float4* sC = sB + cap;
+  double* sc = reinterpret_cast<double*>(sC + cap);   // spc x 3 centres
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const int tb = item % n_tb, sp = item / n_tb;
+    const int j_begin = (int)((long long)N * sp / n_splits);
+    const int j_end = (int)((long long)N * (sp + 1) / n_splits);
+    const long long t = (long long)tb * kTdw + threadIdx.x;
+    const long long tt = t < NP ? t : NP - 1;
+    const int i = (int)(tt / P);
+    const double cx = pos[3 * i], cy = pos[3 * i + 1], cz = pos[3 * i + 2];
+    const double ltx = X[tt] - cx, lty = X[NP + tt] - cy, ltz = X[2 * NP + tt] - cz;
+    dw nx(0.f, 0.f), ny(0.f, 0.f), nz(0.f, 0.f);
+    if (OP == SPS_OP_K) {
+      nx = dw_of(Nr[tt]);
+      ny = dw_of(Nr[NP + tt]);
+      nz = dw_of(Nr[2 * NP + tt]);
+    }
+    int pt = near_ptr[i];
+    const int pe = near_ptr[i + 1];
+    while (pt < pe && near_idx[pt] < j_begin) ++pt;
+    double ox = 0.0, oy = 0.0, oz = 0.0;
+    for (int j0 = j_begin; j0 < j_end; j0 += spc) {
+      const int ns = min(spc, j_end - j0);
+      const int nn = ns * P;
+      const long long g0 = (long long)j0 * P;
+      __syncthreads();
+      for (int k = threadIdx.x; k < nn; k += kTdw) {
+        sA[k] = gA[g0 + k];
+        sB[k] = gB[g0 + k];
+        sC[k] = gC[g0 + k];
+      }
+      for (int k = threadIdx.x; k < 3 * ns; k += kTdw) sc[k] = pos[3 * j0 + k];
+      __syncthreads();
+      for (int js = 0; js < ns; ++js) {
+        const int j = j0 + js;
+        while (pt < pe && near_idx[pt] < j) ++pt;
+        const bool excl = (j == i) || (pt < pe && near_idx[pt] == j);
+        if (excl) continue;          // (the whole sphere's terms are skipped)
+        const dw Ex = dw_of((cx - sc[3 * js]) + ltx), Ey = dw_of((cy - sc[3 * js + 1]) + lty),
+                 Ez = dw_of((cz - sc[3 * js + 2]) + ltz);
+        dw ax(0.f, 0.f), ay(0.f, 0.f), az(0.f, 0.f);
+        const float4* A = sA + js * P;
+        const float4* B = sB + js * P;
+        const float4* C = sC + js * P;
+#pragma unroll 2
+        for (int k = 0; k < P; ++k) {
+          const float4 a4 = A[k], b4 = B[k], c4 = C[k];
+          const dw rx = dw_add_u(Ex, dw(a4.x, a4.y));
+          const dw ry = dw_add_u(Ey, dw(a4.z, a4.w));
+          const dw rz = dw_add_u(Ez, dw(b4.x, b4.y));
+          const dw wx(b4.z, b4.w), wy(c4.x, c4.y), wz(c4.z, c4.w);
+          const dw r2 = dw_norm(dw_add_u(dw_add_u(dw_sqr_u(rx), dw_sqr_u(ry)), dw_sqr_u(rz)));
+          const dw y = dw_rsqrt(r2);
+          const dw rs = dw_norm(dw_add_u(dw_add_u(dw_mul_u(rx, wx), dw_mul_u(ry, wy)), dw_mul_u(rz, wz)));
+          if (OP == SPS_OP_S) {
+            // w G sigma (8 pi) = w sigma / |r| + r (r . w sigma) / |r|^3
+            const dw y3 = dw_norm(dw_mul_u(dw_mul_u(y, y), y));
+            const dw c = dw_norm(dw_mul_u(rs, y3));
+            ax = dw_add_u(ax, dw_add_u(dw_mul_u(wx, y), dw_mul_u(c, rx)));
+            ay = dw_add_u(ay, dw_add_u(dw_mul_u(wy, y), dw_mul_u(c, ry)));
+            az = dw_add_u(az, dw_add_u(dw_mul_u(wz, y), dw_mul_u(c, rz)));
+          } else {
+            // w T : sigma n (-4 pi / 3) = r (r . w sigma)(r . n) / |r|^5
+            const dw rn = dw_norm(dw_add_u(dw_add_u(dw_mul_u(rx, nx), dw_mul_u(ry, ny)), dw_mul_u(rz, nz)));
+            const dw y2 = dw_mul_u(y, y);
+            const dw y5 = dw_norm(dw_mul_u(dw_mul_u(y2, y2), y));
+            const dw c = dw_norm(dw_mul_u(dw_norm(dw_mul_u(rs, rn)), y5));
+            ax = dw_add_u(ax, dw_mul_u(c, rx));
+            ay = dw_add_u(ay, dw_mul_u(c, ry));
+            az = dw_add_u(az, dw_mul_u(c, rz));
+          }
+        }
+        ox += dw_val(ax);
+        oy += dw_val(ay);
+        oz += dw_val(az);
+      }
+    }
+    if (t < NP) {
+      double* o = part + (long long)sp * 3 * NP;
+      o[t] = ox;
+      o[NP + t] = oy;
+      o[2 * NP + t] = oz;
+    }
+  }
+}
+
 }  // namespace
+
+// double-float far sum (op SPS_OP_S or SPS_OP_K), FP64 result added to out
+static int far_dw_run(sps_ctx* ctx, int op, const double* sig, double* out, int phase) {
+  const long long NP = ctx->NP;
+  const int P = ctx->T.P, N = ctx->N;
+  const long long n3 = 3 * NP;
+  SPS_TRY(sps_grow(ctx, &ctx->d_dwsrc, ctx->cap_dwsrc, (size_t)3 * NP));
+  float4 *A = ctx->d_dwsrc, *B = A + NP, *C = B + NP;
+  {
+    SpsPhase timer(ctx, SPS_PH_FAR_AUX);
+    k_dw_src<<<(int)std::min<long long>((NP + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        N, P, ctx->d_pos, ctx->d_X, ctx->d_W, sig, A, B, C);
+    SPS_LAUNCHED(ctx);
+  }
+  const int spc = std::max(1, kChunkDw / P);
+  const size_t smem = (size_t)3 * spc * P * sizeof(float4) + (size_t)spc * 3 * sizeof(double);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  auto kern = (op == SPS_OP_S) ? k_far_dw<SPS_OP_S> : k_far_dw<SPS_OP_K>;
+  if (smem > 48 * 1024)
+    SPS_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTdw, smem);
+  const int resident = std::max(1, per_sm) * std::max(1, sms);
+  const int n_tb = (int)((NP + kTdw - 1) / kTdw);
+  int splits = (int)std::min<long long>(std::max(1, (8 * resident + n_tb - 1) / n_tb), (long long)N);
+  splits = std::min(splits, 64);
+  const int n_items = n_tb * splits;
+  const int grid = std::min(n_items, resident);
+  SPS_TRY(sps_grow(ctx, &ctx->d_part, ctx->cap_part, (size_t)splits * n3 + 1));
+  int* d_work = reinterpret_cast<int*>(ctx->d_part + (size_t)splits * n3);
+  SPS_CUDA(ctx, cudaMemsetAsync(d_work, 0, sizeof(int), ctx->stream));
+  {
+    SpsPhase timer(ctx, phase);
+    kern<<<grid, kTdw, smem, ctx->stream>>>(N, P, spc, n_tb, n_items, splits, ctx->d_pos, ctx->d_X, ctx->d_Nrm,
+                                            A, B, C, ctx->d_near_ptr, ctx->d_near_idx, d_work, ctx->d_part);
+    SPS_LAUNCHED(ctx);
+  }
+  SpsPhase timer(ctx, SPS_PH_FAR_AUX);
+  const double scale = (op == SPS_OP_S) ? 1.0 / (8.0 * SPS_PI) : -3.0 / (4.0 * SPS_PI);
+  k_reduce_parts<<<(int)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+      n3, splits, ctx->d_part, scale, nullptr, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
 
 // FP32 far sum of kind kop (SPS_OP_S, SPS_OP_K or kOpKT): sources carry
 // (Wsrc ? Wsrc : 1) * sig, the result is scaled by (Wtgt ? Wtgt : 1) * scale.
@@ -520,6 +718,7 @@ int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp
   const long long NP = ctx->NP;
   const int P = ctx->T.P, N = ctx->N;
   const int ph = (op == SPS_OP_S) ? SPS_PH_FAR_S : SPS_PH_FAR_K;
+  if (!fp32 && sps_far_dw(ctx)) return far_dw_run(ctx, op, sig, out, ph);
   if (!fp32) {
     SpsPhase timer(ctx, ph);
     const int blocks = (int)((NP + kT64 - 1) / kT64);

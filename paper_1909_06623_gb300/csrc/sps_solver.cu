@@ -461,6 +461,7 @@ extern "C" int sps_default_params(sps_params* o) {
   o->contact_search = SPS_SEARCH_AUTO;
   o->delta_rel = 0.0;
   o->bb_warm = 0;
+  o->ir_dw = 1;
   return SPS_OK;
 }
 
@@ -476,7 +477,8 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
   *out = nullptr;
   if (prm->p < 1 || prm->p > sps::kMaxP || !(prm->beta > 1.0) || !(prm->gmres_tol > 0) ||
       prm->gmres_max < 1 || !(prm->bbpgd_tol > 0) || prm->bbpgd_max < 1 ||
-      (prm->precision != SPS_FP64 && prm->precision != SPS_MIXED) ||
+      (prm->precision != SPS_FP64 && prm->precision != SPS_MIXED && prm->precision != SPS_FP64_DW) ||
+      (prm->ir_dw != 0 && prm->ir_dw != 1) ||
       (prm->bb_variant != 1 && prm->bb_variant != 2) || !(prm->a_c_scale > 0) ||
       !(prm->delta >= 0) || !(prm->delta_rel >= 0) || !std::isfinite(prm->delta_rel) || prm->ir_tol < 0 || prm->ir_max < 0 ||
       (prm->mobility != SPS_MOB_BIE && prm->mobility != SPS_MOB_IDENTITY) ||
@@ -561,7 +563,8 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_flag, ctx->d_bbpart, ctx->d_F3, ctx->d_iFT, ctx->d_sc, ctx->tcA.d,
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
                   ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
-                  ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw, ctx->d_prev_ij, ctx->d_prev_gam};
+                  ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw, ctx->d_prev_ij, ctx->d_prev_gam,
+                  ctx->d_dwsrc};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {

@@ -35,6 +35,7 @@
 // 2 Phi_beta - Phi_P); the velocity needs 10.
 #include <type_traits>
 
+#include "sps_dw.cuh"
 #include "sps_internal.cuh"
 
 // mixed path: VSH analysis / self synthesis on the tensor cores (BF16 split
@@ -223,65 +224,7 @@ __global__ void k_near_coef(int N, int p, int NC, int NR, int L, int E,
   }
 }
 
-// ---------------------------------------------------------------------------
-// Double-float numbers for the close near entries: value h + l with |l| at
-// most half an ulp of h once normalised.  Built from the error-free
-// transforms TwoSum (Knuth), FastTwoSum (Dekker) and TwoProd by FMA; products
-// drop l*l and sums add the low parts without compensation, so an operation's
-// absolute error is about u^2 (u = 2^-24) times its operands, against 2^-53
-// in FP64 -- ample for the close entries, at FP32-pipe throughput (GB300's
-// FP64 pipe is ~1/64 of it).
-// ---------------------------------------------------------------------------
-// Every operation below is an explicitly rounded intrinsic (__fadd_rn,
-// __fmul_rn, fmaf), so the compiler cannot contract a product into a later
-// sum and break the error-free transforms.
-struct dw {
-  float h, l;
-  dw() = default;
-  __device__ __forceinline__ dw(float a, float b) : h(a), l(b) {}
-  __device__ __forceinline__ dw(int a) : h((float)a), l(0.f) {}   // exact for |a| < 2^24
-};
-__device__ __forceinline__ dw two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-  return dw(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
-}
-__device__ __forceinline__ dw fast_two_sum(float a, float b) {   // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return dw(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-__device__ __forceinline__ dw operator+(dw a, dw b) {
-  const dw s = two_sum(a.h, b.h);
-  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ dw operator-(dw a) { return dw(-a.h, -a.l); }
-__device__ __forceinline__ dw operator-(dw a, dw b) { return a + (-b); }
-__device__ __forceinline__ dw& operator+=(dw& a, dw b) { return a = a + b; }
-__device__ __forceinline__ dw operator*(dw a, dw b) {
-  const float p = __fmul_rn(a.h, b.h);
-  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ dw operator*(int a, dw b) { return dw(a) * b; }
-// 1 / a: one Newton step from the FP32 reciprocal, its residual by FMAs
-__device__ __forceinline__ dw recip(dw a) {
-  const float y = __frcp_rn(a.h);
-  const float r = fmaf(-a.l, y, fmaf(-a.h, y, 1.0f));
-  return fast_two_sum(y, __fmul_rn(y, r));
-}
-__device__ __forceinline__ dw operator/(dw a, dw b) { return a * recip(b); }
-// acc += a b without renormalising acc (the low part collects the errors)
-__device__ __forceinline__ void dw_mac(dw& acc, dw a, dw b) {
-  const float p = __fmul_rn(a.h, b.h);
-  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
-  const dw s = two_sum(acc.h, p);
-  acc.h = s.h;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
-}
-__device__ __forceinline__ dw dw_of(double d) {
-  const float h = __double2float_rn(d);
-  return dw(h, __double2float_rn(d - (double)h));
-}
-__device__ __forceinline__ double dw_val(dw a) { return (double)a.h + (double)a.l; }
+using namespace sps_dw;
 
 // 1 / sqrt(a) for the near-field expansion's arithmetic types
 template <typename T>
@@ -290,13 +233,7 @@ __device__ __forceinline__ T inv_sqrt(T a) {
 }
 template <>
 __device__ __forceinline__ dw inv_sqrt<dw>(dw a) {
-  // FP32 estimate refined once in FP32, then one Newton step with the
-  // residual 1 - a y^2 formed by FMAs (y^2 = t + te exactly)
-  float y = rsqrtf(a.h);
-  y = __fmul_rn(y, fmaf(__fmul_rn(-0.5f, a.h), __fmul_rn(y, y), 1.5f));
-  const float t = __fmul_rn(y, y), te = fmaf(y, y, -t);
-  const float r = fmaf(-a.l, t, fmaf(-a.h, te, fmaf(-a.h, t, 1.0f)));
-  return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), r));
+  return dw_rsqrt(a);
 }
 
 // ---------------------------------------------------------------------------

@@ -133,7 +133,7 @@ def test_D_and_DT_match_oracle(sps):
 # layer operators
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("case", ["c1", "c2", "c3"])
-@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX)])
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX), (2, TOL64)])
 def test_layer_operators_tiny(sps, case, precision, tol):
     d = load("tiny_layers.npz")
     C, R, p, sig = d[f"{case}_centers"], d[f"{case}_radii"], int(d[f"{case}_p"]), d[f"{case}_sigma"]
@@ -145,7 +145,7 @@ def test_layer_operators_tiny(sps, case, precision, tol):
         assert relerr(out, d[f"{case}_{key}"]) < tol, (case, key)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX)])
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX), (2, TOL64)])
 def test_layer_operators_cfg2_sampled(sps, precision, tol):
     """Full-size geometry (1,000 spheres, p = 6) in the launch shape the bench
     uses; the oracle evaluated S, K and I/2+K+L on a sample of target spheres."""
@@ -159,6 +159,28 @@ def test_layer_operators_cfg2_sampled(sps, precision, tol):
     for op, key in ((sps.SPS_OP_S, "S"), (sps.SPS_OP_K, "K"), (sps.SPS_OP_A, "A")):
         out = ctx.layer_apply(op, s).cpu().numpy().T[sl]
         assert relerr(out, d[key]) < tol, key
+
+
+@pytest.mark.parametrize("name", ["tiny_layers.npz", "cfg2_sample.npz"])
+def test_double_float_far_field_matches_fp64(sps, name):
+    """SPS_FP64_DW (far-field pair terms in double-float on the FP32 pipe)
+    against the native FP64 kernels on every node: the same operator to
+    1e-13 of its largest value (the FP64 path itself meets the oracle at
+    1e-10); the FP32 far field of the mixed path is ~3e-7 away."""
+    d = load(name)
+    if name == "tiny_layers.npz":
+        C, R, p = d["c3_centers"], d["c3_radii"], int(d["c3_p"])
+    else:
+        C, R, p = d["centers"], d["radii"], int(d["p"])
+    P = (p + 1) * (2 * p + 2)
+    sig = planes(np.random.default_rng(3).standard_normal((len(R) * P, 3)))
+    out = {}
+    for prec in (0, 2):
+        ctx = sps.Context(p=p, precision=prec)
+        ctx.set_geometry(dev(C), dev(R))
+        out[prec] = [ctx.layer_apply(op, sig).cpu().numpy() for op in (sps.SPS_OP_S, sps.SPS_OP_K)]
+    for a, b in zip(out[2], out[0]):
+        assert relerr(a, b) < 1e-13
 
 
 @pytest.mark.parametrize("p", [3, 6, 8])
@@ -219,11 +241,13 @@ def test_mobility_tiny_mixed(sps, case):
     ctx = sps.Context(p=p, gmres_tol=1e-9, gmres_max=300, precision=1)
     U = ctx.mobility_apply(dev(C), dev(R), dev(d[f"{case}_FT"])).cpu().numpy()
     assert relerr(U, d[f"{case}_U"]) < TOLMX
-    # refinement against the FP64 residual recovers the FP64 answer
-    ctx = sps.Context(p=p, gmres_tol=1e-7, gmres_max=300, precision=1, ir_tol=1e-13)
-    U = ctx.mobility_apply(dev(C), dev(R), dev(d[f"{case}_FT"])).cpu().numpy()
-    assert relerr(U, d[f"{case}_U"]) < 1e-10
-    assert ctx.last_stats["ir_sweeps"] >= 1
+    # refinement against an FP64-accurate residual recovers the FP64 answer,
+    # with that residual's far field in double-float (ir_dw = 1) or in FP64
+    for ir_dw in (1, 0):
+        ctx = sps.Context(p=p, gmres_tol=1e-7, gmres_max=300, precision=1, ir_tol=1e-13, ir_dw=ir_dw)
+        U = ctx.mobility_apply(dev(C), dev(R), dev(d[f"{case}_FT"])).cpu().numpy()
+        assert relerr(U, d[f"{case}_U"]) < 1e-10, ir_dw
+        assert ctx.last_stats["ir_sweeps"] >= 1
 
 
 def test_zero_force_and_nonfinite(sps):
