@@ -163,6 +163,21 @@ const char* sps_last_error(const sps_ctx* ctx);
  * (device).  Radii must be positive.  Keeps its own copy of the geometry. */
 int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const double* radii);
 
+/* Grid orientation (Sec. 5.4 orients every sphere's grid at random).  Q
+ * (n x 9, device, row-major Q_i[3 r + c]) holds one rotation per sphere:
+ * node k of sphere i then sits at c_i + a_i Q_i n_k with normal Q_i n_k,
+ * and the sphere's VSH expansions live in its own frame (densities enter the
+ * transforms as Q_i^T sigma, fields leave them as Q_i u).  The orientation
+ * stays in force for every later call on n spheres (sps_set_geometry with
+ * another count fails with INVALID_ARG) until Q = NULL restores identity
+ * grids.  The geometry must be set again afterwards (the solving entry
+ * points do that themselves); warm starts are dropped.  The adjoint entry
+ * points (sps_layer_apply_transpose, sps_mobility_adjoint,
+ * sps_collision_adjoint) return INVALID_ARG while an orientation is set.
+ * Errors: INVALID_ARG (n < 1, a matrix not orthogonal to 1e-12 or with
+ * determinant <= 0), NONFINITE. */
+int sps_set_orientation(sps_ctx* ctx, int n, const double* Q);
+
 /* Nodes of the current geometry: X, normals (3 planes of NP) and quadrature
  * weights (NP), device outputs; any pointer may be NULL.  *np_out = NP. */
 int sps_nodes(sps_ctx* ctx, double* X, double* normals, double* weights, int* np_out);
@@ -342,7 +357,9 @@ typedef enum {
                           (projected step and D)                             */
   SPS_PH_BB_DT = 11,   /* identity mobility: per-contact pass (D^T, + q and
                           the step's statistics)                             */
-  SPS_PH_COUNT = 12
+  SPS_PH_FAR_DW = 12,  /* far field in double-float (SPS_FP64_DW and the
+                          mixed path's refinement), S and K                  */
+  SPS_PH_COUNT = 13
 } sps_phase;
 
 /* enable != 0 starts recording (and clears the totals); 0 stops. */

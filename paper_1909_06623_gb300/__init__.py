@@ -115,6 +115,15 @@ class Context:
         self._check(self.lib.sps_set_geometry(self.h, n, _ptr(pos), _ptr(radii)))
         self.n = n
 
+    def set_orientation(self, Q):
+        """Per-sphere grid rotations Q (n x 3 x 3 CUDA float64 tensor), or
+        None for identity grids (sps_set_orientation)."""
+        if Q is None:
+            self._check(self.lib.sps_set_orientation(self.h, 0, None))
+            return
+        Q = Q.reshape(-1, 9).contiguous()
+        self._check(self.lib.sps_set_orientation(self.h, Q.shape[0], _ptr(Q)))
+
     def geometry_counts(self):
         """(directed near pairs, close near entries) of the current geometry."""
         a, b = ctypes.c_int(), ctypes.c_int()

@@ -300,6 +300,8 @@ extern "C" int sps_layer_apply_transpose(sps_ctx* ctx, int op, const double* v, 
   if (!ctx->have_geom) return sps_fail(ctx, SPS_ERR_NO_GEOMETRY, "no geometry");
   if (op < SPS_OP_S || op > SPS_OP_A || !v || !out)
     return sps_fail(ctx, SPS_ERR_INVALID_ARG, "layer_apply_transpose: bad argument");
+  if (ctx->rot_n > 0)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "layer_apply_transpose: not available with grid orientations");
   SPS_TRY(sps_layer_T(ctx, op, v, out));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return SPS_OK;

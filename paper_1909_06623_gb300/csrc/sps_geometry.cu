@@ -17,8 +17,10 @@ inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); 
 // ---------------------------------------------------------------------------
 // nodes: x = c + a n_k, normals n_k, weights a^2 w_k (Sec. 5.4)
 // ---------------------------------------------------------------------------
+// With rot (N x 9), node k of sphere s sits at c + a Q_s n_k, normal Q_s n_k.
 __global__ void k_grid(int N, int P, const double* __restrict__ pos, const double* __restrict__ rad,
                        const double* __restrict__ un, const double* __restrict__ uw,
+                       const double* __restrict__ rot,
                        double* __restrict__ X, double* __restrict__ Nr, double* __restrict__ W,
                        float* __restrict__ rel32, float* __restrict__ N32, float* __restrict__ W32,
                        float* __restrict__ chi, float* __restrict__ clo) {
@@ -27,8 +29,10 @@ __global__ void k_grid(int N, int P, const double* __restrict__ pos, const doubl
        g += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(g / P), k = (int)(g - (long long)s * P);
     const double a = rad[s];
+    double nv[3] = {un[k], un[P + k], un[2 * P + k]};
+    if (rot) sps_rot_n(rot + 9 * s, nv[0], nv[1], nv[2]);
     for (int c = 0; c < 3; ++c) {
-      const double n = un[c * P + k];
+      const double n = nv[c];
       const double x = pos[3 * s + c] + a * n;
       X[c * NP + g] = x;
       Nr[c * NP + g] = n;
@@ -220,9 +224,37 @@ int sps_launch_grid(sps_ctx* ctx) {
   SpsPhase timer(ctx, SPS_PH_GEOM);
   const long long NP = ctx->NP;
   k_grid<<<nblk(NP), kThreads, 0, ctx->stream>>>(ctx->N, ctx->T.P, ctx->d_pos, ctx->d_rad,
-                                                  ctx->d_unit_nrm, ctx->d_unit_w, ctx->d_X,
+                                                  ctx->d_unit_nrm, ctx->d_unit_w,
+                                                  ctx->rot_n == ctx->N ? ctx->d_rot : nullptr, ctx->d_X,
                                                   ctx->d_Nrm, ctx->d_W, ctx->d_rel32, ctx->d_N32,
                                                   ctx->d_W32, ctx->d_chi, ctx->d_clo);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
+namespace {
+__global__ void k_rotate(int N, int P, const double* __restrict__ rot, const double* in, double* out,
+                         int transpose) {
+  const long long NP = (long long)N * P;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NP;
+       g += (long long)gridDim.x * blockDim.x) {
+    const double* Q = rot + 9 * (g / P);
+    double x = in[g], y = in[NP + g], z = in[2 * NP + g];
+    if (transpose)
+      sps_rot_t(Q, x, y, z);
+    else
+      sps_rot_n(Q, x, y, z);
+    out[g] = x;
+    out[NP + g] = y;
+    out[2 * NP + g] = z;
+  }
+}
+}  // namespace
+
+int sps_launch_rotate(sps_ctx* ctx, const double* in, double* out, bool transpose) {
+  SpsPhase timer(ctx, SPS_PH_SELF);
+  k_rotate<<<(int)std::min<long long>(nblk(ctx->NP), 8 * 152), kThreads, 0, ctx->stream>>>(
+      ctx->N, ctx->T.P, ctx->d_rot, in, out, transpose ? 1 : 0);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }

@@ -93,6 +93,8 @@ struct sps_ctx {
     int R = 0, C = 0, Kpad = 0;
   } tcA, tcS, tcK;
   int* d_tcflag = nullptr;       // set by a tensor-core transform that timed out
+  uint16_t* d_tcsplit = nullptr; // the transform input split into BF16 terms, chunk layout
+  size_t cap_tcsplit = 0;
 
   // geometry
   int N = 0, NP = 0, capN = 0;
@@ -120,6 +122,14 @@ struct sps_ctx {
   size_t cap_part = 0;
   float4 *d_dwsrc = nullptr;     // double-float far field: 3 x NP staged source values
   size_t cap_dwsrc = 0;
+  // grid orientation (Sec. 5.4): rotation Q_i per sphere (N x 9, row-major),
+  // in force while rot_n equals the number of spheres; densities rotated
+  // into the sphere frames for the VSH transforms
+  double *d_rot = nullptr;
+  size_t cap_rot = 0;
+  int rot_n = 0;
+  double *d_sigloc = nullptr;    // 3NP: a density in the sphere frames
+  size_t cap_sigloc = 0;
 
   // GMRES
   int gm_cap_n = 0, gm_cap_k = 0;
@@ -188,6 +198,32 @@ struct sps_ctx {
 // arithmetic: the SPS_FP64_DW path, or the mixed path's refinement with ir_dw
 inline bool sps_far_dw(const sps_ctx* c) {
   return c->prm.precision == SPS_FP64_DW || (c->prm.precision == SPS_MIXED && c->prm.ir_dw);
+}
+
+// the per-sphere grid rotations in force for the current geometry, or null
+inline const double* sps_rot(const sps_ctx* c) {
+  return (c->rot_n > 0 && c->rot_n == c->N && c->have_geom) ? c->d_rot : nullptr;
+}
+
+// v <- Q^T v and v <- Q v for a row-major 3 x 3 rotation Q (an identity Q
+// returns v unchanged to the bit: its zero products vanish exactly)
+template <typename T, typename M>
+__device__ __forceinline__ void sps_rot_t(const M* Q, T& x, T& y, T& z) {
+  const T a = (T)Q[0] * x + (T)Q[3] * y + (T)Q[6] * z;
+  const T b = (T)Q[1] * x + (T)Q[4] * y + (T)Q[7] * z;
+  const T c = (T)Q[2] * x + (T)Q[5] * y + (T)Q[8] * z;
+  x = a;
+  y = b;
+  z = c;
+}
+template <typename T, typename M>
+__device__ __forceinline__ void sps_rot_n(const M* Q, T& x, T& y, T& z) {
+  const T a = (T)Q[0] * x + (T)Q[1] * y + (T)Q[2] * z;
+  const T b = (T)Q[3] * x + (T)Q[4] * y + (T)Q[5] * z;
+  const T c = (T)Q[6] * x + (T)Q[7] * y + (T)Q[8] * z;
+  x = a;
+  y = b;
+  z = c;
 }
 
 // ---------------------------------------------------------------------------
@@ -280,6 +316,8 @@ struct SpsPhase {
 // ---------------------------------------------------------------------------
 // geometry / contacts (sps_geometry.cu)
 int sps_launch_grid(sps_ctx* ctx);
+// out = Q_i^T in (transpose) or Q_i in per node, 3 planes of NP (may alias)
+int sps_launch_rotate(sps_ctx* ctx, const double* in, double* out, bool transpose);
 int sps_launch_near_lists(sps_ctx* ctx);
 int sps_launch_close_lists(sps_ctx* ctx);
 int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii);

@@ -718,7 +718,7 @@ int sps_launch_far(sps_ctx* ctx, int op, const double* sig, double* out, bool fp
   const long long NP = ctx->NP;
   const int P = ctx->T.P, N = ctx->N;
   const int ph = (op == SPS_OP_S) ? SPS_PH_FAR_S : SPS_PH_FAR_K;
-  if (!fp32 && sps_far_dw(ctx)) return far_dw_run(ctx, op, sig, out, ph);
+  if (!fp32 && sps_far_dw(ctx)) return far_dw_run(ctx, op, sig, out, SPS_PH_FAR_DW);
   if (!fp32) {
     SpsPhase timer(ctx, ph);
     const int blocks = (int)((NP + kT64 - 1) / kT64);

@@ -564,7 +564,7 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
                   ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
                   ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw, ctx->d_prev_ij, ctx->d_prev_gam,
-                  ctx->d_dwsrc};
+                  ctx->d_dwsrc, ctx->d_rot, ctx->d_sigloc, ctx->d_tcsplit};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -592,8 +592,54 @@ static int check_finite_host(sps_ctx* ctx, const double* d, long long n, const c
   return SPS_OK;
 }
 
+extern "C" int sps_set_orientation(sps_ctx* ctx, int n, const double* Q) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  ctx->have_geom = false;          // nodes and normals depend on the orientation
+  ctx->zeta_n = ctx->zeta_nc_n = 0;
+  ctx->prev_nc = 0;
+  if (!Q) {
+    ctx->rot_n = 0;
+    return SPS_OK;
+  }
+  if (n < 1) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "set_orientation: n must be positive");
+  std::vector<double> h(9 * (size_t)n);
+  SPS_CUDA(ctx, cudaMemcpyAsync(h.data(), Q, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < n; ++i) {
+    const double* q = h.data() + 9 * (size_t)i;
+    for (int k = 0; k < 9; ++k)
+      if (!std::isfinite(q[k])) return sps_fail(ctx, SPS_ERR_NONFINITE, "orientation not finite");
+    // Q^T Q = I and det Q = +1, to 1e-12
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double d = 0.0;
+        for (int r = 0; r < 3; ++r) d += q[3 * r + a] * q[3 * r + b];
+        if (std::fabs(d - (a == b ? 1.0 : 0.0)) > 1e-12)
+          return sps_fail(ctx, SPS_ERR_INVALID_ARG, "orientation is not orthogonal");
+      }
+    const double det = q[0] * (q[4] * q[8] - q[5] * q[7]) - q[1] * (q[3] * q[8] - q[5] * q[6]) +
+                       q[2] * (q[3] * q[7] - q[4] * q[6]);
+    if (!(det > 0)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "orientation is a reflection");
+  }
+  SPS_TRY(sps_grow(ctx, &ctx->d_rot, ctx->cap_rot, 9 * (size_t)n));
+  SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_rot, Q, sizeof(double) * 9 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->rot_n = n;
+  return SPS_OK;
+}
+
+// oriented grids are not differentiated (the adjoint kernels use lab-frame
+// VSH maps)
+static int no_orientation(sps_ctx* ctx, const char* what) {
+  if (ctx->rot_n > 0)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, std::string(what) + ": not available with grid orientations");
+  return SPS_OK;
+}
+
 extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const double* radii) {
   if (!ctx || n < 1 || !pos || !radii) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "set_geometry: bad argument");
+  if (ctx->rot_n > 0 && ctx->rot_n != n)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "set_geometry: the grid orientation is set for another sphere count");
   const int P = ctx->T.P;
   const long long NP = (long long)n * P;
   {
@@ -893,10 +939,14 @@ static int mobility_solve(sps_ctx* ctx, const double* FT, double* UO, sps_stats*
       SPS_TRY(sps_dot(ctx, ctx->d_r, ctx->d_r, n, &rr));
       final_res = nb > 0 ? std::sqrt(rr) / nb : 0.0;
       if (final_res < ctx->prm.ir_tol) break;
+      // the correction need only shrink the residual by the factor still
+      // missing (with a margin), never below gmres_tol: one sweep's reduction
+      // is limited by the FP32 operator's own error anyway
+      const double need = ctx->prm.ir_tol / std::max(final_res, 1e-300);
+      const double ctol = std::min(1e-1, std::max(ctx->prm.gmres_tol, 0.5 * need));
       int its2 = 0;
       double res2 = 0;
-      int rc2 = gmres(ctx, ctx->d_r, ctx->d_dz, false, ctx->prm.gmres_tol, ctx->prm.gmres_max, true,
-                      &its2, &res2);
+      int rc2 = gmres(ctx, ctx->d_r, ctx->d_dz, false, ctol, ctx->prm.gmres_max, true, &its2, &res2);
       if (rc2 != SPS_OK && rc2 != SPS_ERR_NOT_CONVERGED) return rc2;
       total_its += its2;
       { SpsPhase timer_(ctx, SPS_PH_KRYLOV);
@@ -1445,6 +1495,7 @@ extern "C" int sps_mobility_adjoint(sps_ctx* ctx, int n, const double* pos, cons
                                     double* dL_dpos, sps_stats* st) {
   if (!ctx || !FT || !dL_dU || !dL_dFT || n < 1 || !pos || !radii)
     return sps_fail(ctx, SPS_ERR_INVALID_ARG, "mobility_adjoint: bad argument");
+  SPS_TRY(no_orientation(ctx, "mobility_adjoint"));
   long long l0;
   stats_begin(ctx, st, &l0);
   if (ctx->prm.mobility == SPS_MOB_IDENTITY) {
@@ -1501,6 +1552,7 @@ extern "C" int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, con
                                      double* dL_dFT, double* dL_dpos, sps_stats* st) {
   if (!ctx || n < 1 || !pos || !radii || !FT_ext || !dL_dU || !UO || !dL_dFT)
     return sps_fail(ctx, SPS_ERR_INVALID_ARG, "collision_adjoint: bad argument");
+  SPS_TRY(no_orientation(ctx, "collision_adjoint"));
   long long l0;
   stats_begin(ctx, st, &l0);
   // forward step (positions are not advanced)

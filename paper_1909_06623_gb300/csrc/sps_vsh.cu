@@ -356,12 +356,15 @@ __device__ __forceinline__ void near_contrib(const C* __restrict__ cf0, int L, T
 // One block per target sphere, one thread per node; source spheres from the
 // near list staged in shared memory.  skip_r2 > 0: entries with r^2 < skip_r2
 // (in units of the source radius) are left to k_near_close (FP64).
+// rot (optional, N x 9): the source sphere's grid rotation Q_j; the target and
+// its normal are taken into that sphere's frame (Q_j^T) and the field back
+// out of it (Q_j).
 template <int F, typename T>
 __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict__ pos,
                             const double* __restrict__ rad, const double* __restrict__ X,
                             const double* __restrict__ Nr, const int* __restrict__ near_ptr,
                             const int* __restrict__ near_idx, const double* __restrict__ fcoef,
-                            double skip_r2, double* __restrict__ out) {
+                            double skip_r2, const double* __restrict__ rot, double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char sraw[];
   T* sc = reinterpret_cast<T*>(sraw);
   const int i = blockIdx.x;
@@ -385,10 +388,17 @@ __global__ void k_near_eval(int N, int P, int L, int E, const double* __restrict
     __syncthreads();
     const double aj = rad[j], ia = 1.0 / aj;
     if (skip_r2 > 0.0 && sps_close_r2(pos, ia, gx, gy, gz, j) < skip_r2) continue;
-    const T x = (T)((gx - pos[3 * j]) * ia), y = (T)((gy - pos[3 * j + 1]) * ia),
-            z = (T)((gz - pos[3 * j + 2]) * ia);
+    T x = (T)((gx - pos[3 * j]) * ia), y = (T)((gy - pos[3 * j + 1]) * ia),
+      z = (T)((gz - pos[3 * j + 2]) * ia);
+    T wx = vx, wy = vy, wz = vz;
+    const double* Q = rot ? rot + 9 * j : nullptr;
+    if (Q) {
+      sps_rot_t(Q, x, y, z);
+      if (F == sps::kFieldsK) sps_rot_t(Q, wx, wy, wz);
+    }
     T tx, ty, tz;
-    near_contrib<F, T, T>(sc, L, x, y, z, vx, vy, vz, tx, ty, tz);
+    near_contrib<F, T, T>(sc, L, x, y, z, wx, wy, wz, tx, ty, tz);
+    if (Q) sps_rot_n(Q, tx, ty, tz);
     if (F == sps::kFieldsK) {
       ox += (double)tx;
       oy += (double)ty;
@@ -418,8 +428,9 @@ __global__ void k_near_eval32(int N, int P, int L, int E, const double* __restri
                               const double* __restrict__ rad, const double* __restrict__ X,
                               const double* __restrict__ Nr, const int* __restrict__ near_ptr,
                               const int* __restrict__ near_idx, const float* __restrict__ fcoef,
-                              double* __restrict__ out) {
+                              const double* __restrict__ rot, double* __restrict__ out) {
   constexpr int FP = (F + 1) & ~1;   // padded field count of a staged entry
+  __shared__ float s_rot[9];   // Q_j of the staged source (oriented grids)
   extern __shared__ __align__(16) unsigned char sraw[];
   float2* sc2 = reinterpret_cast<float2*>(sraw);
   __shared__ float s_geo[5];   // (c_i - c_j) / a_j, 1 / a_j, a_j
@@ -468,6 +479,8 @@ __global__ void k_near_eval32(int N, int P, int L, int E, const double* __restri
       s_geo[3] = (float)ia;
       s_geo[4] = (float)aj;
       s_iad = ia;
+      if (rot)
+        for (int c = 0; c < 9; ++c) s_rot[c] = (float)rot[9 * j + c];
     }
     __syncthreads();
     const float ia = s_geo[3];
@@ -477,8 +490,14 @@ __global__ void k_near_eval32(int N, int P, int L, int E, const double* __restri
       if (r2 < lo) continue;
       if (sps_close_r2(pos, s_iad, X[g], X[NP + g], X[2 * NP + g], j) < lim) continue;
     }
+    float xr = x, yr = y, zr = z, wx = vx, wy = vy, wz = vz;
+    if (rot) {
+      sps_rot_t(s_rot, xr, yr, zr);
+      if (F == sps::kFieldsK) sps_rot_t(s_rot, wx, wy, wz);
+    }
     float tx, ty, tz;
-    near_contrib<F, float, float>(reinterpret_cast<const float*>(sc2), L, x, y, z, vx, vy, vz, tx, ty, tz);
+    near_contrib<F, float, float>(reinterpret_cast<const float*>(sc2), L, xr, yr, zr, wx, wy, wz, tx, ty, tz);
+    if (rot) sps_rot_n(s_rot, tx, ty, tz);
     if (F == sps::kFieldsS) {
       const float aj = s_geo[4];
       tx *= aj;
@@ -503,7 +522,8 @@ __global__ void k_near_close(int N, int P, int L, int E, int n_close, const int*
                              const int* __restrict__ cptr, const int* __restrict__ csrc,
                              const double* __restrict__ pos, const double* __restrict__ rad,
                              const double* __restrict__ X, const double* __restrict__ Nr,
-                             const double* __restrict__ fcoef, double* __restrict__ out) {
+                             const double* __restrict__ fcoef, const double* __restrict__ rot,
+                             double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_close) return;
   const long long NP = (long long)N * P;
@@ -519,9 +539,16 @@ __global__ void k_near_close(int N, int P, int L, int E, int n_close, const int*
   for (int q = cptr[t]; q < cptr[t + 1]; ++q) {
     const int j = csrc[q];
     const double aj = rad[j], ia = 1.0 / aj;
-    const double x = (gx - pos[3 * j]) * ia, y = (gy - pos[3 * j + 1]) * ia, z = (gz - pos[3 * j + 2]) * ia;
+    double x = (gx - pos[3 * j]) * ia, y = (gy - pos[3 * j + 1]) * ia, z = (gz - pos[3 * j + 2]) * ia;
+    double wx = vx, wy = vy, wz = vz;
+    const double* Q = rot ? rot + 9 * j : nullptr;
+    if (Q) {
+      sps_rot_t(Q, x, y, z);
+      if (F == sps::kFieldsK) sps_rot_t(Q, wx, wy, wz);
+    }
     double tx, ty, tz;
-    near_contrib<F, double, double>(fcoef + (long long)j * E * F * 2, L, x, y, z, vx, vy, vz, tx, ty, tz);
+    near_contrib<F, double, double>(fcoef + (long long)j * E * F * 2, L, x, y, z, wx, wy, wz, tx, ty, tz);
+    if (Q) sps_rot_n(Q, tx, ty, tz);
     if (F == sps::kFieldsK) {
       ox += tx;
       oy += ty;
@@ -547,7 +574,7 @@ int launch_near_eval(sps_ctx* ctx, double skip_r2, double* out) {
                                        (int)sm));
   k_near_eval<F, T><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
                                                       ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
-                                                      ctx->d_fcoef, skip_r2, out);
+                                                      ctx->d_fcoef, skip_r2, sps_rot(ctx), out);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -562,7 +589,7 @@ int launch_near_eval32(sps_ctx* ctx, double* out) {
                                        (int)sm));
   k_near_eval32<F><<<N, threads, sm, ctx->stream>>>(N, P, L, E, ctx->d_pos, ctx->d_rad, ctx->d_X,
                                                      ctx->d_Nrm, ctx->d_near_ptr, ctx->d_near_idx,
-                                                     ctx->d_fcoef32, out);
+                                                     ctx->d_fcoef32, sps_rot(ctx), out);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -574,30 +601,45 @@ __global__ void k_near_close_dw(int N, int P, int L, int E, int n_close, const i
                                 const int* __restrict__ cptr, const int* __restrict__ csrc,
                                 const double* __restrict__ pos, const double* __restrict__ rad,
                                 const double* __restrict__ X, const double* __restrict__ Nr,
-                                const float4* __restrict__ fcoef, double* __restrict__ out) {
+                                const float4* __restrict__ fcoef, const double* __restrict__ rot,
+                                double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_close) return;
   const long long NP = (long long)N * P;
   const long long g = cnode[t];
   const double gx = X[g], gy = X[NP + g], gz = X[2 * NP + g];
-  dw vx(0), vy(0), vz(0);
+  double nx = 0.0, ny = 0.0, nz = 0.0;
   if (F == sps::kFieldsK) {
-    vx = dw_of(Nr[g]);
-    vy = dw_of(Nr[NP + g]);
-    vz = dw_of(Nr[2 * NP + g]);
+    nx = Nr[g];
+    ny = Nr[NP + g];
+    nz = Nr[2 * NP + g];
   }
+  dw vx = dw_of(nx), vy = dw_of(ny), vz = dw_of(nz);
   double ox = 0, oy = 0, oz = 0;
   for (int q = cptr[t]; q < cptr[t + 1]; ++q) {
     const int j = csrc[q];
     const double aj = rad[j], ia = 1.0 / aj;
-    const dw x = dw_of((gx - pos[3 * j]) * ia), y = dw_of((gy - pos[3 * j + 1]) * ia),
-             z = dw_of((gz - pos[3 * j + 2]) * ia);
+    double x64 = (gx - pos[3 * j]) * ia, y64 = (gy - pos[3 * j + 1]) * ia, z64 = (gz - pos[3 * j + 2]) * ia;
+    const double* Q = rot ? rot + 9 * j : nullptr;
+    if (Q) {
+      sps_rot_t(Q, x64, y64, z64);
+      if (F == sps::kFieldsK) {
+        double mx = nx, my = ny, mz = nz;
+        sps_rot_t(Q, mx, my, mz);
+        vx = dw_of(mx);
+        vy = dw_of(my);
+        vz = dw_of(mz);
+      }
+    }
+    const dw x = dw_of(x64), y = dw_of(y64), z = dw_of(z64);
     dw tx, ty, tz;
     near_contrib<F, dw, float4>(fcoef + (long long)j * E * F, L, x, y, z, vx, vy, vz, tx, ty, tz);
     const double s = (F == sps::kFieldsK) ? 1.0 : aj;
-    ox += s * dw_val(tx);
-    oy += s * dw_val(ty);
-    oz += s * dw_val(tz);
+    double rx = s * dw_val(tx), ry = s * dw_val(ty), rz = s * dw_val(tz);
+    if (Q) sps_rot_n(Q, rx, ry, rz);
+    ox += rx;
+    oy += ry;
+    oz += rz;
   }
   out[g] += ox;
   out[NP + g] += oy;
@@ -614,14 +656,14 @@ int launch_near_close(sps_ctx* ctx, double* out) {
     k_near_close_dw<F><<<(ctx->n_close + 63) / 64, 64, 0, ctx->stream>>>(
         ctx->N, ctx->T.P, ctx->T.L, ctx->T.E, ctx->n_close, ctx->d_close_node, ctx->d_close_ptr,
         ctx->d_close_src, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm,
-        reinterpret_cast<const float4*>(ctx->d_fcoefdw), out);
+        reinterpret_cast<const float4*>(ctx->d_fcoefdw), sps_rot(ctx), out);
     SPS_LAUNCHED(ctx);
     return SPS_OK;
   }
   if (ctx->n_close == 0) return SPS_OK;
   k_near_close<F><<<(ctx->n_close + 63) / 64, 64, 0, ctx->stream>>>(
       ctx->N, ctx->T.P, ctx->T.L, ctx->T.E, ctx->n_close, ctx->d_close_node, ctx->d_close_ptr,
-      ctx->d_close_src, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm, ctx->d_fcoef, out);
+      ctx->d_close_src, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm, ctx->d_fcoef, sps_rot(ctx), out);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }
@@ -819,8 +861,18 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
 #endif
 int sps_layer(sps_ctx* ctx, int op, const double* sig, double* out, bool fp32) {
   ctx->layer_applies += 1;
-  SPS_TRY(sps_launch_analysis(ctx, sig, fp32 && SPS_MIXED_VSH));
-  SPS_TRY(sps_launch_self(ctx, op, sig, out, fp32 && SPS_MIXED_VSH));
+  // oriented grids: the VSH transforms see each density in its sphere's frame
+  // (components Q_i^T sigma), and the self field is rotated back (Q_i u)
+  const bool rot = sps_rot(ctx) != nullptr;
+  const double* sl = sig;
+  if (rot) {
+    SPS_TRY(sps_grow(ctx, &ctx->d_sigloc, ctx->cap_sigloc, 3 * (size_t)ctx->NP));
+    SPS_TRY(sps_launch_rotate(ctx, sig, ctx->d_sigloc, true));
+    sl = ctx->d_sigloc;
+  }
+  SPS_TRY(sps_launch_analysis(ctx, sl, fp32 && SPS_MIXED_VSH));
+  SPS_TRY(sps_launch_self(ctx, op, sl, out, fp32 && SPS_MIXED_VSH));
+  if (rot) SPS_TRY(sps_launch_rotate(ctx, out, out, false));
   const int kop = (op == SPS_OP_S) ? SPS_OP_S : SPS_OP_K;
   SPS_TRY(sps_launch_near(ctx, kop, out, fp32 && SPS_MIXED_NEAR));
   SPS_TRY(sps_launch_far(ctx, kop, sig, out, fp32));

@@ -124,6 +124,39 @@ def tiny_layers():
 
 
 
+def rotated():
+    """Randomly oriented grids (Sec. 5.4, rotations from the seeded generator):
+    the tiny cases' operators and mobility, and the five-sphere active step,
+    all evaluated by the oracle's Suspension(rotations=Q)."""
+    out = {}
+    for seed, N, p in ((1, 6, 4), (3, 5, 5)):
+        w = workloads.tiny(seed, N, p, phi=0.08, gap=5e-3)
+        Q = workloads.random_rotations(workloads.SEED_BASE + 50 + seed, N)
+        sus = Suspension(w.centers, w.radii, p, rotations=Q)
+        rng = np.random.default_rng(seed + 100)
+        sig = rng.standard_normal((sus.N * sus.P, 3))
+        out[f"c{seed}_centers"] = w.centers
+        out[f"c{seed}_radii"] = w.radii
+        out[f"c{seed}_p"] = p
+        out[f"c{seed}_Q"] = Q
+        out[f"c{seed}_sigma"] = sig
+        out[f"c{seed}_X"] = sus.X
+        out[f"c{seed}_S"] = sus.apply("S", sig)
+        out[f"c{seed}_K"] = sus.apply("K", sig)
+        out[f"c{seed}_A"] = 0.5 * sig + out[f"c{seed}_K"] + mobility.apply_L(sus, sig)
+        out[f"c{seed}_FT"] = w.FT
+        out[f"c{seed}_U"] = mobility.mobility_apply(sus, w.FT, 1e-13, 300)
+    d = np.load(os.path.join(HERE, "active_step_p4.npz"))
+    Q = workloads.random_rotations(workloads.SEED_BASE + 57, len(d["radii"]))
+    r = lcp.resolve_collisions(d["centers"], d["radii"], d["FT"], float(d["dt"]), int(d["p"]),
+                               delta=0.1, a_c_scale=1.05, gmres_tol=1e-13, bbpgd_tol=1e-12,
+                               rotations=Q)
+    out.update(step_Q=Q, step_gamma=r["gamma"], step_U=r["U"], step_centers_new=r["centers_new"],
+               step_bbpgd_iters=r["info"]["iters"], step_n_active=r["info"]["n_active"])
+    np.savez_compressed(os.path.join(HERE, "rotated_p4.npz"), **out)
+    print("rotated", r["info"])
+
+
 def collision_grad():
     """The five-sphere active step (p = 4): the assembled mobility, the step's
     contacts and gamma, and central differences (h = 1e-5 max|F|) of
@@ -195,7 +228,7 @@ def sed_steps():
                         n_active=np.array(active))
 
 
-ALL = {"cfg1": cfg1, "active": active, "capped": capped, "cfg2": cfg2_sample, "tiny": tiny_layers,
+ALL = {"cfg1": cfg1, "active": active, "capped": capped, "rotated": rotated, "cfg2": cfg2_sample, "tiny": tiny_layers,
        "collision_grad": collision_grad, "collision_grad_c": collision_grad_c,
        "sed_steps": sed_steps}
 
