@@ -291,6 +291,50 @@ int sps_launch_near_lists(sps_ctx* ctx) {
   return SPS_OK;
 }
 
+namespace {
+// For each position q' of the near CSR (row j, source-major reading: target
+// i = near_idx[q'] of source j): rev[q'] = the position q of j in row i (the
+// relation is symmetric to the bit), and geo[q'] = (c_j - c_i) / a_i, the
+// offset of sphere j's centre seen from near source i in i's radius units
+// (FP32), which the source-major near field reads through rev.
+__global__ void k_near_rev(int N, const int* __restrict__ ptr, const int* __restrict__ idx,
+                           const double* __restrict__ pos, const double* __restrict__ rad,
+                           int* __restrict__ rev, float* __restrict__ geo) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  for (int qp = ptr[j]; qp < ptr[j + 1]; ++qp) {
+    const int i = idx[qp];
+    int lo = ptr[i], hi = ptr[i + 1] - 1, q = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1, v = idx[mid];
+      if (v == j) {
+        q = mid;
+        break;
+      }
+      if (v < j) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    rev[qp] = q;
+    const double ia = 1.0 / rad[i];
+    geo[3 * qp] = (float)((pos[3 * j] - pos[3 * i]) * ia);
+    geo[3 * qp + 1] = (float)((pos[3 * j + 1] - pos[3 * i + 1]) * ia);
+    geo[3 * qp + 2] = (float)((pos[3 * j + 2] - pos[3 * i + 2]) * ia);
+  }
+}
+}  // namespace
+
+int sps_launch_near_rev(sps_ctx* ctx) {
+  SpsPhase timer(ctx, SPS_PH_GEOM);
+  const size_t nq = (size_t)std::max(ctx->n_near, 1);
+  SPS_TRY(sps_grow(ctx, &ctx->d_near_rev, ctx->cap_near_rev, nq));
+  SPS_TRY(sps_grow(ctx, &ctx->d_near_geo, ctx->cap_near_geo, 3 * nq));
+  if (ctx->n_near == 0) return SPS_OK;
+  k_near_rev<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(ctx->N, ctx->d_near_ptr, ctx->d_near_idx, ctx->d_pos,
+                                                          ctx->d_rad, ctx->d_near_rev, ctx->d_near_geo);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
 int sps_launch_close_lists(sps_ctx* ctx) {
   SpsPhase timer(ctx, SPS_PH_GEOM);
   const long long NP = ctx->NP;

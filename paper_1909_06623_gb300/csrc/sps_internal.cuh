@@ -104,6 +104,12 @@ struct sps_ctx {
   float *d_chi = nullptr, *d_clo = nullptr;                       // centres as hi + lo (N x 3)
   int *d_near_ptr = nullptr, *d_near_idx = nullptr;
   int n_near = 0, cap_near = 0;
+  // source-major near field (mixed path): reverse index and per-pair centre
+  // offsets (see k_near_rev), per-(pair, node) results (3 planes of n_near P)
+  int *d_near_rev = nullptr;
+  float *d_near_geo = nullptr;
+  double *d_near_buf = nullptr;
+  size_t cap_near_rev = 0, cap_near_geo = 0, cap_near_buf = 0;
   // close near entries (mixed path FP64 list): nodes, CSR into source spheres
   int n_close = 0, n_close_src = 0;
   int *d_close_node = nullptr, *d_close_ptr = nullptr, *d_close_src = nullptr;
@@ -320,6 +326,7 @@ int sps_launch_grid(sps_ctx* ctx);
 int sps_launch_rotate(sps_ctx* ctx, const double* in, double* out, bool transpose);
 int sps_launch_near_lists(sps_ctx* ctx);
 int sps_launch_close_lists(sps_ctx* ctx);
+int sps_launch_near_rev(sps_ctx* ctx);
 int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii);
 // contacts, D products, identity-mobility BBPGD pieces (sps_contacts.cu)
 int sps_check_inputs(sps_ctx* ctx, int n, const double* pos, const double* radii, const double* FT);

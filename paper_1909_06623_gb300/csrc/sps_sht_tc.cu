@@ -122,17 +122,24 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16&
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
-// stage K chunk kc: A (rows = the CTA's spheres, split on the fly) and the
-// pre-split B chunk of this N tile, into one smem buffer
+// The input operand A (rows = spheres) split into three BF16 terms once per
+// transform, in the layout the chunks are staged in: sphere block sb of 128,
+// chunk kc, split sp -> kM * kKC elements at ((sb * nkc + kc) * 3 + sp) * kM * kKC,
+// canonical K-major inside.  The FP64 -> FP32 conversion runs here, once per
+// element, instead of in every CTA of every N tile.
 template <int MODE>
-__device__ __forceinline__ void stage_chunk(unsigned char* buf, int kc, int s0, int Ns, int P, int K,
-                                            long long NP, const double* __restrict__ in,
-                                            const uint16_t* __restrict__ Bchunk, int nrows) {
-  unsigned char* sA = buf;
-  unsigned char* sB = buf + 3 * kABytes;
-  for (int it = threadIdx.x; it < kM * (kKC / 8); it += 128) {
+__global__ void k_tc_split(int Ns, int P, int K, int nkc, const double* __restrict__ in,
+                           uint16_t* __restrict__ Asp) {
+  const long long NP = (long long)Ns * P;
+  const int nsb = (Ns + kM - 1) / kM;
+  const long long total = (long long)nsb * nkc * kM * (kKC / 8);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int it = (int)(q % (kM * (kKC / 8)));
+    const long long bc = q / (kM * (kKC / 8));       // sb * nkc + kc
+    const int kc = (int)(bc % nkc), sb = (int)(bc / nkc);
     const int r = it / (kKC / 8), k8 = (it % (kKC / 8)) * 8;
-    const int s = s0 + r;
+    const int s = sb * kM + r;
     __align__(16) __nv_bfloat16 vh[8], vm[8], vl[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -148,11 +155,23 @@ __device__ __forceinline__ void stage_chunk(unsigned char* buf, int kc, int s0, 
       }
       split3(x, vh[u], vm[u], vl[u]);
     }
+    unsigned char* base = reinterpret_cast<unsigned char*>(Asp + bc * 3 * (kM * kKC));
     const int off = tc_off(r, k8);
-    *reinterpret_cast<uint4*>(sA + off) = *reinterpret_cast<const uint4*>(vh);
-    *reinterpret_cast<uint4*>(sA + kABytes + off) = *reinterpret_cast<const uint4*>(vm);
-    *reinterpret_cast<uint4*>(sA + 2 * kABytes + off) = *reinterpret_cast<const uint4*>(vl);
+    *reinterpret_cast<uint4*>(base + off) = *reinterpret_cast<const uint4*>(vh);
+    *reinterpret_cast<uint4*>(base + kABytes + off) = *reinterpret_cast<const uint4*>(vm);
+    *reinterpret_cast<uint4*>(base + 2 * kABytes + off) = *reinterpret_cast<const uint4*>(vl);
   }
+}
+
+// stage K chunk kc: the pre-split A chunk of the CTA's spheres and the
+// pre-split B chunk of this N tile, into one smem buffer (plain 16-byte copies)
+__device__ __forceinline__ void stage_chunk(unsigned char* buf, const uint16_t* __restrict__ Achunk,
+                                            const uint16_t* __restrict__ Bchunk, int nrows) {
+  unsigned char* sA = buf;
+  unsigned char* sB = buf + 3 * kABytes;
+  const uint4* srcA = reinterpret_cast<const uint4*>(Achunk);
+  for (int v = threadIdx.x; v < 3 * kABytes / 16; v += 128)
+    *reinterpret_cast<uint4*>(sA + 16 * v) = srcA[v];
   const int bytes = nrows * kKC * 2;
   const uint4* src = reinterpret_cast<const uint4*>(Bchunk);
   for (int v = threadIdx.x; v < 3 * bytes / 16; v += 128) {
@@ -168,7 +187,7 @@ __device__ __forceinline__ void stage_chunk(unsigned char* buf, int kc, int s0, 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_sht_tc(int Ns, int P, int Nout, int K, int Kpad,
                                                const uint16_t* __restrict__ Bt,
-                                               const double* __restrict__ in,
+                                               const uint16_t* __restrict__ Asp,
                                                double* __restrict__ out,
                                                const double* __restrict__ rad, int scale_by_radius,
                                                const double* __restrict__ sig, int half,
@@ -184,6 +203,7 @@ __global__ void __launch_bounds__(128) k_sht_tc(int Ns, int P, int Nout, int K, 
   const long long NP = (long long)Ns * P;
   // tiles before t are full (kNT rows); chunk kc of tile t at tile base + kc * 3 * nrows * kKC
   const uint16_t* Btile = Bt + (size_t)t * 3 * kNT * Kpad;
+  const uint16_t* Ablock = Asp + (size_t)blockIdx.x * nkc * 3 * (kM * kKC);
   const uint32_t bar0 = smem_u32(&bar[0]), bar1 = smem_u32(&bar[1]);
 
   if (warp == 0) {
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(128) k_sht_tc(int Ns, int P, int Nout, int K, 
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  stage_chunk<MODE>(smem, 0, s0, Ns, P, K, NP, in, Btile, nrows);
+  stage_chunk(smem, Ablock, Btile, nrows);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -234,8 +254,8 @@ __global__ void __launch_bounds__(128) k_sht_tc(int Ns, int P, int Nout, int K, 
   for (int kc = 0; kc < nkc; ++kc) {
     if (kc + 1 < nkc) {
       // buffer (kc+1)&1 was read by chunk kc-1, whose completion was awaited
-      stage_chunk<MODE>(smem + ((kc + 1) & 1) * kStage, kc + 1, s0, Ns, P, K, NP, in,
-                        Btile + (size_t)(kc + 1) * 3 * nrows * kKC, nrows);
+      stage_chunk(smem + ((kc + 1) & 1) * kStage, Ablock + (size_t)(kc + 1) * 3 * (kM * kKC),
+                  Btile + (size_t)(kc + 1) * 3 * nrows * kKC, nrows);
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -368,13 +388,24 @@ int sps_launch_sht_tc(sps_ctx* ctx, const sps_ctx::TcMat& m, int mode, const dou
     SPS_CUDA(ctx, cudaFuncSetAttribute(k_sht_tc<MODE_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     attr = true;
   }
-  const dim3 grid((N + kM - 1) / kM, (m.R + kNT - 1) / kNT);
+  const int nsb = (N + kM - 1) / kM, nkc = m.Kpad / kKC;
+  SPS_TRY(sps_grow(ctx, &ctx->d_tcsplit, ctx->cap_tcsplit, (size_t)nsb * nkc * 3 * kM * kKC));
+  const long long items = (long long)nsb * nkc * kM * (kKC / 8);
+  const int sgrid = (int)std::min<long long>((items + 255) / 256, 8 * 152);
   if (mode == 0)
-    k_sht_tc<MODE_ANALYSIS><<<grid, 128, kSmem, ctx->stream>>>(N, P, m.R, m.C, m.Kpad, m.d, in, out, ctx->d_rad,
-                                                               scale_by_radius, sig, half, ctx->d_tcflag);
+    k_tc_split<MODE_ANALYSIS><<<sgrid, 256, 0, ctx->stream>>>(N, P, m.C, nkc, in, ctx->d_tcsplit);
   else
-    k_sht_tc<MODE_SYNTH><<<grid, 128, kSmem, ctx->stream>>>(N, P, m.R, m.C, m.Kpad, m.d, in, out, ctx->d_rad,
-                                                            scale_by_radius, sig, half, ctx->d_tcflag);
+    k_tc_split<MODE_SYNTH><<<sgrid, 256, 0, ctx->stream>>>(N, P, m.C, nkc, in, ctx->d_tcsplit);
+  SPS_LAUNCHED(ctx);
+  const dim3 grid(nsb, (m.R + kNT - 1) / kNT);
+  if (mode == 0)
+    k_sht_tc<MODE_ANALYSIS><<<grid, 128, kSmem, ctx->stream>>>(N, P, m.R, m.C, m.Kpad, m.d, ctx->d_tcsplit, out,
+                                                               ctx->d_rad, scale_by_radius, sig, half,
+                                                               ctx->d_tcflag);
+  else
+    k_sht_tc<MODE_SYNTH><<<grid, 128, kSmem, ctx->stream>>>(N, P, m.R, m.C, m.Kpad, m.d, ctx->d_tcsplit, out,
+                                                            ctx->d_rad, scale_by_radius, sig, half,
+                                                            ctx->d_tcflag);
   SPS_LAUNCHED(ctx);
   return SPS_OK;
 }

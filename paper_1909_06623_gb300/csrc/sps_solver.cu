@@ -564,7 +564,8 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->tcS.d, ctx->tcK.d, ctx->d_tcflag, ctx->d_order,
                   ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
                   ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw, ctx->d_prev_ij, ctx->d_prev_gam,
-                  ctx->d_dwsrc, ctx->d_rot, ctx->d_sigloc, ctx->d_tcsplit};
+                  ctx->d_dwsrc, ctx->d_rot, ctx->d_sigloc, ctx->d_tcsplit, ctx->d_near_rev,
+                  ctx->d_near_geo, ctx->d_near_buf};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -718,6 +719,7 @@ extern "C" int sps_set_geometry(sps_ctx* ctx, int n, const double* pos, const do
   SPS_TRY(sps_launch_grid(ctx));
   SPS_TRY(sps_launch_near_lists(ctx));
   SPS_TRY(sps_launch_close_lists(ctx));
+  SPS_TRY(sps_launch_near_rev(ctx));
   ctx->have_geom = true;
   return SPS_OK;
 }

@@ -646,8 +646,196 @@ __global__ void k_near_close_dw(int N, int P, int L, int E, int n_close, const i
   out[2 * NP + g] += oz;
 }
 
+// ---------------------------------------------------------------------------
+// Source-major near field (mixed path).  One CTA per source sphere j stages
+// j's field coefficients once (FP32 pairs and double-float) and evaluates them
+// at every node of every near target sphere i of j: the items (pair, node).
+// The close / far split is the one of the close list (FP32 distance outside a
+// 1e-4 band around kCloseRadius, the list's FP64 test inside it).  Far items
+// use the FP32 expansion (k_near_eval32's arithmetic); close items are
+// collected in shared memory and evaluated afterwards in double-float
+// (k_near_close_dw's arithmetic), so no warp diverges on them.  Each item's
+// field goes to buf at its target-major pair slot; k_near_reduce adds a
+// node's pairs in near-list order in FP64 (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int kNS = 256;
+constexpr int kMaxClose = 1024;   // close items held per CTA (more are evaluated in place)
+
+template <int F>
+__device__ __forceinline__ void near_src_close(int it, int j, int q0, int P, int L, long long NP, long long NQ,
+                                               const double* __restrict__ pos, double aj, double iad,
+                                               const double* __restrict__ X, const double* __restrict__ Nr,
+                                               const int* __restrict__ near_idx, const int* __restrict__ rev,
+                                               const float4* cdw, const double* Q, double* __restrict__ buf) {
+  const int qq = it / P, k = it - qq * P;
+  const int i = near_idx[q0 + qq], q = rev[q0 + qq];
+  if (q < 0) return;   // (cannot happen: the near relation is symmetric to the bit)
+  const long long g = (long long)i * P + k, o = (long long)q * P + k;
+  double x64 = (X[g] - pos[3 * j]) * iad, y64 = (X[NP + g] - pos[3 * j + 1]) * iad,
+         z64 = (X[2 * NP + g] - pos[3 * j + 2]) * iad;
+  double nx = 0.0, ny = 0.0, nz = 0.0;
+  if (F == sps::kFieldsK) {
+    nx = Nr[g];
+    ny = Nr[NP + g];
+    nz = Nr[2 * NP + g];
+  }
+  if (Q) {
+    sps_rot_t(Q, x64, y64, z64);
+    if (F == sps::kFieldsK) sps_rot_t(Q, nx, ny, nz);
+  }
+  dw tx, ty, tz;
+  near_contrib<F, dw, float4>(cdw, L, dw_of(x64), dw_of(y64), dw_of(z64), dw_of(nx), dw_of(ny), dw_of(nz), tx,
+                              ty, tz);
+  const double sc = (F == sps::kFieldsK) ? 1.0 : aj;
+  double rx = sc * dw_val(tx), ry = sc * dw_val(ty), rz = sc * dw_val(tz);
+  if (Q) sps_rot_n(Q, rx, ry, rz);
+  buf[o] = rx;
+  buf[NQ + o] = ry;
+  buf[2 * NQ + o] = rz;
+}
+
+template <int F>
+__global__ void __launch_bounds__(kNS) k_near_src(int N, int P, int L, int E, long long NQ,
+                                                 const double* __restrict__ pos, const double* __restrict__ rad,
+                                                 const double* __restrict__ X, const double* __restrict__ Nr,
+                                                 const float* __restrict__ rel32, const float* __restrict__ N32,
+                                                 const int* __restrict__ near_ptr, const int* __restrict__ near_idx,
+                                                 const int* __restrict__ rev, const float* __restrict__ geo,
+                                                 const float* __restrict__ fcoef32,
+                                                 const float4* __restrict__ fcoefdw,
+                                                 const double* __restrict__ rot, double* __restrict__ buf) {
+  constexpr int FP = (F + 1) & ~1;
+  extern __shared__ __align__(16) unsigned char sraw[];
+  float4* c32 = reinterpret_cast<float4*>(sraw);     // E x FP/2 field pairs
+  float4* cdw = c32 + E * (FP / 2);                 // E x F double-float fields
+  __shared__ float s_rot[9];
+  __shared__ double s_rotd[9];
+  __shared__ int s_ncl;
+  __shared__ int s_cl[kMaxClose];
+  const int j = blockIdx.x;
+  const int q0 = near_ptr[j], nn = near_ptr[j + 1] - q0;
+  if (nn == 0) return;                               // uniform over the block
+  const float2* src = reinterpret_cast<const float2*>(fcoef32 + (long long)j * E * F * 2);
+  for (int t = threadIdx.x; t < E * (FP / 2); t += kNS) {
+    const int e = t / (FP / 2), l = t - e * (FP / 2);
+    const float2 a = src[e * F + 2 * l];
+    const float2 b = (2 * l + 1 < F) ? src[e * F + 2 * l + 1] : make_float2(0.f, 0.f);
+    c32[t] = make_float4(a.x, b.x, -a.y, -b.y);
+  }
+  const float4* dsrc = fcoefdw + (long long)j * E * F;
+  for (int t = threadIdx.x; t < E * F; t += kNS) cdw[t] = dsrc[t];
+  if (threadIdx.x == 0) {
+    s_ncl = 0;
+    if (rot)
+      for (int c = 0; c < 9; ++c) {
+        s_rotd[c] = rot[9 * j + c];
+        s_rot[c] = (float)rot[9 * j + c];
+      }
+  }
+  __syncthreads();
+  const long long NP = (long long)N * P;
+  const double aj = rad[j], iad = 1.0 / aj;
+  const float ia = (float)iad, ajf = (float)aj;
+  const double lim = sps::kCloseRadius * sps::kCloseRadius;
+  const float lo = (float)(lim * (1.0 - 1e-4)), hi = (float)(lim * (1.0 + 1e-4));
+  const double* Qd = rot ? s_rotd : nullptr;
+  const int items = nn * P;
+  for (int it = threadIdx.x; it < items; it += kNS) {
+    const int qq = it / P, k = it - qq * P;
+    const int i = near_idx[q0 + qq];
+    const int q = rev[q0 + qq];
+    if (q < 0) continue;   // (cannot happen: the near relation is symmetric to the bit)
+    const long long g = (long long)i * P + k;
+    float x = fmaf(rel32[g], ia, geo[3 * q]), y = fmaf(rel32[NP + g], ia, geo[3 * q + 1]),
+          z = fmaf(rel32[2 * NP + g], ia, geo[3 * q + 2]);
+    const float r2 = x * x + y * y + z * z;
+    if (r2 < hi &&
+        (r2 < lo || sps_close_r2(pos, iad, X[g], X[NP + g], X[2 * NP + g], j) < lim)) {
+      const int c = atomicAdd(&s_ncl, 1);
+      if (c < kMaxClose)
+        s_cl[c] = it;
+      else
+        near_src_close<F>(it, j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+      continue;
+    }
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+    if (F == sps::kFieldsK) {
+      vx = N32[g];
+      vy = N32[NP + g];
+      vz = N32[2 * NP + g];
+    }
+    if (rot) {
+      sps_rot_t(s_rot, x, y, z);
+      if (F == sps::kFieldsK) sps_rot_t(s_rot, vx, vy, vz);
+    }
+    float tx, ty, tz;
+    near_contrib<F, float, float>(reinterpret_cast<const float*>(c32), L, x, y, z, vx, vy, vz, tx, ty, tz);
+    if (rot) sps_rot_n(s_rot, tx, ty, tz);
+    if (F == sps::kFieldsS) {
+      tx *= ajf;
+      ty *= ajf;
+      tz *= ajf;
+    }
+    const long long o = (long long)q * P + k;
+    buf[o] = tx;
+    buf[NQ + o] = ty;
+    buf[2 * NQ + o] = tz;
+  }
+  __syncthreads();
+  const int ncl = min(s_ncl, kMaxClose);
+  for (int c = threadIdx.x; c < ncl; c += kNS)
+    near_src_close<F>(s_cl[c], j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+}
+
+// out[g] += sum over the near pairs q of g's sphere (near-list order) of buf
+__global__ void k_near_reduce(int N, int P, long long NQ, const int* __restrict__ near_ptr,
+                              const double* __restrict__ buf, double* __restrict__ out) {
+  const long long NP = (long long)N * P;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NP;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(g / P), k = (int)(g - (long long)i * P);
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int q = near_ptr[i]; q < near_ptr[i + 1]; ++q) {
+      const long long o = (long long)q * P + k;
+      sx += buf[o];
+      sy += buf[NQ + o];
+      sz += buf[2 * NQ + o];
+    }
+    out[g] += sx;
+    out[NP + g] += sy;
+    out[2 * NP + g] += sz;
+  }
+}
+
+template <int F>
+int launch_near_src(sps_ctx* ctx, double* out) {
+  const int N = ctx->N, P = ctx->T.P, L = ctx->T.L, E = ctx->T.E;
+  const long long NQ = (long long)ctx->n_near * P;
+  SPS_TRY(sps_grow(ctx, &ctx->d_near_buf, ctx->cap_near_buf, 3 * (size_t)NQ));
+  constexpr int FP = (F + 1) & ~1;
+  const size_t sm = sizeof(float4) * (size_t)E * (FP / 2 + F);
+  if (sm > 48 * 1024)
+    SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_src<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_near_src<F><<<N, kNS, sm, ctx->stream>>>(N, P, L, E, NQ, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm,
+                                             ctx->d_rel32, ctx->d_N32, ctx->d_near_ptr, ctx->d_near_idx,
+                                             ctx->d_near_rev, ctx->d_near_geo, ctx->d_fcoef32,
+                                             reinterpret_cast<const float4*>(ctx->d_fcoefdw), sps_rot(ctx),
+                                             ctx->d_near_buf);
+  SPS_LAUNCHED(ctx);
+  const long long NP = (long long)N * P;
+  k_near_reduce<<<(int)std::min<long long>((NP + 255) / 256, 8 * 152), 256, 0, ctx->stream>>>(
+      N, P, NQ, ctx->d_near_ptr, ctx->d_near_buf, out);
+  SPS_LAUNCHED(ctx);
+  return SPS_OK;
+}
+
 #ifndef SPS_CLOSE_DW
 #define SPS_CLOSE_DW 1
+#endif
+// 1: the mixed path's near field runs source-major (k_near_src); 0: the
+// target-major kernels k_near_eval32 + k_near_close_dw
+#ifndef SPS_NEAR_SRC
+#define SPS_NEAR_SRC 1
 #endif
 template <int F>
 int launch_near_close(sps_ctx* ctx, double* out) {
@@ -845,10 +1033,12 @@ int sps_launch_near(sps_ctx* ctx, int op, double* out, bool fp32) {
   // FP64 for the close ones (where the expansion's terms do not decay)
   if (S) {
     if (!fp32) return launch_near_eval<sps::kFieldsS, double>(ctx, 0.0, out);
+    if (SPS_NEAR_SRC && SPS_CLOSE_DW) return launch_near_src<sps::kFieldsS>(ctx, out);
     SPS_TRY(launch_near_eval32<sps::kFieldsS>(ctx, out));
     return launch_near_close<sps::kFieldsS>(ctx, out);
   }
   if (!fp32) return launch_near_eval<sps::kFieldsK, double>(ctx, 0.0, out);
+  if (SPS_NEAR_SRC && SPS_CLOSE_DW) return launch_near_src<sps::kFieldsK>(ctx, out);
   SPS_TRY(launch_near_eval32<sps::kFieldsK>(ctx, out));
   return launch_near_close<sps::kFieldsK>(ctx, out);
 }
