@@ -31,6 +31,14 @@ Paper: Yan et al., arXiv 1909.06623.
     without meeting eps_tol (breakdown, growth or j_max) the iterate of
     smallest residual among gamma_0, gamma_1, ... is returned (the earliest
     on ties).  Off by default.
+  * Walls (Sec. 3.3.3, "Extensions"): a boundary does not enter the
+    mobility; each particle-boundary pair adds a column to D with nonzero
+    entries on that particle only.  A wall here is a plane n.x = d with unit
+    normal n pointing into the fluid: Phi = (n.c_i - d) - R_i, in the set
+    when Phi <= delta + delta_rel a_i (the wall has no radius; a reading),
+    column +n on sphere i (the wall acts as a static first body, so
+    D^T U = n.U_i).  Wall contacts follow the pair contacts, sorted by
+    (sphere, wall), recorded as (-1 - w, i).
   * eq. time-step: C^{k+1} = C^k + (U_nc + M D gamma) dt, positions only
     (spheres are isotropic; the grid keeps its lab-frame orientation).
 """
@@ -66,18 +74,44 @@ def build_contacts(centers, radii, delta, a_c_scale=1.0, delta_rel=0.0):
             np.array(ph, dtype=np.float64), np.array(nr, dtype=np.float64).reshape(-1, 3))
 
 
+def build_wall_contacts(centers, radii, walls, delta, a_c_scale=1.0, delta_rel=0.0):
+    """Particle-wall contacts (Sec. 3.3.3): for every sphere i (ascending) and
+    wall w (ascending) with Phi = (n_w . c_i - d_w) - R_i <= delta +
+    delta_rel a_i.  walls: W x 4 rows (n_x, n_y, n_z, d), n a unit normal
+    into the fluid.  Returns ij rows (-1 - w, i), Phi, normals n_w."""
+    c = np.asarray(centers, dtype=np.float64).reshape(-1, 3)
+    a = np.asarray(radii, dtype=np.float64).reshape(-1)
+    W = np.asarray(walls, dtype=np.float64).reshape(-1, 4)
+    ij, ph, nr = [], [], []
+    for i in range(len(a)):
+        for w in range(len(W)):
+            n = W[w, :3]
+            # every operation rounded separately, in this order
+            h = (n[0] * c[i, 0] + n[1] * c[i, 1]) + n[2] * c[i, 2]
+            phi = (h - W[w, 3]) - a[i] * a_c_scale
+            if phi <= delta + delta_rel * a[i]:
+                ij.append((-1 - w, i))
+                ph.append(phi)
+                nr.append(tuple(n))
+    return (np.array(ij, dtype=np.int32).reshape(-1, 2),
+            np.array(ph, dtype=np.float64), np.array(nr, dtype=np.float64).reshape(-1, 3))
+
+
 def D_apply(N, ij, nrm, gamma):
-    """F_c = D gamma (N x 6, torques zero), eq. Dmatdef."""
+    """F_c = D gamma (N x 6, torques zero), eq. Dmatdef; a wall contact
+    (first index negative) acts on its sphere only."""
     FT = np.zeros((N, 6))
     for l, (i, j) in enumerate(ij):
-        FT[i, :3] -= gamma[l] * nrm[l]
+        if i >= 0:
+            FT[i, :3] -= gamma[l] * nrm[l]
         FT[j, :3] += gamma[l] * nrm[l]
     return FT
 
 
 def DT_apply(ij, nrm, UO):
-    """(D^T U)_l = n_l . (U_j - U_i), eq. Dtranspose."""
-    return np.array([nrm[l] @ (UO[j, :3] - UO[i, :3]) for l, (i, j) in enumerate(ij)])
+    """(D^T U)_l = n_l . (U_j - U_i), eq. Dtranspose (a wall does not move)."""
+    return np.array([nrm[l] @ (UO[j, :3] - (UO[i, :3] if i >= 0 else 0.0))
+                     for l, (i, j) in enumerate(ij)])
 
 
 def minmap(gamma, g):
@@ -175,21 +209,29 @@ def lcp_enumerate(Mmat, q):
     return best
 
 
+def _all_contacts(centers, radii, delta, a_c_scale, delta_rel, walls):
+    ij, phi, nrm = build_contacts(centers, radii, delta, a_c_scale, delta_rel)
+    if walls is None or len(walls) == 0:
+        return ij, phi, nrm
+    wij, wphi, wn = build_wall_contacts(centers, radii, walls, delta, a_c_scale, delta_rel)
+    return np.concatenate([ij, wij]), np.concatenate([phi, wphi]), np.concatenate([nrm, wn])
+
+
 def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
                        a_c_scale=1.0, gmres_tol=1e-12, gmres_max=200,
                        bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
-                       delta_rel=0.0, rotations=None, keep_best=False):
+                       delta_rel=0.0, rotations=None, keep_best=False, walls=None):
     """One collision-resolved Euler step (Sec. 3.2, four-step procedure).
 
     1. U_nc = M F_ext; 2. contacts and D; 3. BBPGD for gamma with
     M gamma = D^T M D gamma; 4. U = U_nc + M D gamma, c += U dt.
     keep_best: the failure rule of bbpgd; U then uses M D gamma of the
-    iterate returned.  Returns dict with gamma, ij, phi, normals, U (N x 6),
-    centers_new, info.
+    iterate returned.  walls: optional W x 4 planes (see build_wall_contacts).
+    Returns dict with gamma, ij, phi, normals, U (N x 6), centers_new, info.
     """
     sus = Suspension(centers, radii, p, beta, rotations)
     U_nc, inf0 = mobility.mobility_apply(sus, FT_ext, gmres_tol, gmres_max, return_info=True)
-    ij, phi0, nrm = build_contacts(centers, radii, delta, a_c_scale, delta_rel)
+    ij, phi0, nrm = _all_contacts(centers, radii, delta, a_c_scale, delta_rel, walls)
     q = phi0 / dt + DT_apply(ij, nrm, U_nc)
     state = {"U_c": np.zeros_like(U_nc), "solves": 1, "gmres": inf0["gmres_iters"]}
 
@@ -241,7 +283,9 @@ def contacts_of_sphere(centers, radii, i, delta, a_c_scale=1.0, delta_rel=0.0):
 
 
 def D_apply_vec(N, ij, nrm, gamma):
-    """D gamma of eq. Dmatdef for large contact sets (unbuffered scatter-add)."""
+    """D gamma of eq. Dmatdef for large contact sets (unbuffered scatter-add);
+    sphere pairs only (no wall contacts)."""
+    assert np.all(np.asarray(ij)[:, 0] >= 0)
     FT = np.zeros((N, 6))
     f = np.asarray(gamma, dtype=np.float64)[:, None] * np.asarray(nrm, dtype=np.float64)
     for c in range(3):
@@ -251,14 +295,15 @@ def D_apply_vec(N, ij, nrm, gamma):
 
 
 def DT_apply_vec(ij, nrm, UO):
-    """D^T U of eq. Dtranspose for large contact sets."""
+    """D^T U of eq. Dtranspose for large contact sets (sphere pairs only)."""
+    assert np.all(np.asarray(ij)[:, 0] >= 0)
     dU = UO[ij[:, 1], :3] - UO[ij[:, 0], :3]
     return np.einsum("lc,lc->l", nrm, dU)
 
 
 def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_scale=1.0,
                                 bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
-                                delta_rel=0.0):
+                                delta_rel=0.0, walls=None):
     """The collision step of Sec. 3.2 with the mobility replaced by the
     identity (U = F, Omega = T).  No fluid: M = D^T D is the constraint Gram
     matrix, which isolates contacts, D products and Algorithm 1 at sizes where
@@ -266,7 +311,7 @@ def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_sc
     C = np.asarray(centers, dtype=np.float64)
     FT_ext = np.asarray(FT_ext, dtype=np.float64).reshape(-1, 6)
     N = len(C)
-    ij, phi0, nrm = build_contacts(C, radii, delta, a_c_scale, delta_rel)
+    ij, phi0, nrm = _all_contacts(C, radii, delta, a_c_scale, delta_rel, walls)
     U_nc = FT_ext.copy()
     q = phi0 / dt + DT_apply(ij, nrm, U_nc)
     state = {"U_c": np.zeros_like(U_nc)}

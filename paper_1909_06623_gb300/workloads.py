@@ -125,15 +125,16 @@ def place_close_pairs(rng, C, R, n_pairs, gap_lo, gap_hi, min_gap, L=None,
     return C, pairs
 
 
-def compress(C, R, phi_from, phi_to, gap, sweeps=400):
+def compress(C, R, phi_from, phi_to, gap, sweeps=400, dim=3):
     """Scale the packing about its centre in 40 steps and, after each, push
     overlapping pairs apart (all pairs of a sweep at once) until every gap
-    exceeds gap."""
+    exceeds gap.  dim = 2: phi is an area fraction and the points stay in
+    their plane (z = const)."""
     from scipy.spatial import cKDTree
     C = C.copy()
     mid = C.mean(axis=0)
     steps = 40
-    f = ((phi_from / phi_to) ** (1.0 / 3.0)) ** (1.0 / steps)
+    f = ((phi_from / phi_to) ** (1.0 / dim)) ** (1.0 / steps)
     reach = 2.0 * R.max() + gap
     for _ in range(steps):
         C = mid + (C - mid) * f
@@ -365,3 +366,75 @@ def random_rotations(seed, N):
         np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
         np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
         np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+
+
+def _lognormal_radii(rng, N, mean=1.0, sd=0.3):
+    """Radii with a log-normal law of the given mean and standard deviation
+    (Sec. 7.1 prints the law's parameters as mu = a, sigma = 0.3 a; read here
+    as the radius distribution's mean and standard deviation)."""
+    s2 = np.log(1.0 + (sd / mean) ** 2)
+    return rng.lognormal(np.log(mean) - 0.5 * s2, np.sqrt(s2), N)
+
+
+def rotor_cluster(seed=SEED_BASE + 7, N=10000, phi=0.10, a_c_scale=1.1, p=6, steps=10):
+    """Sec. 7.1: a spherical cluster of N polydisperse rotors (log-normal radii,
+    mean 1, sd 0.3) at volume fraction phi in unbounded fluid, the same torque
+    T = (0, 0, 1) on every sphere and no force, collision radius 1.1 a,
+    dt = 1.0 eta a^3 / T, eps_tol = 1e-5, p = 6, contact threshold 30% of the
+    sum of the radii.  Centres by random sequential addition in a ball at
+    the collision radius with no gap (collision-free start)."""
+    rng = np.random.default_rng(seed)
+    R = _lognormal_radii(rng, N)
+    Rc = a_c_scale * R
+    Rb = (np.sum(R ** 3) / phi) ** (1.0 / 3.0)
+    order = np.argsort(-R, kind="stable")
+    C = np.full((N, 3), np.nan)
+    grid = _Grid(2.0 * Rc.max())
+    for k in order:
+        for _ in range(200000):
+            v = rng.standard_normal(3)
+            c = v / np.linalg.norm(v) * (Rb - R[k]) * rng.random() ** (1.0 / 3.0)
+            if _fits(k, c, Rc[k], C, Rc, grid, 0.0):
+                C[k] = c
+                grid.add(k, c)
+                break
+        else:
+            raise RuntimeError("random sequential addition jammed")
+    FT = np.zeros((N, 6))
+    FT[:, 5] = 1.0
+    return Workload(f"rotor_cluster_N{N}_phi{phi:.2f}", C, R, FT, p=p, dt=1.0, steps=steps,
+                    params=dict(delta=0.0, delta_rel=0.3, a_c_scale=a_c_scale, bbpgd_tol=1e-5))
+
+
+def rotor_monolayer(seed=SEED_BASE + 8, N=20000, area=0.60, a_c_scale=1.1, p=6, steps=10):
+    """Sec. 7.2: a disk of N monodisperse rotors (a = 1) confined to the plane
+    z = 0 at area fraction 0.60 (about 0.73 at the collision radius 1.1 a),
+    torque T = (0, 0, 1) perpendicular to the disk, dt = 0.5 eta a^3 / T,
+    eps_tol = 1e-5, p = 6, contact threshold 30% of the sum of the radii.
+    Random sequential addition in a disk at area fraction 0.45 of the
+    collision disks, then in-plane compression at the collision radius with
+    no gap (no overlap at a_c; many pairs touch)."""
+    rng = np.random.default_rng(seed)
+    R = np.ones(N)
+    ac = a_c_scale
+    Rd0 = ac * np.sqrt(N / 0.45)
+    C = np.full((N, 3), np.nan)
+    grid = _Grid(2.0 * ac)
+    Rcs = np.full(N, ac)
+    for k in range(N):
+        for _ in range(200000):
+            r = (Rd0 - ac) * np.sqrt(rng.random())
+            t = 2 * pi * rng.random()
+            c = np.array([r * np.cos(t), r * np.sin(t), 0.0])
+            if _fits(k, c, ac, C, Rcs, grid, 0.0):
+                C[k] = c
+                grid.add(k, c)
+                break
+        else:
+            raise RuntimeError("random sequential addition jammed")
+    C = compress(C, Rcs, 0.45, area * ac * ac, 0.0, sweeps=4000, dim=2)
+    C[:, 2] = 0.0
+    FT = np.zeros((N, 6))
+    FT[:, 5] = 1.0
+    return Workload(f"rotor_monolayer_N{N}_area{area:.2f}", C, R, FT, p=p, dt=0.5, steps=steps,
+                    params=dict(delta=0.0, delta_rel=0.3, a_c_scale=a_c_scale, bbpgd_tol=1e-5))

@@ -157,6 +157,23 @@ def rotated():
     print("rotated", r["info"])
 
 
+def walls():
+    """The five-sphere active step (p = 4) pressed onto a floor z = -1.1 by an
+    extra downward force (Sec. 3.3.3 particle-wall constraints), and a
+    corner of a floor and a side wall with the identity mobility."""
+    d = np.load(os.path.join(HERE, "active_step_p4.npz"))
+    W = np.array([[0.0, 0.0, 1.0, -1.1]])
+    FT = d["FT"].copy()
+    FT[:, 2] -= 30.0
+    r = lcp.resolve_collisions(d["centers"], d["radii"], FT, float(d["dt"]), int(d["p"]), delta=0.1,
+                               a_c_scale=1.05, gmres_tol=1e-13, bbpgd_tol=1e-12, walls=W)
+    out = dict(walls=W, FT=FT, ij=r["ij"], phi=r["phi"], normals=r["normals"], gamma=r["gamma"],
+               U=r["U"], centers_new=r["centers_new"], n_active=r["info"]["n_active"],
+               bbpgd_iters=r["info"]["iters"])
+    print("walls", r["info"], r["ij"].tolist(), r["gamma"])
+    np.savez_compressed(os.path.join(HERE, "walls_p4.npz"), **out)
+
+
 def collision_grad():
     """The five-sphere active step (p = 4): the assembled mobility, the step's
     contacts and gamma, and central differences (h = 1e-5 max|F|) of
@@ -228,7 +245,7 @@ def sed_steps():
                         n_active=np.array(active))
 
 
-ALL = {"cfg1": cfg1, "active": active, "capped": capped, "rotated": rotated, "cfg2": cfg2_sample, "tiny": tiny_layers,
+ALL = {"cfg1": cfg1, "active": active, "capped": capped, "rotated": rotated, "walls": walls, "cfg2": cfg2_sample, "tiny": tiny_layers,
        "collision_grad": collision_grad, "collision_grad_c": collision_grad_c,
        "sed_steps": sed_steps}
 

@@ -301,3 +301,74 @@ def test_dense_packings_touch_at_the_collision_radius():
     assert phi.min() >= 0.0
     assert np.sum(phi < 1e-6) > 0.2 * len(w.radii)
     assert 1.0 < len(phi) / len(w.radii) < 4.0
+
+
+# ---------------------------------------------------------------------------
+# particle-wall constraints (Sec. 3.3.3): columns of D on one particle only
+# ---------------------------------------------------------------------------
+WALLS = np.array([[0.0, 0.0, 1.0, 0.0],      # floor z = 0, fluid above
+                  [-1.0, 0.0, 0.0, -10.0]])  # side wall x = 10, fluid at x < 10
+
+
+def test_wall_contacts_hand_example():
+    c = np.array([[0.0, 0.0, 1.05], [3.0, 0.0, 1.2], [8.95, 4.0, 5.0], [8.9, 8.0, 1.02]])
+    a = np.ones(4)
+    ij, phi, nrm = lcp.build_wall_contacts(c, a, WALLS, 0.1)
+    assert ij.tolist() == [[-1, 0], [-2, 2], [-1, 3], [-2, 3]]
+    assert np.allclose(phi, [0.05, 0.05, 0.02, 0.1], atol=1e-14)
+    assert np.array_equal(nrm, WALLS[[0, 1, 0, 1], :3])
+    # D and D^T with a wall column: +gamma n on the sphere alone, n . U_i
+    gam = np.array([1.0, 2.0, 3.0, 4.0])
+    FT = lcp.D_apply(4, ij, nrm, gam)
+    assert np.allclose(FT[:, :3], [[0, 0, 1], [0, 0, 0], [-2, 0, 0], [-4, 0, 3]])
+    U = np.arange(24, dtype=float).reshape(4, 6)
+    assert np.allclose(lcp.DT_apply(ij, nrm, U), [2.0, -12.0, 20.0, -18.0])
+    # adjointness <D g, U> = <g, D^T U>
+    assert abs(np.sum(FT[:, :3] * U[:, :3]) - gam @ lcp.DT_apply(ij, nrm, U)) < 1e-12
+
+
+def test_sphere_onto_wall_lands_on_contact():
+    """One sphere pushed into the floor: the LCP is scalar, gamma =
+    -(Phi/dt + n.U_nc) / (n.M n), and the step ends exactly on contact.
+    Identity mobility (n.M n = 1) and the boundary-integral mobility of one
+    sphere (exact drag: n.M n = 1/(6 pi a))."""
+    dt, f = 1e-2, 40.0
+    c = np.array([[0.3, -0.2, 1.0 * 1.05 + 0.07]])
+    a = np.array([1.0])
+    FT = np.array([[0.5, 0.0, -f, 0.0, 0.0, 0.0]])
+    out = lcp.resolve_collisions_identity(c, a, FT, dt, delta=0.1, a_c_scale=1.05, walls=WALLS[:1],
+                                          bbpgd_tol=1e-13)
+    assert abs(out["gamma"][0] - (f - 0.07 / dt)) < 1e-10
+    assert abs(out["centers_new"][0, 2] - 1.05) < 1e-12
+    f = 400.0                       # the fluid slows the sphere: f / (6 pi) > Phi / dt
+    FT[0, 2] = -f
+    out = lcp.resolve_collisions(c, a, FT, dt, 4, delta=0.1, a_c_scale=1.05, walls=WALLS[:1],
+                                 gmres_tol=1e-13, bbpgd_tol=1e-12)
+    U_nc = out["U_nc"][0, 2]
+    assert abs(U_nc + f / (6 * np.pi)) < 1e-12
+    assert abs(out["gamma"][0] - (-(0.07 / dt + U_nc) * 6 * np.pi)) < 1e-9
+    assert abs(out["centers_new"][0, 2] - 1.05) < 1e-12
+    assert abs(out["centers_new"][0, 0] - (0.3 + 0.5 / (6 * np.pi) * dt)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_identity_step_with_walls_matches_enumeration(seed):
+    """Spheres pressed into a corner (floor and side wall) and into each
+    other: Algorithm 1 on pair and wall constraints together equals the
+    enumerated LCP solution with the assembled M = D^T D."""
+    rng = np.random.default_rng(seed)
+    c = np.array([[8.85, 0.0, 1.02], [6.75, 0.1, 1.0], [8.9, 2.1, 1.1], [7.8, 1.0, 2.9]])
+    c = c + 0.01 * rng.standard_normal(c.shape)
+    a = np.ones(4)
+    FT = np.zeros((4, 6))
+    FT[:, :3] = 30.0 * np.array([1.0, 0.2, -1.0]) + 5.0 * rng.standard_normal((4, 3))
+    dt = 1e-2
+    out = lcp.resolve_collisions_identity(c, a, FT, dt, delta=0.2, walls=WALLS, bbpgd_tol=1e-12)
+    ij, nrm, q = out["ij"], out["normals"], out["q"]
+    assert (ij[:, 0] < 0).sum() >= 3 and (ij[:, 0] >= 0).sum() >= 2
+    nc = len(q)
+    Dm = np.stack([lcp.D_apply(4, ij, nrm, np.eye(nc)[l])[:, :3].ravel() for l in range(nc)], axis=1)
+    M = Dm.T @ Dm
+    ref = lcp.lcp_enumerate(M, q)
+    assert np.abs(out["gamma"] - ref).max() < 1e-9 * max(1.0, np.abs(ref).max())
+    assert (out["gamma"] > 0).sum() >= 2
