@@ -126,6 +126,10 @@ def workload(name):
         return workloads.config5(int(N), int(p))
     if name == "sed":
         return workloads.sedimenting_cluster()
+    if name.startswith("rotor_mono"):        # rotor_mono_<N>: monolayer disk (Sec. 7.2)
+        return workloads.rotor_monolayer(N=int(name.split("_")[-1]))
+    if name.startswith("rotor"):             # rotor_<N>: spherical rotor cluster (Sec. 7.1)
+        return workloads.rotor_cluster(N=int(name.split("_")[-1]))
     raise ValueError(name)
 
 
@@ -262,10 +266,11 @@ def run_gpu(args, w):
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     prm = ctx_params(args.precision, args.bb_warm, args.bbpgd_tol)
-    if w.name.startswith("sed"):
-        # the sedimenting cluster of Sec. 6.3 with the paper's own settings:
-        # threshold 30% of the sum of the radii, eps_tol = 1e-4
-        prm.update({k: w.params[k] for k in ("delta", "delta_rel", "bbpgd_tol")})
+    if w.name.startswith("sed") or w.name.startswith("rotor"):
+        # the paper's own settings for its Sec. 6.3 / 7 workloads: threshold
+        # 30% of the sum of the radii, eps_tol, collision radius
+        prm.update({k: w.params[k] for k in ("delta", "delta_rel", "bbpgd_tol", "a_c_scale")
+                    if k in w.params})
     if w.name.startswith("cfg3"):
         # 4,000 spheres at volume fraction 0.40: every mobility solve refined
         # to an FP64-accurate relative residual of 1e-10, eps_tol = 1e-8

@@ -214,8 +214,24 @@ int sps_layer_apply(sps_ctx* ctx, int op, const double* sigma, double* out);
 int sps_build_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii,
                        int* n_contacts);
 
+/* Planar walls (Sec. 3.3.3: a particle-boundary collision adds a column of D
+ * on that particle only; the boundary does not enter the mobility).  walls:
+ * HOST array of n_walls rows (n_x, n_y, n_z, d), the plane n . x = d with unit
+ * normal n pointing into the fluid; 0 <= n_walls <= 8, n_walls = 0 removes
+ * them.  Sphere i and wall w are in the contact set when
+ * Phi = (n . c_i - d) - a_c,i <= delta + delta_rel a_i, with
+ * n . c = (n_x x + n_y y) + n_z z rounded after every operation; the column
+ * carries +n on sphere i, so D^T U = n . U_i.  Every later contact build of
+ * the context (sps_build_contacts, the collision steps, both mobilities)
+ * includes them; sps_collision_adjoint returns INVALID_ARG while walls are
+ * set, and sps_build_contacts_noalloc ignores them.  Errors: INVALID_ARG
+ * (count, normal not unit to 1e-12), NONFINITE. */
+int sps_set_walls(sps_ctx* ctx, int n_walls, const double* walls);
+
 /* Copies the contact list out: ij (n_c x 2 int32), phi (n_c), normals
- * (n_c x 3); device pointers, any may be NULL. */
+ * (n_c x 3); device pointers, any may be NULL.  With walls (sps_set_walls)
+ * the sphere pairs come first, sorted by (i, j), then the wall contacts,
+ * sorted by (sphere, wall), as rows (-1 - w, i) with the wall's normal. */
 int sps_get_contacts(sps_ctx* ctx, int* ij, double* phi, double* normals);
 
 /* D gamma (eq. Dmatdef): FT (n x 6) = force -gamma n on sphere i and

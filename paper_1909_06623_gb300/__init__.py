@@ -124,6 +124,16 @@ class Context:
         Q = Q.reshape(-1, 9).contiguous()
         self._check(self.lib.sps_set_orientation(self.h, Q.shape[0], _ptr(Q)))
 
+    def set_walls(self, walls):
+        """Planar walls: rows (n_x, n_y, n_z, d) of the planes n . x = d, unit
+        normals into the fluid (sps_set_walls); None or empty removes them."""
+        import numpy as np
+        if walls is None or len(walls) == 0:
+            self._check(self.lib.sps_set_walls(self.h, 0, None))
+            return
+        w = np.ascontiguousarray(np.asarray(walls, dtype=np.float64).reshape(-1, 4))
+        self._check(self.lib.sps_set_walls(self.h, len(w), w.ctypes.data_as(ctypes.c_void_p)))
+
     def geometry_counts(self):
         """(directed near pairs, close near entries) of the current geometry."""
         a, b = ctypes.c_int(), ctypes.c_int()

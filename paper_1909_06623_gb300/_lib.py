@@ -59,6 +59,7 @@ SIGNATURES = {
     "sps_geometry_counts": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sps_near_lists": (_I, [_P, _P, _P]),
     "sps_set_orientation": (_I, [_P, _I, _P]),
+    "sps_set_walls": (_I, [_P, _I, _P]),
     "sps_layer_apply": (_I, [_P, _I, _P, _P]),
     "sps_build_contacts": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I)]),
     "sps_get_contacts": (_I, [_P, _P, _P, _P]),

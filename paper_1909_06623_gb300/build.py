@@ -25,7 +25,9 @@ def nvcc():
 
 def _compile(src, verbose):
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(SRC, src), "-o", obj]
+    # SPS_DEFINES: extra -D switches for tuning builds (e.g. "-DSPS_TC_NT=32")
+    extra = os.environ.get("SPS_DEFINES", "").split()
+    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(SRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -14,7 +14,6 @@
 // D and D^T: per sphere, its incident contacts in contact order (a stable sort
 // of the contact ends); per contact, n . (U_j - U_i).  All reductions use a
 // fixed partition and order, so every result is reproducible run to run.
-#include <cub/cub.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -69,7 +68,7 @@ __global__ void k_pairs_fill(int N, const double* pos, const double* rad, double
 // arithmetic of the contact test), and the contact ends for the incidence sort
 __global__ void k_contact_geom(int nc, const int* __restrict__ ij, const double* __restrict__ pos,
                                const double* __restrict__ rad, double acs, double* __restrict__ phi,
-                               double* __restrict__ nrm, int* __restrict__ keys, int* __restrict__ vals) {
+                               double* __restrict__ nrm) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nc) return;
   const int i = ij[2 * l], j = ij[2 * l + 1];
@@ -80,10 +79,6 @@ __global__ void k_contact_geom(int nc, const int* __restrict__ ij, const double*
   nrm[3 * l + 0] = g.nx;
   nrm[3 * l + 1] = g.ny;
   nrm[3 * l + 2] = g.nz;
-  keys[2 * l] = i;
-  vals[2 * l] = 2 * l;          // contact l, sphere is first (sign -1)
-  keys[2 * l + 1] = j;
-  vals[2 * l + 1] = 2 * l + 1;  // contact l, sphere is second (sign +1)
 }
 
 // ---------------------------------------------------------------------------
@@ -161,13 +156,6 @@ __global__ void k_cl_keys(int N, const double* __restrict__ pos, CellGrid G, int
 }
 
 // start[c] = first sorted position whose cell is >= c, for c = 0..ncells
-__global__ void k_cl_start(int N, int ncells, const int* __restrict__ key, int* __restrict__ start) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > N) return;
-  const int c0 = (k == 0) ? 0 : key[k - 1] + 1;
-  const int c1 = (k == N) ? ncells : key[k];
-  for (int c = c0; c <= c1; ++c) start[c] = k;
-}
 
 // sorted copies: FP32 (x, y, z relative to the grid origin, a), FP64 (x, y, z, a)
 __global__ void k_cl_gather(int N, const int* __restrict__ id, const double* __restrict__ pos,
@@ -281,6 +269,44 @@ __global__ void k_add_counts(int N, const int* a, const int* b, int* out) {
   if (i < N) out[i] = a[i] + b[i];
 }
 
+// wall contacts per sphere (entry n set to 0 for the scan), and their rows:
+// (-1 - w, i), Phi, the wall normal, sorted by (sphere, wall)
+__global__ void k_wall_count(int n, const double* __restrict__ pos, const double* __restrict__ rad, SpsWalls W,
+                             double acs, double delta, double drel, int* __restrict__ wcnt,
+                             int* __restrict__ inc_cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) {
+    wcnt[n] = 0;
+    return;
+  }
+  int c = 0;
+  double ph;
+  for (int w = 0; w < W.n; ++w)
+    if (sps_wall_test(W.w[w], pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], rad[i], acs, delta, drel, &ph)) ++c;
+  wcnt[i] = c;
+  inc_cnt[i] += c;
+}
+
+__global__ void k_wall_fill(int n, const double* __restrict__ pos, const double* __restrict__ rad, SpsWalls W,
+                            double acs, double delta, double drel, const int* __restrict__ wptr, int base,
+                            int* __restrict__ ij, double* __restrict__ phi, double* __restrict__ nrm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = base + wptr[i];
+  double ph;
+  for (int w = 0; w < W.n; ++w)
+    if (sps_wall_test(W.w[w], pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], rad[i], acs, delta, drel, &ph)) {
+      ij[2 * o] = -1 - w;
+      ij[2 * o + 1] = i;
+      phi[o] = ph;
+      nrm[3 * o + 0] = W.w[w][0];
+      nrm[3 * o + 1] = W.w[w][1];
+      nrm[3 * o + 2] = W.w[w][2];
+      ++o;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // D and D^T
 // ---------------------------------------------------------------------------
@@ -321,7 +347,8 @@ __global__ void k_DT(int nc, const int* __restrict__ ij, const double* __restric
   if (l >= nc) return;
   const int i = ij[2 * l], j = ij[2 * l + 1];
   double acc = 0.0;
-  for (int c = 0; c < 3; ++c) acc += nrm[3 * l + c] * (UO[6 * j + c] - UO[6 * i + c]);
+  // a wall (first index negative) does not move
+  for (int c = 0; c < 3; ++c) acc += nrm[3 * l + c] * (UO[6 * j + c] - (i >= 0 ? UO[6 * i + c] : 0.0));
   out[l] = acc;
 }
 
@@ -467,9 +494,15 @@ __global__ void __launch_bounds__(kThreads) k_bb_ident_DT(int nc, const int* __r
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nc; l += gridDim.x * blockDim.x) {
     const int i = ij[2 * l], j = ij[2 * l + 1];
     double acc = q[l];
-    acc = fma(nrm[3 * l], F3[3 * j] - F3[3 * i], acc);
-    acc = fma(nrm[3 * l + 1], F3[3 * j + 1] - F3[3 * i + 1], acc);
-    acc = fma(nrm[3 * l + 2], F3[3 * j + 2] - F3[3 * i + 2], acc);
+    double fi0 = 0.0, fi1 = 0.0, fi2 = 0.0;   // a wall (first index negative) does not move
+    if (i >= 0) {
+      fi0 = F3[3 * i];
+      fi1 = F3[3 * i + 1];
+      fi2 = F3[3 * i + 2];
+    }
+    acc = fma(nrm[3 * l], F3[3 * j] - fi0, acc);
+    acc = fma(nrm[3 * l + 1], F3[3 * j + 1] - fi1, acc);
+    acc = fma(nrm[3 * l + 2], F3[3 * j + 2] - fi2, acc);
     g_new[l] = acc;
     const double gn = gam_new[l];
     const double mn = min_bits(gn, acc), sv = gn - gam[l], yv = acc - g[l];
@@ -554,6 +587,133 @@ __global__ void k_count_pos(int n, const double* __restrict__ v, int* __restrict
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// ---------------------------------------------------------------------------
+// exclusive scan of n ints (out may alias in): block scans of 4,096 elements,
+// an exclusive scan of the block totals in one block, then the offsets added
+// ---------------------------------------------------------------------------
+constexpr int kScanT = 1024, kScanPer = 4, kScanTile = kScanT * kScanPer;
+
+__device__ __forceinline__ int block_exclusive(int x, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int v = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  const int ex = v - x + (warp ? wsum[warp - 1] : 0);
+  *total = wsum[31];
+  __syncthreads();
+  return ex;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_blocks(long long n, const int* in, int* out, int* tot) {
+  __shared__ int wsum[32];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+  int v[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  int total;
+  int run = block_exclusive(s, wsum, &total);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) tot[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_totals(int nb, int* tot) {
+  __shared__ int wsum[32];
+  const int per = (nb + kScanT - 1) / kScanT;
+  const int a = min(nb, (int)threadIdx.x * per), b = min(nb, a + per);
+  int s = 0;
+  for (int i = a; i < b; ++i) s += tot[i];
+  int total;
+  int run = block_exclusive(s, wsum, &total);
+  for (int i = a; i < b; ++i) {
+    const int v = tot[i];
+    tot[i] = run;
+    run += v;
+  }
+}
+
+__global__ void k_scan_add(long long n, int* out, const int* __restrict__ tot) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] += tot[i / kScanTile];
+}
+
+// ---------------------------------------------------------------------------
+// cell list by counting sort (the order inside a cell is free: every row of
+// the contact list is sorted by j afterwards)
+// ---------------------------------------------------------------------------
+__global__ void k_cell_hist(int N, const int* __restrict__ key, int* __restrict__ cnt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) atomicAdd(&cnt[key[k]], 1);
+}
+__global__ void k_cell_scatter(int N, const int* __restrict__ key, const int* __restrict__ id,
+                               const int* __restrict__ start, int* __restrict__ fill, int* __restrict__ key2,
+                               int* __restrict__ id2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int c = key[k];
+  const int o = start[c] + atomicAdd(&fill[c], 1);
+  key2[o] = c;
+  id2[o] = id[k];
+}
+
+// ---------------------------------------------------------------------------
+// incidence lists (each sphere's contact ends in contact order): sphere s
+// is the second body of pair contacts in rows i < s (they come first in
+// contact order), then the first body of its own row, then the second body
+// of its wall contacts.  Rows and wall blocks are placed directly; the
+// second-body ends arrive in any order and each sphere sorts them.
+// ---------------------------------------------------------------------------
+__global__ void k_inc_fill(int nc, int npair, const int* __restrict__ ij, const int* __restrict__ cptr,
+                           const int* __restrict__ ccount, const int* __restrict__ ccount2,
+                           const int* __restrict__ wptr, const int* __restrict__ inc_ptr,
+                           int* __restrict__ fill2, int* __restrict__ inc) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nc) return;
+  const int i = ij[2 * l], j = ij[2 * l + 1];
+  if (l < npair) {
+    inc[inc_ptr[i] + ccount2[i] + (l - cptr[i])] = 2 * l;
+    inc[inc_ptr[j] + atomicAdd(&fill2[j], 1)] = 2 * l + 1;
+  } else {
+    inc[inc_ptr[j] + ccount2[j] + ccount[j] + (l - npair - wptr[j])] = 2 * l + 1;
+  }
+}
+__global__ void k_inc_sort(int N, const int* __restrict__ inc_ptr, const int* __restrict__ ccount2,
+                           int* __restrict__ inc) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int* a = inc + inc_ptr[s];
+  const int m = ccount2[s];
+  for (int t = 1; t < m; ++t) {
+    const int v = a[t];
+    int u = t;
+    while (u > 0 && a[u - 1] > v) {
+      a[u] = a[u - 1];
+      --u;
+    }
+    a[u] = v;
+  }
+}
+
 int read_int(sps_ctx* ctx, const int* d, int* h) {
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -561,15 +721,22 @@ int read_int(sps_ctx* ctx, const int* d, int* h) {
   return SPS_OK;
 }
 
-int cub_scratch(sps_ctx* ctx, size_t bytes) {
-  if (bytes <= ctx->cub_bytes && ctx->d_cub) return SPS_OK;
-  size_t cap = 0;
-  char* p = static_cast<char*>(ctx->d_cub);
-  SPS_TRY(sps_grow(ctx, &p, cap, std::max<size_t>(bytes, 1 << 20)));
-  ctx->d_cub = p;
-  ctx->cub_bytes = cap;
+int exclusive_scan_impl(sps_ctx* ctx, const int* in, int* out, long long n) {
+  if (n <= 0) return SPS_OK;
+  const long long nb = (n + kScanTile - 1) / kScanTile;
+  SPS_TRY(sps_grow(ctx, &ctx->d_scan_tot, ctx->cap_scan_tot, (size_t)nb + 1));
+  k_scan_blocks<<<(int)nb, kScanT, 0, ctx->stream>>>(n, in, out, ctx->d_scan_tot);
+  SPS_LAUNCHED(ctx);
+  if (nb > 1) {
+    k_scan_totals<<<1, kScanT, 0, ctx->stream>>>((int)nb, ctx->d_scan_tot);
+    SPS_LAUNCHED(ctx);
+    k_scan_add<<<(int)std::min<long long>((n + 255) / 256, 8 * 152), 256, 0, ctx->stream>>>(n, out,
+                                                                                          ctx->d_scan_tot);
+    SPS_LAUNCHED(ctx);
+  }
   return SPS_OK;
 }
+
 
 // cell-list counts: cnt (as first sphere), cnt2 (as second) for n spheres
 int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, CellGrid* Gout,
@@ -650,17 +817,15 @@ int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, Cel
   }
   k_cl_keys<<<nblk(n), kThreads, 0, ctx->stream>>>(n, pos, G, ctx->d_cl_key, ctx->d_cl_id);
   SPS_LAUNCHED(ctx);
-  int bits = 1;
-  while ((1LL << bits) < (long long)ncells && bits < 31) ++bits;
-  size_t tmp = 0;
-  cub::DeviceRadixSort::SortPairs(nullptr, tmp, ctx->d_cl_key, ctx->d_cl_key2, ctx->d_cl_id,
-                                  ctx->d_cl_id2, n, 0, bits, ctx->stream);
-  SPS_TRY(cub_scratch(ctx, tmp));
-  tmp = ctx->cub_bytes;
-  SPS_CUDA(ctx, cub::DeviceRadixSort::SortPairs(ctx->d_cub, tmp, ctx->d_cl_key, ctx->d_cl_key2,
-                                                ctx->d_cl_id, ctx->d_cl_id2, n, 0, bits, ctx->stream));
-  ctx->launches += 4;
-  k_cl_start<<<nblk(n + 1), kThreads, 0, ctx->stream>>>(n, ncells, ctx->d_cl_key2, ctx->d_cl_range);
+  // counting sort by cell: histogram, exclusive scan (the per-cell ranges), scatter
+  SPS_TRY(sps_grow(ctx, &ctx->d_cl_fill, ctx->cap_cl_fill, (size_t)ncells + 1));
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_cl_fill, 0, sizeof(int) * ((size_t)ncells + 1), ctx->stream));
+  k_cell_hist<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key, ctx->d_cl_fill);
+  SPS_LAUNCHED(ctx);
+  SPS_TRY(exclusive_scan_impl(ctx, ctx->d_cl_fill, ctx->d_cl_range, (long long)ncells + 1));
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_cl_fill, 0, sizeof(int) * ((size_t)ncells + 1), ctx->stream));
+  k_cell_scatter<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key, ctx->d_cl_id, ctx->d_cl_range,
+                                                         ctx->d_cl_fill, ctx->d_cl_key2, ctx->d_cl_id2);
   SPS_LAUNCHED(ctx);
   k_cl_gather<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_id2, pos, radii, G, ctx->d_cl_f,
                                                       ctx->d_cl_d);
@@ -675,6 +840,10 @@ int cell_counts(sps_ctx* ctx, int n, const double* pos, const double* radii, Cel
 }
 
 }  // namespace
+
+int sps_exclusive_scan(sps_ctx* ctx, const int* in, int* out, long long n) {
+  return exclusive_scan_impl(ctx, in, out, n);
+}
 
 int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* radii) {
   SpsPhase timer(ctx, SPS_PH_CONTACT);
@@ -709,21 +878,25 @@ int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* ra
   k_add_counts<<<nblk(n + 1), kThreads, 0, ctx->stream>>>(n + 1, ctx->d_ccount, ctx->d_ccount2,
                                                           ctx->d_inc_cnt);
   SPS_LAUNCHED(ctx);
-  size_t tmp = 0;
-  cub::DeviceScan::ExclusiveSum(nullptr, tmp, ctx->d_ccount, ctx->d_cptr, n + 1, ctx->stream);
-  SPS_TRY(cub_scratch(ctx, tmp));
-  tmp = ctx->cub_bytes;
-  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(ctx->d_cub, tmp, ctx->d_ccount, ctx->d_cptr, n + 1,
-                                              ctx->stream));
-  tmp = ctx->cub_bytes;
-  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(ctx->d_cub, tmp, ctx->d_inc_cnt, ctx->d_inc_ptr, n + 1,
-                                              ctx->stream));
-  ctx->launches += 2;
-  int nc = 0;
-  SPS_TRY(read_int(ctx, ctx->d_cptr + n, &nc));
+  const bool walls = ctx->walls.n > 0;
+  if (walls) {
+    SPS_TRY(sps_grow(ctx, &ctx->d_wcount, ctx->cap_wcount, (size_t)n + 1));
+    SPS_TRY(sps_grow(ctx, &ctx->d_wptr, ctx->cap_wptr, (size_t)n + 1));
+    k_wall_count<<<nblk(n + 1), kThreads, 0, ctx->stream>>>(n, pos, radii, ctx->walls, acs, delta, drel,
+                                                            ctx->d_wcount, ctx->d_inc_cnt);
+    SPS_LAUNCHED(ctx);
+  }
+  SPS_TRY(sps_exclusive_scan(ctx, ctx->d_ccount, ctx->d_cptr, n + 1));
+  SPS_TRY(sps_exclusive_scan(ctx, ctx->d_inc_cnt, ctx->d_inc_ptr, n + 1));
+  if (walls) SPS_TRY(sps_exclusive_scan(ctx, ctx->d_wcount, ctx->d_wptr, n + 1));
+  int npair = 0, nwall = 0;
+  SPS_TRY(read_int(ctx, ctx->d_cptr + n, &npair));
+  if (walls) SPS_TRY(read_int(ctx, ctx->d_wptr + n, &nwall));
+  const int nc = npair + nwall;
   ctx->n_c = nc;
+  ctx->n_pair = npair;
   if (nc > ctx->cap_c) {
-    int** ip[] = {&ctx->d_cij, &ctx->d_inc, &ctx->d_keys, &ctx->d_vals, &ctx->d_keys2};
+    int** ip[] = {&ctx->d_cij, &ctx->d_inc};
     for (auto p : ip) {
       cudaFree(*p);
       *p = nullptr;
@@ -743,29 +916,38 @@ int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* ra
     ctx->cap_c = nc;
   }
   if (nc == 0) return SPS_OK;
-  if (cells) {
-    k_cl_fill<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key2, ctx->d_cl_id2, ctx->d_cl_f,
-                                                      ctx->d_cl_d, ctx->d_cl_range, G, acs, delta, drel,
-                                                      ctx->d_cptr, ctx->d_cij);
-  } else {
-    k_pairs_fill<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, drel, ctx->d_cptr,
-                                                        ctx->d_cij);
+  if (npair > 0) {
+    if (cells) {
+      k_cl_fill<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_cl_key2, ctx->d_cl_id2, ctx->d_cl_f,
+                                                        ctx->d_cl_d, ctx->d_cl_range, G, acs, delta, drel,
+                                                        ctx->d_cptr, ctx->d_cij);
+    } else {
+      k_pairs_fill<<<nblk(n, 128), 128, 0, ctx->stream>>>(n, pos, radii, acs, delta, drel, ctx->d_cptr,
+                                                          ctx->d_cij);
+    }
+    SPS_LAUNCHED(ctx);
+    k_contact_geom<<<nblk(npair), kThreads, 0, ctx->stream>>>(npair, ctx->d_cij, pos, radii, acs,
+                                                               ctx->d_cphi, ctx->d_cn);
+    SPS_LAUNCHED(ctx);
   }
+  if (nwall > 0) {
+    k_wall_fill<<<nblk(n), kThreads, 0, ctx->stream>>>(n, pos, radii, ctx->walls, acs, delta, drel, ctx->d_wptr,
+                                                       npair, ctx->d_cij, ctx->d_cphi, ctx->d_cn);
+    SPS_LAUNCHED(ctx);
+  }
+  // incidence lists: each sphere's contact ends in contact order (a
+  // deterministic transpose of the list)
+  if (!walls) {
+    SPS_TRY(sps_grow(ctx, &ctx->d_wptr, ctx->cap_wptr, (size_t)n + 1));   // read only for wall rows
+  }
+  SPS_TRY(sps_grow(ctx, &ctx->d_inc_fill, ctx->cap_inc_fill, (size_t)n + 1));
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_inc_fill, 0, sizeof(int) * ((size_t)n + 1), ctx->stream));
+  k_inc_fill<<<nblk(nc), kThreads, 0, ctx->stream>>>(nc, npair, ctx->d_cij, ctx->d_cptr, ctx->d_ccount,
+                                                      ctx->d_ccount2, ctx->d_wptr, ctx->d_inc_ptr,
+                                                      ctx->d_inc_fill, ctx->d_inc);
   SPS_LAUNCHED(ctx);
-  k_contact_geom<<<nblk(nc), kThreads, 0, ctx->stream>>>(nc, ctx->d_cij, pos, radii, acs, ctx->d_cphi,
-                                                          ctx->d_cn, ctx->d_keys, ctx->d_vals);
+  k_inc_sort<<<nblk(n), kThreads, 0, ctx->stream>>>(n, ctx->d_inc_ptr, ctx->d_ccount2, ctx->d_inc);
   SPS_LAUNCHED(ctx);
-  // a stable sort of (sphere, contact end) lists each sphere's incident
-  // contacts in contact order: a deterministic transpose of the list
-  int bits = 1;
-  while (bits < 31 && (1 << bits) < n) ++bits;
-  cub::DeviceRadixSort::SortPairs(nullptr, tmp, ctx->d_keys, ctx->d_keys2, ctx->d_vals, ctx->d_inc,
-                                  2 * nc, 0, bits, ctx->stream);
-  SPS_TRY(cub_scratch(ctx, tmp));
-  tmp = ctx->cub_bytes;
-  SPS_CUDA(ctx, cub::DeviceRadixSort::SortPairs(ctx->d_cub, tmp, ctx->d_keys, ctx->d_keys2, ctx->d_vals,
-                                                ctx->d_inc, 2 * nc, 0, bits, ctx->stream));
-  ctx->launches += 4;
   return SPS_OK;
 }
 

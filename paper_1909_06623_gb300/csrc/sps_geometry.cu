@@ -2,7 +2,6 @@
 // rho from force/torque, the local operator L and velocity extraction
 // (Sec. 4.1), and the contact builder that keeps its scratch in a static
 // device array.  The contact search and D products are in sps_contacts.cu.
-#include <cub/cub.cuh>
 
 #include <mutex>
 
@@ -268,18 +267,12 @@ int sps_launch_near_lists(sps_ctx* ctx) {
   k_near_count<<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_pos, ctx->d_rad, ctx->prm.beta, d_cnt);
   SPS_LAUNCHED(ctx);
   // exclusive scan into near_ptr (N+1)
-  size_t tmp = 0;
-  cub::DeviceScan::ExclusiveSum(nullptr, tmp, d_cnt, ctx->d_near_ptr, N + 1, ctx->stream);
-  void* d_tmp = nullptr;
-  SPS_CUDA(ctx, cudaMalloc(&d_tmp, tmp ? tmp : 1));
   SPS_CUDA(ctx, cudaMemsetAsync(d_cnt + N, 0, sizeof(int), ctx->stream));
-  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(d_tmp, tmp, d_cnt, ctx->d_near_ptr, N + 1, ctx->stream));
-  ctx->launches++;
+  SPS_TRY(sps_exclusive_scan(ctx, d_cnt, ctx->d_near_ptr, N + 1));
   int total = 0;
   SPS_CUDA(ctx, cudaMemcpyAsync(&total, ctx->d_near_ptr + N, sizeof(int), cudaMemcpyDeviceToHost,
                                 ctx->stream));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  cudaFree(d_tmp);
   cudaFree(d_cnt);
   size_t capn = ctx->cap_near;
   SPS_TRY(sps_grow(ctx, &ctx->d_near_idx, capn, (size_t)total));
@@ -348,18 +341,12 @@ int sps_launch_close_lists(sps_ctx* ctx) {
                                                              ctx->d_X, ctx->d_near_ptr, ctx->d_near_idx,
                                                              d_cnt, d_flag);
   SPS_LAUNCHED(ctx);
-  size_t tmp = 0;
-  cub::DeviceScan::ExclusiveSum(nullptr, tmp, d_cnt, d_sptr, (int)(NP + 1), ctx->stream);
-  void* d_tmp = nullptr;
-  SPS_CUDA(ctx, cudaMalloc(&d_tmp, tmp ? tmp : 1));
-  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(d_tmp, tmp, d_cnt, d_sptr, (int)(NP + 1), ctx->stream));
-  SPS_CUDA(ctx, cub::DeviceScan::ExclusiveSum(d_tmp, tmp, d_flag, d_fpos, (int)(NP + 1), ctx->stream));
-  ctx->launches += 2;
+  SPS_TRY(sps_exclusive_scan(ctx, d_cnt, d_sptr, NP + 1));
+  SPS_TRY(sps_exclusive_scan(ctx, d_flag, d_fpos, NP + 1));
   int tot[2] = {0, 0};
   SPS_CUDA(ctx, cudaMemcpyAsync(&tot[0], d_fpos + NP, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA(ctx, cudaMemcpyAsync(&tot[1], d_sptr + NP, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  cudaFree(d_tmp);
   ctx->n_close = tot[0];
   ctx->n_close_src = tot[1];
   SPS_TRY(sps_grow(ctx, &ctx->d_close_node, ctx->cap_close_node, (size_t)tot[0] + 1));

@@ -50,8 +50,17 @@ struct DevBuf {
 
 }  // namespace sps
 
+// Planar walls (Sec. 3.3.3 particle-boundary constraints): plane n.x = d with
+// a unit normal n pointing into the fluid, row (n_x, n_y, n_z, d)
+constexpr int kMaxWalls = 8;
+struct SpsWalls {
+  int n = 0;
+  double w[kMaxWalls][4] = {};
+};
+
 struct sps_ctx {
   sps_params prm;
+  SpsWalls walls;
   // phase timers
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -163,6 +172,15 @@ struct sps_ctx {
 
   // contacts
   int n_c = 0, cap_c = 0, c_N = 0;   // contacts, capacity, spheres they refer to
+  int n_pair = 0;                // sphere-pair contacts (the first n_pair); the rest are wall contacts
+  int prev_npair = 0;            // the same count of the previous step's list (bb_warm)
+  int *d_wcount = nullptr;       // N+1: wall contacts per sphere, then their offsets
+  int *d_wptr = nullptr;
+  size_t cap_wcount = 0, cap_wptr = 0;
+  int *d_inc_fill = nullptr;     // N+1 fill counters of the incidence transpose
+  int *d_cl_fill = nullptr;      // cells + 1 fill counters of the cell counting sort
+  int *d_scan_tot = nullptr;     // block totals of sps_exclusive_scan
+  size_t cap_inc_fill = 0, cap_cl_fill = 0, cap_scan_tot = 0;
   int *d_cij = nullptr;          // n_c x 2
   double *d_cphi = nullptr, *d_cn = nullptr;
   int *d_ccount = nullptr, *d_cptr = nullptr;  // N+1
@@ -289,6 +307,17 @@ __device__ __forceinline__ double sps_close_r2(const double* pos, double ia, dou
 struct SpsContactGeom {
   double phi, nx, ny, nz;
 };
+
+// Wall contact test on loaded values: Phi = (n . c - d) - a acs with
+// n . c = (n_x x + n_y y) + n_z z, threshold delta + drel a, every operation
+// rounded separately (the same list to the bit wherever it is evaluated)
+__device__ __forceinline__ bool sps_wall_test(const double* wl, double x, double y, double z, double a,
+                                              double acs, double delta, double drel, double* phi) {
+  const double h = __dadd_rn(__dadd_rn(__dmul_rn(wl[0], x), __dmul_rn(wl[1], y)), __dmul_rn(wl[2], z));
+  const double ph = __dsub_rn(__dsub_rn(h, wl[3]), __dmul_rn(a, acs));
+  *phi = ph;
+  return ph <= __dadd_rn(delta, __dmul_rn(drel, a));
+}
 __device__ __forceinline__ bool sps_contact_test(double xi, double yi, double zi, double ai, double xj,
                                                  double yj, double zj, double aj, double acs,
                                                  double delta, double drel, SpsContactGeom* g) {
@@ -331,6 +360,8 @@ int sps_launch_contacts(sps_ctx* ctx, int n, const double* pos, const double* ra
 // contacts, D products, identity-mobility BBPGD pieces (sps_contacts.cu)
 int sps_check_inputs(sps_ctx* ctx, int n, const double* pos, const double* radii, const double* FT);
 int sps_count_positive(sps_ctx* ctx, const double* v, int n, int* out);
+// exclusive prefix sum of n ints on the context's stream (out may alias in)
+int sps_exclusive_scan(sps_ctx* ctx, const int* in, int* out, long long n);
 // the five BBPGD statistics land in sps_bb_out(ctx) (device, 5 doubles)
 int sps_bb_stats_dev(sps_ctx* ctx, const double* gn, const double* ggn, const double* go,
                      const double* ggo);

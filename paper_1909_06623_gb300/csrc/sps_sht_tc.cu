@@ -43,7 +43,11 @@ constexpr int kM = 128;                    // spheres per CTA (MMA M)
 #define SPS_TC_KC 32
 #endif
 constexpr int kKC = SPS_TC_KC;             // K chunk (one FP32 accumulation in tensor memory)
-constexpr int kNT = 64;                    // N tile: one CTA per (128 spheres, 64 matrix rows)
+#ifndef SPS_TC_NT
+#define SPS_TC_NT 16
+#endif
+constexpr int kNT = SPS_TC_NT;             // N tile: one CTA per (128 spheres, kNT matrix rows)
+static_assert(kNT == 16 || kNT == 32 || kNT == 64, "N tile of 16, 32 or 64 rows");
 constexpr int kSBO = (kKC / 8) * 128;      // bytes between 8-row groups
 constexpr int kABytes = kM * kKC * 2;      // one split of the A chunk
 constexpr int kBBytes = kNT * kKC * 2;     // one split of the B chunk

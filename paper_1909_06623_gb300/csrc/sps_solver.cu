@@ -123,19 +123,27 @@ __global__ void k_add(int n, const double* __restrict__ a, const double* __restr
 // gamma_0 for a new contact list from the previous step's solution: the
 // value of the same pair (i, j) if it was a contact then, else 0 (both lists
 // sorted by (i, j); binary search)
-__global__ void k_map_gamma(int nc, const int* __restrict__ ij, int nprev, const int* __restrict__ pij,
-                            const double* __restrict__ pgam, double* __restrict__ gam) {
+// gamma_0 from the previous step's list: sphere pairs are sorted by (i, j),
+// wall contacts (first index -1 - w) after them by (sphere, wall); each block
+// is searched on its own order
+__global__ void k_map_gamma(int nc, const int* __restrict__ ij, int npair, int nprev, int nprev_pair,
+                            const int* __restrict__ pij, const double* __restrict__ pgam,
+                            double* __restrict__ gam) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nc) return;
   const int i = ij[2 * l], j = ij[2 * l + 1];
-  int lo = 0, hi = nprev;
+  const bool wall = l >= npair;
+  // key (a, b): (i, j) for pairs, (sphere, wall) for walls
+  const int a = wall ? j : i, b = wall ? -1 - i : j;
+  int lo = wall ? nprev_pair : 0, hi = wall ? nprev : nprev_pair;
+  const int end = hi;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    const int pi = pij[2 * mid], pj = pij[2 * mid + 1];
-    if (pi < i || (pi == i && pj < j)) lo = mid + 1;
+    const int pa = wall ? pij[2 * mid + 1] : pij[2 * mid], pb = wall ? -1 - pij[2 * mid] : pij[2 * mid + 1];
+    if (pa < a || (pa == a && pb < b)) lo = mid + 1;
     else hi = mid;
   }
-  gam[l] = (lo < nprev && pij[2 * lo] == i && pij[2 * lo + 1] == j) ? pgam[lo] : 0.0;
+  gam[l] = (lo < end && pij[2 * lo] == i && pij[2 * lo + 1] == j) ? pgam[lo] : 0.0;
 }
 
 // q = phi/dt + D^T U_nc (D^T U_nc already in q)
@@ -565,7 +573,8 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_adj6a, ctx->d_adj6b, ctx->d_adjc, ctx->d_gam_best, ctx->d_aux_best,
                   ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw, ctx->d_prev_ij, ctx->d_prev_gam,
                   ctx->d_dwsrc, ctx->d_rot, ctx->d_sigloc, ctx->d_tcsplit, ctx->d_near_rev,
-                  ctx->d_near_geo, ctx->d_near_buf};
+                  ctx->d_near_geo, ctx->d_near_buf, ctx->d_wcount, ctx->d_wptr, ctx->d_inc_fill,
+                  ctx->d_cl_fill, ctx->d_scan_tot};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -626,6 +635,25 @@ extern "C" int sps_set_orientation(sps_ctx* ctx, int n, const double* Q) {
   SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_rot, Q, sizeof(double) * 9 * n, cudaMemcpyDeviceToDevice, ctx->stream));
   SPS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->rot_n = n;
+  return SPS_OK;
+}
+
+extern "C" int sps_set_walls(sps_ctx* ctx, int n_walls, const double* walls) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (n_walls < 0 || n_walls > kMaxWalls || (n_walls > 0 && !walls))
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "set_walls: 0 to 8 walls");
+  SpsWalls W;
+  W.n = n_walls;
+  for (int w = 0; w < n_walls; ++w) {
+    const double* r = walls + 4 * w;
+    for (int k = 0; k < 4; ++k)
+      if (!std::isfinite(r[k])) return sps_fail(ctx, SPS_ERR_NONFINITE, "set_walls: not finite");
+    const double nn = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    if (std::fabs(nn - 1.0) > 1e-12) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "set_walls: normal not unit");
+    for (int k = 0; k < 4; ++k) W.w[w][k] = r[k];
+  }
+  ctx->walls = W;
+  ctx->prev_nc = 0;     // the previous list's wall rows refer to the old walls
   return SPS_OK;
 }
 
@@ -1281,7 +1309,8 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
     bool warm0 = false;
     if (ctx->prm.bb_warm && ctx->prev_nc > 0 && ctx->prev_N == n) {
       { SpsPhase timer_(ctx, SPS_PH_BBPGD);
-      k_map_gamma<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_cij, ctx->prev_nc, ctx->d_prev_ij,
+      k_map_gamma<<<tb, 256, 0, ctx->stream>>>(nc, ctx->d_cij, ctx->n_pair, ctx->prev_nc, ctx->prev_npair,
+                                               ctx->d_prev_ij,
                                                ctx->d_prev_gam, ctx->d_gam); }
       SPS_LAUNCHED(ctx);
       int npos = 0;
@@ -1307,6 +1336,7 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
     SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_prev_gam, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice,
                                   ctx->stream));
     ctx->prev_nc = nc;
+    ctx->prev_npair = ctx->n_pair;
   }
   ctx->prev_N = n;
   SPS_TRY(finish_bb_stats(ctx, nc, r, st));
@@ -1555,6 +1585,8 @@ extern "C" int sps_collision_adjoint(sps_ctx* ctx, int n, const double* pos, con
   if (!ctx || n < 1 || !pos || !radii || !FT_ext || !dL_dU || !UO || !dL_dFT)
     return sps_fail(ctx, SPS_ERR_INVALID_ARG, "collision_adjoint: bad argument");
   SPS_TRY(no_orientation(ctx, "collision_adjoint"));
+  if (ctx->walls.n > 0)
+    return sps_fail(ctx, SPS_ERR_INVALID_ARG, "collision_adjoint: not available with walls");
   long long l0;
   stats_begin(ctx, st, &l0);
   // forward step (positions are not advanced)
