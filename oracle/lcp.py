@@ -17,7 +17,16 @@ Paper: Yan et al., arXiv 1909.06623.
     so D^T U = n_l . (U_j - U_i) = dPhi/dt.
   * eq. lcp:LCPdef: M = D^T M D, q = Phi/dt + D^T U_nc.
   * Algorithm 1 (BBPGD) with the min-map residual of eq. mmapnorm and the BB1
-    step (BB2 optional).  Readings where the algorithm is silent: gamma_0 = 0,
+    step (BB2 optional; variant 3 alternates BB1 on odd and BB2 on even
+    steps, the alternation the paper mentions for Algorithm 1).
+  * APGD (Sec. 3.3.1 cites it as the comparison method, no listing): Nesterov's
+    accelerated projected gradient with an adaptive Lipschitz estimate
+    (Mazhar et al. 2015): the gradient at the extrapolated point y is formed
+    with its own product M y, the step 1/L is halved until the sufficient-
+    decrease test f(x) <= f(y) + g(y).(x - y) + L/2 |x - y|^2 holds, the momentum
+    restarts when g(x).(x - x_old) > 0, L shrinks by 0.9 after each accepted
+    step, L_0 from |M (e - 0)| / |e| for the vector of ones e, stop on the
+    min-map residual of eq. mmapnorm at the new iterate.  Readings where the algorithm is silent: gamma_0 = 0,
     whose product M gamma_0 = 0 needs no mobility solve; a non-positive s^T y
     (or y^T y for BB2) stops with status "breakdown", or, with safeguard=True,
     keeps the previous step length and continues (the discrete mobility is
@@ -183,8 +192,59 @@ def bbpgd(Mop, q, tol, jmax=10000, variant=1, safeguard=False, gamma0=None, keep
                 return stop("breakdown")
             info["safeguards"] += 1          # keep the previous step length
             continue
-        alpha = (s @ s) / sy if variant == 1 else sy / yy
+        bb1 = variant == 1 or (variant == 3 and j % 2 == 1)
+        alpha = (s @ s) / sy if bb1 else sy / yy
     return stop("not_converged")
+
+
+def apgd(Mop, q, tol, jmax=10000):
+    """APGD for the CQP of eq. CQPdef (see the module docstring).  Mop(x) ->
+    M x.  f(x) = x.M x / 2 + q.x.  Returns gamma, g, info (info["mvops"]
+    counts the evaluations of M, the expensive part)."""
+    q = np.asarray(q, dtype=np.float64)
+    n = len(q)
+    mv = 0
+    gam = np.zeros(n)
+    g0 = q.copy()                                   # M 0 + q
+    info = {"iters": 0, "mvops": 0, "status": "ok", "phi": minmap(gam, g0)}
+    if info["phi"] < tol:
+        return gam, g0, info
+    e = np.ones(n)
+    L = np.linalg.norm(Mop(e)) / np.linalg.norm(e)
+    mv += 1
+    t = 1.0 / L
+    y, theta = gam.copy(), 1.0
+    Mgam = np.zeros(n)
+    for k in range(1, jmax + 1):
+        My = Mop(y) if np.any(y) else np.zeros(n)   # the gradient at the extrapolated point
+        mv += int(np.any(y))
+        gy = My + q
+        for _ in range(200):                        # doubling L: bounded by the largest eigenvalue
+            x = np.maximum(y - t * gy, 0.0)
+            Mx = Mop(x)
+            mv += 1
+            d = x - y
+            # f(x) <= f(y) + g(y).d + L/2 |d|^2, written for the quadratic f as
+            # d.M d <= L |d|^2 (exact; free of the cancellation in f(x) - f(y))
+            if d @ (Mx - My) <= L * (d @ d):
+                break
+            L *= 2.0
+            t = 1.0 / L
+        gx = Mx + q
+        phi = minmap(x, gx)
+        info.update(iters=k, mvops=mv, phi=phi)
+        if phi < tol:
+            return x, gx, info
+        theta_new = 0.5 * (-theta * theta + theta * np.sqrt(theta * theta + 4.0))
+        beta = theta * (1.0 - theta) / (theta * theta + theta_new)
+        y_new = x + beta * (x - gam)
+        if gx @ (x - gam) > 0:                      # restart the momentum
+            y_new, theta_new = x.copy(), 1.0
+        gam, Mgam, y, theta = x, Mx, y_new, theta_new
+        L *= 0.9
+        t = 1.0 / L
+    info["status"] = "not_converged"
+    return gam, Mgam + q, info
 
 
 def lcp_enumerate(Mmat, q):
@@ -220,7 +280,8 @@ def _all_contacts(centers, radii, delta, a_c_scale, delta_rel, walls):
 def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
                        a_c_scale=1.0, gmres_tol=1e-12, gmres_max=200,
                        bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
-                       delta_rel=0.0, rotations=None, keep_best=False, walls=None):
+                       delta_rel=0.0, rotations=None, keep_best=False, walls=None,
+                       solver="bbpgd"):
     """One collision-resolved Euler step (Sec. 3.2, four-step procedure).
 
     1. U_nc = M F_ext; 2. contacts and D; 3. BBPGD for gamma with
@@ -245,8 +306,18 @@ def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
         return DT_apply(ij, nrm, UO)
 
     state["U_c_of"] = []
-    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard, keep_best=keep_best)
-    if info["iters"] == 0 or info["best"] == 0:
+    if solver == "apgd":
+        gamma, g, info = apgd(Mop, q, bbpgd_tol, bbpgd_max)
+        info["best"] = info["iters"]
+        # U_c of the returned iterate: one more solve (APGD's products mix
+        # iterates through the momentum)
+        U_c = (mobility.mobility_apply(sus, D_apply(sus.N, ij, nrm, gamma), gmres_tol, gmres_max)
+               if np.any(gamma) else np.zeros_like(U_nc))
+    else:
+        gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard, keep_best=keep_best)
+    if solver == "apgd":
+        pass
+    elif info["iters"] == 0 or info["best"] == 0:
         U_c = np.zeros_like(U_nc)       # gamma = gamma_0 = 0
     else:
         # the solve of the returned iterate: Mop's calls are M g_0, then one
@@ -303,7 +374,7 @@ def DT_apply_vec(ij, nrm, UO):
 
 def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_scale=1.0,
                                 bbpgd_tol=1e-10, bbpgd_max=10000, variant=1, safeguard=False,
-                                delta_rel=0.0, walls=None):
+                                delta_rel=0.0, walls=None, solver="bbpgd"):
     """The collision step of Sec. 3.2 with the mobility replaced by the
     identity (U = F, Omega = T).  No fluid: M = D^T D is the constraint Gram
     matrix, which isolates contacts, D products and Algorithm 1 at sizes where
@@ -320,8 +391,12 @@ def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_sc
         state["U_c"] = D_apply(N, ij, nrm, gam)
         return DT_apply(ij, nrm, state["U_c"])
 
-    gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard)
-    U_c = np.zeros_like(U_nc) if info["iters"] == 0 else state["U_c"]
+    if solver == "apgd":
+        gamma, g, info = apgd(Mop, q, bbpgd_tol, bbpgd_max)
+        U_c = D_apply(N, ij, nrm, gamma)
+    else:
+        gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard)
+        U_c = np.zeros_like(U_nc) if info["iters"] == 0 else state["U_c"]
     U = U_nc + U_c
     info.update(n_contacts=len(q), n_active=int(np.sum(gamma > 0)))
     return {"gamma": gamma, "g": g, "q": q, "ij": ij, "phi": phi0, "normals": nrm,

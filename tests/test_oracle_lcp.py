@@ -372,3 +372,40 @@ def test_identity_step_with_walls_matches_enumeration(seed):
     ref = lcp.lcp_enumerate(M, q)
     assert np.abs(out["gamma"] - ref).max() < 1e-9 * max(1.0, np.abs(ref).max())
     assert (out["gamma"] > 0).sum() >= 2
+
+
+# ---------------------------------------------------------------------------
+# comparison solvers (Sec. 3.3.1): APGD and the alternating BB step
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(4))
+def test_apgd_and_alternating_bb_match_enumeration(seed):
+    """APGD (Nesterov with an adaptive Lipschitz estimate) and Algorithm 1
+    with BB1/BB2 alternating reach the enumerated LCP solution of a random
+    SPD problem; APGD spends more products of M per iteration (its
+    sufficient-decrease checks), the reason the paper prefers BBPGD."""
+    rng = np.random.default_rng(100 + seed)
+    n = 6
+    A = rng.standard_normal((n, n))
+    M = A @ A.T + 0.5 * np.eye(n)
+    q = rng.standard_normal(n) * 3
+    ref = lcp.lcp_enumerate(M, q)
+    mop = lambda x: M @ x
+    ga, _, ia = lcp.apgd(mop, q, 1e-11, jmax=20000)
+    gb, _, ib = lcp.bbpgd(mop, q, 1e-11, jmax=20000, variant=3, safeguard=True)
+    for gam in (ga, gb):
+        assert np.abs(gam - ref).max() < 1e-9 * max(1.0, np.abs(ref).max())
+    assert ia["status"] == "ok" and ib["status"] == "ok"
+    assert ia["mvops"] > ia["iters"]
+
+
+def test_apgd_identity_step_matches_bbpgd():
+    """The identity-mobility collision step solved by APGD equals the one
+    solved by Algorithm 1 (a jittered lattice with active contacts)."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.jittered_lattice(7, 125)
+    kw = dict(delta=0.1, a_c_scale=1.05, bbpgd_tol=1e-12, bbpgd_max=50000)
+    a = lcp.resolve_collisions_identity(w.centers, w.radii, w.FT, w.dt, solver="apgd", **kw)
+    b = lcp.resolve_collisions_identity(w.centers, w.radii, w.FT, w.dt, **kw)
+    assert b["info"]["n_active"] > 5
+    assert np.abs(a["gamma"] - b["gamma"]).max() < 1e-8 * np.abs(b["gamma"]).max()
+    assert np.abs(a["U"] - b["U"]).max() < 1e-8 * np.abs(b["U"]).max()
