@@ -275,7 +275,7 @@ def run_gpu(args, w):
         # 4,000 spheres at volume fraction 0.40: every mobility solve refined
         # to an FP64-accurate relative residual of 1e-10, eps_tol = 1e-8
         prm.update(ir_tol=w.params["ir_tol"], ir_max=12, bbpgd_tol=w.params["bbpgd_tol"],
-                   bbpgd_max=300)
+                   bbpgd_max=100)
     ctx = sps.Context(stream=stream, **prm)
     pos = dev(w.centers)
     rad = dev(w.radii)
@@ -313,6 +313,14 @@ def run_gpu(args, w):
         stats.append(dict(step(pos)))
         ev[k][1].record(stream)
         pos.copy_(pos_out)
+        if args.progress:                  # one line per step on stderr (survives a killed run)
+            torch.cuda.synchronize()
+            st_ = stats[-1]
+            print(json.dumps({"step": k, "ms": ev[k][0].elapsed_time(ev[k][1]), "status": st_["status"],
+                              "bbpgd_iters": st_["bbpgd_iters"], "gmres_iters": st_["gmres_iters"],
+                              "n_contacts": st_["n_contacts"], "n_active": st_["n_active"],
+                              "final_phi": st_["final_phi"], "ir_sweeps": st_["ir_sweeps"],
+                              "layer_applies": st_["layer_applies"]}), file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     nc_last = stats[-1]["n_contacts"]
@@ -407,9 +415,9 @@ def run_gpu(args, w):
             prm64 = dict(prm, precision=0, gmres_tol=1e-10, bb_warm=0)
             fp64_step = rerun(prm64, "plain FP64 path, this benchmark's eps_tol")
             fp64_step["mixed_speedup"] = fp64_step["ms"] / step_ms[-1]
-        prm_ref = dict(prm, precision=2, gmres_tol=1e-12, gmres_max=300, bbpgd_tol=1e-9,
-                       bbpgd_max=1000, bb_warm=0)
-        ref_step = rerun(prm_ref, "FP64-accurate reference (double-float far field), tight tolerances")
+            prm_ref = dict(prm, precision=2, gmres_tol=1e-12, gmres_max=300, bbpgd_tol=1e-9,
+                           bbpgd_max=1000, bb_warm=0)
+            ref_step = rerun(prm_ref, "FP64-accurate reference (double-float far field), tight tolerances")
     err_vs_fp64 = None
     if ref_step:
         err_vs_fp64 = dict(ref_step["err"], norm="relative 2-norm over all spheres / contacts",
@@ -793,8 +801,11 @@ def main():
     ap.add_argument("--single-op", choices=["K", "S", "A"], default=None,
                     help="apply one layer operator on the workload geometry and exit")
     ap.add_argument("--no-contact-bench", action="store_true")
+    ap.add_argument("--progress", action="store_true",
+                    help="print one JSON line per timed step to stderr as it completes")
     ap.add_argument("--no-fp64-step", action="store_true",
-                    help="skip the FP64 rerun of the last timed step (error and FP64 rate)")
+                    help="skip the FP64 and FP64-accurate reruns of the last timed step "
+                         "(FP64 rate and error against FP64)")
     ap.add_argument("--gamma0-steps", type=int, default=3,
                     help="steps of the gamma_0 = 0 comparison leg (0: skip)")
     ap.add_argument("--bb-warm", type=int, default=1, choices=[0, 1],

@@ -84,7 +84,8 @@ typedef struct sps_params {
   double bbpgd_tol;   /* min-map residual tolerance eps_tol (eq. mmapnorm)    */
   int bbpgd_max;      /* j_max of Algorithm 1                                 */
   int precision;      /* sps_precision                                        */
-  int bb_variant;     /* 1: alpha^BB1, 2: alpha^BB2 (Algorithm 1)            */
+  int bb_variant;     /* 1: alpha^BB1, 2: alpha^BB2, 3: BB1 on odd and BB2 on
+                         even steps (Algorithm 1)                            */
   double ir_tol;      /* SPS_MIXED: refine against an FP64-accurate residual
                          until ||r||/||b|| < ir_tol (the velocity of a
                          refined solve is then evaluated FP64-accurate too);
@@ -121,6 +122,13 @@ typedef struct sps_params {
                          (ir_tol > 0): 1 evaluates their far field as
                          SPS_FP64_DW does (double-float on the FP32 pipe), 0
                          in native FP64.  Default 1.                         */
+  int lcp_solver;     /* 0: BBPGD (Algorithm 1); 1: APGD, the accelerated
+                         projected gradient method Sec. 3.3.1 compares with
+                         (Nesterov momentum, an adaptive Lipschitz estimate
+                         with a sufficient-decrease test, gradient restart; at
+                         least two mobility solves per iteration).  Both stop
+                         on the min-map residual bbpgd_tol and cap at
+                         bbpgd_max iterations.  Default 0.                   */
 } sps_params;
 
 typedef struct sps_stats {

@@ -82,6 +82,9 @@ def far_sum(op, Xt, Nt, sph_t, Xs, Ws, Ss, sph_s, excl, chunk=2048):
     excl(i) -> set of source spheres skipped for target sphere i.
     """
     out = np.zeros_like(Xt)
+    # targets per pass: each pass holds a few (targets x sources) arrays, so
+    # the chunk shrinks with the source count (the per-target sums do not change)
+    chunk = max(1, min(chunk, int(4e6 // max(len(Xs), 1))))
     for i0 in range(0, len(Xt), chunk):
         i1 = min(i0 + chunk, len(Xt))
         r = Xt[i0:i1, None, :] - Xs[None, :, :]

@@ -28,7 +28,8 @@ class sps_params(ctypes.Structure):
                 ("bb_variant", ctypes.c_int), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("bb_safeguard", ctypes.c_int),
                 ("mobility", ctypes.c_int), ("contact_search", ctypes.c_int),
-                ("delta_rel", ctypes.c_double), ("bb_warm", ctypes.c_int), ("ir_dw", ctypes.c_int)]
+                ("delta_rel", ctypes.c_double), ("bb_warm", ctypes.c_int), ("ir_dw", ctypes.c_int),
+                ("lcp_solver", ctypes.c_int)]
 
 
 class sps_stats(ctypes.Structure):

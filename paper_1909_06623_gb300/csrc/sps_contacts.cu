@@ -1013,7 +1013,7 @@ int sps_launch_bb_identity(sps_ctx* ctx, double alpha, const double* gam, const 
   {
     SpsPhase timer(ctx, SPS_PH_BB_DT);
     k_bb_ident_DT<<<nb, kThreads, 0, ctx->stream>>>(nc, ctx->d_cij, ctx->d_cn, ctx->d_F3, ctx->d_q,
-                                                    gam_new, gam, g, ctx->prm.bb_variant == 2, g_new,
+                                                    gam_new, gam, g, ctx->prm.bb_variant != 1, g_new,
                                                     ctx->d_bbpart);
     SPS_LAUNCHED(ctx);
   }

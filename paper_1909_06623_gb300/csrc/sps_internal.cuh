@@ -206,6 +206,8 @@ struct sps_ctx {
   double *d_FT = nullptr, *d_Unc = nullptr, *d_Uc = nullptr;
   int cap_bb = 0;
   double *d_bbpart = nullptr;    // BBPGD statistic partials (5 x blocks)
+  double *d_apgd = nullptr;      // APGD: y, M y, scratch (n_c each) and reduction partials
+  size_t cap_apgd = 0;
   double *d_gam_best = nullptr, *d_aux_best = nullptr;  // smallest-residual BBPGD iterate
   size_t cap_gam_best = 0, cap_aux_best = 0;
   // identity mobility: contact forces (N x 3), FT / U_nc / U_c (N x 6)

@@ -470,6 +470,7 @@ extern "C" int sps_default_params(sps_params* o) {
   o->delta_rel = 0.0;
   o->bb_warm = 0;
   o->ir_dw = 1;
+  o->lcp_solver = 0;
   return SPS_OK;
 }
 
@@ -487,7 +488,8 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
       prm->gmres_max < 1 || !(prm->bbpgd_tol > 0) || prm->bbpgd_max < 1 ||
       (prm->precision != SPS_FP64 && prm->precision != SPS_MIXED && prm->precision != SPS_FP64_DW) ||
       (prm->ir_dw != 0 && prm->ir_dw != 1) ||
-      (prm->bb_variant != 1 && prm->bb_variant != 2) || !(prm->a_c_scale > 0) ||
+      (prm->bb_variant < 1 || prm->bb_variant > 3) || (prm->lcp_solver != 0 && prm->lcp_solver != 1) ||
+      !(prm->a_c_scale > 0) ||
       !(prm->delta >= 0) || !(prm->delta_rel >= 0) || !std::isfinite(prm->delta_rel) || prm->ir_tol < 0 || prm->ir_max < 0 ||
       (prm->mobility != SPS_MOB_BIE && prm->mobility != SPS_MOB_IDENTITY) ||
       prm->contact_search < SPS_SEARCH_AUTO || prm->contact_search > SPS_SEARCH_CELLS ||
@@ -574,7 +576,7 @@ extern "C" int sps_destroy(sps_ctx* ctx) {
                   ctx->d_Pb, ctx->d_Px, ctx->d_fcoef32, ctx->d_fcoefdw, ctx->d_prev_ij, ctx->d_prev_gam,
                   ctx->d_dwsrc, ctx->d_rot, ctx->d_sigloc, ctx->d_tcsplit, ctx->d_near_rev,
                   ctx->d_near_geo, ctx->d_near_buf, ctx->d_wcount, ctx->d_wptr, ctx->d_inc_fill,
-                  ctx->d_cl_fill, ctx->d_scan_tot};
+                  ctx->d_cl_fill, ctx->d_scan_tot, ctx->d_apgd};
   for (void* b : more)
     if (b) cudaFree(b);
   for (sps_ctx::Sparse* m : {&ctx->fmK, &ctx->fmS, &ctx->fmKt, &ctx->fmSt}) {
@@ -1243,16 +1245,182 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
                                     cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (!(r.phi < phi_limit)) return fail(SPS_ERR_BREAKDOWN, j);
-    const bool ok = (ctx->prm.bb_variant == 1) ? (s5[2] > 0) : (s5[2] > 0 && s5[3] > 0);
+    // BB1 throughout (variant 1), BB2 throughout (2), or BB1 on odd and BB2 on
+    // even steps (3)
+    const bool bb1 = ctx->prm.bb_variant == 1 || (ctx->prm.bb_variant == 3 && (j & 1));
+    const bool ok = bb1 ? (s5[2] > 0) : (s5[2] > 0 && s5[3] > 0);
     if (!ok) {
       // s^T y <= 0: Algorithm 1 defines no step; stop, or keep the previous one
       if (!ctx->prm.bb_safeguard) return fail(SPS_ERR_BREAKDOWN, j);
       if (st) st->bb_safeguards += 1;
     } else {
-      alpha = (ctx->prm.bb_variant == 1) ? s5[1] / s5[2] : s5[2] / s5[3];
+      alpha = bb1 ? s5[1] / s5[2] : s5[2] / s5[3];
     }
   }
   return fail(SPS_ERR_NOT_CONVERGED, j - 1);
+}
+
+// ---------------------------------------------------------------------------
+// APGD (Sec. 3.3.1's comparison method): Nesterov's accelerated projected
+// gradient with an adaptive Lipschitz estimate L (Mazhar et al. 2015).  Per
+// iteration: M y at the extrapolated point, then x = max(y - g(y)/L, 0) and
+// M x, with L doubled until the sufficient-decrease test, written for the
+// quadratic objective as d.M d <= L |d|^2 (d = x - y), holds; the min-map
+// residual of x decides convergence; the momentum restarts when
+// g(x).(x - gamma) > 0; L shrinks by 0.9 after each accepted step.
+// ---------------------------------------------------------------------------
+constexpr int kApBlocks = 256;
+__global__ void k_fill(int n, double v, double* __restrict__ out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) out[l] = v;
+}
+__global__ void k_apgd_step(int n, double t, const double* __restrict__ y, const double* __restrict__ My,
+                            const double* __restrict__ q, double* __restrict__ x) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) x[l] = fmax(y[l] - t * (My[l] + q[l]), 0.0);
+}
+__global__ void k_apgd_extrap(int n, double beta, const double* __restrict__ x, const double* __restrict__ gam,
+                              double* __restrict__ y) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) y[l] = x[l] + beta * (x[l] - gam[l]);
+}
+// per-block partials of [sum min(x, gx)^2, (x - gam).gx, (x - y).(Mx - My), |x - y|^2]
+__global__ void __launch_bounds__(256) k_apgd_stats(int n, const double* __restrict__ x, const double* __restrict__ y,
+                                                    const double* __restrict__ Mx, const double* __restrict__ My,
+                                                    const double* __restrict__ q, const double* __restrict__ gam,
+                                                    double* __restrict__ part) {
+  __shared__ double sh[4][256];
+  double a[4] = {0, 0, 0, 0};
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+    const double gx = Mx[l] + q[l], d = x[l] - y[l], mn = fmin(x[l], gx);
+    a[0] = fma(mn, mn, a[0]);
+    a[1] = fma(x[l] - gam[l], gx, a[1]);
+    a[2] = fma(d, Mx[l] - My[l], a[2]);
+    a[3] = fma(d, d, a[3]);
+  }
+  for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] = a[c];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 4; ++c) part[c * kApBlocks + blockIdx.x] = sh[c][0];
+}
+__global__ void k_apgd_finish(const double* __restrict__ part, double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= 4) return;
+  double s = 0.0;
+  for (int b = 0; b < kApBlocks; ++b) s += part[c * kApBlocks + b];
+  out[c] = s;
+}
+
+// mul(v, out): out = M v, one evaluation of M (a mobility solve for the
+// boundary-integral mobility) leaving M D v in aux when aux is not null.
+// On return d_gam holds the returned iterate and aux its M D gamma.
+template <class Mul>
+static int apgd_run(sps_ctx* ctx, int nc, sps_stats* st, Mul mul, BBResult& r, double* aux, size_t aux_len) {
+  const int tb = (nc + 255) / 256;
+  SPS_TRY(sps_grow(ctx, &ctx->d_apgd, ctx->cap_apgd, 3 * (size_t)nc + 8 * kApBlocks + 8));
+  double* y = ctx->d_apgd;
+  double* My = y + nc;
+  double* tmp = My + nc;
+  double* part = tmp + nc;
+  double* res = part + 4 * kApBlocks;
+  double* x = ctx->d_gam_new;
+  double* Mx = ctx->d_Mg;
+  if (aux) SPS_TRY(sps_grow(ctx, &ctx->d_aux_best, ctx->cap_aux_best, std::max<size_t>(aux_len, 1)));
+  int rc = SPS_OK;
+  auto note = [&](int rc2) -> int {
+    if (rc2 != SPS_OK && rc2 != SPS_ERR_NOT_CONVERGED) return rc2;
+    if (rc2) r.worst = rc2;
+    if (st) st->mvops += 1;
+    return SPS_OK;
+  };
+  SPS_CUDA(ctx, cudaMemsetAsync(ctx->d_gam, 0, sizeof(double) * nc, ctx->stream));
+  SPS_CUDA(ctx, cudaMemsetAsync(y, 0, sizeof(double) * nc, ctx->stream));
+  SPS_CUDA(ctx, cudaMemsetAsync(My, 0, sizeof(double) * nc, ctx->stream));
+  if (aux) SPS_CUDA(ctx, cudaMemsetAsync(aux, 0, sizeof(double) * aux_len, ctx->stream));
+  // gamma_0 = 0: residual |min(0, q)|
+  double s5[5];
+  SPS_TRY(bb_stats(ctx, ctx->d_gam, ctx->d_q, nullptr, nullptr, s5));
+  r.phi = std::sqrt(s5[0]);
+  const double tol = ctx->prm.bbpgd_tol;
+  if (r.phi < tol) return SPS_OK;
+  // L_0 = |M e| / |e| for the vector of ones e
+  k_fill<<<tb, 256, 0, ctx->stream>>>(nc, 1.0, tmp);
+  SPS_LAUNCHED(ctx);
+  SPS_TRY(note(mul(tmp, Mx)));
+  double mm = 0.0;
+  SPS_TRY(sps_dot(ctx, Mx, Mx, nc, &mm));
+  double L = std::sqrt(mm / nc);
+  if (!(L > 0) || !std::isfinite(L)) {
+    r.bb_rc = SPS_ERR_BREAKDOWN;
+    return SPS_OK;
+  }
+  double theta = 1.0;
+  bool y_zero = true, y_known = false;   // M y already in My (y = 0, or a restart at x)
+  double st4[4] = {0, 0, 0, 0};
+  for (int k = 1; k <= ctx->prm.bbpgd_max; ++k) {
+    if (!y_zero && !y_known) SPS_TRY(note(mul(y, My)));
+    y_known = false;
+    bool accepted = false;
+    for (int bt = 0; bt < 64 && !accepted; ++bt) {
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_apgd_step<<<tb, 256, 0, ctx->stream>>>(nc, 1.0 / L, y, My, ctx->d_q, x); }
+      SPS_LAUNCHED(ctx);
+      SPS_TRY(note(mul(x, Mx)));
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_apgd_stats<<<kApBlocks, 256, 0, ctx->stream>>>(nc, x, y, Mx, My, ctx->d_q, ctx->d_gam, part);
+      k_apgd_finish<<<1, 32, 0, ctx->stream>>>(part, res); }
+      SPS_LAUNCHED(ctx);
+      SPS_TRY(to_host(ctx, res, 4, st4));
+      for (int c = 0; c < 4; ++c)
+        if (!std::isfinite(st4[c])) return sps_fail(ctx, SPS_ERR_NONFINITE, "APGD: non-finite residual");
+      if (st4[2] <= L * st4[3]) accepted = true;
+      else L *= 2.0;
+    }
+    if (!accepted) {
+      r.bb_rc = SPS_ERR_BREAKDOWN;    // no step length satisfied the decrease test
+      return SPS_OK;
+    }
+    r.iters = k;
+    r.best_iter = k;
+    r.phi = std::sqrt(st4[0]);
+    const bool restart = st4[1] > 0;
+    // gamma <- x (its M D x is in aux)
+    std::swap(ctx->d_gam, ctx->d_gam_new);
+    x = ctx->d_gam_new;
+    if (aux) SPS_CUDA(ctx, cudaMemcpyAsync(ctx->d_aux_best, aux, sizeof(double) * aux_len, cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
+    if (r.phi < tol) break;
+    if (k == ctx->prm.bbpgd_max) {
+      r.bb_rc = SPS_ERR_NOT_CONVERGED;
+      break;
+    }
+    const double th2 = theta * theta;
+    double theta_new = 0.5 * (-th2 + theta * std::sqrt(th2 + 4.0));
+    const double beta = theta * (1.0 - theta) / (th2 + theta_new);
+    if (restart) {
+      // y = gamma_k, whose product M gamma_k is the accepted M x
+      SPS_CUDA(ctx, cudaMemcpyAsync(y, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+      SPS_CUDA(ctx, cudaMemcpyAsync(My, Mx, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+      theta_new = 1.0;
+      y_known = true;
+    } else {
+      // y = gamma_k + beta (gamma_k - gamma_{k-1}); gamma_{k-1} is in x's buffer now
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_apgd_extrap<<<tb, 256, 0, ctx->stream>>>(nc, beta, ctx->d_gam, x, y); }
+      SPS_LAUNCHED(ctx);
+    }
+    y_zero = false;
+    theta = theta_new;
+    L *= 0.9;
+  }
+  if (aux) SPS_CUDA(ctx, cudaMemcpyAsync(aux, ctx->d_aux_best, sizeof(double) * aux_len, cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+  return rc;
 }
 
 static int finish_bb_stats(sps_ctx* ctx, int nc, const BBResult& r, sps_stats* st) {
@@ -1318,7 +1486,13 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
       warm0 = npos > 0;
     }
     auto mul_gam = [&]() { return apply_M(ctx, ctx->d_gam, ctx->d_Mg, st, false); };
-    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, ctx->d_Uc, 6 * (size_t)n, warm0, mul_gam));
+    if (ctx->prm.lcp_solver == 1) {
+      auto mul = [&](const double* v, double* out) { return apply_M(ctx, v, out, st, ctx->prm.warm_start != 0); };
+      SPS_TRY(apgd_run(ctx, nc, st, mul, r, ctx->d_Uc, 6 * (size_t)n));
+      warm0 = true;   // (U_c below is the solve of the returned iterate, also at iteration 0)
+    } else {
+      SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, ctx->d_Uc, 6 * (size_t)n, warm0, mul_gam));
+    }
     if (r.worst) worst = r.worst;
     // U_c is the solve of the returned iterate; gamma_0 = 0 needs none
     if (r.iters == 0 && !warm0)
@@ -1400,13 +1574,28 @@ static int resolve_identity(sps_ctx* ctx, int n, const double* pos, const double
       SPS_TRY(sps_launch_bb_identity(ctx, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new, ctx->d_g_new));
       return read5(ctx, s5);
     };
-    SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, nullptr, 0, false, []() { return SPS_OK; }));
+    if (ctx->prm.lcp_solver == 1) {
+      auto mul = [&](const double* v, double* out) -> int {
+        SPS_TRY(sps_launch_D(ctx, v, ctx->d_iFT));
+        return sps_launch_DT(ctx, ctx->d_iFT, out);
+      };
+      SPS_TRY(apgd_run(ctx, nc, st, mul, r, nullptr, 0));
+    } else {
+      SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, nullptr, 0, false, []() { return SPS_OK; }));
+    }
     if (gamma)
       SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   SPS_TRY(finish_bb_stats(ctx, nc, r, st));
-  // U = F_ext + D gamma (d_F3 holds D of the returned iterate after a step)
-  SPS_TRY(sps_launch_identity_U(ctx, n, FT_ext, r.iters > 0 ? ctx->d_F3 : nullptr, UO));
+  // U = F_ext + D gamma (d_F3 holds D of the returned iterate after a BBPGD step)
+  if (ctx->prm.lcp_solver == 1 && nc > 0) {
+    SPS_TRY(sps_launch_D(ctx, ctx->d_gam, ctx->d_iFT));
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_axpby<<<gblocks(6LL * n), 256, 0, ctx->stream>>>(6LL * n, 1.0, FT_ext, 1.0, ctx->d_iFT, UO); }
+    SPS_LAUNCHED(ctx);
+  } else {
+    SPS_TRY(sps_launch_identity_U(ctx, n, FT_ext, r.iters > 0 ? ctx->d_F3 : nullptr, UO));
+  }
   if (pos_out) {
     { SpsPhase timer_(ctx, SPS_PH_BBPGD);
     k_pos_update<<<(3 * n + 255) / 256, 256, 0, ctx->stream>>>(n, pos, UO, dt, pos_out); }

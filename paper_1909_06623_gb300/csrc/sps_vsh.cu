@@ -43,6 +43,12 @@
 #ifndef SPS_SHT_TC
 #define SPS_SHT_TC 1
 #endif
+// 1: the source-major near field in two kernels (FP32 items at 3 CTAs per SM;
+// close items in double-float), 0: one kernel doing both.  Measured on 1,000
+// spheres: 0.35 ms per traction application either way.
+#ifndef SPS_NEAR_SPLIT
+#define SPS_NEAR_SPLIT 0
+#endif
 
 namespace {
 
@@ -694,8 +700,10 @@ __device__ __forceinline__ void near_src_close(int it, int j, int q0, int P, int
   buf[2 * NQ + o] = rz;
 }
 
-template <int F>
-__global__ void __launch_bounds__(kNS) k_near_src(int N, int P, int L, int E, long long NQ,
+// FAR_ONLY = 1: the FP32 items only (close items are left to k_near_src_close,
+// and the double-float path does not weigh on this kernel's registers)
+template <int F, int FAR_ONLY>
+__global__ void __launch_bounds__(kNS, FAR_ONLY ? 3 : 2) k_near_src(int N, int P, int L, int E, long long NQ,
                                                  const double* __restrict__ pos, const double* __restrict__ rad,
                                                  const double* __restrict__ X, const double* __restrict__ Nr,
                                                  const float* __restrict__ rel32, const float* __restrict__ N32,
@@ -707,7 +715,7 @@ __global__ void __launch_bounds__(kNS) k_near_src(int N, int P, int L, int E, lo
   constexpr int FP = (F + 1) & ~1;
   extern __shared__ __align__(16) unsigned char sraw[];
   float4* c32 = reinterpret_cast<float4*>(sraw);     // E x FP/2 field pairs
-  float4* cdw = c32 + E * (FP / 2);                 // E x F double-float fields
+  float4* cdw = c32 + E * (FP / 2);                 // E x F double-float fields (unless FAR_ONLY)
   __shared__ float s_rot[9];
   __shared__ double s_rotd[9];
   __shared__ int s_ncl;
@@ -722,8 +730,10 @@ __global__ void __launch_bounds__(kNS) k_near_src(int N, int P, int L, int E, lo
     const float2 b = (2 * l + 1 < F) ? src[e * F + 2 * l + 1] : make_float2(0.f, 0.f);
     c32[t] = make_float4(a.x, b.x, -a.y, -b.y);
   }
-  const float4* dsrc = fcoefdw + (long long)j * E * F;
-  for (int t = threadIdx.x; t < E * F; t += kNS) cdw[t] = dsrc[t];
+  if (!FAR_ONLY) {
+    const float4* dsrc = fcoefdw + (long long)j * E * F;
+    for (int t = threadIdx.x; t < E * F; t += kNS) cdw[t] = dsrc[t];
+  }
   if (threadIdx.x == 0) {
     s_ncl = 0;
     if (rot)
@@ -751,6 +761,7 @@ __global__ void __launch_bounds__(kNS) k_near_src(int N, int P, int L, int E, lo
     const float r2 = x * x + y * y + z * z;
     if (r2 < hi &&
         (r2 < lo || sps_close_r2(pos, iad, X[g], X[NP + g], X[2 * NP + g], j) < lim)) {
+      if (FAR_ONLY) continue;
       const int c = atomicAdd(&s_ncl, 1);
       if (c < kMaxClose)
         s_cl[c] = it;
@@ -781,10 +792,87 @@ __global__ void __launch_bounds__(kNS) k_near_src(int N, int P, int L, int E, lo
     buf[NQ + o] = ty;
     buf[2 * NQ + o] = tz;
   }
+  if (FAR_ONLY) return;
   __syncthreads();
   const int ncl = min(s_ncl, kMaxClose);
   for (int c = threadIdx.x; c < ncl; c += kNS)
     near_src_close<F>(s_cl[c], j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+}
+
+// The close items of source j (the same split as k_near_src's), in
+// double-float with j's coefficients staged once: the companion of
+// k_near_src<F, 1>.
+constexpr int kNC = 128;
+template <int F>
+__global__ void __launch_bounds__(kNC) k_near_src_close(int N, int P, int L, int E, long long NQ,
+                                                        const double* __restrict__ pos,
+                                                        const double* __restrict__ rad,
+                                                        const double* __restrict__ X, const double* __restrict__ Nr,
+                                                        const float* __restrict__ rel32,
+                                                        const int* __restrict__ near_ptr,
+                                                        const int* __restrict__ near_idx,
+                                                        const int* __restrict__ rev, const float* __restrict__ geo,
+                                                        const float4* __restrict__ fcoefdw,
+                                                        const double* __restrict__ rot, double* __restrict__ buf) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  float4* cdw = reinterpret_cast<float4*>(sraw);    // E x F double-float fields
+  __shared__ double s_rotd[9];
+  __shared__ int s_ncl;
+  __shared__ int s_cl[kMaxClose];
+  const int j = blockIdx.x;
+  const int q0 = near_ptr[j], nn = near_ptr[j + 1] - q0;
+  if (nn == 0) return;
+  if (threadIdx.x == 0) {
+    s_ncl = 0;
+    if (rot)
+      for (int c = 0; c < 9; ++c) s_rotd[c] = rot[9 * j + c];
+  }
+  __syncthreads();
+  const long long NP = (long long)N * P;
+  const double aj = rad[j], iad = 1.0 / aj;
+  const float ia = (float)iad;
+  const double lim = sps::kCloseRadius * sps::kCloseRadius;
+  const float lo = (float)(lim * (1.0 - 1e-4)), hi = (float)(lim * (1.0 + 1e-4));
+  const double* Qd = rot ? s_rotd : nullptr;
+  const int items = nn * P;
+  for (int it = threadIdx.x; it < items; it += kNC) {
+    const int qq = it / P, k = it - qq * P;
+    const int i = near_idx[q0 + qq];
+    const int q = rev[q0 + qq];
+    if (q < 0) continue;
+    const long long g = (long long)i * P + k;
+    const float x = fmaf(rel32[g], ia, geo[3 * q]), y = fmaf(rel32[NP + g], ia, geo[3 * q + 1]),
+                z = fmaf(rel32[2 * NP + g], ia, geo[3 * q + 2]);
+    const float r2 = x * x + y * y + z * z;
+    if (r2 < hi && (r2 < lo || sps_close_r2(pos, iad, X[g], X[NP + g], X[2 * NP + g], j) < lim)) {
+      const int c = atomicAdd(&s_ncl, 1);
+      if (c < kMaxClose) s_cl[c] = it;
+    }
+  }
+  __syncthreads();
+  const int ncl = s_ncl;
+  if (ncl == 0) return;
+  const float4* dsrc = fcoefdw + (long long)j * E * F;
+  for (int t = threadIdx.x; t < E * F; t += kNC) cdw[t] = dsrc[t];
+  __syncthreads();
+  for (int c = threadIdx.x; c < min(ncl, kMaxClose); c += kNC)
+    near_src_close<F>(s_cl[c], j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+  // more close items than the list holds: every close item is found again and
+  // evaluated in place (the writes are idempotent, so the listed ones may repeat)
+  if (ncl > kMaxClose) {
+    for (int it = threadIdx.x; it < items; it += kNC) {
+      const int qq = it / P, k = it - qq * P;
+      const int i = near_idx[q0 + qq];
+      const int q = rev[q0 + qq];
+      if (q < 0) continue;
+      const long long g = (long long)i * P + k;
+      const float x = fmaf(rel32[g], ia, geo[3 * q]), y = fmaf(rel32[NP + g], ia, geo[3 * q + 1]),
+                  z = fmaf(rel32[2 * NP + g], ia, geo[3 * q + 2]);
+      const float r2 = x * x + y * y + z * z;
+      if (r2 < hi && (r2 < lo || sps_close_r2(pos, iad, X[g], X[NP + g], X[2 * NP + g], j) < lim))
+        near_src_close<F>(it, j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+    }
+  }
 }
 
 // out[g] += sum over the near pairs q of g's sphere (near-list order) of buf
@@ -813,15 +901,36 @@ int launch_near_src(sps_ctx* ctx, double* out) {
   const long long NQ = (long long)ctx->n_near * P;
   SPS_TRY(sps_grow(ctx, &ctx->d_near_buf, ctx->cap_near_buf, 3 * (size_t)NQ));
   constexpr int FP = (F + 1) & ~1;
-  const size_t sm = sizeof(float4) * (size_t)E * (FP / 2 + F);
-  if (sm > 48 * 1024)
-    SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_src<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_near_src<F><<<N, kNS, sm, ctx->stream>>>(N, P, L, E, NQ, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm,
-                                             ctx->d_rel32, ctx->d_N32, ctx->d_near_ptr, ctx->d_near_idx,
-                                             ctx->d_near_rev, ctx->d_near_geo, ctx->d_fcoef32,
-                                             reinterpret_cast<const float4*>(ctx->d_fcoefdw), sps_rot(ctx),
-                                             ctx->d_near_buf);
-  SPS_LAUNCHED(ctx);
+  const float4* fdw = reinterpret_cast<const float4*>(ctx->d_fcoefdw);
+  if (SPS_NEAR_SPLIT) {
+    // FP32 items, then the close items of each source in double-float
+    const size_t sm = sizeof(float4) * (size_t)E * (FP / 2);
+    if (sm > 48 * 1024)
+      SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_src<F, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near_src<F, 1><<<N, kNS, sm, ctx->stream>>>(N, P, L, E, NQ, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm,
+                                                  ctx->d_rel32, ctx->d_N32, ctx->d_near_ptr, ctx->d_near_idx,
+                                                  ctx->d_near_rev, ctx->d_near_geo, ctx->d_fcoef32, fdw,
+                                                  sps_rot(ctx), ctx->d_near_buf);
+    SPS_LAUNCHED(ctx);
+    const size_t smc = sizeof(float4) * (size_t)E * F;
+    if (smc > 48 * 1024)
+      SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_src_close<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smc));
+    k_near_src_close<F><<<N, kNC, smc, ctx->stream>>>(N, P, L, E, NQ, ctx->d_pos, ctx->d_rad, ctx->d_X,
+                                                      ctx->d_Nrm, ctx->d_rel32, ctx->d_near_ptr, ctx->d_near_idx,
+                                                      ctx->d_near_rev, ctx->d_near_geo, fdw, sps_rot(ctx),
+                                                      ctx->d_near_buf);
+    SPS_LAUNCHED(ctx);
+  } else {
+    const size_t sm = sizeof(float4) * (size_t)E * (FP / 2 + F);
+    if (sm > 48 * 1024)
+      SPS_CUDA(ctx, cudaFuncSetAttribute(k_near_src<F, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near_src<F, 0><<<N, kNS, sm, ctx->stream>>>(N, P, L, E, NQ, ctx->d_pos, ctx->d_rad, ctx->d_X, ctx->d_Nrm,
+                                                  ctx->d_rel32, ctx->d_N32, ctx->d_near_ptr, ctx->d_near_idx,
+                                                  ctx->d_near_rev, ctx->d_near_geo, ctx->d_fcoef32, fdw,
+                                                  sps_rot(ctx), ctx->d_near_buf);
+    SPS_LAUNCHED(ctx);
+  }
   const long long NP = (long long)N * P;
   k_near_reduce<<<(int)std::min<long long>((NP + 255) / 256, 8 * 152), 256, 0, ctx->stream>>>(
       N, P, NQ, ctx->d_near_ptr, ctx->d_near_buf, out);

@@ -39,7 +39,7 @@ def test_default_params(lib):
     assert prm.p == 6 and prm.beta == 1.75 and prm.bb_variant == 1
     # the fields appended last: the Python mirror of the struct ends where the C one does
     assert prm.delta_rel == 0.0 and prm.bb_warm == 0 and prm.contact_search == 0
-    assert prm.ir_dw == 1
+    assert prm.ir_dw == 1 and prm.lcp_solver == 0
 
 
 def test_create_rejects_bad_params(lib):
@@ -50,7 +50,8 @@ def test_create_rejects_bad_params(lib):
     assert lib.sps_create(ctypes.byref(prm), None, ctypes.byref(h)) == 1
     assert lib.sps_unit_tables(0, None, None, None, None) == 1
     for field, bad in (("delta_rel", -0.1), ("delta_rel", float("inf")), ("bb_warm", 2),
-                       ("delta", -1.0), ("mobility", 5), ("ir_dw", 2), ("precision", 3)):
+                       ("delta", -1.0), ("mobility", 5), ("ir_dw", 2), ("precision", 3),
+                       ("lcp_solver", 2), ("bb_variant", 4)):
         lib.sps_default_params(ctypes.byref(prm))
         setattr(prm, field, bad)
         assert lib.sps_create(ctypes.byref(prm), None, ctypes.byref(h)) == 1, field
