@@ -160,20 +160,28 @@ def ctx_params(precision, bb_warm=1, bbpgd_tol=1e-6):
 ORACLE_APPLIES_PER_STEP = 185.0
 
 
+_SUS = {}
+
+
 def _oracle_worker(job):
     """One process of the oracle sample: the traction operator K on its share
-    of the target spheres (seconds spent in the operator)."""
+    of the target spheres (seconds spent in the operator).  The geometry is
+    built once per process and workload."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     centers, radii, p, seed, targets = job
     from oracle.layer import Suspension
-    sus = Suspension(centers, radii, p)
+    key = (len(radii), p, float(centers[0, 0]), float(centers[-1, 2]))
+    if key not in _SUS:
+        _SUS.clear()
+        _SUS[key] = Suspension(centers, radii, p)
+    sus = _SUS[key]
     sig = np.random.default_rng(seed).standard_normal((sus.N * sus.P, 3))
     t0 = time.perf_counter()
     sus.apply("K", sig, targets=list(targets))
     return time.perf_counter() - t0
 
 
-def oracle_sample(w, n_targets=3, seed=0, cores=1):
+def oracle_sample(w, n_targets=3, seed=0, cores=1, pool=None):
     """Times the FP64 oracle's traction operator K (self + near + all-pairs
     far field) on n_targets target spheres per core and scales it to one full
     application.  cores > 1 runs one spawned process per core, each on its own
@@ -186,11 +194,19 @@ def oracle_sample(w, n_targets=3, seed=0, cores=1):
         return dt * w.N / len(tg), dt, len(tg)
     import multiprocessing as mp
     jobs = [(w.centers, w.radii, w.p, seed, part) for part in np.array_split(tg, cores)]
-    with mp.get_context("spawn").Pool(cores) as pool:
-        pool.map(_oracle_worker, jobs[:cores])       # start-up: imports, geometry
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+    try:
+        if own:
+            pool.map(_oracle_worker, jobs)           # start-up: imports, geometry
         t0 = time.perf_counter()
         pool.map(_oracle_worker, jobs)
         dt = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
     return dt * w.N / len(tg), dt, len(tg)
 
 
@@ -212,12 +228,15 @@ def matvecs_per_step_estimate(stats_list):
 # ---------------------------------------------------------------------------
 def run_reference(args, w):
     steps, warm = args.steps, args.warmup
+    import multiprocessing as mp
     cores = host_cores()
     times = []
-    for k in range(warm + steps):
-        full, sample, ntg = oracle_sample(w, seed=k, cores=cores)
-        if k >= warm:
-            times.append(full)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for k in range(warm + steps):
+            # each worker builds the geometry on its first job (a warm-up step)
+            full, sample, ntg = oracle_sample(w, seed=k, cores=cores, pool=pool)
+            if k >= warm:
+                times.append(full)
     mv = args.ref_matvecs_per_step
     step_s = float(np.mean(times)) * mv
     val = 1.0 / step_s
