@@ -409,3 +409,21 @@ def test_apgd_identity_step_matches_bbpgd():
     assert b["info"]["n_active"] > 5
     assert np.abs(a["gamma"] - b["gamma"]).max() < 1e-8 * np.abs(b["gamma"]).max()
     assert np.abs(a["U"] - b["U"]).max() < 1e-8 * np.abs(b["U"]).max()
+
+
+def test_rotor_workloads():
+    """Sec. 7 workloads: the rotor cluster's radii follow the log-normal law
+    with mean 1 and standard deviation 0.3 and start collision-free at the
+    collision radius 1.1 a; the monolayer lies in z = 0 with no overlap at
+    a_c and many pairs touching; both carry the torque (0, 0, 1) only."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.rotor_cluster(N=600)
+    assert abs(w.radii.mean() - 1.0) < 0.05 and abs(w.radii.std() - 0.3) < 0.05
+    _, phi, _ = lcp.build_contacts(w.centers, w.radii, 0.0, 1.1, 0.3)
+    assert len(phi) > 0 and phi.min() >= 0.0
+    assert np.all(w.FT[:, :5] == 0) and np.all(w.FT[:, 5] == 1.0) and w.dt == 1.0
+    m = workloads.rotor_monolayer(N=300)
+    assert np.all(m.centers[:, 2] == 0.0)
+    _, phi, _ = lcp.build_contacts(m.centers, m.radii, 0.0, 1.1, 0.3)
+    assert phi.min() >= 0.0 and np.sum(phi < 1e-6) > 0.5 * len(m.radii)
+    assert np.all(m.FT[:, 5] == 1.0) and m.dt == 0.5
