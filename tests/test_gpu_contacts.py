@@ -173,6 +173,26 @@ def test_identity_step_matches_oracle(sps, N, seed, search):
     assert st["n_active"] == ref["info"]["n_active"]
 
 
+@pytest.mark.parametrize("scale", [1e-30, 1e-12, 1e30])
+def test_identity_step_scale_equivariance(sps, scale):
+    """Algorithm 1 with the identity mobility is equivariant under F -> sF,
+    dt -> dt/s, eps_tol -> s eps_tol: gamma and U scale by s and the positions
+    move alike.  FP64 against the oracle at s = 1, 1e-10."""
+    w = workloads.jittered_lattice(31, 512)
+    ref = lcp.resolve_collisions_identity(w.centers, w.radii, w.FT, w.dt, delta=0.1, a_c_scale=1.05,
+                                          bbpgd_tol=1e-10, bbpgd_max=5000)
+    ctx = sps.Context(p=2, delta=0.1, a_c_scale=1.05, mobility=sps.SPS_MOB_IDENTITY,
+                      bbpgd_tol=1e-10 * scale, bbpgd_max=5000)
+    gam, UO, pos_out = ctx.resolve_collisions(dev(w.centers), dev(w.radii), dev(scale * w.FT),
+                                              w.dt / scale)
+    assert ctx.last_stats["status"] == 0
+    assert ctx.last_stats["n_active"] == ref["info"]["n_active"]
+    gs = np.abs(ref["gamma"]).max()
+    assert np.abs(gam.cpu().numpy() / scale - ref["gamma"]).max() < TOL64 * gs
+    assert np.abs(UO.cpu().numpy() / scale - ref["U"]).max() < TOL64 * np.abs(ref["U"]).max()
+    assert np.abs(pos_out.cpu().numpy() - ref["centers_new"]).max() < 1e-12 * np.abs(w.centers).max()
+
+
 def test_identity_mobility_apply_and_adjoint(sps):
     w = workloads.jittered_lattice(33, 64)
     ctx = sps.Context(p=2, mobility=sps.SPS_MOB_IDENTITY)
