@@ -126,9 +126,15 @@ typedef struct sps_params {
                          projected gradient method Sec. 3.3.1 compares with
                          (Nesterov momentum, an adaptive Lipschitz estimate
                          with a sufficient-decrease test, gradient restart; at
-                         least two mobility solves per iteration).  Both stop
-                         on the min-map residual bbpgd_tol and cap at
-                         bbpgd_max iterations.  Default 0.                   */
+                         least two mobility solves per iteration); 2: the
+                         minimum-map Newton method Sec. 3.3.1 names as the
+                         second-order alternative (Newton on min(gamma, g)
+                         with the step's free block solved by conjugate
+                         gradients, one mobility solve per CG iteration, and
+                         an Armijo line search; gamma may end with entries
+                         down to -bbpgd_tol).  All stop on the min-map
+                         residual bbpgd_tol and cap at bbpgd_max (Newton)
+                         iterations.  Default 0.                             */
 } sps_params;
 
 typedef struct sps_stats {

@@ -48,6 +48,21 @@ Paper: Yan et al., arXiv 1909.06623.
     column +n on sphere i (the wall acts as a static first body, so
     D^T U = n.U_i).  Wall contacts follow the pair contacts, sorted by
     (sphere, wall), recorded as (-1 - w, i).
+  * Minimum-map Newton (Sec. 3.3.1 names it, after Niebe and Erleben 2015,
+    as the second-order alternative it rejects; no listing): a root of
+    H(gamma) = min(gamma, g) (eq. mmapnorm) by Newton steps J Delta = -H with
+    J the element of the generalised Jacobian taking row l of M where
+    g_l < gamma_l (the set F) and row l of the identity elsewhere.  Readings
+    where the paper is silent: the step splits into Delta_l = -gamma_l off F
+    and M_FF Delta_F = -(g + M [0; Delta_off F])_F, solved "iteratively" by
+    conjugate gradients from 0 to relative residual NEWTON_CG_TOL (at most
+    NEWTON_CG_MAX products); M Delta is the sum of those products with the CG
+    coefficients, so g(gamma + t Delta) = g + t M Delta costs no further
+    product; t = 1, halved (at most NEWTON_HALVINGS times, else "breakdown")
+    until the Armijo test |H(gamma + t Delta)|^2 <= (1 - 2 sigma t) |H(gamma)|^2,
+    sigma = NEWTON_SIGMA; gamma_0 = 0; stop on eq. mmapnorm below eps_tol.
+    gamma may end with entries down to -eps_tol (H is zero at the root, not
+    the projection).
   * eq. time-step: C^{k+1} = C^k + (U_nc + M D gamma) dt, positions only
     (spheres are isotropic; the grid keeps its lab-frame orientation).
 """
@@ -247,6 +262,85 @@ def apgd(Mop, q, tol, jmax=10000):
     return gam, Mgam + q, info
 
 
+NEWTON_CG_TOL = 1e-3     # relative residual of the CG solve of each Newton system
+NEWTON_CG_MAX = 200
+NEWTON_SIGMA = 1e-4      # Armijo constant of the line search on theta = |H|^2 / 2
+NEWTON_HALVINGS = 30
+
+
+def minmap_newton(Mop, q, tol, jmax=100):
+    """Minimum-map Newton for the LCP of eq. lcp:LCPdef (see the module
+    docstring): a root of H(gamma) = min(gamma, g), g = M gamma + q.  Mop(x) ->
+    M x.  Returns gamma, g, info (info["mvops"] counts products of M,
+    info["cg_iters"] the CG iterations over all Newton steps)."""
+    q = np.asarray(q, dtype=np.float64)
+    n = len(q)
+    gam = np.zeros(n)
+    g = q.copy()                                    # M 0 + q
+    phi = minmap(gam, g)
+    info = {"iters": 0, "mvops": 0, "cg_iters": 0, "status": "ok", "phi": phi}
+    if phi < tol:
+        return gam, g, info
+    mv = cg = 0
+    for k in range(1, jmax + 1):
+        # Jacobian of H: row l of M where H_l = g_l (g_l < gamma_l, the set F),
+        # row l of the identity elsewhere (ties included)
+        free = g < gam
+        dC = np.where(free, 0.0, -gam)              # identity rows: Delta_l = -gamma_l
+        MdC = np.zeros(n)
+        if np.any(dC):
+            MdC = Mop(dC)
+            mv += 1
+        # M_FF Delta_F = -(g + M dC)_F by CG from 0; the unmasked products of
+        # the search directions add up to M [Delta_F; 0]
+        b = np.where(free, -g - MdC, 0.0)
+        x, MxF = np.zeros(n), np.zeros(n)
+        r = b.copy()
+        pd = r.copy()
+        rr = r @ r
+        bnorm = np.sqrt(rr)
+        for _ in range(NEWTON_CG_MAX):
+            if np.sqrt(rr) <= NEWTON_CG_TOL * bnorm:
+                break
+            Mp = Mop(pd)
+            mv += 1
+            cg += 1
+            Ap = np.where(free, Mp, 0.0)
+            pAp = pd @ Ap
+            if not pAp > 0:
+                break
+            a = rr / pAp
+            x += a * pd
+            MxF += a * Mp
+            r -= a * Ap
+            rr_new = r @ r
+            pd = r + (rr_new / rr) * pd
+            rr = rr_new
+        d = x + dC
+        Md = MxF + MdC
+        # Armijo backtracking on theta: the exact Newton direction has
+        # directional derivative -2 theta, so accept theta(t) <= (1 - 2 sigma t) theta(0)
+        theta0 = 0.5 * phi * phi
+        t, accepted = 1.0, False
+        for _ in range(NEWTON_HALVINGS + 1):
+            gam_t, g_t = gam + t * d, g + t * Md
+            phi_t = minmap(gam_t, g_t)
+            if 0.5 * phi_t * phi_t <= (1.0 - 2.0 * NEWTON_SIGMA * t) * theta0:
+                accepted = True
+                break
+            t *= 0.5
+        info.update(mvops=mv, cg_iters=cg)
+        if not accepted:
+            info["status"] = "breakdown"
+            return gam, g, info
+        gam, g, phi = gam_t, g_t, phi_t
+        info.update(iters=k, phi=phi)
+        if phi < tol:
+            return gam, g, info
+    info["status"] = "not_converged"
+    return gam, g, info
+
+
 def lcp_enumerate(Mmat, q):
     """Exact LCP solution by trying every active set (small n_c only).
 
@@ -306,16 +400,19 @@ def resolve_collisions(centers, radii, FT_ext, dt, p, *, beta=1.75, delta=0.1,
         return DT_apply(ij, nrm, UO)
 
     state["U_c_of"] = []
-    if solver == "apgd":
-        gamma, g, info = apgd(Mop, q, bbpgd_tol, bbpgd_max)
+    if solver in ("apgd", "newton"):
+        if solver == "apgd":
+            gamma, g, info = apgd(Mop, q, bbpgd_tol, bbpgd_max)
+        else:
+            gamma, g, info = minmap_newton(Mop, q, bbpgd_tol, bbpgd_max)
         info["best"] = info["iters"]
-        # U_c of the returned iterate: one more solve (APGD's products mix
-        # iterates through the momentum)
+        # U_c of the returned iterate: one more solve (the products of APGD
+        # and Newton are not products of the iterates)
         U_c = (mobility.mobility_apply(sus, D_apply(sus.N, ij, nrm, gamma), gmres_tol, gmres_max)
                if np.any(gamma) else np.zeros_like(U_nc))
     else:
         gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard, keep_best=keep_best)
-    if solver == "apgd":
+    if solver in ("apgd", "newton"):
         pass
     elif info["iters"] == 0 or info["best"] == 0:
         U_c = np.zeros_like(U_nc)       # gamma = gamma_0 = 0
@@ -391,8 +488,11 @@ def resolve_collisions_identity(centers, radii, FT_ext, dt, *, delta=0.1, a_c_sc
         state["U_c"] = D_apply(N, ij, nrm, gam)
         return DT_apply(ij, nrm, state["U_c"])
 
-    if solver == "apgd":
-        gamma, g, info = apgd(Mop, q, bbpgd_tol, bbpgd_max)
+    if solver in ("apgd", "newton"):
+        if solver == "apgd":
+            gamma, g, info = apgd(Mop, q, bbpgd_tol, bbpgd_max)
+        else:
+            gamma, g, info = minmap_newton(Mop, q, bbpgd_tol, bbpgd_max)
         U_c = D_apply(N, ij, nrm, gamma)
     else:
         gamma, g, info = bbpgd(Mop, q, bbpgd_tol, bbpgd_max, variant, safeguard)

@@ -488,7 +488,7 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
       prm->gmres_max < 1 || !(prm->bbpgd_tol > 0) || prm->bbpgd_max < 1 ||
       (prm->precision != SPS_FP64 && prm->precision != SPS_MIXED && prm->precision != SPS_FP64_DW) ||
       (prm->ir_dw != 0 && prm->ir_dw != 1) ||
-      (prm->bb_variant < 1 || prm->bb_variant > 3) || (prm->lcp_solver != 0 && prm->lcp_solver != 1) ||
+      (prm->bb_variant < 1 || prm->bb_variant > 3) || (prm->lcp_solver < 0 || prm->lcp_solver > 2) ||
       !(prm->a_c_scale > 0) ||
       !(prm->delta >= 0) || !(prm->delta_rel >= 0) || !std::isfinite(prm->delta_rel) || prm->ir_tol < 0 || prm->ir_max < 0 ||
       (prm->mobility != SPS_MOB_BIE && prm->mobility != SPS_MOB_IDENTITY) ||
@@ -1431,6 +1431,190 @@ static int finish_bb_stats(sps_ctx* ctx, int nc, const BBResult& r, sps_stats* s
   return SPS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Minimum-map Newton (Sec. 3.3.1's second-order comparison method, after
+// Niebe and Erleben 2015): Newton steps on H(gamma) = min(gamma, g),
+// g = M gamma + q.  The Jacobian takes row l of M where g_l < gamma_l (the set
+// F) and row l of the identity elsewhere, so Delta_l = -gamma_l off F and
+// M_FF Delta_F = -(g + M [0; Delta_off F])_F, solved by conjugate gradients
+// from 0 to relative residual kNtCgTol; M Delta is the CG-weighted sum of the
+// products, so every line-search trial is free of products.  Step t = 1,
+// halved until |H(gamma + t Delta)|^2 <= (1 - 2 sigma t) |H(gamma)|^2.
+// ---------------------------------------------------------------------------
+constexpr double kNtCgTol = 1e-3, kNtSigma = 1e-4;
+constexpr int kNtCgMax = 200, kNtHalvings = 30;
+
+__device__ __forceinline__ bool nt_free(const double* gam, const double* g, int l) { return g[l] < gam[l]; }
+
+// dC = -gamma off F, 0 on F
+__global__ void k_nt_offset(int n, const double* __restrict__ gam, const double* __restrict__ g,
+                            double* __restrict__ dC) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) dC[l] = nt_free(gam, g, l) ? 0.0 : -gam[l];
+}
+// r = p = -(g + M dC) on F, 0 elsewhere; x = M x_F = 0
+__global__ void k_nt_rhs(int n, const double* __restrict__ gam, const double* __restrict__ g,
+                         const double* __restrict__ MdC, double* __restrict__ r, double* __restrict__ pd,
+                         double* __restrict__ x, double* __restrict__ MxF) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  const double v = nt_free(gam, g, l) ? -g[l] - MdC[l] : 0.0;
+  r[l] = v;
+  pd[l] = v;
+  x[l] = 0.0;
+  MxF[l] = 0.0;
+}
+// x += a p, M x_F += a M p, r -= a (M p restricted to F)
+__global__ void k_nt_cg(int n, double a, const double* __restrict__ gam, const double* __restrict__ g,
+                        const double* __restrict__ pd, const double* __restrict__ Mp, double* __restrict__ x,
+                        double* __restrict__ MxF, double* __restrict__ r) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  x[l] += a * pd[l];
+  MxF[l] += a * Mp[l];
+  if (nt_free(gam, g, l)) r[l] -= a * Mp[l];
+}
+__global__ void k_nt_dir(int n, double b, const double* __restrict__ r, double* __restrict__ pd) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n) pd[l] = r[l] + b * pd[l];
+}
+// Delta = x + dC, M Delta = M x_F + M dC (in place of x and M x_F)
+__global__ void k_nt_step(int n, const double* __restrict__ dC, const double* __restrict__ MdC,
+                          double* __restrict__ d, double* __restrict__ Md) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  d[l] += dC[l];
+  Md[l] += MdC[l];
+}
+// partials of |min(gamma + t Delta, g + t M Delta)|^2 (slot 0 of the APGD layout)
+__global__ void __launch_bounds__(256) k_nt_merit(int n, double t, const double* __restrict__ gam,
+                                                  const double* __restrict__ g, const double* __restrict__ d,
+                                                  const double* __restrict__ Md, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+    const double mn = fmin(fma(t, d[l], gam[l]), fma(t, Md[l], g[l]));
+    a = fma(mn, mn, a);
+  }
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sh[0];
+    for (int c = 1; c < 4; ++c) part[c * kApBlocks + blockIdx.x] = 0.0;
+  }
+}
+__global__ void k_nt_accept(int n, double t, double* __restrict__ gam, double* __restrict__ g,
+                            const double* __restrict__ d, const double* __restrict__ Md) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  gam[l] = fma(t, d[l], gam[l]);
+  g[l] = fma(t, Md[l], g[l]);
+}
+
+// mul(v, out): out = M v.  From gamma_0 = 0; on return d_gam / d_g hold the
+// last accepted iterate and its g.
+template <class Mul>
+static int newton_run(sps_ctx* ctx, int nc, sps_stats* st, Mul mul, BBResult& r) {
+  const int tb = (nc + 255) / 256;
+  SPS_TRY(sps_grow(ctx, &ctx->d_apgd, ctx->cap_apgd, 7 * (size_t)nc + 8 * kApBlocks + 8));
+  double* dC = ctx->d_apgd;
+  double* MdC = dC + nc;
+  double* x = MdC + nc;      // becomes Delta
+  double* MxF = x + nc;      // becomes M Delta
+  double* rv = MxF + nc;
+  double* pd = rv + nc;
+  double* Mp = pd + nc;
+  double* part = Mp + nc;
+  double* res = part + 4 * kApBlocks;
+  double* gam = ctx->d_gam;
+  double* g = ctx->d_g;
+  auto note = [&](int rc2) -> int {
+    if (rc2 != SPS_OK && rc2 != SPS_ERR_NOT_CONVERGED) return rc2;
+    if (rc2) r.worst = rc2;
+    if (st) st->mvops += 1;
+    return SPS_OK;
+  };
+  SPS_CUDA(ctx, cudaMemsetAsync(gam, 0, sizeof(double) * nc, ctx->stream));
+  SPS_CUDA(ctx, cudaMemcpyAsync(g, ctx->d_q, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
+  double s5[5];
+  SPS_TRY(bb_stats(ctx, gam, g, nullptr, nullptr, s5));
+  double phi = std::sqrt(s5[0]);
+  r.phi = phi;
+  const double tol = ctx->prm.bbpgd_tol;
+  if (phi < tol) return SPS_OK;
+  for (int k = 1; k <= ctx->prm.bbpgd_max; ++k) {
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_nt_offset<<<tb, 256, 0, ctx->stream>>>(nc, gam, g, dC); }
+    SPS_LAUNCHED(ctx);
+    double cc = 0.0;
+    SPS_TRY(sps_dot(ctx, dC, dC, nc, &cc));
+    if (cc > 0) SPS_TRY(note(mul(dC, MdC)));
+    else SPS_CUDA(ctx, cudaMemsetAsync(MdC, 0, sizeof(double) * nc, ctx->stream));
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_nt_rhs<<<tb, 256, 0, ctx->stream>>>(nc, gam, g, MdC, rv, pd, x, MxF); }
+    SPS_LAUNCHED(ctx);
+    double rr = 0.0;
+    SPS_TRY(sps_dot(ctx, rv, rv, nc, &rr));
+    const double bnorm = std::sqrt(rr);
+    for (int it = 0; it < kNtCgMax; ++it) {
+      if (std::sqrt(rr) <= kNtCgTol * bnorm) break;
+      SPS_TRY(note(mul(pd, Mp)));
+      double pAp = 0.0;   // p vanishes off F, so p . M p = p . (M p)_F
+      SPS_TRY(sps_dot(ctx, pd, Mp, nc, &pAp));
+      if (!(pAp > 0)) break;
+      const double a = rr / pAp;
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_nt_cg<<<tb, 256, 0, ctx->stream>>>(nc, a, gam, g, pd, Mp, x, MxF, rv); }
+      SPS_LAUNCHED(ctx);
+      double rr_new = 0.0;
+      SPS_TRY(sps_dot(ctx, rv, rv, nc, &rr_new));
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_nt_dir<<<tb, 256, 0, ctx->stream>>>(nc, rr_new / rr, rv, pd); }
+      SPS_LAUNCHED(ctx);
+      rr = rr_new;
+    }
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_nt_step<<<tb, 256, 0, ctx->stream>>>(nc, dC, MdC, x, MxF); }
+    SPS_LAUNCHED(ctx);
+    const double theta0 = 0.5 * phi * phi;
+    double t = 1.0, phi_t = 0.0;
+    bool accepted = false;
+    for (int h = 0; h <= kNtHalvings; ++h) {
+      double st4[4];
+      { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+      k_nt_merit<<<kApBlocks, 256, 0, ctx->stream>>>(nc, t, gam, g, x, MxF, part);
+      k_apgd_finish<<<1, 32, 0, ctx->stream>>>(part, res); }
+      SPS_LAUNCHED(ctx);
+      SPS_TRY(to_host(ctx, res, 4, st4));
+      if (!std::isfinite(st4[0])) return sps_fail(ctx, SPS_ERR_NONFINITE, "Newton: non-finite residual");
+      phi_t = std::sqrt(st4[0]);
+      if (0.5 * st4[0] <= (1.0 - 2.0 * kNtSigma * t) * theta0) {
+        accepted = true;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!accepted) {
+      r.bb_rc = SPS_ERR_BREAKDOWN;   // no step length met the Armijo test
+      return SPS_OK;
+    }
+    { SpsPhase timer_(ctx, SPS_PH_BBPGD);
+    k_nt_accept<<<tb, 256, 0, ctx->stream>>>(nc, t, gam, g, x, MxF); }
+    SPS_LAUNCHED(ctx);
+    phi = phi_t;
+    r.iters = k;
+    r.best_iter = k;
+    r.phi = phi;
+    if (phi < tol) return SPS_OK;
+  }
+  r.bb_rc = SPS_ERR_NOT_CONVERGED;
+  return SPS_OK;
+}
+
 static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, const double* FT_ext,
                    double dt, double* gamma, int gamma_cap, double* UO, double* pos_out, sps_stats* st) {
   if (!(dt > 0)) return sps_fail(ctx, SPS_ERR_INVALID_ARG, "dt must be positive");
@@ -1490,6 +1674,17 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
       auto mul = [&](const double* v, double* out) { return apply_M(ctx, v, out, st, ctx->prm.warm_start != 0); };
       SPS_TRY(apgd_run(ctx, nc, st, mul, r, ctx->d_Uc, 6 * (size_t)n));
       warm0 = true;   // (U_c below is the solve of the returned iterate, also at iteration 0)
+    } else if (ctx->prm.lcp_solver == 2) {
+      // products of CG directions: no useful warm start between them
+      auto mul = [&](const double* v, double* out) { return apply_M(ctx, v, out, st, false); };
+      SPS_TRY(newton_run(ctx, nc, st, mul, r));
+      warm0 = false;
+      if (r.iters > 0) {
+        // U_c of the returned iterate: one more solve, M D gamma in d_Uc
+        const int rc2 = apply_M(ctx, ctx->d_gam, ctx->d_Mg, st, false);
+        if (rc2 != SPS_OK && rc2 != SPS_ERR_NOT_CONVERGED) return rc2;
+        if (rc2) r.worst = rc2;
+      }
     } else {
       SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, ctx->d_Uc, 6 * (size_t)n, warm0, mul_gam));
     }
@@ -1574,12 +1769,13 @@ static int resolve_identity(sps_ctx* ctx, int n, const double* pos, const double
       SPS_TRY(sps_launch_bb_identity(ctx, alpha, ctx->d_gam, ctx->d_g, ctx->d_gam_new, ctx->d_g_new));
       return read5(ctx, s5);
     };
-    if (ctx->prm.lcp_solver == 1) {
+    if (ctx->prm.lcp_solver != 0) {
       auto mul = [&](const double* v, double* out) -> int {
         SPS_TRY(sps_launch_D(ctx, v, ctx->d_iFT));
         return sps_launch_DT(ctx, ctx->d_iFT, out);
       };
-      SPS_TRY(apgd_run(ctx, nc, st, mul, r, nullptr, 0));
+      if (ctx->prm.lcp_solver == 1) SPS_TRY(apgd_run(ctx, nc, st, mul, r, nullptr, 0));
+      else SPS_TRY(newton_run(ctx, nc, st, mul, r));
     } else {
       SPS_TRY(bbpgd_run(ctx, nc, st, mul_g, step, r, nullptr, 0, false, []() { return SPS_OK; }));
     }
@@ -1588,7 +1784,7 @@ static int resolve_identity(sps_ctx* ctx, int n, const double* pos, const double
   }
   SPS_TRY(finish_bb_stats(ctx, nc, r, st));
   // U = F_ext + D gamma (d_F3 holds D of the returned iterate after a BBPGD step)
-  if (ctx->prm.lcp_solver == 1 && nc > 0) {
+  if (ctx->prm.lcp_solver != 0 && nc > 0) {
     SPS_TRY(sps_launch_D(ctx, ctx->d_gam, ctx->d_iFT));
     { SpsPhase timer_(ctx, SPS_PH_BBPGD);
     k_axpby<<<gblocks(6LL * n), 256, 0, ctx->stream>>>(6LL * n, 1.0, FT_ext, 1.0, ctx->d_iFT, UO); }

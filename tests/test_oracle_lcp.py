@@ -7,7 +7,9 @@
   M, Sec. 3.3.2), complementarity at convergence, the absolute error bound of
   eq. abserrcqp, and the scalar-LCP fact of Sec. 6.2 (one GD step solves it);
 * the full collision-resolved step against enumeration with the explicitly
-  assembled M = D^T M D (n_c = 3 contacts, p = 4)."""
+  assembled M = D^T M D (n_c = 3 contacts, p = 4);
+* the comparison solvers of Sec. 3.3.1 (APGD, minimum-map Newton) against
+  enumeration and against Algorithm 1."""
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
@@ -409,6 +411,74 @@ def test_apgd_identity_step_matches_bbpgd():
     assert b["info"]["n_active"] > 5
     assert np.abs(a["gamma"] - b["gamma"]).max() < 1e-8 * np.abs(b["gamma"]).max()
     assert np.abs(a["U"] - b["U"]).max() < 1e-8 * np.abs(b["U"]).max()
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_minmap_newton_matches_enumeration(seed):
+    """Minimum-map Newton (Sec. 3.3.1) reaches the enumerated solution of a
+    random SPD LCP, H = min(gamma, g) = 0 to rounding, in a few Newton steps;
+    info counts every product of M."""
+    rng = np.random.default_rng(100 + seed)
+    n = 3 + seed
+    A = rng.standard_normal((n, n))
+    M = A @ A.T + 0.5 * np.eye(n)
+    q = rng.standard_normal(n) * 3
+    ref = lcp.lcp_enumerate(M, q)
+    calls = [0]
+
+    def mop(x):
+        calls[0] += 1
+        return M @ x
+
+    gam, g, info = lcp.minmap_newton(mop, q, 1e-12, jmax=100)
+    assert info["status"] == "ok" and info["phi"] < 1e-12
+    assert np.abs(gam - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+    assert np.abs(g - (M @ gam + q)).max() < 1e-11 * max(1.0, np.abs(q).max())
+    assert info["mvops"] == calls[0] and info["cg_iters"] <= info["mvops"]
+    assert info["iters"] <= 10
+
+
+def test_minmap_newton_decoupled_and_trivial_cases():
+    """M = m I decouples the LCP into gamma_l = max(0, -q_l / m): the first
+    Newton step (F = {q < 0}, one CG step on a multiple of the identity)
+    lands on it; q >= 0 needs no step and no product."""
+    q = np.array([-3.0, 2.0, -0.5, 0.0, -7.0])
+    gam, g, info = lcp.minmap_newton(lambda x: 2.0 * x, q, 1e-14)
+    assert info["iters"] == 1 and info["mvops"] == 1 and info["status"] == "ok"
+    assert np.array_equal(gam, np.maximum(0.0, -q / 2.0))
+    gam, g, info = lcp.minmap_newton(lambda x: 2.0 * x, np.array([3.0, 0.5]), 1e-14)
+    assert info["iters"] == 0 and info["mvops"] == 0 and not np.any(gam)
+
+
+def test_minmap_newton_collision_steps():
+    """The collision step with Newton as the LCP solver: the identity-mobility
+    step equals Algorithm 1's (jittered lattice with active contacts), and the
+    boundary-integral step (p = 4, three contacts) equals the enumerated
+    solution of its assembled M = D^T M D."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.jittered_lattice(7, 125)
+    kw = dict(delta=0.1, a_c_scale=1.05, bbpgd_tol=1e-12, bbpgd_max=50000)
+    a = lcp.resolve_collisions_identity(w.centers, w.radii, w.FT, w.dt, solver="newton", **kw)
+    b = lcp.resolve_collisions_identity(w.centers, w.radii, w.FT, w.dt, **kw)
+    assert a["info"]["status"] == "ok" and b["info"]["n_active"] > 5
+    assert a["info"]["iters"] < b["info"]["iters"] / 4
+    assert np.abs(a["gamma"] - b["gamma"]).max() < 1e-10 * np.abs(b["gamma"]).max()
+    assert np.abs(a["U"] - b["U"]).max() < 1e-10 * np.abs(b["U"]).max()
+    c = np.array([[0, 0, 0], [2.02, 0, 0], [1.0, 1.76, 0.0], [5.0, 0.3, 0.2]])
+    FT = np.zeros((4, 6))
+    FT[:, :3] = 20.0 * np.array([[1.0, 0.3, 0.0], [-1.0, 0.2, 0.0], [0.0, -1.0, 0.1], [-0.5, 0, 0]])
+    out = lcp.resolve_collisions(c, np.ones(4), FT, 0.05, 4, gmres_tol=1e-13, bbpgd_tol=1e-11,
+                                 solver="newton")
+    ij, nrm = out["ij"], out["normals"]
+    sus = Suspension(c, np.ones(4), 4)
+    M = np.zeros((3, 3))
+    for l in range(3):
+        e = np.zeros(3)
+        e[l] = 1.0
+        M[:, l] = lcp.DT_apply(ij, nrm, mobility.mobility_apply(sus, lcp.D_apply(4, ij, nrm, e), 1e-13))
+    exact = lcp.lcp_enumerate(M, out["q"])
+    assert out["info"]["status"] == "ok" and out["info"]["n_active"] >= 1
+    assert np.abs(out["gamma"] - exact).max() < 1e-7 * max(1.0, np.abs(exact).max())
 
 
 def test_rotor_workloads():
