@@ -665,7 +665,32 @@ __global__ void k_near_close_dw(int N, int P, int L, int E, int n_close, const i
 // node's pairs in near-list order in FP64 (deterministic).
 // ---------------------------------------------------------------------------
 constexpr int kNS = 256;
-constexpr int kMaxClose = 1024;   // close items held per CTA (more are evaluated in place)
+constexpr int kMaxClose = 1024;   // close items listed per CTA (beyond: a rescan of all items)
+
+// Item it of source j (target node k of the qq-th near target): its
+// position relative to the source centre in source radii (FP32, before any
+// rotation) and whether it is a close item.  The split is the close list's:
+// decided in FP32 outside a 1e-4 band around kCloseRadius, by the list's
+// FP64 test inside it.  Returns false for a missing reverse slot (q < 0).
+__device__ __forceinline__ bool near_item(int it, int j, int q0, int P, long long NP,
+                                          const int* __restrict__ near_idx, const int* __restrict__ rev,
+                                          const float* __restrict__ rel32, const float* __restrict__ geo,
+                                          const double* __restrict__ pos, const double* __restrict__ X,
+                                          float ia, double iad, float lo, float hi, double lim, long long& g,
+                                          int& q, int& k, float& x, float& y, float& z, bool& close) {
+  const int qq = it / P;
+  k = it - qq * P;
+  const int i = near_idx[q0 + qq];
+  q = rev[q0 + qq];
+  if (q < 0) return false;   // (cannot happen: the near relation is symmetric to the bit)
+  g = (long long)i * P + k;
+  x = fmaf(rel32[g], ia, geo[3 * q]);
+  y = fmaf(rel32[NP + g], ia, geo[3 * q + 1]);
+  z = fmaf(rel32[2 * NP + g], ia, geo[3 * q + 2]);
+  const float r2 = x * x + y * y + z * z;
+  close = r2 < hi && (r2 < lo || sps_close_r2(pos, iad, X[g], X[NP + g], X[2 * NP + g], j) < lim);
+  return true;
+}
 
 template <int F>
 __device__ __forceinline__ void near_src_close(int it, int j, int q0, int P, int L, long long NP, long long NQ,
@@ -730,10 +755,6 @@ __global__ void __launch_bounds__(kNS, FAR_ONLY ? 3 : 2) k_near_src(int N, int P
     const float2 b = (2 * l + 1 < F) ? src[e * F + 2 * l + 1] : make_float2(0.f, 0.f);
     c32[t] = make_float4(a.x, b.x, -a.y, -b.y);
   }
-  if (!FAR_ONLY) {
-    const float4* dsrc = fcoefdw + (long long)j * E * F;
-    for (int t = threadIdx.x; t < E * F; t += kNS) cdw[t] = dsrc[t];
-  }
   if (threadIdx.x == 0) {
     s_ncl = 0;
     if (rot)
@@ -751,22 +772,17 @@ __global__ void __launch_bounds__(kNS, FAR_ONLY ? 3 : 2) k_near_src(int N, int P
   const double* Qd = rot ? s_rotd : nullptr;
   const int items = nn * P;
   for (int it = threadIdx.x; it < items; it += kNS) {
-    const int qq = it / P, k = it - qq * P;
-    const int i = near_idx[q0 + qq];
-    const int q = rev[q0 + qq];
-    if (q < 0) continue;   // (cannot happen: the near relation is symmetric to the bit)
-    const long long g = (long long)i * P + k;
-    float x = fmaf(rel32[g], ia, geo[3 * q]), y = fmaf(rel32[NP + g], ia, geo[3 * q + 1]),
-          z = fmaf(rel32[2 * NP + g], ia, geo[3 * q + 2]);
-    const float r2 = x * x + y * y + z * z;
-    if (r2 < hi &&
-        (r2 < lo || sps_close_r2(pos, iad, X[g], X[NP + g], X[2 * NP + g], j) < lim)) {
+    long long g;
+    int q, k;
+    float x, y, z;
+    bool close;
+    if (!near_item(it, j, q0, P, NP, near_idx, rev, rel32, geo, pos, X, ia, iad, lo, hi, lim, g, q, k, x, y, z,
+                   close))
+      continue;
+    if (close) {
       if (FAR_ONLY) continue;
       const int c = atomicAdd(&s_ncl, 1);
-      if (c < kMaxClose)
-        s_cl[c] = it;
-      else
-        near_src_close<F>(it, j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+      if (c < kMaxClose) s_cl[c] = it;
       continue;
     }
     float vx = 0.f, vy = 0.f, vz = 0.f;
@@ -793,10 +809,29 @@ __global__ void __launch_bounds__(kNS, FAR_ONLY ? 3 : 2) k_near_src(int N, int P
     buf[2 * NQ + o] = tz;
   }
   if (FAR_ONLY) return;
+  // close items: the source's double-float coefficients are staged only by
+  // CTAs that have some (most sources have none)
   __syncthreads();
-  const int ncl = min(s_ncl, kMaxClose);
-  for (int c = threadIdx.x; c < ncl; c += kNS)
-    near_src_close<F>(s_cl[c], j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+  const int ncl = s_ncl;
+  if (ncl == 0) return;                              // uniform over the block
+  const float4* dsrc = fcoefdw + (long long)j * E * F;
+  for (int t = threadIdx.x; t < E * F; t += kNS) cdw[t] = dsrc[t];
+  __syncthreads();
+  if (ncl <= kMaxClose) {
+    for (int c = threadIdx.x; c < ncl; c += kNS)
+      near_src_close<F>(s_cl[c], j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+    return;
+  }
+  // the list overflowed: find every close item again (the same test) instead
+  for (int it = threadIdx.x; it < items; it += kNS) {
+    long long g;
+    int q, k;
+    float x, y, z;
+    bool close;
+    if (near_item(it, j, q0, P, NP, near_idx, rev, rel32, geo, pos, X, ia, iad, lo, hi, lim, g, q, k, x, y, z,
+                  close) && close)
+      near_src_close<F>(it, j, q0, P, L, NP, NQ, pos, aj, iad, X, Nr, near_idx, rev, cdw, Qd, buf);
+  }
 }
 
 // The close items of source j (the same split as k_near_src's), in

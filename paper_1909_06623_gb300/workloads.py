@@ -285,6 +285,26 @@ def tiny(seed, N, p, phi=0.2, a_lo=0.5, a_hi=1.0, n_pairs=1, gap=1e-2):
     return Workload(f"tiny_N{N}_p{p}_s{seed}", C, R, FT, p=p, dt=1e-3, steps=1)
 
 
+def crowded_shell(seed, n_small=24, a_big=4.0, a_small=0.5, gap_lo=0.02, gap_hi=0.3, p=4):
+    """One large sphere at the origin ringed by n_small small ones at gaps
+    U[gap_lo, gap_hi] from its surface, directions on a Fibonacci lattice of
+    the sphere, each turned by a seeded random angle about the axis.  Every
+    small sphere's nodes lie within 1.5 large-sphere radii of its centre, so
+    the large source has n_small * (p + 1)(2p + 2) close items: a parity case
+    for near-field paths that hold a bounded number of close items."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(n_small) + 0.5
+    z = 1.0 - 2.0 * k / n_small
+    th = np.pi * (1.0 + 5.0 ** 0.5) * k + 2 * np.pi * rng.random()
+    u = np.stack([np.sqrt(1 - z * z) * np.cos(th), np.sqrt(1 - z * z) * np.sin(th), z], axis=1)
+    dist = a_big + a_small + gap_lo + (gap_hi - gap_lo) * rng.random(n_small)
+    C = np.concatenate([np.zeros((1, 3)), u * dist[:, None]])
+    R = np.concatenate([[a_big], np.full(n_small, a_small)])
+    FT = np.concatenate([rng.standard_normal((n_small + 1, 3)),
+                         0.1 * rng.standard_normal((n_small + 1, 3))], axis=1)
+    return Workload(f"crowded_shell_n{n_small}_p{p}_s{seed}", C, R, FT, p=p, dt=1e-3, steps=1)
+
+
 def jittered_lattice(seed, N, phi=0.35, a_lo=0.5, a_hi=1.0, jitter=0.1):
     """Large contact workload: N spheres, a ~ U[a_lo, a_hi], centres on a
     simple-cubic lattice whose spacing s gives volume fraction phi, each moved

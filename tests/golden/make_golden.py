@@ -124,6 +124,20 @@ def tiny_layers():
 
 
 
+def crowded():
+    """One sphere of radius 4 ringed by 24 of radius 0.5 (p = 4): the large
+    source has 1,200 close items.  Full operators S, K, I/2 + K + L."""
+    t0 = time.time()
+    w = workloads.crowded_shell(4)
+    sus = Suspension(w.centers, w.radii, w.p)
+    sig = np.random.default_rng(404).standard_normal((sus.N * sus.P, 3))
+    K = sus.apply("K", sig)
+    np.savez_compressed(os.path.join(HERE, "crowded_p4.npz"), centers=w.centers, radii=w.radii,
+                        p=w.p, sigma=sig, S=sus.apply("S", sig), K=K,
+                        A=0.5 * sig + K + mobility.apply_L(sus, sig))
+    print("crowded", f"{time.time() - t0:.1f}s")
+
+
 def rotated():
     """Randomly oriented grids (Sec. 5.4, rotations from the seeded generator):
     the tiny cases' operators and mobility, and the five-sphere active step,
@@ -246,6 +260,7 @@ def sed_steps():
 
 
 ALL = {"cfg1": cfg1, "active": active, "capped": capped, "rotated": rotated, "walls": walls, "cfg2": cfg2_sample, "tiny": tiny_layers,
+       "crowded": crowded,
        "collision_grad": collision_grad, "collision_grad_c": collision_grad_c,
        "sed_steps": sed_steps}
 

@@ -146,6 +146,26 @@ def test_layer_operators_tiny(sps, case, precision, tol):
 
 
 @pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX), (2, TOL64)])
+def test_layer_operators_crowded_close_items(sps, precision, tol):
+    """One sphere of radius 4 ringed by 24 of radius 0.5 at gaps 0.04-0.3
+    (p = 4): every node of the small spheres lies within 1.5 radii of the
+    large one, so that source has 1,200 close items, more than the 1,024 a
+    near-field CTA lists (the mixed path then finds them again by the same
+    test).  S, K and I/2 + K + L against the oracle on every node."""
+    d = load("crowded_p4.npz")
+    C, R, p = d["centers"], d["radii"], int(d["p"])
+    P = (p + 1) * (2 * p + 2)
+    dist = np.linalg.norm(C[1:], axis=1)
+    assert np.all(dist + R[1:] < 1.5 * R[0]) and (len(R) - 1) * P > 1024
+    ctx = sps.Context(p=p, precision=precision)
+    ctx.set_geometry(dev(C), dev(R))
+    s = planes(d["sigma"])
+    for op, key in ((sps.SPS_OP_S, "S"), (sps.SPS_OP_K, "K"), (sps.SPS_OP_A, "A")):
+        out = ctx.layer_apply(op, s).cpu().numpy().T
+        assert relerr(out, d[key]) < tol, key
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMX), (2, TOL64)])
 def test_layer_operators_cfg2_sampled(sps, precision, tol):
     """Full-size geometry (1,000 spheres, p = 6) in the launch shape the bench
     uses; the oracle evaluated S, K and I/2+K+L on a sample of target spheres."""
