@@ -136,14 +136,15 @@ def workload(name):
 PRECISION = {"fp64": 0, "mixed": 1, "fp64dw": 2}
 
 
-def ctx_params(precision, bb_warm=1, bbpgd_tol=1e-6):
+def ctx_params(precision, bb_warm=2, bbpgd_tol=1e-6):
     """Solver settings of the benchmark step.  Collision radius a_c = 1.05 a is
     the paper's choice at p = 6 (Sec. 6.1).  eps_tol = 1e-6 (the paper runs
     1e-3 to 1e-5, Sec. 6.2) keeps gamma within 1e-5 of a tightly solved
     FP64-accurate step (at 1e-5 the gap is 4.5e-5, set by eps_tol, not by the
     arithmetic).  The GMRES tolerance and the BBPGD cap are this benchmark's.
-    bb_warm = 1 starts Algorithm 1 from the previous step's gamma (the paper's
-    runs: gamma_0 = 0, --bb-warm 0)."""
+    bb_warm = 1 starts Algorithm 1 from the previous step's gamma, 2 also from
+    its last step length (no product M g_0 for alpha_0; the paper's runs:
+    gamma_0 = 0, --bb-warm 0)."""
     return dict(p=6, delta=0.1, beta=1.75, a_c_scale=1.05,
                 gmres_tol=1e-6 if precision == "mixed" else 1e-8, gmres_max=150,
                 bbpgd_tol=bbpgd_tol, bbpgd_max=100, bb_safeguard=1, warm_start=1, bb_warm=bb_warm,
@@ -523,7 +524,8 @@ def run_gpu(args, w):
                        "gmres_tol": ctx.prm.gmres_tol, "bbpgd_tol": ctx.prm.bbpgd_tol,
                        "ir_tol": ctx.prm.ir_tol,
                        "delta": ctx.prm.delta, "delta_rel": ctx.prm.delta_rel,
-                       "bbpgd_gamma0": "previous step" if ctx.prm.bb_warm else "zero",
+                       "bbpgd_gamma0": {0: "zero", 1: "previous step",
+                                        2: "previous step (gamma and step length)"}[ctx.prm.bb_warm],
                        "a_c_scale": ctx.prm.a_c_scale, "bbpgd_max": ctx.prm.bbpgd_max,
                        "dt": w.dt, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -827,8 +829,9 @@ def main():
                          "(FP64 rate and error against FP64)")
     ap.add_argument("--gamma0-steps", type=int, default=3,
                     help="steps of the gamma_0 = 0 comparison leg (0: skip)")
-    ap.add_argument("--bb-warm", type=int, default=1, choices=[0, 1],
-                    help="1: Algorithm 1 starts from the previous step's gamma; 0: gamma_0 = 0")
+    ap.add_argument("--bb-warm", type=int, default=2, choices=[0, 1, 2],
+                    help="1: Algorithm 1 starts from the previous step's gamma; 2: also from its "
+                         "last step length; 0: gamma_0 = 0")
     ap.add_argument("--contact-n", type=int, default=CONTACT_N)
     ap.add_argument("--contact-only", action="store_true",
                     help="run only the identity-mobility contact benchmark")

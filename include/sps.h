@@ -117,7 +117,11 @@ typedef struct sps_params {
                          min-map residual is not below that of gamma_0 = 0.
                          Every step still meets bbpgd_tol.  Boundary-integral
                          mobility only (the identity mobility always starts
-                         from 0).  Default 0.                                */
+                         from 0).  2: as 1, and alpha_0 is the last step
+                         length of the previous step's converged Algorithm 1
+                         instead of g_0^T g_0 / g_0^T M g_0 (one mobility
+                         solve fewer; Algorithm 1's alpha_0 when there is
+                         none).  Default 0.                                  */
   int ir_dw;          /* the FP64-accurate applications of the refinement
                          (ir_tol > 0): 1 evaluates their far field as
                          SPS_FP64_DW does (double-float on the FP32 pipe), 0

@@ -169,6 +169,8 @@ struct sps_ctx {
   double *d_prev_gam = nullptr;
   size_t cap_prev_ij = 0, cap_prev_gam = 0;
   int prev_nc = 0, prev_N = 0;
+  double prev_alpha = 0.0;       // bb_warm = 2: the previous step's last BB step length (0: none)
+  double bb_alpha_last = 0.0;    // the step length Algorithm 1 used last
 
   // contacts
   int n_c = 0, cap_c = 0, c_N = 0;   // contacts, capacity, spheres they refer to

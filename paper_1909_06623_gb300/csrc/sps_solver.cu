@@ -493,7 +493,7 @@ extern "C" int sps_create(const sps_params* prm, void* stream, sps_ctx** out) {
       !(prm->delta >= 0) || !(prm->delta_rel >= 0) || !std::isfinite(prm->delta_rel) || prm->ir_tol < 0 || prm->ir_max < 0 ||
       (prm->mobility != SPS_MOB_BIE && prm->mobility != SPS_MOB_IDENTITY) ||
       prm->contact_search < SPS_SEARCH_AUTO || prm->contact_search > SPS_SEARCH_CELLS ||
-      (prm->bb_warm != 0 && prm->bb_warm != 1))
+      (prm->bb_warm < 0 || prm->bb_warm > 2))
     return SPS_ERR_INVALID_ARG;
   sps_ctx* ctx = new sps_ctx();
   ctx->prm = *prm;
@@ -1189,17 +1189,23 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
                                     cudaMemcpyDeviceToDevice, ctx->stream));
     }
   }
-  rc = mul_g();
-  if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
-  if (rc) r.worst = rc;
-  if (st) st->mvops += 1;
-  double gMg = 0.0;
-  SPS_TRY(sps_dot(ctx, ctx->d_g, ctx->d_Mg, nc, &gMg));
-  if (!(gMg > 0)) {
-    r.bb_rc = SPS_ERR_BREAKDOWN;
-    return SPS_OK;
+  double alpha = 0.0;
+  if (warm0 && ctx->prm.bb_warm == 2 && ctx->prev_alpha > 0) {
+    alpha = ctx->prev_alpha;   // the previous step's last step length: no product M g_0
+  } else {
+    rc = mul_g();
+    if (rc != SPS_OK && rc != SPS_ERR_NOT_CONVERGED) return rc;
+    if (rc) r.worst = rc;
+    if (st) st->mvops += 1;
+    double gMg = 0.0;
+    SPS_TRY(sps_dot(ctx, ctx->d_g, ctx->d_Mg, nc, &gMg));
+    if (!(gMg > 0)) {
+      r.bb_rc = SPS_ERR_BREAKDOWN;
+      return SPS_OK;
+    }
+    alpha = s5[4] / gMg;
   }
-  double alpha = s5[4] / gMg;
+  ctx->bb_alpha_last = alpha;
   // divergence: an indefinite discrete M (nearly touching spheres at low
   // order) makes the projected steps grow without bound
   const double phi_limit = 1e6 * std::max(r.phi, tol);
@@ -1255,6 +1261,7 @@ static int bbpgd_run(sps_ctx* ctx, int nc, sps_stats* st, MulG mul_g, Step step,
       if (st) st->bb_safeguards += 1;
     } else {
       alpha = bb1 ? s5[1] / s5[2] : s5[2] / s5[3];
+      ctx->bb_alpha_last = alpha;
     }
   }
   return fail(SPS_ERR_NOT_CONVERGED, j - 1);
@@ -1695,8 +1702,10 @@ static int resolve(sps_ctx* ctx, int n, const double* pos, const double* radii, 
     if (gamma)
       SPS_CUDA(ctx, cudaMemcpyAsync(gamma, ctx->d_gam, sizeof(double) * nc, cudaMemcpyDeviceToDevice, ctx->stream));
   }
-  // this step's pairs and gamma: the next step's initial guess
+  // this step's pairs and gamma: the next step's initial guess (bb_warm = 2:
+  // with the last step length of a converged Algorithm 1)
   ctx->prev_nc = 0;
+  ctx->prev_alpha = (ctx->prm.lcp_solver == 0 && r.bb_rc == SPS_OK && r.iters > 0) ? ctx->bb_alpha_last : 0.0;
   if (ctx->prm.bb_warm && nc > 0) {
     SPS_TRY(sps_grow(ctx, &ctx->d_prev_ij, ctx->cap_prev_ij, 2 * (size_t)nc));
     SPS_TRY(sps_grow(ctx, &ctx->d_prev_gam, ctx->cap_prev_gam, (size_t)nc));

@@ -49,7 +49,7 @@ def test_create_rejects_bad_params(lib):
     h = ctypes.c_void_p()
     assert lib.sps_create(ctypes.byref(prm), None, ctypes.byref(h)) == 1
     assert lib.sps_unit_tables(0, None, None, None, None) == 1
-    for field, bad in (("delta_rel", -0.1), ("delta_rel", float("inf")), ("bb_warm", 2),
+    for field, bad in (("delta_rel", -0.1), ("delta_rel", float("inf")), ("bb_warm", 3),
                        ("delta", -1.0), ("mobility", 5), ("ir_dw", 2), ("precision", 3),
                        ("lcp_solver", 3), ("lcp_solver", -1), ("bb_variant", 4)):
         lib.sps_default_params(ctypes.byref(prm))

@@ -186,7 +186,9 @@ def test_gpu_bb_warm_start_config2_mixed(sps):
     warm-up steps (which resolve the initial overlaps at the collision
     radius), three steps from gamma_0 = 0 and three from the previous step's
     gamma reach the same velocities within the mixed-path tolerance, the
-    warm-started steps with fewer BBPGD iterations."""
+    warm-started steps with fewer BBPGD iterations.  With bb_warm = 2 (the
+    previous step's last step length as alpha_0) the same, with no more
+    products of M beyond the iterations than bb_warm = 1 takes."""
     w = workloads.config2()
     # the benchmark's solver settings (eps_tol = 1e-5: the mixed operator's
     # rounding keeps the min-map residual from settling much below that)
@@ -200,15 +202,18 @@ def test_gpu_bb_warm_start_config2_mixed(sps):
         pos.copy_(pos_out)
     start = pos.clone()
     out = {}
-    for warm in (0, 1):
+    for warm in (0, 1, 2):
         c = sps.Context(bb_warm=warm, **kw)
         p, UO, stats = c.simulate(start.clone(), rad, FT, w.dt, 3)
         assert all(s["status"] == 0 for s in stats)
         out[warm] = (p.cpu().numpy(), UO.cpu().numpy(), stats)
-    U0, U1 = out[0][1], out[1][1]
-    assert np.abs(U1 - U0).max() <= 1e-5 * np.abs(U0).max()
+    U0 = out[0][1]
     disp = np.abs(out[0][0] - start.cpu().numpy()).max()
-    assert np.abs(out[1][0] - out[0][0]).max() <= 1e-5 * disp
+    for warm in (1, 2):
+        assert np.abs(out[warm][1] - U0).max() <= 1e-5 * np.abs(U0).max()
+        assert np.abs(out[warm][0] - out[0][0]).max() <= 1e-5 * disp
     it0 = sum(s["bbpgd_iters"] for s in out[0][2][1:])
     it1 = sum(s["bbpgd_iters"] for s in out[1][2][1:])
     assert it1 < it0
+    extra = {warm: sum(s["mvops"] - s["bbpgd_iters"] for s in out[warm][2][1:]) for warm in (1, 2)}
+    assert extra[2] <= extra[1]
