@@ -240,3 +240,24 @@ def test_near_lists_match_kdtree_brute_force():
         assert list(near[i]) == sorted(ref[i])
     total = sum(len(x) for x in near)
     assert 5 * len(R) < total < 30 * len(R)   # about 15 per sphere at this packing
+
+
+def test_crowded_shell_workload():
+    """The crowded-shell parity case: gaps to the large sphere within the
+    stated range, no overlaps, every small sphere's surface within 1.5 large
+    radii of its centre (so all of its nodes are close items of the large
+    source), and near lists (beta = 1.75) pairing the large sphere with every
+    small one and no two small ones."""
+    from paper_1909_06623_gb300 import workloads
+    w = workloads.crowded_shell(4)
+    C, R = w.centers, w.radii
+    assert R[0] == 4.0 and np.all(R[1:] == 0.5) and len(R) == 25
+    gap_big = np.linalg.norm(C[1:], axis=1) - R[0] - R[1:]
+    assert gap_big.min() >= 0.02 and gap_big.max() <= 0.3
+    d = np.linalg.norm(C[:, None] - C[None], axis=-1) - R[:, None] - R[None]
+    np.fill_diagonal(d, np.inf)
+    assert d.min() > 0
+    assert np.all(np.linalg.norm(C[1:], axis=1) + R[1:] < 1.5 * R[0])
+    near = layer.near_lists(C, R, 1.75)
+    assert np.array_equal(near[0], np.arange(1, 25))
+    assert all(np.array_equal(near[i], [0]) for i in range(1, 25))
